@@ -1,0 +1,485 @@
+"""Pins for the FP64 oracle: every check compares the oracle with something
+other than itself -- eigen-decomposition closed forms, the paper's printed
+counts, brute-force series on tiny matrices, scipy's Cholesky solve, torch's
+bfloat16 conversion -- so that a dropped term, a wrong sign, a wrong index or a
+transposed operand fails at least one of them (see also test_oracle_mutations)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+from workloads import make_spd
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")))
+
+
+def spd(n=20, kappa=30.0, nrhs=2, seed=0):
+    return make_spd(n, kappa, nrhs=nrhs, seed=seed)
+
+
+def sdd_spd(n=12, seed=3):
+    """Strictly diagonally dominant SPD matrix with a non-constant diagonal, so
+    the Jacobi preconditioner does not commute with A (Section 2)."""
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(-1, 1, (n, n))
+    M = 0.5 * (M + M.T)
+    np.fill_diagonal(M, 0.0)
+    d = np.abs(M).sum(1) + rng.uniform(0.5, 3.0, n)
+    return M + np.diag(d)
+
+
+def eig_power(prob, alpha, e):
+    """(I - alpha A)^e from the generator's spectral factors (closed form)."""
+    Q, lam = prob.Q, prob.lam
+    return (Q * (1.0 - alpha * lam) ** e) @ Q.T
+
+
+def eig_series(prob, alpha, h):
+    """{sum_{j<h} (I - alpha A)^j} alpha I in closed form."""
+    Q, lam = prob.Q, prob.lam
+    x = 1.0 - alpha * lam
+    s = np.array([alpha * sum(xi ** j for j in range(h)) for xi in x])
+    return (Q * s) @ Q.T
+
+
+def fro(X):
+    return float(np.sqrt(np.sum(X * X)))
+
+
+# ---------------------------------------------------------------- Section 2
+
+def test_alpha_frobenius_gives_contraction():
+    p = spd(16, 50.0)
+    a = O.alpha_frobenius(p.A)
+    assert a == pytest.approx(1.0 / np.linalg.norm(p.A, "fro"), rel=1e-15)
+    x = 1.0 - a * p.lam
+    assert np.all(x >= 0) and np.all(x < 1)
+
+
+def test_alpha_inf_matches_definition_and_contracts():
+    p = spd(16, 50.0)
+    a = O.alpha_inf(p.A)
+    ninf = np.linalg.norm(p.A, np.inf)
+    assert 1.0 / a == pytest.approx(ninf / 2 * (1 + 2e-8), rel=1e-14)
+    # 2S - A = ||A||_inf I + 2 eps I - A is PD => rho(I - a A) < 1 (eq. spro)
+    ev = np.linalg.eigvalsh(np.eye(16) - a * p.A)
+    assert np.max(np.abs(ev)) < 1
+
+
+def test_jacobi_splitting_contracts_for_sdd():
+    A = sdd_spd()
+    Sinv = O.jacobi_preconditioner(A)
+    assert np.allclose(np.diag(Sinv) * np.diag(A), 1.0)
+    rho = np.max(np.abs(np.linalg.eigvals(O.splitting_residual(A, Sinv))))
+    assert rho < 1
+
+
+# ---------------------------------------------------------------- Section 3
+
+@pytest.mark.parametrize("order", [2, 3, 4, 8])
+@pytest.mark.parametrize("form", ["factorized", "horner"])
+def test_exponent_law_plain_ns(order, form):
+    """eq. fk1: I - G_k A = F_0^{n^k}, and the right residual I - A G_k too."""
+    p = spd(20, 30.0)
+    a = O.alpha_frobenius(p.A)
+    G = a * np.eye(20)
+    for k in range(1, 4):
+        G, _ = O.ns_step(p.A, G, order, form)
+        ref = eig_power(p, a, order ** k)
+        assert fro(O.residual_left(G, p.A) - ref) <= 1e-12
+        assert fro(O.residual_right(p.A, G) - ref) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 3, 5])
+def test_classical_step_exponent_law(order):
+    """eq. ns with eq. fk1 on the left form (Horner evaluation)."""
+    p = spd(14, 20.0, seed=4)
+    a = O.alpha_frobenius(p.A)
+    G = a * np.eye(14)
+    for k in range(1, 4):
+        G = O.ns_classical_step(G, p.A, order)
+        assert fro(O.residual_left(G, p.A) - eig_power(p, a, order ** k)) <= 1e-12
+
+
+@pytest.mark.parametrize("p_,w", [(0, 3), (1, 1), (1, 2), (2, 2), (3, 2), (2, 3)])
+def test_initial_series_g01_g03(p_, w):
+    """eqs. g01-g03 with S^{-1} = alpha I: G0 = sum_{j<h} (S^{-1}D)^j S^{-1},
+    F0 = (S^{-1}D)^h."""
+    p = spd(12, 10.0, seed=5)
+    a = O.alpha_frobenius(p.A)
+    G0, F0 = O.initial_series(p.A, a * np.eye(12), p_, w)
+    h = w * (p_ + 1)
+    assert fro(G0 - eig_series(p, a, h)) <= 1e-13
+    assert fro(F0 - eig_power(p, a, h)) <= 1e-13
+
+
+def test_special_case_n_w_m_equal_one():
+    """Remark after eq. ga1: for n = w = m = 1 the composite method is
+    G_k = (S^{-1}D) G_{k-1} + S^{-1}."""
+    p = spd(10, 8.0, seed=6)
+    a = O.alpha_frobenius(p.A)
+    Sinv = a * np.eye(10)
+    SD = O.splitting_residual(p.A, Sinv)
+    st = O.composite_init(Sinv, 1)
+    G = Sinv.copy()
+    for _ in range(4):
+        st = O.composite_iterate(p.A, st, 1, [1])
+        G = SD @ G + Sinv
+        assert fro(st.G - G) <= 1e-14 * max(1, fro(G))
+
+
+# ---------------------------------------------------------------- Section 4
+
+def brute_series(X, A, h):
+    """sum_{j<h} Y^j X by explicit powers (brute force)."""
+    Y = np.eye(A.shape[0]) - X @ A
+    out = np.zeros_like(X)
+    P = np.eye(A.shape[0])
+    for _ in range(h):
+        out += P @ X
+        P = P @ Y
+    return out
+
+
+@pytest.mark.parametrize("h", list(range(2, 20)))
+def test_toolkit_rows_equal_series(h):
+    """Tables t1-t3: every factorized row equals the unfactorized series
+    (eq. z1a), both for a commuting X = alpha I (closed form) and a
+    non-commuting Jacobi X (brute force)."""
+    p = spd(10, 6.0, seed=7)
+    a = O.alpha_frobenius(p.A)
+    Z = O.toolkit(a * np.eye(10), p.A, h)
+    assert fro(Z - eig_series(p, a, h)) <= 1e-13 * max(1, fro(Z))
+    A = sdd_spd(9)
+    X = O.jacobi_preconditioner(A)
+    Z = O.toolkit(X, A, h)
+    ref = brute_series(X, A, h)
+    assert fro(Z - ref) <= 1e-12 * max(1, fro(ref))
+
+
+def test_toolkit_table_matches_paper_rows():
+    rows = GOLD["toolkit_rows"]["rows"]
+    assert {int(k): tuple(v) for k, v in rows.items()} == O.TOOLKIT_TABLE
+    for h, (kind, p_, w) in O.TOOLKIT_TABLE.items():
+        assert h == w * (p_ + 1) + (1 if kind == "z1" else 0)   # eqs. hape, hape1
+
+
+@pytest.mark.parametrize("p_,w", [(1, 1), (2, 1), (0, 2), (0, 4), (1, 2), (3, 2), (2, 3), (4, 2), (8, 5),
+                                  (5, 3), (2, 6), (8, 2), (1, 9)])
+def test_unified_factorization_order_and_mmm(p_, w):
+    """eqs. h1, np1: order w(p+1) in p + w + 1 mmm (p + 1 if w = 1, w if p = 0)."""
+    pr = spd(8, 4.0, seed=8)
+    a = O.alpha_frobenius(pr.A)
+    cnt = O.MMCount()
+    Z = O.unified_factorization(a * np.eye(8), pr.A, p_, w, cnt)
+    h = w * (p_ + 1)
+    assert fro(Z - eig_series(pr, a, h)) <= 1e-13 * max(1, fro(Z))
+    expect = p_ + 1 if w == 1 else (w if p_ == 0 else p_ + w + 1)
+    assert cnt.n == expect
+
+
+def test_order18_four_factorizations():
+    """Appendix: the four (p, w) choices for order 18 give the same series."""
+    pr = spd(8, 4.0, seed=9)
+    a = O.alpha_frobenius(pr.A)
+    ref = eig_series(pr, a, 18)
+    for p_, w in GOLD["order18_alternatives"]["pw"]:
+        assert w * (p_ + 1) == 18
+        Z = O.unified_factorization(a * np.eye(8), pr.A, p_, w)
+        assert fro(Z - ref) <= 1e-13 * fro(ref)
+
+
+def test_binary_chain_mmm_counts_match_paper():
+    """Appendix: orders 4 and 8 in 4 and 6 mmm; order 2 in 2; order 3 in 3."""
+    pr = spd(8, 4.0)
+    G = O.alpha_frobenius(pr.A) * np.eye(8)
+    for order, mmm in GOLD["binary_orders_mmm"]["values"].items():
+        cnt = O.MMCount()
+        O.ns_step(pr.A, G, int(order), "factorized", "square", cnt)
+        assert cnt.n == mmm
+        cnt = O.MMCount()
+        O.ns_step(pr.A, G, int(order), "factorized", "residual", cnt)
+        assert cnt.n == mmm
+    for order, mmm in ((2, 2), (3, 3)):
+        cnt = O.MMCount()
+        O.ns_step(pr.A, G, order, "factorized", "square", cnt)
+        assert cnt.n == mmm
+
+
+def test_pow_modes_agree():
+    """eq. ua1: Y^{p+1} = I - U A equals the square of Y (exact arithmetic)."""
+    pr = spd(16, 20.0, seed=2)
+    G = O.alpha_frobenius(pr.A) * np.eye(16)
+    for order in (4, 8):
+        G1, _ = O.ns_step(pr.A, G, order, "factorized", "square")
+        G2, _ = O.ns_step(pr.A, G, order, "factorized", "residual")
+        assert fro(G1 - G2) <= 1e-14 * fro(G1)
+
+
+def test_nested_order45_ten_mmm():
+    """Section 4 example, eqs. ex1-ex3."""
+    g = GOLD["nested_order45"]
+    pr = spd(8, 3.0, seed=10)
+    a = O.alpha_frobenius(pr.A)
+    cnt = O.MMCount()
+    Z = O.nested_order45(a * np.eye(8), pr.A, cnt)
+    assert cnt.n == g["mmm"]
+    assert fro(Z - eig_series(pr, a, g["order"])) <= 1e-13 * fro(Z)
+    A = sdd_spd(7, seed=11)
+    X = O.jacobi_preconditioner(A)
+    Z = O.nested_order45(X, A)
+    ref = brute_series(X, A, 45)
+    assert fro(Z - ref) <= 1e-11 * fro(ref)
+    # eq. ex1 alone: p = 8, w = 5 costs p + w + 1 = 14 mmm
+    cnt = O.MMCount()
+    O.unified_factorization(a * np.eye(8), pr.A, g["ex1_p"], g["ex1_w"], cnt)
+    assert cnt.n == g["ex1_mmm"]
+    # efficiency index of eq. ei generalised to (order, mmm): 45^(1/10)
+    assert round(g["order"] ** (1.0 / g["mmm"]), 4) == g["ei"]
+
+
+def test_efficiency_index_order2():
+    """eq. ei with p = 1, w = 1: EI = 2^(1/2) (Section 4)."""
+    p_, w = 1, 1
+    ei = (w * (p_ + 1)) ** (1.0 / (p_ + w))   # order 2 costs p + 1 = 2 mmm
+    assert round(ei, 4) == GOLD["ei_order2"]["value"]
+
+
+def test_identity_ex3():
+    """eq. ex3: I + Y + Y^2 = 3I + (XA)(-3I + XA) with Y = I - XA."""
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((6, 6))
+    A = rng.standard_normal((6, 6))
+    I = np.eye(6)
+    Y = I - X @ A
+    assert fro(I + Y + Y @ Y - (3 * I + (X @ A) @ (-3 * I + X @ A))) <= 1e-12
+
+
+def test_push_through_right_equals_left_noncommuting():
+    """The right chain G (I + F)(I + F^2)... with F = I - A G equals the left
+    series {sum_j (I - G A)^j} G for a G0 that does not commute with A."""
+    A = sdd_spd(10, seed=12)
+    G = O.jacobi_preconditioner(A)
+    assert fro(G @ A - A @ G) > 1e-3
+    for order in (2, 3, 4, 8):
+        Gr, _ = O.ns_step(A, G, order, "factorized")
+        Gl = O.ns_classical_step(G, A, order)
+        assert fro(Gr - Gl) <= 1e-13 * fro(Gl)
+
+
+def test_commutation_with_scalar_g0():
+    pr = spd(24, 50.0, seed=13)
+    G = O.alpha_frobenius(pr.A) * np.eye(24)
+    for order in (2, 3, 4, 8):
+        Gk = G
+        for _ in range(3):
+            Gk, _ = O.ns_step(pr.A, Gk, order)
+            assert fro(Gk @ pr.A - pr.A @ Gk) <= 1e-13 * fro(pr.A) * fro(Gk)
+
+
+def test_brute_force_tiny_order2():
+    """N = 4, order 2, k steps: G_k = sum_{j < 2^k} F_0^j G_0 (eq. ser1 with
+    h = 1, n = 2), by explicit powers."""
+    pr = spd(4, 5.0, seed=14)
+    A = pr.A
+    G0 = O.alpha_frobenius(A) * np.eye(4)
+    F0 = np.eye(4) - G0 @ A
+    G = G0
+    for k in range(1, 5):
+        G, _ = O.ns_step(A, G, 2)
+        ref = sum(np.linalg.matrix_power(F0, j) for j in range(2 ** k)) @ G0
+        assert fro(G - ref) <= 1e-13 * fro(ref)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 8])
+def test_converges_to_closed_form_inverse(order):
+    pr = spd(16, 10.0, seed=15)
+    Ainv = (pr.Q / pr.lam) @ pr.Q.T
+    G, norms = O.ns_invert(pr.A, order=order, iters=40 if order == 2 else 20)
+    assert fro(G - Ainv) / fro(Ainv) <= 1e-13
+    assert norms[0] > norms[-1]
+
+
+# ---------------------------------------------------------------- Section 5
+
+@pytest.mark.parametrize("n,rates", [(2, [2]), (2, [2, 3]), (3, [2]), (2, [3, 2, 2])])
+def test_composite_exponent_law(n, rates):
+    """eqs. rel1, gem1 with eqs. ti/ga1 (x_i = m_i^k): F_k = (S^{-1}D)^{e_k},
+    e_0 = 1, e_k = sum_i m_i^k + n e_{k-1}."""
+    pr = spd(12, 6.0, seed=16)
+    a = O.alpha_frobenius(pr.A)
+    st = O.composite_init(a * np.eye(12), len(rates))
+    e = O.composite_exponents(n, rates, 1, 3)
+    for k in range(1, 4):
+        st = O.composite_iterate(pr.A, st, n, rates)
+        for Ti, m in zip(st.T, rates):
+            assert fro(O.residual_left(Ti, pr.A) - eig_power(pr, a, m ** k)) <= 1e-12
+        assert fro(O.residual_left(st.G, pr.A) - eig_power(pr, a, e[k])) <= 1e-12
+
+
+def test_composite_exponent_values():
+    """n = 2, rates (2, 3): e = 1, 7, 27, 89 (worked by hand from eq. gem1)."""
+    assert O.composite_exponents(2, [2, 3], 1, 3) == [1, 7, 27, 89]
+
+
+def test_composite_telescoping_noncommuting():
+    """eq. rel1 T_c A = I - Gamma_c and eq. gem1 F_k = Gamma_c F_{k-1}^n hold
+    for any T_i, including ones that do not commute with A."""
+    A = sdd_spd(9, seed=17)
+    rng = np.random.default_rng(1)
+    T = [O.jacobi_preconditioner(A) + 0.01 * rng.standard_normal((9, 9)) for _ in range(3)]
+    Tc, Gc = O.composite_combine(A, T)
+    assert fro(Tc @ A - (np.eye(9) - Gc)) <= 1e-13 * fro(Tc @ A)
+    Gprev = O.jacobi_preconditioner(A)
+    Fprev = np.eye(9) - Gprev @ A
+    G = O.composite_step(A, Gprev, T, 3)
+    assert fro((np.eye(9) - G @ A) - Gc @ np.linalg.matrix_power(Fprev, 3)) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_double_ns_exponent(n):
+    """eq. ermoex1: F_k = (S^{-1}D)^{h (k n^{k+1} + n^k)} with G0 = S^{-1} (h = 1)
+    and with the order-2 initial series (h = 2)."""
+    pr = spd(12, 5.0, seed=18)
+    a = O.alpha_frobenius(pr.A)
+    for h, G0 in ((1, a * np.eye(12)), (2, O.initial_series(pr.A, a * np.eye(12), 1, 1)[0])):
+        st = O.double_ns_init(pr.A, G0, n)
+        for k in range(1, 3):
+            st = O.double_ns_iterate(pr.A, st, n)
+            e = O.double_ns_exponent(n, h, k)
+            assert fro(st.F - eig_power(pr, a, e)) <= 1e-12
+            assert fro(st.GamN - eig_power(pr, a, h * n ** (k + 1))) <= 1e-12
+
+
+def test_double_ns_exponent_values():
+    assert [O.double_ns_exponent(3, 1, k) for k in (1, 2, 3)] == [12, 63, 270]
+
+
+# ---------------------------------------------------------------- Section 6
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+@pytest.mark.parametrize("updated", [False, True])
+def test_richardson_error_model(order, updated):
+    """theta_{k+1} - theta_* = (I - G_k A)(theta_k - theta_*) with
+    I - G_k A = F_0^{n^k}, so after K coupled steps the error is
+    F_0^{(n^K - 1)/(n - 1)} theta~_0 (G_k applied), or F_0^{n (n^K-1)/(n-1)}
+    theta~_0 when G_{k+1} is applied (eq. ttk1 ordering)."""
+    pr = spd(14, 8.0, nrhs=2, seed=19)
+    a = O.alpha_frobenius(pr.A)
+    tstar = np.linalg.solve(pr.A, pr.B)
+    for K in (1, 2, 3):
+        r = O.ns_richardson_solve(pr.A, pr.B, order=order, ns_iters=K, use_updated_G=updated)
+        e = (order ** K - 1) // (order - 1)
+        if updated:
+            e *= order
+        ref = eig_power(pr, a, e) @ (0 - tstar)
+        assert fro((r.theta - tstar) - ref) <= 1e-11 * max(1, fro(tstar))
+
+
+def test_richardson_converges_to_cholesky():
+    pr = spd(32, 100.0, nrhs=3, seed=20)
+    r = O.ns_richardson_solve(pr.A, pr.B, order=4, ns_iters=8, tol=1e-12, max_sweeps=50)
+    ref = scipy.linalg.cho_solve(scipy.linalg.cho_factor(pr.A), pr.B)
+    assert r.converged
+    assert fro(r.theta - ref) / fro(ref) <= 1e-10
+    assert np.max(O.rel_residual(pr.A, r.theta, pr.B)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_accelerated_richardson_gamma(n):
+    """eqs. riem1-riem6 (q = n): theta~_k = (S^{-1}D)^{gamma_k} theta~_0 with
+    theta_0 = L_0 b."""
+    pr = spd(10, 3.0, nrhs=1, seed=21)
+    a = O.alpha_frobenius(pr.A)
+    tstar = np.linalg.solve(pr.A, pr.B)
+    st = O.double_ns_init(pr.A, a * np.eye(10), n)
+    theta = st.L @ pr.B
+    t0 = theta - tstar
+    for k in range(1, 3):
+        st = O.double_ns_iterate(pr.A, st, n)
+        theta = O.accelerated_richardson_step(pr.A, pr.B, theta, st, q=n)
+        g = O.accelerated_richardson_exponent(n, 1, k)
+        assert g == int(g)
+        ref = eig_power(pr, a, int(g)) @ t0
+        assert fro((theta - tstar) - ref) <= 1e-12 * max(1.0, fro(t0))
+
+
+def test_gamma_closed_form_equals_sum():
+    """eq. riem6 equals the running sum of the per-step exponents of eq. riem4."""
+    for n in (2, 3, 4):
+        for k in (1, 2, 3):
+            s = sum(i * n ** (i + 2) + 2 * n ** (i + 1) for i in range(1, k + 1))
+            assert O.accelerated_richardson_exponent(n, 1, k) == s
+    assert O.accelerated_richardson_exponent(2, 1, 1) == 16
+
+
+def test_omega_recursive_equals_direct():
+    """eq. gkrecu1 and the second part (L_k, Gamma_k^n) reproduce eq. redttk2."""
+    pr = spd(10, 4.0, seed=22)
+    a = O.alpha_frobenius(pr.A)
+    n = 2
+    st = O.double_ns_init(pr.A, a * np.eye(10), n)
+    st = O.double_ns_iterate(pr.A, st, n)
+    SG = O.ns_classical_step(st.G, pr.A, n)
+    omega = st.L + st.GamN @ SG
+    for _ in range(2):
+        st_next = O.double_ns_iterate(pr.A, st, n)
+        omega, SG, GamN, L, G = O.omega_recursive(pr.A, omega, SG, st.GamN, st.L, n)
+        direct = st_next.L + st_next.GamN @ O.ns_classical_step(st_next.G, pr.A, n)
+        assert fro(G - st_next.G) <= 1e-13 * fro(G)
+        assert fro(omega - direct) <= 1e-13 * fro(direct)
+        st = st_next
+
+
+# ---------------------------------------------------------------- precision defs
+
+def test_round_bf16_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, -1.0e-40, 1e-45])])
+    x32 = x.astype(np.float32)
+    ref = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    got = O.round_bf16(x32)
+    assert np.array_equal(got, ref)
+
+
+def test_split_bf16_error_bound():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(10000)
+    x32 = O.round_f32(x)
+    hi, lo = O.split_bf16(x)
+    assert np.array_equal(O.round_bf16(hi), hi) and np.array_equal(O.round_bf16(lo), lo)
+    # bf16 keeps 8 significant bits: |x32 - hi| <= 2^-8 |x32| (half an ulp),
+    # and lo rounds that difference to 8 bits again
+    assert np.all(np.abs(x32 - hi) <= 2.0 ** -8 * np.abs(x32))
+    assert np.all(np.abs(x32 - hi - lo) <= 2.0 ** -16 * np.abs(x32))
+
+
+def test_split_product_terms():
+    """bf16x3 drops only lo*lo: its error against the binary32 product is
+    bounded by the three neglected pieces."""
+    rng = np.random.default_rng(2)
+    L = rng.standard_normal((8, 16))
+    R = rng.standard_normal((16, 5))
+    Lh, Ll = O.split_bf16(L)
+    Rh, Rl = O.split_bf16(R)
+    assert np.array_equal(O.split_product(L, R, "bf16"), Lh @ Rh)
+    d = O.split_product(L, R, "bf16x3") - (Lh @ Rh + Lh @ Rl + Ll @ Rh)
+    assert np.max(np.abs(d)) <= 1e-14
+    full = O.round_f32(L) @ O.round_f32(R)
+    # dropped lo*lo (<= 2^-16) plus the two split remainders (<= 2^-16 each)
+    bound = 3 * 2.0 ** -16 * (np.abs(L) @ np.abs(R)) + 1e-12
+    assert np.all(np.abs(O.split_product(L, R, "bf16x3") - full) <= bound)
+
+
+def test_gemm_epilogue_forms():
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal((5, 5))
+    C = rng.standard_normal((5, 5))
+    assert np.allclose(O.gemm_epilogue(P, -1.0, gamma=1.0), np.eye(5) - P)
+    assert np.allclose(O.gemm_epilogue(P, 1.0, C, 1.0), C + P)
