@@ -1,0 +1,202 @@
+/*
+ * nsgb -- factorized high-order Newton-Schulz inversion of SPD matrices coupled
+ * to Richardson iteration, on GB300 (sm_103a).
+ *
+ * The method is A. Stotsky, "Convergence Rate Improvement of Richardson and
+ * Newton-Schulz Iterations" (arXiv 2008.11480):
+ *   problem        A theta_* = b with A symmetric positive definite (Section 1, eq. ae1)
+ *   G0             S^{-1} = alpha I (Section 2; default alpha = 1/||A||_F, option
+ *                  alpha = 1/(||A||_inf/2 + eps))
+ *   NS step        G_{k+1} = {sum_{j<n} F_k^j} G_k, error F_k = F_0^{n^k} (Section 3,
+ *                  eqs. ns, fk1), evaluated in the factorized product form of Section 4
+ *                  and Appendix Tables t1-t2: order 2^m as
+ *                  G (I + F)(I + F^2)...(I + F^{2^{m-1}}), F = I - A G (2m products);
+ *                  order 3 as G + G (F + F F) (3 products); or unfactorized (Horner).
+ *   Richardson     theta_{k+1} = theta_k + G_k (b - A theta_k) (Section 6, eq. ttk1 with
+ *                  the current inverse estimate as the gain).
+ *
+ * Conventions for every call below.
+ *   - Matrices are row-major FP64, n x n (A, G) or n x nrhs (B, theta), contiguous.
+ *   - Pointers may be device pointers (cudaMalloc / torch) or host pointers (pinned or
+ *     pageable); host buffers are staged through the context's device workspace, so a
+ *     host-pointer call includes the host<->device copies.
+ *   - The caller owns every buffer it passes; the library never frees caller memory.
+ *     The context owns its workspace (bf16 splits, f32 masters, residuals, scalars).
+ *   - Calls run on the context's stream (ns_set_stream, default: the legacy default
+ *     stream) and return after the stream has been synchronised, because the
+ *     convergence controller reads norms on the host once per iteration.
+ *   - Errors are return codes; no exception crosses the ABI.  ns_last_error() gives
+ *     a one-line message for the last failing call on a context.
+ *   - One context may not be used from two threads at once.
+ */
+#ifndef NSGB_H
+#define NSGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ns_ctx ns_ctx;
+
+typedef enum ns_status {
+  NS_OK = 0,
+  NS_NOT_CONVERGED = 1,   /* soft: results are written, tolerance not met */
+  NS_ERR_ARG = -1,        /* bad size, order, pointer or option */
+  NS_ERR_CUDA = -2,       /* a CUDA runtime call failed (see ns_last_error) */
+  NS_ERR_OOM = -3,        /* device workspace could not be allocated */
+  NS_ERR_DIVERGED = -4,   /* ||F_k||_F grew past sqrt(n) + 1: no contraction */
+  NS_ERR_TIMEOUT = -5,    /* a bounded device-side wait ran out; context stays usable */
+  NS_ERR_NONFINITE = -6,  /* a norm became NaN or Inf */
+  NS_ERR_UNSUPPORTED = -7 /* option combination not built */
+} ns_status;
+
+typedef enum ns_precision {
+  NS_FP64 = 0,   /* every product in FP64 on the CUDA cores (plain path) */
+  NS_BF16 = 2,   /* products hi*hi of bf16 operands, f32 accumulation (tcgen05) */
+  NS_BF16X3 = 3, /* split bf16: hi*hi + hi*lo + lo*hi into one f32 accumulator */
+  NS_AUTO = 5    /* bf16 while ||F_k||_F keeps falling, then bf16x3 (one-step rollback) */
+} ns_precision;
+
+typedef struct ns_options {
+  int precision;       /* ns_precision; default NS_AUTO */
+  int form;            /* 0 factorized (orders 3 and 2^m), 1 unfactorized Horner (any order) */
+  int pow_mode;        /* 0: F^{2^{j+1}} = F^{2^j} F^{2^j}; 1: F^{2^{j+1}} = I - A X_{j+1} (eq. ua1) */
+  int g0_mode;         /* 0: alpha = 1/||A||_F; 1: alpha = 1/(||A||_inf/2 + 1e-8 ||A||_inf) */
+  int ns_stop;         /* 0: take exactly `iters` NS steps; 1: stop NS at the precision floor */
+  double ns_stop_frob; /* with ns_stop = 1, also stop once ||F_k||_F <= this; default 0.02 */
+  int max_sweeps;      /* Richardson-only sweeps allowed after NS stops; default 200 */
+  int use_updated_G;   /* 1: theta_{k+1} = theta_k + G_{k+1} r_k (ordering of eq. ttk1) */
+  int profile;         /* 1: time each GEMM launch with CUDA events (ns_stats.gemm_ms) */
+  int gemm_bn;         /* 0: automatic; else 64, 128 or 256 output columns per tile */
+  double timeout_s;    /* bound on every device-side wait; default 2 s */
+  int aux_ahead;       /* composite only: 1 starts the auxiliary loops one step ahead,
+                          T_i = NS_{m_i}(G0), so rates = {n} gives the double Newton-Schulz
+                          method of Section 5.1 (eqs. gamk11-fks1); 0: T_i start at G0 */
+} ns_options;
+
+#define NS_MAX_HIST 256
+
+typedef struct ns_stats {
+  int status;                        /* ns_status of the call */
+  int ns_iters;                      /* accepted Newton-Schulz steps */
+  int sweeps;                        /* Richardson updates applied */
+  int rollbacks;                     /* rejected bf16 steps redone in bf16x3 */
+  int n_frob;                        /* entries in frob_F / prec_hist */
+  int n_res;                         /* entries in rel_res_hist */
+  double rel_res;                    /* last max_c ||b_c - A theta_c|| / ||b_c|| */
+  double frob_F[NS_MAX_HIST];        /* ||F_k||_F, F_k = I - A G_k, per computed F */
+  int prec_hist[NS_MAX_HIST];        /* precision used for that F and step */
+  double rel_res_hist[NS_MAX_HIST];  /* relative residual before each update */
+  long long gemm_launches;           /* GEMM kernel launches */
+  long long kernel_launches;         /* all kernel launches of the call */
+  double gemm_flops;                 /* executed products: sum of 2 M N K per bf16 pass / fp64 */
+  double gemm_ms;                    /* summed GEMM durations (profile = 1) */
+  double tc_gemm_ms;                 /* ... of tcgen05 launches only */
+  long long tc_gemm_launches;
+  double tc_gemm_flops;
+  double wall_ms;                    /* host wall time of the call */
+} ns_stats;
+
+/* Fill *opt with the defaults documented in ns_options. */
+void ns_default_options(ns_options* opt);
+
+/* Create a context for n x n systems (paper: A theta = b, Section 1, eq. ae1).
+ *   order   Newton-Schulz order n of eq. ns: 2, 3, 4, 8, 16 (factorized) or any
+ *           order >= 2 with form = 1.
+ *   rates   composite mixed-rate orders m_i of eqs. gkgen1-ga1 (Section 5): n_rates
+ *           auxiliary expansions T_i with x_i = m_i^k; n_rates = 0 for plain NS.
+ *   opt     NULL for defaults.
+ * Errors: NS_ERR_ARG (n <= 0, order < 2, order not factorizable with form = 0,
+ * n_rates < 0 or a rate < 1), NS_ERR_CUDA (no device), NS_ERR_OOM.  On success *out
+ * owns the workspace (about 14 n^2 bytes for NS_FP64 plus 32 n^2 for mixed precision,
+ * allocated on first use). */
+ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const ns_options* opt, ns_ctx** out);
+
+/* Release the context and its workspace.  NULL is accepted. */
+ns_status ns_destroy(ns_ctx* ctx);
+
+/* Run subsequent calls on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
+ns_status ns_set_stream(ns_ctx* ctx, void* cuda_stream);
+
+/* Newton-Schulz inversion (Section 3, eqs. ns, fk1; factorized per Section 4).
+ *   A      n x n SPD (read only).
+ *   G0     n x n initial estimate, or NULL for alpha I (Section 2).
+ *   iters  number of NS steps (a cap when opt.ns_stop = 1).
+ *   G_out  n x n result (FP64; from the f32 master on the mixed-precision paths),
+ *          or NULL to keep it resident in the context only.
+ *   st     optional statistics.
+ * Returns NS_OK, or an error above. */
+ns_status ns_invert(ns_ctx* ctx, const double* A, const double* G0, int iters, double* G_out, ns_stats* st);
+
+/* Newton-Schulz coupled to Richardson iteration for A Theta = B (nrhs columns).
+ * Each pass forms R = B - A Theta in FP64 and its relative residual
+ * max_c ||R_c|| / ||B_c||; the call stops once that is <= tol (tol <= 0: never).
+ * While fewer than `iters` NS steps were taken (and the precision floor is not
+ * reached when opt.ns_stop = 1) it applies Theta += G_k R and advances
+ * G_{k+1} = NS(G_k); afterwards up to opt.max_sweeps updates Theta += G R.
+ *   Theta0     n x nrhs start, or NULL for zero.
+ *   Theta_out  n x nrhs result (may alias Theta0).
+ * Returns NS_OK when tol was met, NS_NOT_CONVERGED when it was not (results
+ * written), or an error. */
+ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int nrhs, const double* Theta0,
+                              int iters, double tol, double* Theta_out, ns_stats* st);
+
+/* Relative residuals rel_res_out[c] = ||B_c - A Theta_c||_2 / ||B_c||_2 in FP64
+ * (the parameter-estimation error of eq. ttk1 measured through A). */
+ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const double* B, int nrhs,
+                      double* rel_res_out);
+
+/* Message for the last failing call on ctx ("" if none; static text for NULL). */
+const char* ns_last_error(const ns_ctx* ctx);
+const char* ns_status_string(ns_status s);
+
+/* ---------------------------------------------------------------------------
+ * Single-kernel entry points.  Device pointers only; `stream` is a cudaStream_t
+ * (NULL = legacy default).  Each returns after launching, without synchronising,
+ * except where a result is returned through a host pointer.  Scratch memory they
+ * need is allocated stream-ordered (cudaMallocAsync) and freed after use.
+ * ------------------------------------------------------------------------- */
+
+/* Split X (rows x cols, leading dimension ldx; x_dtype 0 = FP64, 1 = FP32) into
+ * bf16 hi = RN(RN32(x)) and lo = RN(RN32(x) - hi) with leading dimension ld
+ * (a multiple of 8).  This is the operand format of the tensor-core products. */
+ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo,
+                     int64_t ld, void* stream);
+
+/* Tensor-core product with the Newton-Schulz epilogue (Section 4 factor products).
+ * Synchronises `stream` before returning, to read the kernel's error word:
+ *   D = s * P + beta * C + gamma * I,  P = Lhi Rhi            (precision NS_BF16)
+ *                                     P = Lhi Rhi + Lhi Rlo + Llo Rhi (NS_BF16X3)
+ * L is M x K (ldl), R is K x N (ldr), bf16 splits from ns_k_split; C (f32, ldc) may
+ * be NULL.  Outputs (each may be NULL): D32 f32 (ldd32), Dhi/Dlo bf16 split of D
+ * (ldd16), frob_out a device double receiving sum(D^2).  Leading dimensions of bf16
+ * arrays must be multiples of 8 and of f32 arrays multiples of 4; base pointers
+ * 16-byte aligned.  bn = 0 picks the tile width.  Returns NS_ERR_ARG on violations. */
+ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
+                         int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
+                         int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
+                         int64_t ldd16, double* frob_out, int bn, void* stream);
+
+/* FP64 product with the same epilogue: D = s L R + beta C + gamma I (C may be NULL). */
+ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,
+                        int64_t ldr, double s, const double* C, int64_t ldc, double beta, double gamma, double* D,
+                        int64_t ldd, double* frob_out, void* stream);
+
+/* Richardson residual R = B - A Theta (n x nrhs, FP64); rsq_out (device, nrhs
+ * doubles, may be NULL) receives ||R_c||^2. */
+ns_status ns_k_resid(const double* A, int64_t lda, const double* Theta, const double* B, double* R, int64_t n,
+                     int nrhs, double* rsq_out, void* stream);
+
+/* Richardson update Theta += G R; G is f32 (g_dtype 1) or FP64 (g_dtype 0) with
+ * leading dimension ldg. */
+ns_status ns_k_update(const void* G, int g_dtype, int64_t ldg, const double* R, double* Theta, int64_t n, int nrhs,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSGB_H */

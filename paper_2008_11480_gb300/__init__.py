@@ -1,0 +1,337 @@
+"""GB300-native factorized high-order Newton-Schulz inversion coupled to
+Richardson iteration (A. Stotsky, arXiv 2008.11480).
+
+This module is a thin ctypes binding over ``libnsgb.so`` (C ABI declared in
+``include/nsgb.h``): it marshals torch tensors (device or host) into pointers
+and sizes and calls the library; every step of the method runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing
+the calls raise.
+
+Functions keep the ABI names (``ns_create``, ``ns_invert``,
+``ns_richardson_solve``, ``ns_residual``, and the single-kernel ``ns_k_*``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import torch
+
+__all__ = [
+    "NS_OK", "NS_NOT_CONVERGED", "NS_ERR_ARG", "NS_ERR_CUDA", "NS_ERR_OOM", "NS_ERR_DIVERGED",
+    "NS_ERR_TIMEOUT", "NS_ERR_NONFINITE", "NS_ERR_UNSUPPORTED",
+    "NS_FP64", "NS_BF16", "NS_BF16X3", "NS_AUTO",
+    "NSError", "ns_options", "ns_stats", "lib", "lib_path", "header_path", "default_options",
+    "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
+    "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
+    "ns_k_update", "Context",
+]
+
+NS_OK, NS_NOT_CONVERGED = 0, 1
+NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_DIVERGED = -1, -2, -3, -4
+NS_ERR_TIMEOUT, NS_ERR_NONFINITE, NS_ERR_UNSUPPORTED = -5, -6, -7
+NS_FP64, NS_BF16, NS_BF16X3, NS_AUTO = 0, 2, 3, 5
+NS_MAX_HIST = 256
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_PKG, "libnsgb.so")
+header_path = os.path.join(os.path.dirname(_PKG), "include", "nsgb.h")
+
+
+class NSError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{_status_name(status)}: {msg}" if msg else _status_name(status))
+
+
+class ns_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("form", ctypes.c_int),
+        ("pow_mode", ctypes.c_int),
+        ("g0_mode", ctypes.c_int),
+        ("ns_stop", ctypes.c_int),
+        ("ns_stop_frob", ctypes.c_double),
+        ("max_sweeps", ctypes.c_int),
+        ("use_updated_G", ctypes.c_int),
+        ("profile", ctypes.c_int),
+        ("gemm_bn", ctypes.c_int),
+        ("timeout_s", ctypes.c_double),
+        ("aux_ahead", ctypes.c_int),
+    ]
+
+
+class ns_stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("ns_iters", ctypes.c_int),
+        ("sweeps", ctypes.c_int),
+        ("rollbacks", ctypes.c_int),
+        ("n_frob", ctypes.c_int),
+        ("n_res", ctypes.c_int),
+        ("rel_res", ctypes.c_double),
+        ("frob_F", ctypes.c_double * NS_MAX_HIST),
+        ("prec_hist", ctypes.c_int * NS_MAX_HIST),
+        ("rel_res_hist", ctypes.c_double * NS_MAX_HIST),
+        ("gemm_launches", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("gemm_flops", ctypes.c_double),
+        ("gemm_ms", ctypes.c_double),
+        ("tc_gemm_ms", ctypes.c_double),
+        ("tc_gemm_launches", ctypes.c_longlong),
+        ("tc_gemm_flops", ctypes.c_double),
+        ("wall_ms", ctypes.c_double),
+    ]
+
+    def frob_history(self) -> list[float]:
+        return [self.frob_F[i] for i in range(self.n_frob)]
+
+    def prec_history(self) -> list[int]:
+        return [self.prec_hist[i] for i in range(self.n_frob)]
+
+    def res_history(self) -> list[float]:
+        return [self.rel_res_hist[i] for i in range(self.n_res)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnsgb.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(lib_path):
+        raise RuntimeError(f"{lib_path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(lib_path)
+    sig = {
+        "ns_default_options": (None, [ctypes.POINTER(ns_options)]),
+        "ns_create": (_int, [_i64, _int, ctypes.POINTER(_int), _int, ctypes.POINTER(ns_options), ctypes.POINTER(_vp)]),
+        "ns_destroy": (_int, [_vp]),
+        "ns_set_stream": (_int, [_vp, _vp]),
+        "ns_invert": (_int, [_vp, _vp, _vp, _int, _vp, ctypes.POINTER(ns_stats)]),
+        "ns_richardson_solve": (_int, [_vp, _vp, _vp, _int, _vp, _int, ctypes.c_double, _vp, ctypes.POINTER(ns_stats)]),
+        "ns_residual": (_int, [_vp, _vp, _vp, _vp, _int, _vp]),
+        "ns_last_error": (ctypes.c_char_p, [_vp]),
+        "ns_status_string": (ctypes.c_char_p, [_int]),
+        "ns_k_split": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
+        "ns_k_gemm_bf16": (_int, [_int, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, _vp, _i64,
+                                  ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, _int, _vp]),
+        "ns_k_gemm_f64": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
+                                 ctypes.c_double, _vp, _i64, _vp, _vp]),
+        "ns_k_resid": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
+        "ns_k_update": (_int, [_vp, _int, _i64, _vp, _vp, _i64, _int, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/nsgb.h declares."""
+    txt = open(header_path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ns_[a-z0-9_]+)\s*\(", txt, re.M)))
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().ns_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def ns_status_string(s: int) -> str:
+    return lib().ns_status_string(s).decode()
+
+
+def default_options(**kw) -> ns_options:
+    o = ns_options()
+    lib().ns_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float64) -> int | None:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def ns_create(n: int, order: int, rates=(), opt: ns_options | None = None) -> int:
+    arr = (_int * max(1, len(rates)))(*rates) if rates else None
+    h = _vp()
+    s = lib().ns_create(int(n), int(order), arr, len(rates), ctypes.byref(opt) if opt is not None else None,
+                        ctypes.byref(h))
+    if s != NS_OK:
+        raise NSError(s, "ns_create")
+    return h.value
+
+
+def ns_destroy(ctx: int) -> None:
+    lib().ns_destroy(ctx)
+
+
+def ns_set_stream(ctx: int, stream) -> None:
+    s = lib().ns_set_stream(ctx, _stream_ptr(stream))
+    if s != NS_OK:
+        raise NSError(s)
+
+
+def ns_last_error(ctx: int) -> str:
+    return lib().ns_last_error(ctx).decode()
+
+
+def _check(ctx: int, s: int, allow=(NS_OK, NS_NOT_CONVERGED)) -> int:
+    if s not in allow:
+        raise NSError(s, ns_last_error(ctx))
+    return s
+
+
+def ns_invert(ctx: int, A: torch.Tensor, G0: torch.Tensor | None, iters: int, G_out: torch.Tensor | None,
+              check: bool = True) -> tuple[int, ns_stats]:
+    st = ns_stats()
+    s = lib().ns_invert(ctx, _ptr(A), _ptr(G0), int(iters), _ptr(G_out), ctypes.byref(st))
+    if check:
+        _check(ctx, s)
+    return s, st
+
+
+def ns_richardson_solve(ctx: int, A: torch.Tensor, B: torch.Tensor, theta0: torch.Tensor | None, iters: int,
+                        tol: float, theta_out: torch.Tensor, check: bool = True) -> tuple[int, ns_stats]:
+    st = ns_stats()
+    nrhs = B.shape[1] if B.dim() == 2 else 1
+    s = lib().ns_richardson_solve(ctx, _ptr(A), _ptr(B), nrhs, _ptr(theta0), int(iters), float(tol),
+                                  _ptr(theta_out), ctypes.byref(st))
+    if check:
+        _check(ctx, s)
+    return s, st
+
+
+def ns_residual(ctx: int, A: torch.Tensor, theta: torch.Tensor, B: torch.Tensor) -> list[float]:
+    nrhs = B.shape[1] if B.dim() == 2 else 1
+    out = (ctypes.c_double * nrhs)()
+    s = lib().ns_residual(ctx, _ptr(A), _ptr(theta), _ptr(B), nrhs, out)
+    _check(ctx, s, (NS_OK,))
+    return list(out)
+
+
+# ---------------------------------------------------------------- single kernels
+
+def _raise(s: int, what: str):
+    if s != NS_OK:
+        raise NSError(s, what)
+
+
+def ns_k_split(X: torch.Tensor, hi: torch.Tensor, lo: torch.Tensor, rows: int, cols: int, ldx: int, ld: int,
+               stream=None) -> None:
+    dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
+    _raise(lib().ns_k_split(X.data_ptr(), dt, rows, cols, ldx, _ptr(hi, torch.bfloat16), _ptr(lo, torch.bfloat16),
+                            ld, _stream_ptr(stream)), "ns_k_split")
+
+
+def ns_k_gemm_bf16(precision: int, M: int, N: int, K: int, Lhi, Llo, ldl: int, Rhi, Rlo, ldr: int, s: float = 1.0,
+                   C=None, ldc: int = 0, beta: float = 0.0, gamma: float = 0.0, D32=None, ldd32: int = 0,
+                   Dhi=None, Dlo=None, ldd16: int = 0, frob_out=None, bn: int = 0, stream=None) -> None:
+    bf = torch.bfloat16
+    r = lib().ns_k_gemm_bf16(precision, M, N, K, _ptr(Lhi, bf), _ptr(Llo, bf), ldl, _ptr(Rhi, bf), _ptr(Rlo, bf), ldr,
+                             s, _ptr(C, torch.float32), ldc, beta, gamma, _ptr(D32, torch.float32), ldd32,
+                             _ptr(Dhi, bf), _ptr(Dlo, bf), ldd16, _ptr(frob_out), bn, _stream_ptr(stream))
+    _raise(r, "ns_k_gemm_bf16")
+
+
+def ns_k_gemm_f64(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float, C, ldc: int, beta: float, gamma: float,
+                  D, ldd: int, frob_out=None, stream=None) -> None:
+    r = lib().ns_k_gemm_f64(M, N, K, _ptr(L), ldl, _ptr(R), ldr, s, _ptr(C), ldc, beta, gamma, _ptr(D), ldd,
+                            _ptr(frob_out), _stream_ptr(stream))
+    _raise(r, "ns_k_gemm_f64")
+
+
+def ns_k_resid(A, lda: int, theta, B, R, n: int, nrhs: int, rsq_out=None, stream=None) -> None:
+    _raise(lib().ns_k_resid(_ptr(A), lda, _ptr(theta), _ptr(B), _ptr(R), n, nrhs, _ptr(rsq_out),
+                            _stream_ptr(stream)), "ns_k_resid")
+
+
+def ns_k_update(G, ldg: int, R, theta, n: int, nrhs: int, stream=None) -> None:
+    dt = {torch.float64: 0, torch.float32: 1}[G.dtype]
+    _raise(lib().ns_k_update(G.data_ptr(), dt, ldg, _ptr(R), _ptr(theta), n, nrhs, _stream_ptr(stream)),
+           "ns_k_update")
+
+
+# ---------------------------------------------------------------- convenience
+
+@dataclass
+class SolveResult:
+    theta: torch.Tensor
+    status: int
+    stats: ns_stats
+
+
+class Context:
+    """Owns one ``ns_ctx``: ``Context(n, order=4, rates=(), **options)``."""
+
+    def __init__(self, n: int, order: int = 4, rates=(), stream=None, **options):
+        self.n = int(n)
+        self.opt = default_options(**options)
+        self.handle = ns_create(n, order, tuple(rates), self.opt)
+        if stream is not None:
+            ns_set_stream(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def invert(self, A: torch.Tensor, iters: int, G0: torch.Tensor | None = None,
+               out: torch.Tensor | None = None) -> tuple[torch.Tensor, ns_stats]:
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.float64, device=A.device)
+        _, st = ns_invert(self.handle, A, G0, iters, out)
+        return out, st
+
+    def solve(self, A: torch.Tensor, B: torch.Tensor, iters: int = 64, tol: float = 1e-10,
+              theta0: torch.Tensor | None = None, out: torch.Tensor | None = None) -> SolveResult:
+        if out is None:
+            out = torch.empty_like(B)
+        s, st = ns_richardson_solve(self.handle, A, B, theta0, iters, tol, out)
+        return SolveResult(out, s, st)
+
+    def residual(self, A, theta, B) -> list[float]:
+        return ns_residual(self.handle, A, theta, B)

@@ -1,0 +1,412 @@
+// Persistent grouped bf16 / split-bf16 GEMM on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in TMEM, operands staged by TMA), with the fused
+// epilogue every Newton-Schulz product needs:
+//
+//   D = s * (L R) + beta * C + gamma * I
+//
+// which covers F = I - A G (s = -1, gamma = 1), X_{j+1} = X_j + X_j P_j
+// (beta = 1, C = X_j), P_{j+1} = P_j P_j and T_c + Gamma_c X.  The epilogue
+// writes the f32 master of D, its bf16 hi/lo split (the operands of the next
+// product) and per-tile partial sums of D^2 (for ||F||_F).
+//
+// Roles (192 threads, one CTA per SM):
+//   warp 0 lane 0   TMA producer: fills a ring of shared-memory stages
+//   warp 1          TMEM allocator; lane 0 issues tcgen05.mma for a tile
+//   warps 2..5      epilogue: TMEM -> registers -> fused math -> global
+// The accumulator is double-buffered in TMEM (2 x BN columns), so the
+// epilogue of tile i overlaps the MMAs of tile i+1.
+//
+// Shared-memory layouts (both 128-byte swizzled, atoms of 8 rows x 128 B):
+//   L tile 128 x 64 (K-major):  row r at r*128 B; MMA K-slice k at +32k B.
+//   R tile 64 x BN (N-major):   BN/64 chunks of 64 K-rows x 64 N-columns,
+//                               chunk j at j*8 KiB (LBO), 8-row groups at 1 KiB
+//                               (SBO); MMA K-slice k at +2 KiB*k.
+#include <cstdio>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace nsgb {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;
+constexpr int kThreads = 192;
+
+template <int BN>
+struct TcCfg {
+  static constexpr int kABytes = kBM * kBK * 2;  // 16 KiB
+  static constexpr int kBBytes = BN * kBK * 2;   // BN * 128 B
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = BN == 256 ? 4 : (BN == 128 ? 6 : 8);
+  static constexpr uint32_t kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
+};
+
+__device__ __forceinline__ void decode_tile(const TcParams& p, int t, int& pi, int& m0, int& n0, int BN) {
+  pi = 0;
+#pragma unroll 1
+  for (int i = 1; i < p.nprob; ++i)
+    if (t >= p.prob[i].tile_begin) pi = i;
+  const TcProblem& P = p.prob[pi];
+  const int local = t - P.tile_begin;
+  m0 = (local / P.tiles_n) * kBM;
+  n0 = (local % P.tiles_n) * BN;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
+  using Cfg = TcCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + Cfg::kStages * Cfg::kABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + Cfg::kStages * Cfg::kBBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + Cfg::kStages;
+  uint64_t* tfull = bars + 2 * Cfg::kStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint64_t tlim = p.timeout_ns;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    for (int i = 0; i < p.nprob; ++i) {
+      tma_prefetch_desc(&p.prob[i].L[0]);
+      tma_prefetch_desc(&p.prob[i].R[0]);
+      if (p.npass > 1) {
+        tma_prefetch_desc(&p.prob[i].L[1]);
+        tma_prefetch_desc(&p.prob[i].R[1]);
+      }
+    }
+    int armed[Cfg::kStages];
+    for (int s = 0; s < Cfg::kStages; ++s) armed[s] = -1;
+    int stage = 0;
+    uint32_t phase = 0;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+      int pi, m0, n0;
+      decode_tile(p, t, pi, m0, n0, BN);
+      const TcProblem& P = p.prob[pi];
+      const int nkb = (P.K + kBK - 1) / kBK;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        for (int ps = 0; ps < p.npass; ++ps) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, tlim, abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (it != p.debug_stall_iter) {
+            const CUtensorMap* ml = &P.L[ps == 2 ? 1 : 0];
+            const CUtensorMap* mr = &P.R[ps == 1 ? 1 : 0];
+            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+            armed[stage] = static_cast<int>(phase);
+            uint8_t* a = sA + stage * Cfg::kABytes;
+            uint8_t* b = sB + stage * Cfg::kBBytes;
+            tma_load_2d(a, ml, &full[stage], kb * kBK, m0);
+            tma_load_2d(a + 8192, ml, &full[stage], kb * kBK, m0 + 64);
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j) tma_load_2d(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK);
+          }
+          ++it;
+          if (++stage == Cfg::kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(p.err, DEV_TIMEOUT);
+      // let every load this thread issued land before the CTA exits
+      volatile int never = 0;
+      for (int s = 0; s < Cfg::kStages; ++s)
+        if (armed[s] >= 0) mbar_wait(&full[s], static_cast<uint32_t>(armed[s]), 100000000ull, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t idesc = make_idesc_bf16(kBM, BN, 0, 1);
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    bool issued = false;
+    for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+      int pi, m0, n0;
+      decode_tile(p, t, pi, m0, n0, BN);
+      const TcProblem& P = p.prob[pi];
+      const int nkb = (P.K + kBK - 1) / kBK;
+      if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, tlim, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+      uint32_t accumulate = 0;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        for (int ps = 0; ps < p.npass; ++ps) {
+          if (!mbar_wait(&full[stage], phase, tlim, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(sA + stage * Cfg::kABytes);
+          const uint32_t b_base = smem_u32(sB + stage * Cfg::kBBytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint64_t ad = make_sdesc(a_base + 32u * k, 16u, 1024u);
+            const uint64_t bd = make_sdesc(b_base + 2048u * k, 8192u, 1024u);
+            tc_mma_bf16(d_tmem, ad, bd, idesc, accumulate);
+            accumulate = 1;
+          }
+          issued = true;
+          tc_commit(&empty[stage]);
+          if (++stage == Cfg::kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) break;
+      tc_commit(&tfull[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(p.err, DEV_TIMEOUT);
+      if (issued) {
+        // all MMAs this thread issued must finish before TMEM is released
+        volatile int never = 0;
+        tc_commit(drain);
+        mbar_wait(drain, 0, 100000000ull, &never);
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+      int pi, m0, n0;
+      decode_tile(p, t, pi, m0, n0, BN);
+      const TcProblem& P = p.prob[pi];
+      bool ok = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        *abort_flag = 1;
+        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int row = m0 + q * 32 + lane;
+      const bool row_ok = row < P.M;
+      float frob = 0.f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN + c0),
+                           r);
+        tmem_wait_ld();
+        const int col0 = n0 + c0;
+        if (!row_ok || col0 >= P.N) continue;
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = P.s * __uint_as_float(r[i]);
+        const bool full_chunk = col0 + 32 <= P.N;
+        if (P.C != nullptr && P.beta != 0.f) {
+          const float* crow = P.C + static_cast<int64_t>(row) * P.ldc + col0;
+          if (full_chunk) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 c = *reinterpret_cast<const float4*>(crow + i);
+              v[i] += P.beta * c.x;
+              v[i + 1] += P.beta * c.y;
+              v[i + 2] += P.beta * c.z;
+              v[i + 3] += P.beta * c.w;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (col0 + i < P.N) v[i] += P.beta * crow[i];
+          }
+        }
+        if (P.gamma != 0.f) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += (row == col0 + i) ? P.gamma : 0.f;
+        }
+        if (full_chunk) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) frob += v[i] * v[i];
+          if (P.D32 != nullptr) {
+            float* drow = P.D32 + static_cast<int64_t>(row) * P.ldd32 + col0;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(drow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          }
+          if (P.Dhi != nullptr) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[i]);
+              const __nv_bfloat16 h1 = __float2bfloat16_rn(v[i + 1]);
+              __nv_bfloat162 hh;
+              hh.x = h0;
+              hh.y = h1;
+              hi[i / 2] = *reinterpret_cast<uint32_t*>(&hh);
+              lo[i / 2] = pack_bf16x2(v[i] - __bfloat162float(h0), v[i + 1] - __bfloat162float(h1));
+            }
+            bf16* hrow = P.Dhi + static_cast<int64_t>(row) * P.ldd16 + col0;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+              *reinterpret_cast<uint4*>(hrow + 2 * i) = make_uint4(hi[i], hi[i + 1], hi[i + 2], hi[i + 3]);
+            if (P.Dlo != nullptr) {
+              bf16* lrow = P.Dlo + static_cast<int64_t>(row) * P.ldd16 + col0;
+#pragma unroll
+              for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<uint4*>(lrow + 2 * i) = make_uint4(lo[i], lo[i + 1], lo[i + 2], lo[i + 3]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (col0 + i >= P.N) continue;
+            frob += v[i] * v[i];
+            const int64_t o32 = static_cast<int64_t>(row) * P.ldd32 + col0 + i;
+            const int64_t o16 = static_cast<int64_t>(row) * P.ldd16 + col0 + i;
+            if (P.D32 != nullptr) P.D32[o32] = v[i];
+            if (P.Dhi != nullptr) {
+              const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
+              P.Dhi[o16] = h;
+              if (P.Dlo != nullptr) P.Dlo[o16] = __float2bfloat16_rn(v[i] - __bfloat162float(h));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      if (P.frob_partials != nullptr) {
+        double f = static_cast<double>(frob);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0) P.frob_partials[(t - P.tile_begin) * 4 + q] = f;
+      }
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  }
+}
+
+template <int BN>
+cudaError_t launch_bn(const TcParams& p, int num_sms, cudaStream_t s) {
+  using Cfg = TcCfg<BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = p.total_tiles < num_sms ? p.total_tiles : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  k_gemm_tc<BN><<<grid, kThreads, Cfg::kSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_tiles(int M, int N, int BN) { return ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN); }
+
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, int num_sms, cudaStream_t s) {
+  switch (BN) {
+    case 64:
+      return launch_bn<64>(p, num_sms, s);
+    case 128:
+      return launch_bn<128>(p, num_sms, s);
+    case 256:
+      return launch_bn<256>(p, num_sms, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------------ tensor maps
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  if (fn == nullptr) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(ptr);
+  }
+  return fn;
+}
+}  // namespace
+
+bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld) {
+  EncodeFn enc = get_encode();
+  if (enc == nullptr) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 2) % 16 != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * 2)};
+  cuuint32_t box[2] = {64, 64};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace nsgb

@@ -1,0 +1,105 @@
+// Internal interfaces between the solver runtime and the kernels.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace nsgb {
+
+using bf16 = __nv_bfloat16;
+
+// Device error word values written by kernels whose bounded waits ran out.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+constexpr int kTcMaxProblems = 4;
+
+// One GEMM of a grouped tcgen05 launch:
+//   D = s * (sum over passes of L_a R_b) + beta * C + gamma * I
+// L is M x K and R is K x N, both row-major bf16 reached through 2-D tensor
+// maps (box 64 x 64, 128-byte swizzle).  Index 0 of L/R is the hi part of the
+// split, index 1 the lo part.  Outputs (each optional): the f32 master D32,
+// the bf16 split Dhi/Dlo, and per-(tile, epilogue warp) partial sums of D^2.
+struct TcProblem {
+  CUtensorMap L[2];
+  CUtensorMap R[2];
+  int M, N, K;
+  int tiles_n;     // ceil(N / BN)
+  int tile_begin;  // first global tile index of this problem
+  int tile_count;
+  float s, beta, gamma;
+  int ldc, ldd32, ldd16;
+  const float* C;
+  float* D32;
+  bf16* Dhi;
+  bf16* Dlo;
+  double* frob_partials;  // tile_count * 4 values
+};
+
+struct TcParams {
+  TcProblem prob[kTcMaxProblems];
+  int nprob;
+  int total_tiles;
+  int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3)
+  int debug_stall_iter;  // -1 for none; else the producer withholds that load
+  unsigned long long timeout_ns;
+  int* err;
+};
+
+// Launch a grouped tcgen05 GEMM; BN in {64, 128, 256}.
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, int num_sms, cudaStream_t s);
+int tc_tiles(int M, int N, int BN);
+
+// Encode a 2-D bf16 tensor map (rows x cols, leading dimension ld elements).
+bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld);
+
+// ---- FP64 CUDA-core GEMM with the same epilogue (plain FP64 path)
+struct F64Gemm {
+  int M, N, K;
+  const double* L; int ldl;
+  const double* R; int ldr;
+  double s, beta, gamma;
+  const double* C; int ldc;
+  double* D; int ldd;
+  double* frob_partials;  // one per 64x64 tile (row-major tile order), may be null
+};
+cudaError_t launch_gemm_f64(const F64Gemm& g, cudaStream_t s);
+int f64_tiles(int M, int N);
+
+// ---- HBM-bound FP64 kernels
+// R = B - A Theta; per-block partial sums of R^2 per column (nblocks x nrhs).
+cudaError_t launch_resid(const double* A, int64_t lda, const double* Theta, const double* B, double* R,
+                         int n, int nrhs, double* partials, int* nblocks_out, cudaStream_t s);
+int resid_blocks(int n);
+// Theta += G R with G float (ldg) or double.
+cudaError_t launch_update_f32(const float* G, int64_t ldg, const double* R, double* Theta, int n, int nrhs,
+                              cudaStream_t s);
+cudaError_t launch_update_f64(const double* G, int64_t ldg, const double* R, double* Theta, int n, int nrhs,
+                              cudaStream_t s);
+// Column sums of squares of a rows x cols row-major matrix -> partials (nblocks x cols).
+cudaError_t launch_colsumsq(const double* X, int64_t ldx, int rows, int cols, double* partials,
+                            int* nblocks_out, cudaStream_t s);
+// Sum of squares and max row |.|-sum of an n x n FP64 matrix -> partials.
+cudaError_t launch_matnorms(const double* A, int64_t lda, int n, double* ss_partials, double* rowmax_partials,
+                            int* nblocks_out, cudaStream_t s);
+// out[c] = sum_b partials[b * ncols + c] (fixed order) for c < ncols.
+cudaError_t launch_reduce_sum(const double* partials, int nblocks, int ncols, double* out, cudaStream_t s);
+cudaError_t launch_reduce_max(const double* partials, int nblocks, double* out, cudaStream_t s);
+// Split an FP64 or FP32 rows x cols matrix into bf16 hi/lo (ld elements) and,
+// optionally, its f32 rounding.
+cudaError_t launch_split_f64(const double* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, float* x32,
+                             int64_t ld, cudaStream_t s);
+cudaError_t launch_split_f32(const float* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, int64_t ld,
+                             cudaStream_t s);
+// G = alpha I where alpha is read on the device: mode 0 -> 1/sqrt(scal[0])
+// (Frobenius), mode 1 -> 1/(scal[1]/2 + 1e-8 scal[1]) (infinity norm).
+cudaError_t launch_init_g0_mp(const double* scal, int mode, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,
+                              cudaStream_t s);
+cudaError_t launch_init_g0_f64(const double* scal, int mode, int n, int64_t ld, double* G, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
+                              cudaStream_t s);
+cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
+                            cudaStream_t s);
+
+}  // namespace nsgb

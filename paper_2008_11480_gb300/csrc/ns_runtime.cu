@@ -1,0 +1,1194 @@
+// Solver runtime behind the C ABI of include/nsgb.h: context and workspace,
+// the Newton-Schulz product chain (Section 4 / Appendix Tables t1-t2), the
+// composite mixed-rate and double-loop variants (Section 5, 5.1), the coupled
+// Richardson iteration (Section 6) and the precision controller.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nsgb.h"
+#include "internal.h"
+
+using namespace nsgb;
+
+namespace {
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A bf16-split matrix with its f32 master and tensor maps (workspace layout:
+// n x n, leading dimension ld, padding never written and kept zero).
+struct MpMat {
+  float* m32 = nullptr;
+  bf16* hi = nullptr;
+  bf16* lo = nullptr;
+  CUtensorMap map_hi, map_lo;
+};
+
+struct GemmSpec {
+  const MpMat* L;
+  const MpMat* R;
+  float s;
+  const float* C;
+  float beta;
+  float gamma;
+  MpMat* D;
+  bool want32;
+  double* frob_dst;  // device scalar receiving sum(D^2), or null
+};
+
+struct EventPair {
+  cudaEvent_t a, b;
+  bool tc;
+};
+
+}  // namespace
+
+struct ns_ctx {
+  int64_t n = 0, ld = 0;
+  int order = 2;
+  std::vector<int> rates;
+  ns_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 148;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // shared workspace
+  double* dscal = nullptr;  // [0] ||A||_F^2 [1] ||A||_inf [2] ||F||_F^2 [3] err (as int) [8..] rsq, bsq
+  double* hscal = nullptr;  // pinned mirror
+  int scal_cap = 0;
+  double* partials = nullptr;
+  size_t partials_cap = 0;
+  double* Astage = nullptr;
+  double *Bd = nullptr, *Thd = nullptr, *Rd = nullptr;
+  int nrhs_cap = 0;
+  int* derr = nullptr;
+
+  // mixed precision
+  bool mp_ready = false;
+  MpMat A, G[2], X[2], F, P[2];
+  // composite
+  bool comp_ready = false;
+  std::vector<MpMat> T[2];  // per rate, ping-pong
+  MpMat Gam, Tc[2], Pre[2], Xs[2];
+  // fp64
+  bool f64_ready = false;
+  double *G64[2] = {nullptr, nullptr}, *X64[2] = {nullptr, nullptr}, *F64 = nullptr, *P64[2] = {nullptr, nullptr};
+  std::vector<double*> T64[2];
+  double *Gam64 = nullptr, *Tc64[2] = {nullptr, nullptr}, *Pre64[2] = {nullptr, nullptr}, *Xs64[2] = {nullptr, nullptr};
+
+  // per-call accounting
+  std::vector<EventPair> evs;
+  std::vector<EventPair> ev_pool;
+  ns_stats* st = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+ns_status fail(ns_ctx* c, ns_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define NS_CK(call)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+#define NS_TRY(expr)                  \
+  do {                                \
+    ns_status s_ = (expr);            \
+    if (s_ < 0) return s_;            \
+  } while (0)
+
+template <typename T>
+ns_status alloc(ns_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, NS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(q, 0, count * sizeof(T) + 256, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+  ctx->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return NS_OK;
+}
+
+// Rows and columns are both padded to ld (a multiple of 64) and the padding is
+// zero, so every 64 x 64 TMA box lies inside the tensor's extent.
+ns_status alloc_mp(ns_ctx* ctx, MpMat& m, bool with32) {
+  const size_t cnt = static_cast<size_t>(ctx->ld) * ctx->ld;
+  if (with32) NS_TRY(alloc(ctx, &m.m32, cnt));
+  NS_TRY(alloc(ctx, &m.hi, cnt));
+  NS_TRY(alloc(ctx, &m.lo, cnt));
+  if (!encode_bf16_map(&m.map_hi, m.hi, ctx->ld, ctx->ld, ctx->ld) ||
+      !encode_bf16_map(&m.map_lo, m.lo, ctx->ld, ctx->ld, ctx->ld))
+    return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return NS_OK;
+}
+
+ns_status ensure_common(ns_ctx* ctx, int nrhs) {
+  if (nrhs > ctx->nrhs_cap || ctx->dscal == nullptr) {
+    const int cap = std::max(nrhs, std::max(1, ctx->nrhs_cap));
+    NS_TRY(alloc(ctx, &ctx->dscal, 8 + 2 * static_cast<size_t>(cap)));
+    if (ctx->hscal) cudaFreeHost(ctx->hscal);
+    NS_CK(cudaMallocHost(&ctx->hscal, (8 + 2 * static_cast<size_t>(cap)) * sizeof(double)));
+    ctx->scal_cap = cap;
+    NS_TRY(alloc(ctx, &ctx->Rd, static_cast<size_t>(ctx->n) * cap));
+    NS_TRY(alloc(ctx, &ctx->Bd, static_cast<size_t>(ctx->n) * cap));
+    NS_TRY(alloc(ctx, &ctx->Thd, static_cast<size_t>(ctx->n) * cap));
+    ctx->nrhs_cap = cap;
+    ctx->derr = reinterpret_cast<int*>(ctx->dscal + 3);
+    // partial sums: GEMM tiles (4 per tile at the smallest tile width), fp64
+    // tiles, residual blocks x nrhs, norm blocks
+    const int n = static_cast<int>(ctx->n);
+    size_t need = std::max<size_t>(static_cast<size_t>(tc_tiles(n, n, 64)) * 4, f64_tiles(n, n));
+    need = std::max<size_t>(need, static_cast<size_t>(resid_blocks(n)) * cap);
+    need = std::max<size_t>(need, 2 * static_cast<size_t>((n + 7) / 8) + 2);
+    if (need > ctx->partials_cap) {
+      NS_TRY(alloc(ctx, &ctx->partials, need));
+      ctx->partials_cap = need;
+    }
+  }
+  return NS_OK;
+}
+
+ns_status ensure_mp(ns_ctx* ctx) {
+  if (ctx->mp_ready) return NS_OK;
+  NS_TRY(alloc_mp(ctx, ctx->A, false));
+  for (int i = 0; i < 2; ++i) {
+    NS_TRY(alloc_mp(ctx, ctx->G[i], true));
+    NS_TRY(alloc_mp(ctx, ctx->X[i], true));
+    NS_TRY(alloc_mp(ctx, ctx->P[i], false));
+  }
+  NS_TRY(alloc_mp(ctx, ctx->F, true));
+  ctx->mp_ready = true;
+  return NS_OK;
+}
+
+ns_status ensure_f64(ns_ctx* ctx) {
+  if (ctx->f64_ready) return NS_OK;
+  const size_t cnt = static_cast<size_t>(ctx->n) * ctx->ld;
+  for (int i = 0; i < 2; ++i) {
+    NS_TRY(alloc(ctx, &ctx->G64[i], cnt));
+    NS_TRY(alloc(ctx, &ctx->X64[i], cnt));
+    NS_TRY(alloc(ctx, &ctx->P64[i], cnt));
+  }
+  NS_TRY(alloc(ctx, &ctx->F64, cnt));
+  ctx->f64_ready = true;
+  return NS_OK;
+}
+
+ns_status ensure_composite(ns_ctx* ctx, bool fp64) {
+  const size_t w = ctx->rates.size();
+  if (w == 0) return NS_OK;
+  const size_t cnt = static_cast<size_t>(ctx->n) * ctx->ld;
+  if (fp64) {
+    if (!ctx->T64[0].empty()) return NS_OK;
+    for (int b = 0; b < 2; ++b) {
+      ctx->T64[b].assign(w, nullptr);
+      for (size_t i = 0; i < w; ++i) NS_TRY(alloc(ctx, &ctx->T64[b][i], cnt));
+      NS_TRY(alloc(ctx, &ctx->Tc64[b], cnt));
+      NS_TRY(alloc(ctx, &ctx->Pre64[b], cnt));
+      NS_TRY(alloc(ctx, &ctx->Xs64[b], cnt));
+    }
+    NS_TRY(alloc(ctx, &ctx->Gam64, cnt));
+    return NS_OK;
+  }
+  if (ctx->comp_ready) return NS_OK;
+  for (int b = 0; b < 2; ++b) {
+    ctx->T[b].assign(w, MpMat());
+    for (size_t i = 0; i < w; ++i) NS_TRY(alloc_mp(ctx, ctx->T[b][i], true));
+    NS_TRY(alloc_mp(ctx, ctx->Tc[b], true));
+    NS_TRY(alloc_mp(ctx, ctx->Pre[b], false));
+    NS_TRY(alloc_mp(ctx, ctx->Xs[b], true));
+  }
+  NS_TRY(alloc_mp(ctx, ctx->Gam, false));
+  ctx->comp_ready = true;
+  return NS_OK;
+}
+
+// ---------------------------------------------------------------- timing
+EventPair* ev_begin(ns_ctx* ctx, bool tc) {
+  if (!ctx->opt.profile) return nullptr;
+  EventPair e;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else {
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+  }
+  e.tc = tc;
+  cudaEventRecord(e.a, ctx->stream);
+  ctx->evs.push_back(e);
+  return &ctx->evs.back();
+}
+void ev_end(ns_ctx* ctx, EventPair* e) {
+  if (e) cudaEventRecord(e->b, ctx->stream);
+}
+void ev_collect(ns_ctx* ctx) {
+  for (auto& e : ctx->evs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess && ctx->st) {
+      ctx->st->gemm_ms += ms;
+      if (e.tc) ctx->st->tc_gemm_ms += ms;
+    }
+    ctx->ev_pool.push_back(e);
+  }
+  ctx->evs.clear();
+  cudaGetLastError();
+}
+
+int pick_bn(const ns_ctx* ctx, int nprob) {
+  if (ctx->opt.gemm_bn == 64 || ctx->opt.gemm_bn == 128 || ctx->opt.gemm_bn == 256) return ctx->opt.gemm_bn;
+  const int n = static_cast<int>(ctx->n);
+  const int bns[3] = {256, 128, 64};
+  const double eff[3] = {1.0, 0.93, 0.80};
+  int best = 256;
+  double best_e = -1.0;
+  for (int i = 0; i < 3; ++i) {
+    const int tiles = nprob * tc_tiles(n, n, bns[i]);
+    const int waves = (tiles + ctx->num_sms - 1) / ctx->num_sms;
+    const double e = static_cast<double>(tiles) / (static_cast<double>(waves) * ctx->num_sms) * eff[i];
+    if (e > best_e + 1e-9) {
+      best_e = e;
+      best = bns[i];
+    }
+  }
+  return best;
+}
+
+// One grouped tcgen05 launch of up to kTcMaxProblems products of n x n matrices.
+ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
+  const int n = static_cast<int>(ctx->n);
+  const int bn = pick_bn(ctx, nspec);
+  TcParams p;
+  memset(&p, 0, sizeof(p));
+  p.nprob = nspec;
+  p.npass = prec == NS_BF16X3 ? 3 : 1;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
+  p.err = ctx->derr;
+  int tile = 0;
+  std::vector<std::pair<double*, int>> reduces;
+  size_t poff = 0;
+  for (int i = 0; i < nspec; ++i) {
+    const GemmSpec& g = specs[i];
+    TcProblem& P = p.prob[i];
+    P.L[0] = g.L->map_hi;
+    P.L[1] = g.L->map_lo;
+    P.R[0] = g.R->map_hi;
+    P.R[1] = g.R->map_lo;
+    P.M = n;
+    P.N = n;
+    P.K = n;
+    P.tiles_n = (n + bn - 1) / bn;
+    P.tile_begin = tile;
+    P.tile_count = tc_tiles(n, n, bn);
+    tile += P.tile_count;
+    P.s = g.s;
+    P.beta = g.beta;
+    P.gamma = g.gamma;
+    P.C = g.C;
+    P.ldc = static_cast<int>(ctx->ld);
+    P.D32 = g.want32 ? g.D->m32 : nullptr;
+    P.ldd32 = static_cast<int>(ctx->ld);
+    P.Dhi = g.D->hi;
+    P.Dlo = g.D->lo;
+    P.ldd16 = static_cast<int>(ctx->ld);
+    if (g.frob_dst != nullptr) {
+      if (poff + static_cast<size_t>(P.tile_count) * 4 > ctx->partials_cap)
+        return fail(ctx, NS_ERR_ARG, "partials workspace too small");
+      P.frob_partials = ctx->partials + poff;
+      reduces.emplace_back(g.frob_dst, P.tile_count * 4);
+      poff += static_cast<size_t>(P.tile_count) * 4;
+    }
+    if (ctx->st) {
+      const double f = 2.0 * n * static_cast<double>(n) * n * p.npass;
+      ctx->st->gemm_flops += f;
+      ctx->st->tc_gemm_flops += f;
+    }
+  }
+  p.total_tiles = tile;
+  EventPair* e = ev_begin(ctx, true);
+  NS_CK(launch_gemm_tc(p, bn, ctx->num_sms, ctx->stream));
+  ev_end(ctx, e);
+  ctx->launches++;
+  if (ctx->st) {
+    ctx->st->gemm_launches++;
+    ctx->st->tc_gemm_launches++;
+  }
+  size_t off = 0;
+  for (auto& r : reduces) {
+    NS_CK(launch_reduce_sum(ctx->partials + off, r.second, 1, r.first, ctx->stream));
+    off += r.second;
+    ctx->launches++;
+  }
+  return NS_OK;
+}
+
+ns_status f64_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const double* C, double beta,
+                   double gamma, double* D, double* frob_dst) {
+  const int n = static_cast<int>(ctx->n);
+  F64Gemm g;
+  g.M = g.N = g.K = n;
+  g.L = L;
+  g.ldl = static_cast<int>(ctx->ld);
+  g.R = R;
+  g.ldr = static_cast<int>(ctx->ld);
+  g.s = s;
+  g.C = C;
+  g.ldc = static_cast<int>(ctx->ld);
+  g.beta = beta;
+  g.gamma = gamma;
+  g.D = D;
+  g.ldd = static_cast<int>(ctx->ld);
+  g.frob_partials = frob_dst ? ctx->partials : nullptr;
+  EventPair* e = ev_begin(ctx, false);
+  NS_CK(launch_gemm_f64(g, ctx->stream));
+  ev_end(ctx, e);
+  ctx->launches++;
+  if (ctx->st) {
+    ctx->st->gemm_launches++;
+    ctx->st->gemm_flops += 2.0 * n * static_cast<double>(n) * n;
+  }
+  if (frob_dst) {
+    NS_CK(launch_reduce_sum(ctx->partials, f64_tiles(n, n), 1, frob_dst, ctx->stream));
+    ctx->launches++;
+  }
+  return NS_OK;
+}
+
+// Read the scalar block back (one small D2H copy + stream sync) and check the
+// device error word.
+ns_status sync_scalars(ns_ctx* ctx, int nrhs) {
+  const size_t bytes = (8 + 2 * static_cast<size_t>(ctx->scal_cap)) * sizeof(double);
+  NS_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  NS_CK(cudaStreamSynchronize(ctx->stream));
+  (void)nrhs;
+  int derr = 0;
+  memcpy(&derr, &ctx->hscal[3], sizeof(int));
+  if (derr != DEV_OK) {
+    cudaMemsetAsync(ctx->derr, 0, sizeof(double), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, NS_ERR_TIMEOUT, "a bounded device-side wait ran out (tcgen05 GEMM)");
+  }
+  return NS_OK;
+}
+
+// ---------------------------------------------------------------- mixed-precision steps
+// F = I - A G (right residual, the first product of every step), with ||F||_F^2.
+ns_status mp_residual_F(ns_ctx* ctx, const MpMat& Gm, int prec, bool want32) {
+  GemmSpec g{&ctx->A, &Gm, -1.f, nullptr, 0.f, 1.f, &ctx->F, want32, ctx->dscal + 2};
+  return mp_gemm(ctx, &g, 1, prec);
+}
+
+// Remaining products of one NS step of G = Gin (F already formed): result in Gout.
+// Order 2^m: X_{j+1} = X_j + X_j P_j, P_{j+1} = P_j P_j (or I - A X_{j+1}).
+// Order 3: W = F + F F, G' = G + G W.  Horner (form = 1): X = G + X F, n - 1 times.
+ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int prec) {
+  if (ctx->opt.form == 1) {
+    const MpMat* Xc = &Gin;
+    for (int j = 0; j < order - 1; ++j) {
+      MpMat* out = (j == order - 2) ? &Gout : &ctx->X[j & 1];
+      GemmSpec g{Xc, &ctx->F, 1.f, Gin.m32, 1.f, 0.f, out, true, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, prec));
+      Xc = out;
+    }
+    return NS_OK;
+  }
+  if (order == 3) {
+    GemmSpec w{&ctx->F, &ctx->F, 1.f, ctx->F.m32, 1.f, 0.f, &ctx->P[0], false, nullptr};
+    NS_TRY(mp_gemm(ctx, &w, 1, prec));
+    GemmSpec g{&Gin, &ctx->P[0], 1.f, Gin.m32, 1.f, 0.f, &Gout, true, nullptr};
+    return mp_gemm(ctx, &g, 1, prec);
+  }
+  int levels = 0;
+  while ((1 << levels) < order) ++levels;
+  const MpMat* Xc = &Gin;
+  const MpMat* Pc = &ctx->F;
+  for (int j = 0; j < levels; ++j) {
+    const bool last = j == levels - 1;
+    MpMat* xo = last ? &Gout : &ctx->X[j & 1];
+    MpMat* po = &ctx->P[j & 1];
+    GemmSpec gx{Xc, Pc, 1.f, Xc->m32, 1.f, 0.f, xo, true, nullptr};
+    if (last) {
+      NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+    } else if (ctx->opt.pow_mode == 0) {
+      GemmSpec two[2] = {gx, GemmSpec{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr}};
+      NS_TRY(mp_gemm(ctx, two, 2, prec));
+    } else {
+      NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+      GemmSpec gp{&ctx->A, xo, -1.f, nullptr, 0.f, 1.f, po, false, nullptr};
+      NS_TRY(mp_gemm(ctx, &gp, 1, prec));
+    }
+    Xc = xo;
+    Pc = po;
+  }
+  return NS_OK;
+}
+
+// ---------------------------------------------------------------- fp64 steps
+ns_status f64_chain(ns_ctx* ctx, const double* Gin, double* Gout, int order) {
+  const int n = static_cast<int>(ctx->n);
+  (void)n;
+  if (ctx->opt.form == 1) {
+    const double* Xc = Gin;
+    for (int j = 0; j < order - 1; ++j) {
+      double* out = (j == order - 2) ? Gout : ctx->X64[j & 1];
+      NS_TRY(f64_gemm(ctx, Xc, ctx->F64, 1.0, Gin, 1.0, 0.0, out, nullptr));
+      Xc = out;
+    }
+    return NS_OK;
+  }
+  if (order == 3) {
+    NS_TRY(f64_gemm(ctx, ctx->F64, ctx->F64, 1.0, ctx->F64, 1.0, 0.0, ctx->P64[0], nullptr));
+    return f64_gemm(ctx, Gin, ctx->P64[0], 1.0, Gin, 1.0, 0.0, Gout, nullptr);
+  }
+  int levels = 0;
+  while ((1 << levels) < order) ++levels;
+  const double* Xc = Gin;
+  const double* Pc = ctx->F64;
+  for (int j = 0; j < levels; ++j) {
+    const bool last = j == levels - 1;
+    double* xo = last ? Gout : ctx->X64[j & 1];
+    double* po = ctx->P64[j & 1];
+    NS_TRY(f64_gemm(ctx, Xc, Pc, 1.0, Xc, 1.0, 0.0, xo, nullptr));
+    if (!last) {
+      if (ctx->opt.pow_mode == 0)
+        NS_TRY(f64_gemm(ctx, Pc, Pc, 1.0, nullptr, 0.0, 0.0, po, nullptr));
+      else
+        NS_TRY(f64_gemm(ctx, ctx->Astage, xo, -1.0, nullptr, 0.0, 1.0, po, nullptr));
+    }
+    Xc = xo;
+    Pc = po;
+  }
+  return NS_OK;
+}
+
+bool order_ok(int order, int form) {
+  if (order < 2) return false;
+  if (form == 1) return true;
+  if (order == 3) return true;
+  return (order & (order - 1)) == 0;
+}
+
+// Everything one solve needs, shared by ns_invert and ns_richardson_solve.
+struct Solve {
+  const double* A = nullptr;  // device, lda = ld_a
+  int64_t lda = 0;
+  const double* B = nullptr;  // device n x nrhs or null (invert only)
+  double* Th = nullptr;       // device n x nrhs
+  int nrhs = 0;
+  bool fp64 = false;
+  int prec = NS_BF16X3;
+  int cur = 0;  // G buffer holding G_k
+  int ccur = 0; // composite buffers holding T_i
+};
+
+ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bool richardson, ns_stats* st) {
+  const int n = static_cast<int>(ctx->n);
+  const int64_t ld = ctx->ld;
+  cudaStream_t s = ctx->stream;
+  const bool fp64 = S.fp64;
+  const bool comp = !ctx->rates.empty();
+  const double sqrt_n = std::sqrt(static_cast<double>(n));
+  double* ss = ctx->dscal + 0;
+  double* rsq = ctx->dscal + 8;
+  double* bsq = ctx->dscal + 8 + ctx->scal_cap;
+
+  // ---- prep: norms of A, operand splits, G0, ||B_c||
+  int nb = 0;
+  NS_CK(launch_matnorms(S.A, S.lda, n, ctx->partials, ctx->partials + ((n + 7) / 8) + 1, &nb, s));
+  NS_CK(launch_reduce_sum(ctx->partials, nb, 1, ss, s));
+  NS_CK(launch_reduce_max(ctx->partials + nb + 1, nb, ctx->dscal + 1, s));
+  ctx->launches += 3;
+  if (fp64) {
+    // the fp64 products read A with leading dimension ld: copy if needed
+    if (S.A != ctx->Astage || S.lda != ld) {
+      if (ctx->Astage == nullptr) NS_TRY(alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ld));
+      NS_CK(launch_copy_f64(S.A, S.lda, n, n, ctx->Astage, ld, s));
+      ctx->launches++;
+    }
+    if (G0)
+      NS_CK(launch_copy_f64(G0, n, n, n, ctx->G64[0], ld, s));
+    else
+      NS_CK(launch_init_g0_f64(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G64[0], s));
+    ctx->launches++;
+  } else {
+    NS_CK(launch_split_f64(S.A, S.lda, n, n, ctx->A.hi, ctx->A.lo, nullptr, ld, s));
+    if (G0)
+      NS_CK(launch_split_f64(G0, n, n, n, ctx->G[0].hi, ctx->G[0].lo, ctx->G[0].m32, ld, s));
+    else
+      NS_CK(launch_init_g0_mp(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G[0].m32, ctx->G[0].hi, ctx->G[0].lo, s));
+    ctx->launches += 2;
+  }
+  if (richardson) {
+    NS_CK(launch_colsumsq(S.B, S.nrhs, n, S.nrhs, bsq, nullptr, s));
+    ctx->launches++;
+  }
+  S.cur = 0;
+
+  // composite: auxiliary expansions T_i start at G0 (or one NS step ahead)
+  if (comp) {
+    const size_t w = ctx->rates.size();
+    for (size_t i = 0; i < w; ++i) {
+      if (fp64) {
+        NS_CK(cudaMemcpyAsync(ctx->T64[0][i], ctx->G64[0], sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, s));
+      } else {
+        MpMat& t = ctx->T[0][i];
+        NS_CK(cudaMemcpyAsync(t.m32, ctx->G[0].m32, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(t.hi, ctx->G[0].hi, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(t.lo, ctx->G[0].lo, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    S.ccur = 0;
+  }
+
+  const bool autop = !fp64 && ctx->opt.precision == NS_AUTO;
+  int prec = fp64 ? NS_FP64 : (autop ? NS_BF16 : ctx->opt.precision);
+  int done = 0;
+  int sweeps_left = ctx->opt.max_sweeps;
+  bool ns_active = iters > 0;
+  double prev_frob = INFINITY;
+  bool converged = false;
+  int aux_steps = 0;
+
+  // advance every auxiliary expansion T_i by one NS step of its own order m_i
+  auto composite_aux_step = [&](int p) -> ns_status {
+    const size_t w = ctx->rates.size();
+    const int nc = S.ccur ^ 1;
+    for (size_t i = 0; i < w; ++i) {
+      const int m = ctx->rates[i];
+      if (fp64) {
+        if (m == 1) {
+          NS_CK(cudaMemcpyAsync(ctx->T64[nc][i], ctx->T64[S.ccur][i], sizeof(double) * n * ld,
+                                cudaMemcpyDeviceToDevice, s));
+          continue;
+        }
+        NS_TRY(f64_gemm(ctx, ctx->Astage, ctx->T64[S.ccur][i], -1.0, nullptr, 0.0, 1.0, ctx->F64, nullptr));
+        NS_TRY(f64_chain(ctx, ctx->T64[S.ccur][i], ctx->T64[nc][i], m));
+      } else {
+        MpMat& tin = ctx->T[S.ccur][i];
+        MpMat& tout = ctx->T[nc][i];
+        if (m == 1) {
+          NS_CK(cudaMemcpyAsync(tout.m32, tin.m32, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
+          NS_CK(cudaMemcpyAsync(tout.hi, tin.hi, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+          NS_CK(cudaMemcpyAsync(tout.lo, tin.lo, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+          continue;
+        }
+        NS_TRY(mp_residual_F(ctx, tin, p, m == 3));
+        NS_TRY(mp_chain(ctx, tin, tout, m, p));
+      }
+    }
+    S.ccur = nc;
+    return NS_OK;
+  };
+  if (comp && ctx->opt.aux_ahead) {
+    NS_TRY(composite_aux_step(prec));
+    aux_steps++;
+  }
+
+  // G_{k+1} = T_c + Gamma_c X with X the NS step of G_k (eq. gkgen1); the
+  // plain NS product chain when there are no rates.
+  auto ns_update = [&](int p) -> ns_status {
+    const int nx = S.cur ^ 1;
+    if (!comp) {
+      if (fp64) return f64_chain(ctx, ctx->G64[S.cur], ctx->G64[nx], ctx->order);
+      return mp_chain(ctx, ctx->G[S.cur], ctx->G[nx], ctx->order, p);
+    }
+    // the main chain consumes the F of G_k, so it runs before the auxiliary
+    // loops reuse the F workspace
+    if (fp64)
+      NS_TRY(f64_chain(ctx, ctx->G64[S.cur], ctx->Xs64[0], ctx->order));
+    else
+      NS_TRY(mp_chain(ctx, ctx->G[S.cur], ctx->Xs[0], ctx->order, p));
+    NS_TRY(composite_aux_step(p));
+    const size_t w = ctx->rates.size();
+    const int cc = S.ccur;
+    if (fp64) {
+      // Gamma_1 = I - T_1 A ; T_c = T_1 ; prefix = Gamma_1
+      NS_TRY(f64_gemm(ctx, ctx->T64[cc][0], ctx->Astage, -1.0, nullptr, 0.0, 1.0, ctx->Pre64[0], nullptr));
+      const double* Tcur = ctx->T64[cc][0];
+      int pb = 0, tb = 0;
+      for (size_t i = 1; i < w; ++i) {
+        NS_TRY(f64_gemm(ctx, ctx->Pre64[pb], ctx->T64[cc][i], 1.0, Tcur, 1.0, 0.0, ctx->Tc64[tb], nullptr));
+        Tcur = ctx->Tc64[tb];
+        tb ^= 1;
+        NS_TRY(f64_gemm(ctx, ctx->T64[cc][i], ctx->Astage, -1.0, nullptr, 0.0, 1.0, ctx->Gam64, nullptr));
+        NS_TRY(f64_gemm(ctx, ctx->Pre64[pb], ctx->Gam64, 1.0, nullptr, 0.0, 0.0, ctx->Pre64[pb ^ 1], nullptr));
+        pb ^= 1;
+      }
+      return f64_gemm(ctx, ctx->Pre64[pb], ctx->Xs64[0], 1.0, Tcur, 1.0, 0.0, ctx->G64[nx], nullptr);
+    }
+    {
+      GemmSpec g{&ctx->T[cc][0], &ctx->A, -1.f, nullptr, 0.f, 1.f, &ctx->Pre[0], false, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, p));
+    }
+    const MpMat* Tcur = &ctx->T[cc][0];
+    int pb = 0, tb = 0;
+    for (size_t i = 1; i < w; ++i) {
+      GemmSpec a{&ctx->Pre[pb], &ctx->T[cc][i], 1.f, Tcur->m32, 1.f, 0.f, &ctx->Tc[tb], true, nullptr};
+      GemmSpec gm{&ctx->T[cc][i], &ctx->A, -1.f, nullptr, 0.f, 1.f, &ctx->Gam, false, nullptr};
+      NS_TRY(mp_gemm(ctx, &a, 1, p));
+      NS_TRY(mp_gemm(ctx, &gm, 1, p));
+      GemmSpec pr{&ctx->Pre[pb], &ctx->Gam, 1.f, nullptr, 0.f, 0.f, &ctx->Pre[pb ^ 1], false, nullptr};
+      NS_TRY(mp_gemm(ctx, &pr, 1, p));
+      Tcur = &ctx->Tc[tb];
+      tb ^= 1;
+      pb ^= 1;
+    }
+    GemmSpec g{&ctx->Pre[pb], &ctx->Xs[0], 1.f, Tcur->m32, 1.f, 0.f, &ctx->G[nx], true, nullptr};
+    return mp_gemm(ctx, &g, 1, p);
+  };
+
+  auto push_frob = [&](double f, int p) {
+    if (st && st->n_frob < NS_MAX_HIST) {
+      st->frob_F[st->n_frob] = f;
+      st->prec_hist[st->n_frob] = p;
+      st->n_frob++;
+    }
+  };
+
+  for (;;) {
+    if (richardson) {
+      NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
+      NS_CK(launch_reduce_sum(ctx->partials, nb, S.nrhs, rsq, s));
+      ctx->launches += 2 + (S.nrhs + 7) / 8;
+    }
+    double frob = 0.0;
+  recompute_F:
+    if (ns_active) {
+      if (fp64)
+        NS_TRY(f64_gemm(ctx, ctx->Astage, ctx->G64[S.cur], -1.0, nullptr, 0.0, 1.0, ctx->F64, ctx->dscal + 2));
+      else
+        NS_TRY(mp_residual_F(ctx, ctx->G[S.cur], prec, ctx->order == 3 || ctx->opt.form == 1));
+    }
+    NS_TRY(sync_scalars(ctx, S.nrhs));
+    if (richardson) {
+      double rr = 0.0;
+      for (int c = 0; c < S.nrhs; ++c) {
+        const double b = ctx->hscal[8 + ctx->scal_cap + c];
+        const double r = ctx->hscal[8 + c];
+        const double q = b > 0 ? std::sqrt(r / b) : std::sqrt(r);
+        rr = std::max(rr, std::isnan(q) ? INFINITY : q);
+      }
+      if (st) {
+        st->rel_res = rr;
+        if (st->n_res < NS_MAX_HIST) st->rel_res_hist[st->n_res++] = rr;
+      }
+      if (!std::isfinite(rr)) return fail(ctx, NS_ERR_NONFINITE, "residual norm is not finite");
+      if (tol > 0 && rr <= tol) {
+        converged = true;
+        break;
+      }
+    }
+    if (ns_active) {
+      frob = std::sqrt(ctx->hscal[2]);
+      push_frob(frob, prec);
+      if (!std::isfinite(frob)) return fail(ctx, NS_ERR_NONFINITE, "||F||_F is not finite");
+      if (autop && prec == NS_BF16 && done > 0 && frob >= prev_frob) {
+        // bf16 rounding has stopped the contraction: redo the last step in bf16x3
+        S.cur ^= 1;
+        if (comp) S.ccur ^= 1;
+        done--;
+        prec = NS_BF16X3;
+        prev_frob = INFINITY;
+        if (st) st->rollbacks++;
+        goto recompute_F;
+      }
+      if (frob > 2.0 * sqrt_n + 1.0 && frob > 2.0 * prev_frob)
+        return fail(ctx, NS_ERR_DIVERGED, "Newton-Schulz diverged (||F||_F grew past sqrt(n))");
+      if (ctx->opt.ns_stop && (!autop || prec != NS_BF16)) {
+        bool stop = frob <= ctx->opt.ns_stop_frob;
+        if (!stop && prev_frob < 1.0 && frob >= 0.5 * prev_frob) {
+          stop = true;  // quadratic contraction has stalled at the precision floor
+          if (frob > prev_frob) {
+            S.cur ^= 1;  // keep the better previous estimate
+            if (comp) S.ccur ^= 1;
+          }
+        }
+        if (stop) ns_active = false;
+      }
+    }
+    if (ns_active) {
+      const int g_used = S.cur;
+      NS_TRY(ns_update(prec));
+      const int g_next = S.cur ^ 1;
+      if (richardson) {
+        const int gi = ctx->opt.use_updated_G ? g_next : g_used;
+        if (fp64)
+          NS_CK(launch_update_f64(ctx->G64[gi], ld, ctx->Rd, S.Th, n, S.nrhs, s));
+        else
+          NS_CK(launch_update_f32(ctx->G[gi].m32, ld, ctx->Rd, S.Th, n, S.nrhs, s));
+        ctx->launches += (S.nrhs + 7) / 8;
+        if (st) st->sweeps++;
+      }
+      S.cur = g_next;
+      prev_frob = frob;
+      done++;
+      if (st) st->ns_iters = done;
+      if (done >= iters) ns_active = false;
+      continue;
+    }
+    if (!richardson || sweeps_left <= 0) break;
+    if (fp64)
+      NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, s));
+    else
+      NS_CK(launch_update_f32(ctx->G[S.cur].m32, ld, ctx->Rd, S.Th, n, S.nrhs, s));
+    ctx->launches += (S.nrhs + 7) / 8;
+    sweeps_left--;
+    if (st) st->sweeps++;
+  }
+  (void)aux_steps;
+  if (richardson) return converged || tol <= 0 ? NS_OK : NS_NOT_CONVERGED;
+  return NS_OK;
+}
+
+ns_status begin_call(ns_ctx* ctx, ns_stats* st) {
+  if (!ctx) return NS_ERR_ARG;
+  ctx->err.clear();
+  ctx->st = st;
+  ctx->launches = 0;
+  if (st) {
+    memset(st, 0, sizeof(*st));
+  }
+  NS_CK(cudaSetDevice(ctx->device));
+  return NS_OK;
+}
+
+ns_status end_call(ns_ctx* ctx, ns_status r, std::chrono::steady_clock::time_point t0) {
+  cudaStreamSynchronize(ctx->stream);
+  ev_collect(ctx);
+  if (ctx->st) {
+    ctx->st->status = r;
+    ctx->st->kernel_launches = ctx->launches;
+    ctx->st->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  ctx->st = nullptr;
+  return r;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void ns_default_options(ns_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = NS_AUTO;
+  o->form = 0;
+  o->pow_mode = 0;
+  o->g0_mode = 0;
+  o->ns_stop = 1;
+  o->ns_stop_frob = 0.02;
+  o->max_sweeps = 200;
+  o->use_updated_G = 0;
+  o->profile = 0;
+  o->gemm_bn = 0;
+  o->timeout_s = 2.0;
+  o->aux_ahead = 0;
+}
+
+const char* ns_status_string(ns_status s) {
+  switch (s) {
+    case NS_OK: return "NS_OK";
+    case NS_NOT_CONVERGED: return "NS_NOT_CONVERGED";
+    case NS_ERR_ARG: return "NS_ERR_ARG";
+    case NS_ERR_CUDA: return "NS_ERR_CUDA";
+    case NS_ERR_OOM: return "NS_ERR_OOM";
+    case NS_ERR_DIVERGED: return "NS_ERR_DIVERGED";
+    case NS_ERR_TIMEOUT: return "NS_ERR_TIMEOUT";
+    case NS_ERR_NONFINITE: return "NS_ERR_NONFINITE";
+    case NS_ERR_UNSUPPORTED: return "NS_ERR_UNSUPPORTED";
+  }
+  return "unknown";
+}
+
+ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const ns_options* opt, ns_ctx** out) {
+  if (!out || n <= 0 || n > (1 << 20) || n_rates < 0 || (n_rates > 0 && !rates)) return NS_ERR_ARG;
+  ns_options o;
+  if (opt)
+    o = *opt;
+  else
+    ns_default_options(&o);
+  if (!order_ok(order, o.form)) return NS_ERR_ARG;
+  if (o.precision != NS_FP64 && o.precision != NS_BF16 && o.precision != NS_BF16X3 && o.precision != NS_AUTO)
+    return NS_ERR_ARG;
+  if (o.timeout_s <= 0) o.timeout_s = 2.0;
+  for (int i = 0; i < n_rates; ++i)
+    if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
+  ns_ctx* c = new ns_ctx();
+  c->n = n;
+  c->ld = round_up(n, 64);
+  c->order = order;
+  c->rates.assign(rates, rates + n_rates);
+  c->opt = o;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return NS_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  *out = c;
+  return NS_OK;
+}
+
+ns_status ns_destroy(ns_ctx* ctx) {
+  if (!ctx) return NS_OK;
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->hscal) cudaFreeHost(ctx->hscal);
+  for (auto& e : ctx->ev_pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete ctx;
+  return NS_OK;
+}
+
+ns_status ns_set_stream(ns_ctx* ctx, void* stream) {
+  if (!ctx) return NS_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return NS_OK;
+}
+
+const char* ns_last_error(const ns_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+static ns_status stage_in(ns_ctx* ctx, const double* src, double* dst, size_t count) {
+  NS_CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  return NS_OK;
+}
+
+ns_status ns_invert(ns_ctx* ctx, const double* A, const double* G0, int iters, double* G_out, ns_stats* st) {
+  auto t0 = std::chrono::steady_clock::now();
+  NS_TRY(begin_call(ctx, st));
+  if (!A || iters < 0) return end_call(ctx, fail(ctx, NS_ERR_ARG, "null A or negative iters"), t0);
+  const int n = static_cast<int>(ctx->n);
+  const bool fp64 = ctx->opt.precision == NS_FP64;
+  ns_status r = ensure_common(ctx, 1);
+  if (r == NS_OK) r = fp64 ? ensure_f64(ctx) : ensure_mp(ctx);
+  if (r == NS_OK) r = ensure_composite(ctx, fp64);
+  if (r == NS_OK && !is_device_ptr(A)) {
+    if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
+    if (r == NS_OK) {
+      cudaError_t e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double),
+                                        n * sizeof(double), n, cudaMemcpyDefault, ctx->stream);
+      if (e != cudaSuccess) r = fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    A = ctx->Astage;
+  }
+  const double* G0d = G0;
+  if (r == NS_OK && G0 && !is_device_ptr(G0)) {
+    double* tmp = ctx->X64[0];
+    if (!fp64 || !tmp) {
+      r = ensure_f64(ctx);
+      tmp = ctx->X64[0];
+    }
+    if (r == NS_OK) r = stage_in(ctx, G0, tmp, static_cast<size_t>(n) * n);
+    G0d = tmp;
+  }
+  if (r != NS_OK) return end_call(ctx, r, t0);
+  Solve S;
+  S.A = A;
+  S.lda = (A == ctx->Astage) ? ctx->ld : n;
+  S.fp64 = fp64;
+  r = run(ctx, S, G0d, iters, 0.0, false, st);
+  if (r >= 0 && G_out) {
+    const bool dev = is_device_ptr(G_out);
+    cudaError_t e = cudaSuccess;
+    if (fp64) {
+      if (dev)
+        e = launch_copy_f64(ctx->G64[S.cur], ctx->ld, n, n, G_out, n, ctx->stream);
+      else
+        e = cudaMemcpy2DAsync(G_out, n * sizeof(double), ctx->G64[S.cur], ctx->ld * sizeof(double),
+                              n * sizeof(double), n, cudaMemcpyDeviceToHost, ctx->stream);
+    } else {
+      double* tgt = G_out;
+      if (!dev) {
+        if (ctx->Astage == nullptr) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
+        tgt = ctx->Astage;  // A is no longer needed
+      }
+      if (r == NS_OK) e = launch_f32_to_f64(ctx->G[S.cur].m32, ctx->ld, n, n, tgt, n, ctx->stream);
+      if (r == NS_OK && e == cudaSuccess && !dev)
+        e = cudaMemcpyAsync(G_out, tgt, sizeof(double) * n * n, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e != cudaSuccess) r = fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return end_call(ctx, r, t0);
+}
+
+ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int nrhs, const double* Theta0,
+                              int iters, double tol, double* Theta_out, ns_stats* st) {
+  auto t0 = std::chrono::steady_clock::now();
+  NS_TRY(begin_call(ctx, st));
+  if (!A || !B || !Theta_out || nrhs <= 0 || iters < 0)
+    return end_call(ctx, fail(ctx, NS_ERR_ARG, "null pointer, nrhs <= 0 or iters < 0"), t0);
+  const int n = static_cast<int>(ctx->n);
+  const bool fp64 = ctx->opt.precision == NS_FP64;
+  ns_status r = ensure_common(ctx, nrhs);
+  if (r == NS_OK) r = fp64 ? ensure_f64(ctx) : ensure_mp(ctx);
+  if (r == NS_OK) r = ensure_composite(ctx, fp64);
+  if (r != NS_OK) return end_call(ctx, r, t0);
+  const size_t nb = static_cast<size_t>(n) * nrhs;
+  cudaError_t e = cudaSuccess;
+  if (!is_device_ptr(A)) {
+    if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
+    if (r != NS_OK) return end_call(ctx, r, t0);
+    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyDefault, ctx->stream);
+    A = ctx->Astage;
+  }
+  const double* Bd = B;
+  if (e == cudaSuccess && !is_device_ptr(B)) {
+    e = cudaMemcpyAsync(ctx->Bd, B, nb * sizeof(double), cudaMemcpyDefault, ctx->stream);
+    Bd = ctx->Bd;
+  }
+  const bool out_dev = is_device_ptr(Theta_out);
+  double* Th = out_dev ? Theta_out : ctx->Thd;
+  if (e == cudaSuccess) {
+    if (Theta0)
+      e = (Theta0 == Th) ? cudaSuccess
+                         : cudaMemcpyAsync(Th, Theta0, nb * sizeof(double), cudaMemcpyDefault, ctx->stream);
+    else
+      e = cudaMemsetAsync(Th, 0, nb * sizeof(double), ctx->stream);
+  }
+  if (e != cudaSuccess) return end_call(ctx, fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e)), t0);
+  Solve S;
+  S.A = A;
+  S.lda = (A == ctx->Astage) ? ctx->ld : n;
+  S.B = Bd;
+  S.Th = Th;
+  S.nrhs = nrhs;
+  S.fp64 = fp64;
+  r = run(ctx, S, nullptr, iters, tol, true, st);
+  if (r >= 0 && !out_dev) {
+    e = cudaMemcpyAsync(Theta_out, Th, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) r = fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return end_call(ctx, r, t0);
+}
+
+ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const double* B, int nrhs,
+                      double* rel_res_out) {
+  auto t0 = std::chrono::steady_clock::now();
+  NS_TRY(begin_call(ctx, nullptr));
+  if (!A || !Theta || !B || !rel_res_out || nrhs <= 0) return end_call(ctx, fail(ctx, NS_ERR_ARG, "bad argument"), t0);
+  const int n = static_cast<int>(ctx->n);
+  ns_status r = ensure_common(ctx, nrhs);
+  if (r != NS_OK) return end_call(ctx, r, t0);
+  const size_t nb = static_cast<size_t>(n) * nrhs;
+  cudaError_t e = cudaSuccess;
+  int64_t lda = n;
+  if (!is_device_ptr(A)) {
+    if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
+    if (r != NS_OK) return end_call(ctx, r, t0);
+    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyDefault, ctx->stream);
+    A = ctx->Astage;
+    lda = ctx->ld;
+  }
+  if (e == cudaSuccess && !is_device_ptr(B)) {
+    e = cudaMemcpyAsync(ctx->Bd, B, nb * sizeof(double), cudaMemcpyDefault, ctx->stream);
+    B = ctx->Bd;
+  }
+  if (e == cudaSuccess && !is_device_ptr(Theta)) {
+    e = cudaMemcpyAsync(ctx->Thd, Theta, nb * sizeof(double), cudaMemcpyDefault, ctx->stream);
+    Theta = ctx->Thd;
+  }
+  if (e != cudaSuccess) return end_call(ctx, fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e)), t0);
+  int nblk = 0;
+  double* rsq = ctx->dscal + 8;
+  double* bsq = ctx->dscal + 8 + ctx->scal_cap;
+  e = launch_resid(A, lda, Theta, B, ctx->Rd, n, nrhs, ctx->partials, &nblk, ctx->stream);
+  if (e == cudaSuccess) e = launch_reduce_sum(ctx->partials, nblk, nrhs, rsq, ctx->stream);
+  if (e == cudaSuccess) e = launch_colsumsq(B, nrhs, n, nrhs, bsq, nullptr, ctx->stream);
+  if (e != cudaSuccess) return end_call(ctx, fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e)), t0);
+  r = sync_scalars(ctx, nrhs);
+  if (r == NS_OK) {
+    for (int c = 0; c < nrhs; ++c) {
+      const double b = ctx->hscal[8 + ctx->scal_cap + c];
+      const double q = ctx->hscal[8 + c];
+      rel_res_out[c] = b > 0 ? std::sqrt(q / b) : std::sqrt(q);
+    }
+  }
+  return end_call(ctx, r, t0);
+}
+
+// ---------------------------------------------------------------- single kernels
+static bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo,
+                     int64_t ld, void* stream) {
+  if (!X || !hi || !lo || rows < 0 || cols < 0 || ldx < cols || ld < cols || (x_dtype != 0 && x_dtype != 1))
+    return NS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = x_dtype == 0 ? launch_split_f64(static_cast<const double*>(X), ldx, static_cast<int>(rows),
+                                                  static_cast<int>(cols), static_cast<bf16*>(hi),
+                                                  static_cast<bf16*>(lo), nullptr, ld, s)
+                               : launch_split_f32(static_cast<const float*>(X), ldx, static_cast<int>(rows),
+                                                  static_cast<int>(cols), static_cast<bf16*>(hi),
+                                                  static_cast<bf16*>(lo), ld, s);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
+                         int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
+                         int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
+                         int64_t ldd16, double* frob_out, int bn, void* stream) {
+  if (precision != NS_BF16 && precision != NS_BF16X3) return NS_ERR_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
+  if (!Lhi || !Rhi || (precision == NS_BF16X3 && (!Llo || !Rlo))) return NS_ERR_ARG;
+  if (ldl < K || ldr < N || ldl % 8 || ldr % 8 || !al16(Lhi) || !al16(Rhi)) return NS_ERR_ARG;
+  if (precision == NS_BF16X3 && (!al16(Llo) || !al16(Rlo))) return NS_ERR_ARG;
+  if (C && (ldc < N || ldc % 4 || !al16(C))) return NS_ERR_ARG;
+  if (D32 && (ldd32 < N || ldd32 % 4 || !al16(D32))) return NS_ERR_ARG;
+  if ((Dhi || Dlo) && (ldd16 < N || ldd16 % 8)) return NS_ERR_ARG;
+  if ((Dhi && !al16(Dhi)) || (Dlo && !al16(Dlo)) || (Dlo && !Dhi)) return NS_ERR_ARG;
+  if (bn == 0) bn = N >= 2048 ? 256 : (N > 64 ? 128 : 64);
+  if (bn != 64 && bn != 128 && bn != 256) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TcParams p;
+  memset(&p, 0, sizeof(p));
+  p.nprob = 1;
+  p.npass = precision == NS_BF16X3 ? 3 : 1;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = 2000000000ull;
+  TcProblem& P = p.prob[0];
+  if (!encode_bf16_map(&P.L[0], Lhi, M, K, ldl) || !encode_bf16_map(&P.R[0], Rhi, K, N, ldr)) return NS_ERR_ARG;
+  if (p.npass == 3 && (!encode_bf16_map(&P.L[1], Llo, M, K, ldl) || !encode_bf16_map(&P.R[1], Rlo, K, N, ldr)))
+    return NS_ERR_ARG;
+  if (p.npass == 1) {
+    P.L[1] = P.L[0];
+    P.R[1] = P.R[0];
+  }
+  P.M = static_cast<int>(M);
+  P.N = static_cast<int>(N);
+  P.K = static_cast<int>(K);
+  P.tiles_n = static_cast<int>((N + bn - 1) / bn);
+  P.tile_begin = 0;
+  P.tile_count = tc_tiles(P.M, P.N, bn);
+  P.s = s;
+  P.beta = beta;
+  P.gamma = gamma;
+  P.C = C;
+  P.ldc = static_cast<int>(ldc);
+  P.D32 = D32;
+  P.ldd32 = static_cast<int>(ldd32);
+  P.Dhi = static_cast<bf16*>(Dhi);
+  P.Dlo = static_cast<bf16*>(Dlo);
+  P.ldd16 = static_cast<int>(ldd16);
+  p.total_tiles = P.tile_count;
+  void* scratch = nullptr;
+  const size_t scratch_bytes = sizeof(int) * 4 + (frob_out ? sizeof(double) * P.tile_count * 4 : 0);
+  if (cudaMallocAsync(&scratch, scratch_bytes + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  cudaMemsetAsync(scratch, 0, sizeof(int) * 4, st);
+  p.err = static_cast<int*>(scratch);
+  if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
+  cudaError_t e = launch_gemm_tc(p, bn, sms, st);
+  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, P.tile_count * 4, 1, frob_out, st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NS_ERR_CUDA;
+  return herr == DEV_OK ? NS_OK : NS_ERR_TIMEOUT;
+}
+
+ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,
+                        int64_t ldr, double s, const double* C, int64_t ldc, double beta, double gamma, double* D,
+                        int64_t ldd, double* frob_out, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !L || !R || !D || ldl < K || ldr < N || ldd < N || (C && ldc < N))
+    return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  F64Gemm g;
+  g.M = static_cast<int>(M);
+  g.N = static_cast<int>(N);
+  g.K = static_cast<int>(K);
+  g.L = L;
+  g.ldl = static_cast<int>(ldl);
+  g.R = R;
+  g.ldr = static_cast<int>(ldr);
+  g.s = s;
+  g.C = C;
+  g.ldc = static_cast<int>(ldc);
+  g.beta = beta;
+  g.gamma = gamma;
+  g.D = D;
+  g.ldd = static_cast<int>(ldd);
+  g.frob_partials = nullptr;
+  void* scratch = nullptr;
+  const int tiles = f64_tiles(g.M, g.N);
+  if (frob_out) {
+    if (cudaMallocAsync(&scratch, sizeof(double) * tiles, st) != cudaSuccess) {
+      cudaGetLastError();
+      return NS_ERR_OOM;
+    }
+    g.frob_partials = static_cast<double*>(scratch);
+  }
+  cudaError_t e = launch_gemm_f64(g, st);
+  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(g.frob_partials, tiles, 1, frob_out, st);
+  if (scratch) cudaFreeAsync(scratch, st);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_resid(const double* A, int64_t lda, const double* Theta, const double* B, double* R, int64_t n,
+                     int nrhs, double* rsq_out, void* stream) {
+  if (!A || !Theta || !B || !R || n <= 0 || nrhs <= 0 || lda < n) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = resid_blocks(static_cast<int>(n));
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, sizeof(double) * nb * nrhs, st) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  double* part = static_cast<double*>(scratch);
+  int nbo = 0;
+  cudaError_t e = launch_resid(A, lda, Theta, B, R, static_cast<int>(n), nrhs, part, &nbo, st);
+  if (e == cudaSuccess && rsq_out) e = launch_reduce_sum(part, nbo, nrhs, rsq_out, st);
+  cudaFreeAsync(scratch, st);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_update(const void* G, int g_dtype, int64_t ldg, const double* R, double* Theta, int64_t n, int nrhs,
+                      void* stream) {
+  if (!G || !R || !Theta || n <= 0 || nrhs <= 0 || ldg < n || (g_dtype != 0 && g_dtype != 1)) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g_dtype == 1
+                      ? launch_update_f32(static_cast<const float*>(G), ldg, R, Theta, static_cast<int>(n), nrhs, st)
+                      : launch_update_f64(static_cast<const double*>(G), ldg, R, Theta, static_cast<int>(n), nrhs, st);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+}  // extern "C"

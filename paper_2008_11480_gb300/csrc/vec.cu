@@ -1,0 +1,534 @@
+// Memory-bound kernels around the GEMM chain: the Richardson residual
+// R = B - A Theta (FP64), the update Theta += G R, matrix/column norms,
+// fixed-order (deterministic) reductions, the bf16 hi/lo splits and G0.
+#include "internal.h"
+
+namespace nsgb {
+namespace {
+
+constexpr int kRowsPerWarp = 2;
+constexpr int kWarps = 8;
+constexpr int kRowsPerBlock = kRowsPerWarp * kWarps;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- residual
+// Each warp owns two consecutive rows; lanes stride the row with 16-byte
+// loads (two doubles) when rows are 16-byte aligned.  NR right-hand sides
+// [c0, c0+NR) are handled per launch.
+template <int NR, bool VEC>
+__global__ void __launch_bounds__(256) k_resid(const double* __restrict__ A, int64_t lda,
+                                               const double* __restrict__ Th, const double* __restrict__ B,
+                                               double* __restrict__ R, int n, int nrhs, int c0,
+                                               double* __restrict__ partials) {
+  __shared__ double sq[kWarps][NR];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  double acc[kRowsPerWarp][NR];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[r][c] = 0.0;
+  const bool r0 = row0 < n, r1 = row0 + 1 < n;
+  const double* a0p = A + static_cast<int64_t>(r0 ? row0 : 0) * lda;
+  const double* a1p = A + static_cast<int64_t>(r1 ? row0 + 1 : 0) * lda;
+  int kend = 0;
+  if (VEC) {
+    const int n2 = n & ~1;
+#pragma unroll 4
+    for (int k = 2 * lane; k < n2; k += 64) {
+      const double2 x0 = r0 ? *reinterpret_cast<const double2*>(a0p + k) : make_double2(0.0, 0.0);
+      const double2 x1 = r1 ? *reinterpret_cast<const double2*>(a1p + k) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const double t0 = __ldg(Th + static_cast<int64_t>(k) * nrhs + c0 + c);
+        const double t1 = __ldg(Th + static_cast<int64_t>(k + 1) * nrhs + c0 + c);
+        acc[0][c] = fma(x0.x, t0, acc[0][c]);
+        acc[0][c] = fma(x0.y, t1, acc[0][c]);
+        acc[1][c] = fma(x1.x, t0, acc[1][c]);
+        acc[1][c] = fma(x1.y, t1, acc[1][c]);
+      }
+    }
+    kend = n2;
+  }
+  for (int k = kend + lane; k < n; k += 32) {
+    const double x0 = r0 ? a0p[k] : 0.0;
+    const double x1 = r1 ? a1p[k] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double t = __ldg(Th + static_cast<int64_t>(k) * nrhs + c0 + c);
+      acc[0][c] = fma(x0, t, acc[0][c]);
+      acc[1][c] = fma(x1, t, acc[1][c]);
+    }
+  }
+  double mysq[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) mysq[c] = 0.0;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double s = warp_sum(acc[r][c]);
+      const int row = row0 + r;
+      if (lane == 0 && row < n) {
+        const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+        const double v = B[o] - s;
+        R[o] = v;
+        mysq[c] += v * v;
+      }
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) sq[warp][c] = mysq[c];
+  __syncthreads();
+  if (threadIdx.x < NR) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += sq[w][threadIdx.x];
+    partials[static_cast<int64_t>(blockIdx.x) * nrhs + c0 + threadIdx.x] = t;
+  }
+}
+
+template <int NR>
+void resid_chunk(const double* A, int64_t lda, const double* Th, const double* B, double* R, int n, int nrhs,
+                 int c0, double* partials, int nb, bool vec, cudaStream_t s) {
+  if (vec)
+    k_resid<NR, true><<<nb, 256, 0, s>>>(A, lda, Th, B, R, n, nrhs, c0, partials);
+  else
+    k_resid<NR, false><<<nb, 256, 0, s>>>(A, lda, Th, B, R, n, nrhs, c0, partials);
+}
+
+// ---------------------------------------------------------------- update
+// Theta[i][c] += sum_k G[i][k] R[k][c].  With an f32 G the products and each
+// lane's running sum are f32 (G itself is only an f32 approximation of the
+// inverse, so this adds an error well below G's own); lane sums are combined
+// in f64 and added to the f64 Theta.
+template <int NR, bool VEC>
+__global__ void __launch_bounds__(256) k_update_f32(const float* __restrict__ G, int64_t ldg,
+                                                    const double* __restrict__ Rm, double* __restrict__ Th, int n,
+                                                    int nrhs, int c0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const bool r0 = row0 < n, r1 = row0 + 1 < n;
+  const float* g0 = G + static_cast<int64_t>(r0 ? row0 : 0) * ldg;
+  const float* g1 = G + static_cast<int64_t>(r1 ? row0 + 1 : 0) * ldg;
+  float acc[kRowsPerWarp][NR];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[r][c] = 0.f;
+  int kend = 0;
+  if (VEC) {
+    const int n4 = n & ~3;
+#pragma unroll 2
+    for (int k = 4 * lane; k < n4; k += 128) {
+      const float4 x0 = r0 ? *reinterpret_cast<const float4*>(g0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 x1 = r1 ? *reinterpret_cast<const float4*>(g1 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const float t0 = static_cast<float>(__ldg(Rm + static_cast<int64_t>(k) * nrhs + c0 + c));
+        const float t1 = static_cast<float>(__ldg(Rm + static_cast<int64_t>(k + 1) * nrhs + c0 + c));
+        const float t2 = static_cast<float>(__ldg(Rm + static_cast<int64_t>(k + 2) * nrhs + c0 + c));
+        const float t3 = static_cast<float>(__ldg(Rm + static_cast<int64_t>(k + 3) * nrhs + c0 + c));
+        acc[0][c] = fmaf(x0.x, t0, fmaf(x0.y, t1, fmaf(x0.z, t2, fmaf(x0.w, t3, acc[0][c]))));
+        acc[1][c] = fmaf(x1.x, t0, fmaf(x1.y, t1, fmaf(x1.z, t2, fmaf(x1.w, t3, acc[1][c]))));
+      }
+    }
+    kend = n4;
+  }
+  for (int k = kend + lane; k < n; k += 32) {
+    const float x0 = r0 ? g0[k] : 0.f;
+    const float x1 = r1 ? g1[k] : 0.f;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const float t = static_cast<float>(__ldg(Rm + static_cast<int64_t>(k) * nrhs + c0 + c));
+      acc[0][c] = fmaf(x0, t, acc[0][c]);
+      acc[1][c] = fmaf(x1, t, acc[1][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double s = warp_sum(static_cast<double>(acc[r][c]));
+      const int row = row0 + r;
+      if (lane == 0 && row < n) Th[static_cast<int64_t>(row) * nrhs + c0 + c] += s;
+    }
+}
+
+template <int NR, bool VEC>
+__global__ void __launch_bounds__(256) k_update_f64(const double* __restrict__ G, int64_t ldg,
+                                                    const double* __restrict__ Rm, double* __restrict__ Th, int n,
+                                                    int nrhs, int c0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const bool r0 = row0 < n, r1 = row0 + 1 < n;
+  const double* g0 = G + static_cast<int64_t>(r0 ? row0 : 0) * ldg;
+  const double* g1 = G + static_cast<int64_t>(r1 ? row0 + 1 : 0) * ldg;
+  double acc[kRowsPerWarp][NR];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[r][c] = 0.0;
+  int kend = 0;
+  if (VEC) {
+    const int n2 = n & ~1;
+#pragma unroll 4
+    for (int k = 2 * lane; k < n2; k += 64) {
+      const double2 x0 = r0 ? *reinterpret_cast<const double2*>(g0 + k) : make_double2(0.0, 0.0);
+      const double2 x1 = r1 ? *reinterpret_cast<const double2*>(g1 + k) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const double t0 = __ldg(Rm + static_cast<int64_t>(k) * nrhs + c0 + c);
+        const double t1 = __ldg(Rm + static_cast<int64_t>(k + 1) * nrhs + c0 + c);
+        acc[0][c] = fma(x0.x, t0, fma(x0.y, t1, acc[0][c]));
+        acc[1][c] = fma(x1.x, t0, fma(x1.y, t1, acc[1][c]));
+      }
+    }
+    kend = n2;
+  }
+  for (int k = kend + lane; k < n; k += 32) {
+    const double x0 = r0 ? g0[k] : 0.0;
+    const double x1 = r1 ? g1[k] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double t = __ldg(Rm + static_cast<int64_t>(k) * nrhs + c0 + c);
+      acc[0][c] = fma(x0, t, acc[0][c]);
+      acc[1][c] = fma(x1, t, acc[1][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double s = warp_sum(acc[r][c]);
+      const int row = row0 + r;
+      if (lane == 0 && row < n) Th[static_cast<int64_t>(row) * nrhs + c0 + c] += s;
+    }
+}
+
+// ---------------------------------------------------------------- norms
+// One block per column: fixed-order strided sums then a fixed-order tree.
+__global__ void k_colsumsq(const double* __restrict__ X, int64_t ldx, int rows, int cols,
+                           double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < rows; r += 256) {
+    const double v = X[static_cast<int64_t>(r) * ldx + c];
+    s += v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// One warp per row: sum of squares and sum of |a|; block partials (8 rows).
+__global__ void __launch_bounds__(256) k_matnorms(const double* __restrict__ A, int64_t lda, int n,
+                                                  double* __restrict__ ss_part, double* __restrict__ rm_part) {
+  __shared__ double ss[kWarps], ra[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kWarps + warp;
+  double s = 0.0, a = 0.0;
+  if (row < n) {
+    const double* p = A + static_cast<int64_t>(row) * lda;
+    for (int k = lane; k < n; k += 32) {
+      const double v = p[k];
+      s += v * v;
+      a += fabs(v);
+    }
+  }
+  s = warp_sum(s);
+  a = warp_sum(a);
+  if (lane == 0) {
+    ss[warp] = s;
+    ra[warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tm = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      ts += ss[w];
+      tm = fmax(tm, ra[w]);
+    }
+    ss_part[blockIdx.x] = ts;
+    rm_part[blockIdx.x] = tm;
+  }
+}
+
+__global__ void k_reduce_sum(const double* __restrict__ part, int nblocks, int ncols, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) s += part[static_cast<int64_t>(b) * ncols + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void k_reduce_max(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) s = fmax(s, part[b]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// ---------------------------------------------------------------- splits
+// hi = RN_bf16(RN_f32(x)), lo = RN_bf16(RN_f32(x) - hi) (difference exact in f32).
+__global__ void k_split_f64(const double* __restrict__ X, int64_t ldx, int rows, int cols, bf16* __restrict__ hi,
+                            bf16* __restrict__ lo, float* __restrict__ x32, int64_t ld) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    const float v = static_cast<float>(X[r * ldx + c]);
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[r * ld + c] = h;
+    lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (x32 != nullptr) x32[r * ld + c] = v;
+  }
+}
+
+__global__ void k_split_f32(const float* __restrict__ X, int64_t ldx, int rows, int cols, bf16* __restrict__ hi,
+                            bf16* __restrict__ lo, int64_t ld) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    const float v = X[r * ldx + c];
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[r * ld + c] = h;
+    lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+__device__ __forceinline__ double g0_alpha(const double* scal, int mode) {
+  if (mode == 0) return 1.0 / sqrt(scal[0]);
+  const double ninf = scal[1];
+  return 1.0 / (0.5 * ninf + 1e-8 * ninf);
+}
+
+__global__ void k_init_g0_mp(const double* __restrict__ scal, int mode, int n, int64_t ld, float* __restrict__ G32,
+                             bf16* __restrict__ hi, bf16* __restrict__ lo) {
+  const float a = static_cast<float>(g0_alpha(scal, mode));
+  const bf16 ah = __float2bfloat16_rn(a);
+  const bf16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
+  const bf16 z = __float2bfloat16_rn(0.f);
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n, c = e % n;
+    const bool d = r == c;
+    G32[r * ld + c] = d ? a : 0.f;
+    hi[r * ld + c] = d ? ah : z;
+    lo[r * ld + c] = d ? al : z;
+  }
+}
+
+__global__ void k_init_g0_f64(const double* __restrict__ scal, int mode, int n, int64_t ld, double* __restrict__ G) {
+  const double a = g0_alpha(scal, mode);
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n, c = e % n;
+    G[r * ld + c] = (r == c) ? a : 0.0;
+  }
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ X, int64_t ldx, int rows, int cols, double* __restrict__ Y,
+                             int64_t ldy) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    Y[r * ldy + c] = static_cast<double>(X[r * ldx + c]);
+  }
+}
+
+__global__ void k_copy_f64(const double* __restrict__ X, int64_t ldx, int rows, int cols, double* __restrict__ Y,
+                           int64_t ldy) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    Y[r * ldy + c] = X[r * ldx + c];
+  }
+}
+
+int ew_grid(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+int resid_blocks(int n) { return (n + kRowsPerBlock - 1) / kRowsPerBlock; }
+
+cudaError_t launch_resid(const double* A, int64_t lda, const double* Th, const double* B, double* R, int n, int nrhs,
+                         double* partials, int* nblocks_out, cudaStream_t s) {
+  const int nb = resid_blocks(n);
+  if (nblocks_out) *nblocks_out = nb;
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const bool vec = (lda % 2 == 0) && aligned16(A);
+  int c0 = 0;
+  while (c0 < nrhs) {
+    const int left = nrhs - c0;
+    if (left >= 8) {
+      resid_chunk<8>(A, lda, Th, B, R, n, nrhs, c0, partials, nb, vec, s);
+      c0 += 8;
+    } else if (left >= 4) {
+      resid_chunk<4>(A, lda, Th, B, R, n, nrhs, c0, partials, nb, vec, s);
+      c0 += 4;
+    } else if (left >= 2) {
+      resid_chunk<2>(A, lda, Th, B, R, n, nrhs, c0, partials, nb, vec, s);
+      c0 += 2;
+    } else {
+      resid_chunk<1>(A, lda, Th, B, R, n, nrhs, c0, partials, nb, vec, s);
+      c0 += 1;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_f32(const float* G, int64_t ldg, const double* R, double* Th, int n, int nrhs,
+                              cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int nb = resid_blocks(n);
+  const bool vec = (ldg % 4 == 0) && aligned16(G);
+  int c0 = 0;
+  while (c0 < nrhs) {
+    const int left = nrhs - c0;
+    const int nr = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+#define NSGB_UPD(NRV)                                                                  \
+  if (nr == NRV) {                                                                     \
+    if (vec)                                                                           \
+      k_update_f32<NRV, true><<<nb, 256, 0, s>>>(G, ldg, R, Th, n, nrhs, c0);          \
+    else                                                                               \
+      k_update_f32<NRV, false><<<nb, 256, 0, s>>>(G, ldg, R, Th, n, nrhs, c0);         \
+  }
+    NSGB_UPD(8) NSGB_UPD(4) NSGB_UPD(2) NSGB_UPD(1)
+#undef NSGB_UPD
+    c0 += nr;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_f64(const double* G, int64_t ldg, const double* R, double* Th, int n, int nrhs,
+                              cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int nb = resid_blocks(n);
+  const bool vec = (ldg % 2 == 0) && aligned16(G);
+  int c0 = 0;
+  while (c0 < nrhs) {
+    const int left = nrhs - c0;
+    const int nr = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+#define NSGB_UPD(NRV)                                                                  \
+  if (nr == NRV) {                                                                     \
+    if (vec)                                                                           \
+      k_update_f64<NRV, true><<<nb, 256, 0, s>>>(G, ldg, R, Th, n, nrhs, c0);          \
+    else                                                                               \
+      k_update_f64<NRV, false><<<nb, 256, 0, s>>>(G, ldg, R, Th, n, nrhs, c0);         \
+  }
+    NSGB_UPD(8) NSGB_UPD(4) NSGB_UPD(2) NSGB_UPD(1)
+#undef NSGB_UPD
+    c0 += nr;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsumsq(const double* X, int64_t ldx, int rows, int cols, double* out, int* nblocks_out,
+                            cudaStream_t s) {
+  if (nblocks_out) *nblocks_out = 1;
+  if (cols <= 0) return cudaSuccess;
+  k_colsumsq<<<cols, 256, 0, s>>>(X, ldx, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matnorms(const double* A, int64_t lda, int n, double* ss_part, double* rm_part, int* nblocks_out,
+                            cudaStream_t s) {
+  const int nb = (n + kWarps - 1) / kWarps;
+  if (nblocks_out) *nblocks_out = nb;
+  if (n <= 0) return cudaSuccess;
+  k_matnorms<<<nb, 256, 0, s>>>(A, lda, n, ss_part, rm_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_sum(const double* part, int nblocks, int ncols, double* out, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  k_reduce_sum<<<ncols, 256, 0, s>>>(part, nblocks, ncols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_max(const double* part, int nblocks, double* out, cudaStream_t s) {
+  k_reduce_max<<<1, 256, 0, s>>>(part, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_f64(const double* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, float* x32,
+                             int64_t ld, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  if (total <= 0) return cudaSuccess;
+  k_split_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, x32, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_f32(const float* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, int64_t ld,
+                             cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  if (total <= 0) return cudaSuccess;
+  k_split_f32<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_g0_mp(const double* scal, int mode, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,
+                              cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_init_g0_mp<<<ew_grid(total), 256, 0, s>>>(scal, mode, n, ld, G32, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_g0_f64(const double* scal, int mode, int n, int64_t ld, double* G, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_init_g0_f64<<<ew_grid(total), 256, 0, s>>>(scal, mode, n, ld, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
+                              cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  if (total <= 0) return cudaSuccess;
+  k_f32_to_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, Y, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
+                            cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(rows) * cols;
+  if (total <= 0) return cudaSuccess;
+  k_copy_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, Y, ldy);
+  return cudaGetLastError();
+}
+
+}  // namespace nsgb

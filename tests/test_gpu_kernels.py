@@ -1,0 +1,192 @@
+"""Kernel-level parity on the GPU, through the C ABI, against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances follow from the arithmetic:
+* bf16 splits are integer-like (round-to-nearest-even of a fixed value):
+  compared bit for bit.
+* Tensor-core products: every bf16 x bf16 product is exact in f32, so the only
+  error is the f32 accumulation of K terms plus the f32 epilogue.  Whatever the
+  summation order, |err| <= K * 2^-23 * sum_k |terms| + 2^-22 (|D| + |beta C|
+  + |gamma|) (2^-23 allows truncating adds).  A dropped pass (2^-9 relative)
+  or a wrong operand (O(1)) fails it.  The typical error is also checked:
+  median(|err| / sum|terms|) <= 2^-20.
+* FP64 products: |err| <= K * 2^-52 * sum|L||R| + 2^-51 |D|.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2008_11480_gb300 as nsgb
+
+pytestmark = pytest.mark.gpu
+dev = torch.device("cuda:0")
+
+
+def rnd(shape, seed, scale=1.0):
+    return np.random.default_rng(seed).standard_normal(shape) * scale
+
+
+def to_dev_padded(X, ld, dtype=torch.float64):
+    rows, cols = X.shape
+    t = torch.zeros((rows, ld), dtype=dtype, device=dev)
+    t[:, :cols] = torch.from_numpy(X).to(dtype)
+    return t
+
+
+def gpu_split(X, ld):
+    rows, cols = X.shape
+    x = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    hi = torch.zeros((rows, ld), dtype=torch.bfloat16, device=dev)
+    lo = torch.zeros((rows, ld), dtype=torch.bfloat16, device=dev)
+    nsgb.ns_k_split(x, hi, lo, rows, cols, cols, ld)
+    return hi, lo
+
+
+def rup(x, m=8):
+    return (x + m - 1) // m * m
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (7, 13), (130, 70), (64, 64), (513, 257)])
+def test_split_bit_exact(rows, cols):
+    X = rnd((rows, cols), 1, 10.0) * np.exp(np.random.default_rng(2).uniform(-20, 20, (rows, cols)))
+    ld = rup(cols)
+    hi, lo = gpu_split(X, ld)
+    rh, rl = O.split_bf16(X)
+    gh = hi.float().cpu().numpy()[:, :cols].astype(np.float64)
+    gl = lo.float().cpu().numpy()[:, :cols].astype(np.float64)
+    assert np.array_equal(gh, rh)
+    assert np.array_equal(gl, rl)
+    assert not torch.any(hi[:, cols:].float() != 0)
+
+
+def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0, scale=1.0):
+    L = rnd((M, K), seed, scale)
+    R = rnd((K, N), seed + 1, scale)
+    C = rnd((M, N), seed + 2) if with_c else None
+    ldl, ldr, ldd = rup(K), rup(N), rup(N)
+    Lh, Ll = gpu_split(L, ldl)
+    Rh, Rl = gpu_split(R, ldr)
+    Cd = to_dev_padded(O.round_f32(C), ldd, torch.float32) if with_c else None
+    D32 = torch.full((M, ldd), 7.0, dtype=torch.float32, device=dev)
+    Dh = torch.zeros((M, ldd), dtype=torch.bfloat16, device=dev)
+    Dl = torch.zeros((M, ldd), dtype=torch.bfloat16, device=dev)
+    fro = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_bf16(prec, M, N, K, Lh, Ll, ldl, Rh, Rl, ldr, s, Cd, ldd if with_c else 0, beta, gamma,
+                        D32, ldd, Dh, Dl, ldd, fro, bn)
+    torch.cuda.synchronize()
+    pname = "bf16" if prec == nsgb.NS_BF16 else "bf16x3"
+    prod = O.split_product(L, R, pname)
+    absprod = O.split_abs_product(L, R, pname)
+    ref = O.gemm_epilogue(prod, s, O.round_f32(C) if with_c else None, beta, gamma)
+    out = D32.cpu().numpy()[:, :N].astype(np.float64)
+    assert np.all(D32.cpu().numpy()[:, N:] == 7.0), "wrote past N"
+    cabs = np.abs(beta * O.round_f32(C)) if with_c else 0.0
+    tol = K * 2.0 ** -23 * absprod * abs(s) + 2.0 ** -22 * (np.abs(ref) + cabs + abs(gamma)) + 1e-30
+    err = np.abs(out - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    assert np.median(err / (absprod * abs(s) + 1e-30)) <= 2.0 ** -20
+    hi = Dh.float().cpu().numpy()[:, :N].astype(np.float64)
+    lo = Dl.float().cpu().numpy()[:, :N].astype(np.float64)
+    assert np.all(np.abs(hi + lo - ref) <= tol + 2.0 ** -16 * np.abs(ref))
+    assert np.all(np.abs(hi - ref) <= tol + 2.0 ** -8 * np.abs(ref))
+    f = float(fro.item())
+    assert f == pytest.approx(float(np.sum(ref * ref)), rel=1e-4)
+    return err, tol
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (130, 200, 70), (256, 512, 1024), (64, 64, 64), (1, 1, 1),
+                                   (17, 33, 9), (300, 130, 257)])
+def test_gemm_tc_plain(prec, M, N, K):
+    run_gemm(prec, M, N, K, seed=M + N + K)
+
+
+@pytest.mark.parametrize("bn", [64, 128, 256])
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+def test_gemm_tc_tile_widths(prec, bn):
+    run_gemm(prec, 390, 520, 200, seed=11, bn=bn)
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+def test_gemm_tc_residual_epilogue(prec):
+    """F = I - A G form: s = -1, gamma = 1 on a square problem."""
+    run_gemm(prec, 200, 200, 200, seed=5, s=-1.0, gamma=1.0, scale=0.07)
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+def test_gemm_tc_accumulate_epilogue(prec):
+    """X + X P form: C = X, beta = 1."""
+    run_gemm(prec, 333, 333, 333, seed=6, beta=1.0, with_c=True)
+
+
+def test_gemm_tc_full_size_sampled():
+    """4096^3 bf16x3 (the bench's product size and launch configuration):
+    sampled outputs recomputed one by one by the oracle."""
+    n = 4096
+    rng = np.random.default_rng(40)
+    L = rng.standard_normal((n, n)) * 0.02
+    R = rng.standard_normal((n, n)) * 0.02
+    Lh, Ll = gpu_split(L, n)
+    Rh, Rl = gpu_split(R, n)
+    D32 = torch.zeros((n, n), dtype=torch.float32, device=dev)
+    nsgb.ns_k_gemm_bf16(nsgb.NS_BF16X3, n, n, n, Lh, Ll, n, Rh, Rl, n, -1.0, None, 0, 0.0, 1.0, D32, n,
+                        None, None, 0, None, 256)
+    torch.cuda.synchronize()
+    idx = rng.integers(0, n, (96, 2))
+    idx[:8, 1] = idx[:8, 0]   # include diagonal entries (identity term)
+    out = D32.cpu().numpy()
+    for i, j in idx:
+        p = O.split_product(L[i:i + 1], R[:, j:j + 1], "bf16x3")[0, 0]
+        a = O.split_abs_product(L[i:i + 1], R[:, j:j + 1], "bf16x3")[0, 0]
+        ref = -p + (1.0 if i == j else 0.0)
+        tol = n * 2.0 ** -23 * a + 2.0 ** -22 * (abs(ref) + 1.0)
+        assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(64, 64, 64), (130, 70, 33), (1, 1, 1), (200, 300, 150)])
+def test_gemm_f64(M, N, K):
+    L, R, C = rnd((M, K), 1), rnd((K, N), 2), rnd((M, N), 3)
+    Ld, Rd, Cd = (torch.from_numpy(x).to(dev) for x in (L, R, C))
+    D = torch.zeros((M, N), dtype=torch.float64, device=dev)
+    fro = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_f64(M, N, K, Ld, K, Rd, N, -0.5, Cd, N, 2.0, 1.0, D, N, fro)
+    torch.cuda.synchronize()
+    ref = O.gemm_epilogue(L @ R, -0.5, C, 2.0, 1.0)
+    tol = K * 2.0 ** -52 * 0.5 * (np.abs(L) @ np.abs(R)) + 2.0 ** -51 * (np.abs(ref) + 2 * np.abs(C) + 1)
+    assert np.all(np.abs(D.cpu().numpy() - ref) <= tol)
+    assert float(fro.item()) == pytest.approx(float(np.sum(ref * ref)), rel=1e-12)
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (64, 1), (130, 3), (257, 9), (1000, 4), (33, 16)])
+def test_resid_and_update(n, nrhs):
+    A, Th, B = rnd((n, n), 4), rnd((n, nrhs), 5), rnd((n, nrhs), 6)
+    Ad, Thd, Bd = (torch.from_numpy(x).to(dev) for x in (A, Th, B))
+    R = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
+    rsq = torch.zeros(nrhs, dtype=torch.float64, device=dev)
+    nsgb.ns_k_resid(Ad, n, Thd, Bd, R, n, nrhs, rsq)
+    torch.cuda.synchronize()
+    ref = B - A @ Th
+    tol = n * 2.0 ** -52 * (np.abs(A) @ np.abs(Th) + np.abs(B))
+    assert np.all(np.abs(R.cpu().numpy() - ref) <= tol)
+    assert np.allclose(rsq.cpu().numpy(), np.sum(ref * ref, axis=0), rtol=1e-12)
+    # update with an FP64 gain: Theta += G R
+    G = rnd((n, n), 7)
+    Gd = torch.from_numpy(G).to(dev)
+    th1 = Thd.clone()
+    nsgb.ns_k_update(Gd, n, R, th1, n, nrhs)
+    torch.cuda.synchronize()
+    Rn = R.cpu().numpy()
+    ref1 = Th + G @ Rn
+    tol1 = n * 2.0 ** -52 * (np.abs(G) @ np.abs(Rn)) + 2.0 ** -52 * np.abs(ref1)
+    assert np.all(np.abs(th1.cpu().numpy() - ref1) <= tol1)
+    # update with an f32 gain: products and lane sums in f32 (ceil(n/32) terms per lane)
+    G32 = O.round_f32(G)
+    G32d = torch.from_numpy(G32).to(dev).float()
+    th2 = Thd.clone()
+    nsgb.ns_k_update(G32d, n, R, th2, n, nrhs)
+    torch.cuda.synchronize()
+    ref2 = Th + G32 @ Rn
+    terms = -(-n // 32) + 2
+    tol2 = terms * 2.0 ** -23 * (np.abs(G32) @ np.abs(Rn)) + 2.0 ** -52 * np.abs(ref2)
+    assert np.all(np.abs(th2.cpu().numpy() - ref2) <= tol2)

@@ -1,0 +1,233 @@
+"""Solver-level parity on the GPU through the C ABI.
+
+* Plain FP64 path: iterates of G and theta agree with the FP64 oracle to 1e-12
+  relative Frobenius (the two differ only in summation order; at kappa <= 100
+  the rounding floor is ~1e-14).
+* Mixed precision (tcgen05 bf16 / bf16x3 products, FP64 Richardson): the
+  relative residual max_c ||b_c - A theta_c|| / ||b_c|| is recomputed by the
+  oracle in FP64 and must be <= 1e-10; theta then lies within
+  kappa * 1e-10 (times a safety factor 10) of the exact solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2008_11480_gb300 as nsgb
+from workloads import make_spd
+
+pytestmark = pytest.mark.gpu
+dev = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def tens(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def test_fp64_cfg1_solve_matches_oracle():
+    """n = 64, lambda log-uniform in [1, 100], one RHS, order 4 factorized
+    (I + F)(I + F^2), 8 coupled iterations, G0 = I/||A||_F."""
+    p = make_spd(64, 100.0, nrhs=1, seed=0)
+    ref = O.ns_richardson_solve(p.A, p.B, order=4, ns_iters=8)
+    with nsgb.Context(64, order=4, precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=0) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=8, tol=0.0)
+        G, _ = ctx.invert(tens(p.A), iters=8)
+    assert rel(r.theta.cpu().numpy(), ref.theta) <= 1e-12
+    assert rel(G.cpu().numpy(), ref.G) <= 1e-12
+    assert np.allclose(r.stats.frob_history(), ref.frob_E, rtol=1e-10, atol=1e-13)
+    assert np.allclose(r.stats.res_history(), ref.rel_res, rtol=1e-9, atol=1e-14)
+    # the closed form of the error model: I - G_8 A = F_0^{4^8}
+    a = O.alpha_frobenius(p.A)
+    F8 = (p.Q * (1 - a * p.lam) ** (4 ** 8)) @ p.Q.T
+    assert np.linalg.norm(np.eye(64) - G.cpu().numpy() @ p.A - F8) <= 1e-11
+
+
+@pytest.mark.parametrize("order,form,pow_mode", [(2, 0, 0), (3, 0, 0), (4, 0, 1), (8, 0, 0), (8, 0, 1),
+                                                 (5, 1, 0), (4, 1, 0)])
+def test_fp64_invert_orders_forms(order, form, pow_mode):
+    n = 130
+    p = make_spd(n, 50.0, seed=3)
+    iters = 4 if order >= 4 else 6
+    with nsgb.Context(n, order=order, precision=nsgb.NS_FP64, ns_stop=0, form=form, pow_mode=pow_mode) as ctx:
+        G, st = ctx.invert(tens(p.A), iters=iters)
+    Gref, norms = O.ns_invert(p.A, order=order, iters=iters, form="horner" if form else "factorized",
+                              pow_mode="residual" if pow_mode else "square")
+    assert rel(G.cpu().numpy(), Gref) <= 1e-12
+    assert np.allclose(st.frob_history(), norms, rtol=1e-10)
+
+
+@pytest.mark.parametrize("g0_mode", [0, 1])
+def test_fp64_g0_modes(g0_mode):
+    n = 96
+    p = make_spd(n, 20.0, seed=4)
+    a = O.alpha_frobenius(p.A) if g0_mode == 0 else O.alpha_inf(p.A)
+    with nsgb.Context(n, order=2, precision=nsgb.NS_FP64, ns_stop=0, g0_mode=g0_mode) as ctx:
+        G, _ = ctx.invert(tens(p.A), iters=5)
+    Gref, _ = O.ns_invert(p.A, G0=a * np.eye(n), order=2, iters=5)
+    assert rel(G.cpu().numpy(), Gref) <= 1e-12
+
+
+def test_fp64_user_g0_noncommuting():
+    """A Jacobi G0 (Section 2, S = diag(A)) does not commute with A; the right
+    product chain still matches the left series of eq. ns."""
+    rng = np.random.default_rng(8)
+    n = 72
+    M = rng.uniform(-1, 1, (n, n))
+    M = 0.5 * (M + M.T)
+    np.fill_diagonal(M, 0)
+    A = M + np.diag(np.abs(M).sum(1) + rng.uniform(0.5, 3, n))
+    G0 = O.jacobi_preconditioner(A)
+    with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, ns_stop=0) as ctx:
+        G, _ = ctx.invert(tens(A), iters=3, G0=tens(G0))
+    ref = G0
+    for _ in range(3):
+        ref = O.ns_classical_step(ref, A, 4)
+    assert rel(G.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n_order,rates", [(2, [2]), (2, [2, 3]), (3, [2])])
+def test_fp64_composite_matches_oracle(n_order, rates):
+    n = 80
+    p = make_spd(n, 10.0, seed=9)
+    K = 3
+    with nsgb.Context(n, order=n_order, rates=rates, precision=nsgb.NS_FP64, ns_stop=0) as ctx:
+        G, _ = ctx.invert(tens(p.A), iters=K)
+    st = O.composite_init(O.alpha_frobenius(p.A) * np.eye(n), len(rates))
+    for _ in range(K):
+        st = O.composite_iterate(p.A, st, n_order, rates)
+    assert rel(G.cpu().numpy(), st.G) <= 1e-12
+    e = O.composite_exponents(n_order, rates, 1, K)[K]
+    a = O.alpha_frobenius(p.A)
+    ref = (p.Q * (1 - a * p.lam) ** e) @ p.Q.T
+    assert np.linalg.norm(np.eye(n) - G.cpu().numpy() @ p.A - ref) <= 1e-11
+
+
+@pytest.mark.parametrize("n_order", [2, 3])
+def test_fp64_double_ns_matches_oracle(n_order):
+    """Section 5.1: composite with one auxiliary loop started one step ahead."""
+    n = 64
+    p = make_spd(n, 6.0, seed=10)
+    K = 2
+    with nsgb.Context(n, order=n_order, rates=[n_order], precision=nsgb.NS_FP64, ns_stop=0, aux_ahead=1) as ctx:
+        G, _ = ctx.invert(tens(p.A), iters=K)
+    st = O.double_ns_init(p.A, O.alpha_frobenius(p.A) * np.eye(n), n_order)
+    for _ in range(K):
+        st = O.double_ns_iterate(p.A, st, n_order)
+    assert rel(G.cpu().numpy(), st.G) <= 1e-12
+
+
+@pytest.mark.parametrize("updated", [0, 1])
+def test_fp64_richardson_orderings(updated):
+    n = 50
+    p = make_spd(n, 30.0, nrhs=2, seed=11)
+    ref = O.ns_richardson_solve(p.A, p.B, order=2, ns_iters=5, max_sweeps=3, use_updated_G=bool(updated))
+    with nsgb.Context(n, order=2, precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=3, use_updated_G=updated) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=5, tol=0.0)
+    assert rel(r.theta.cpu().numpy(), ref.theta) <= 1e-12
+    assert r.stats.sweeps == ref.sweeps
+
+
+@pytest.mark.parametrize("n,kappa,order,nrhs", [(64, 100.0, 4, 1), (256, 1e3, 4, 3), (200, 1e4, 8, 4),
+                                                (130, 1e2, 3, 2), (512, 1e4, 2, 5)])
+def test_mixed_precision_solve_reaches_tolerance(n, kappa, order, nrhs):
+    p = make_spd(n, kappa, nrhs=nrhs, seed=12)
+    with nsgb.Context(n, order=order) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    th = r.theta.cpu().numpy()
+    rr = float(np.max(O.rel_residual(p.A, th, p.B)))
+    assert r.status == nsgb.NS_OK, (r.status, r.stats.res_history())
+    assert rr <= 1e-10
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(th, tstar) <= 10 * kappa * 1e-10
+    assert r.stats.gemm_launches > 0
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+def test_fixed_precision_solve(prec):
+    p = make_spd(128, 50.0, nrhs=2, seed=13)
+    with nsgb.Context(128, order=4, precision=prec) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=40, tol=1e-10)
+    assert r.status == nsgb.NS_OK
+    assert np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B)) <= 1e-10
+    assert set(r.stats.prec_history()) == {prec}
+
+
+def test_mixed_invert_close_to_inverse():
+    n = 256
+    p = make_spd(n, 1e3, seed=14)
+    Ainv = (p.Q / p.lam) @ p.Q.T
+    with nsgb.Context(n, order=4, precision=nsgb.NS_BF16X3) as ctx:
+        G, st = ctx.invert(tens(p.A), iters=30)
+    # bf16x3 floor at kappa = 1e3: rho(I - A G) ~ 1e-3 => ||G - A^-1|| / ||A^-1|| small
+    assert rel(G.cpu().numpy(), Ainv) <= 1e-2
+    assert min(st.frob_history()) <= 0.05
+
+
+def test_host_pointers_match_device_pointers():
+    p = make_spd(100, 100.0, nrhs=2, seed=15)
+    with nsgb.Context(100, order=4) as ctx:
+        rd = ctx.solve(tens(p.A), tens(p.B), iters=40, tol=1e-10)
+        Ah = torch.from_numpy(p.A).pin_memory()
+        Bh = torch.from_numpy(p.B).pin_memory()
+        out = torch.empty_like(Bh).pin_memory()
+        rh = ctx.solve(Ah, Bh, iters=40, tol=1e-10, out=out)
+        rp = ctx.solve(torch.from_numpy(p.A), torch.from_numpy(p.B), iters=40, tol=1e-10)  # pageable
+    a = rd.theta.cpu().numpy()
+    assert np.array_equal(a, rh.theta.numpy())
+    assert np.array_equal(a, rp.theta.numpy())
+
+
+def test_repeatable_bitwise():
+    p = make_spd(300, 1e3, nrhs=2, seed=16)
+    outs = []
+    with nsgb.Context(300, order=8) as ctx:
+        for _ in range(2):
+            outs.append(ctx.solve(tens(p.A), tens(p.B), iters=40, tol=1e-10).theta.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_residual_entry_point():
+    p = make_spd(77, 10.0, nrhs=3, seed=17)
+    th = np.random.default_rng(0).standard_normal((77, 3))
+    with nsgb.Context(77, order=2) as ctx:
+        got = ctx.residual(tens(p.A), tens(th), tens(p.B))
+    assert np.allclose(got, O.rel_residual(p.A, th, p.B), rtol=1e-12)
+
+
+def test_degenerate_sizes():
+    for n in (1, 2, 3):
+        p = make_spd(n, 2.0, nrhs=1, seed=18)
+        with nsgb.Context(n, order=4) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=30, tol=1e-12)
+        assert np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B)) <= 1e-12
+
+
+def test_errors_leave_context_usable():
+    p = make_spd(32, 10.0, nrhs=1, seed=19)
+    with nsgb.Context(32, order=4) as ctx:
+        A = tens(p.A)
+        Abad = A.clone()
+        Abad[3, 5] = float("nan")
+        s, _ = nsgb.ns_richardson_solve(ctx.handle, Abad, tens(p.B), None, 10, 1e-10,
+                                        torch.empty_like(tens(p.B)), check=False)
+        assert s == nsgb.NS_ERR_NONFINITE
+        r = ctx.solve(A, tens(p.B), iters=30, tol=1e-10)
+        assert r.status == nsgb.NS_OK
+
+
+def test_bench_size_solve():
+    """The benchmark workload: n = 4096, kappa = 1e4, 4 RHS, order 8, mixed
+    precision; the residual is recomputed in FP64 by the oracle and theta is
+    compared with the closed-form solution."""
+    p = make_spd(4096, 1e4, nrhs=4, seed=1)
+    with nsgb.Context(4096, order=8) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    th = r.theta.cpu().numpy()
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(th, tstar) <= 10 * 1e4 * 1e-10
