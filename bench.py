@@ -1,0 +1,325 @@
+"""Benchmark: SPD solves/s at relative residual <= 1e-10 on one dense system
+n = 4096, kappa = 1e4, 4 right-hand sides (A = Q diag(lambda) Q^T, lambda
+log-uniform in [1, 1e4]), by factorized Newton-Schulz (mixed bf16/bf16x3
+products on the tensor cores) coupled to FP64 Richardson iteration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete solve from the system alone (norms, splits, G0, every
+NS step and Richardson sweep until the residual test passes), inputs resident
+in HBM.  L2 is flushed (512 MiB write) between timed steps, outside the timed
+events.  Under torchrun each rank solves its own system (independent replicas;
+the problem does not shard without an exchange per product).  Rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SPD solves/s at rel. residual ≤1e-10 vs plain FP64 NS on GB300; p50/p99 latency"
+UNIT = "solves/s"
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def workload_config(a):
+    return {
+        "workload": f"dense SPD n={a.n} kappa={a.kappa:g} nrhs={a.nrhs}: A = Q diag(lambda) Q^T, Q Haar, "
+                    f"lambda log-uniform in [1, kappa]; B ~ N(0,1)",
+        "n": a.n, "kappa": a.kappa, "nrhs": a.nrhs, "order": a.order, "form": "factorized",
+        "precision": "auto: bf16 products while ||F||_F falls, then bf16x3; f32 accumulate; FP64 residual "
+                     "and Richardson",
+        "tol": 1e-10, "l2": "flushed between timed steps (512 MiB write)", "seed": 1,
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) leg
+def oracle_sample(a, ns_iters: int, sweeps: int, reps: int = 1):
+    """Time the FP64 oracle as it stands on the host cores: one Newton-Schulz
+    step of the configured order plus one Richardson sweep on the same system,
+    and extrapolate to a whole solve with the given step / sweep counts."""
+    import oracle as O
+    from workloads import make_spd
+    p = make_spd(a.n, a.kappa, nrhs=a.nrhs, seed=1)
+    G = O.alpha_frobenius(p.A) * np.eye(a.n)
+    theta = np.zeros_like(p.B)
+    t_ns, t_sw = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        G1, _ = O.ns_step(p.A, G, a.order)
+        t1 = time.perf_counter()
+        O.richardson_step(p.A, p.B, theta, G1)
+        t2 = time.perf_counter()
+        t_ns.append(t1 - t0)
+        t_sw.append(t2 - t1)
+    tns, tsw = min(t_ns), min(t_sw)
+    solve_s = ns_iters * tns + max(sweeps, ns_iters) * tsw
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / solve_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one order-{a.order} NS step ({tns:.2f} s) + one Richardson sweep ({tsw:.3f} s) of the "
+                      f"numpy FP64 oracle at n={a.n}, extrapolated to {ns_iters} NS steps + "
+                      f"{max(sweeps, ns_iters)} sweeps (the FP64 GPU path's counts for this system)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ns_iters, sweeps = a.ref_ns_iters, a.ref_sweeps
+    for _ in range(a.warmup if a.warmup < 1 else 1):
+        oracle_sample(a, ns_iters, sweeps)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        vals.append(oracle_sample(a, ns_iters, sweeps))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_spd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    p = make_spd(a.n, a.kappa, nrhs=a.nrhs, seed=1 + rank)
+    A = torch.from_numpy(p.A).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    out = torch.empty_like(B)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1)
+    for _ in range(max(3, a.warmup)):
+        r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+    assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
+
+    sampler = ClockSampler(local)
+    step_ms, tc_ms, tc_flops, tc_launch, launches, ns_it, sw = [], 0.0, 0.0, 0, 0, [], []
+    barrier()
+    sampler.start()
+    for _ in range(a.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        assert r.status == nsgb.NS_OK
+        step_ms.append(e0.elapsed_time(e1))
+        st = r.stats
+        tc_ms += st.tc_gemm_ms
+        tc_flops += st.tc_gemm_flops
+        tc_launch += st.tc_gemm_launches
+        launches += st.kernel_launches
+        ns_it.append(st.ns_iters)
+        sw.append(st.sweeps)
+    barrier()
+    clocks = sampler.stop()
+    rel = max(ctx.residual(A, out, B))
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * a.steps / total_s
+
+    # end to end through the same C-ABI call with host (pinned) buffers: the
+    # host->device copy of A and B and the device->host copy of theta are
+    # inside the timed region
+    Ah = torch.from_numpy(p.A).pin_memory()
+    Bh = torch.from_numpy(p.B).pin_memory()
+    Th = torch.empty_like(Bh).pin_memory()
+    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream)
+    ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
+    e2e_steps = max(1, min(a.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
+        assert r.status == nsgb.NS_OK
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    ctx_h.close()
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Ah.numel() * 8 + Bh.numel() * 8), "d2h_bytes_per_step": int(Th.numel() * 8)}
+
+    # plain FP64 Newton-Schulz + FP64 Richardson on the GPU (same algorithm, same stopping rule)
+    fp64 = None
+    if not a.no_fp64:
+        ctx64 = nsgb.Context(a.n, order=a.order, stream=stream, precision=nsgb.NS_FP64)
+        small = make_spd(256, a.kappa, nrhs=a.nrhs, seed=2)
+        with nsgb.Context(256, order=a.order, precision=nsgb.NS_FP64) as cw:
+            cw.solve(torch.from_numpy(small.A).to(dev), torch.from_numpy(small.B).to(dev), iters=a.iters, tol=1e-10)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        out64 = torch.empty_like(B)
+        e0.record(stream)
+        r64 = ctx64.solve(A, B, iters=a.iters, tol=1e-10, out=out64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "status": int(r64.status),
+                "ns_iters": r64.stats.ns_iters, "sweeps": r64.stats.sweeps, "rel_res": r64.stats.rel_res,
+                "speedup_of_mixed": value / max(world, 1) / (1e3 / ms64)}
+        ctx64.close()
+
+    pk, pk_kind = peaks()
+    achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
+    roof = {"bound": "tensor", "kernel": "k_gemm_tc (tcgen05 bf16 / bf16x3 product with fused NS epilogue)",
+            "achieved": achieved, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+            "frac": achieved / pk["bf16_tflops_sustained"] if achieved else None,
+            "peak_kind": f"bf16 dense sustained ({pk_kind}); kernel timed inside back-to-back solves",
+            "frac_of_burst": achieved / pk["bf16_tflops"] if achieved else None,
+            "traffic": None, "launches_timed": tc_launch,
+            "flops_per_launch": tc_flops / max(tc_launch, 1),
+            "avg_launch_ms": tc_ms / max(tc_launch, 1)}
+    if rank == 0:
+        ns_med = int(statistics.median(ns_it))
+        cpu = None
+        if not a.no_cpu:
+            ref_it = fp64["ns_iters"] if fp64 else ns_med
+            ref_sw = fp64["sweeps"] if fp64 else int(statistics.median(sw))
+            cpu = oracle_sample(a, ref_it, ref_sw)
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(a),
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                           "min": srt[0], "max": srt[-1]},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+            "fp64_path": fp64, "verified_rel_res": rel, "ns_iters": ns_med, "sweeps": int(statistics.median(sw)),
+            "gemm_ms_per_step": tc_ms / a.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--kappa", type=float, default=1e4)
+    ap.add_argument("--nrhs", type=int, default=4)
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--iters", type=int, default=60)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-ns-iters", type=int, default=8)
+    ap.add_argument("--ref-sweeps", type=int, default=9)
+    a = ap.parse_args()
+    if a.warmup < 3 and a.impl == "ours":
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()
