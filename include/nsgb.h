@@ -195,6 +195,24 @@ ns_status ns_k_resid(const double* A, int64_t lda, const double* Theta, const do
 ns_status ns_k_update(const void* G, int g_dtype, int64_t ldg, const double* R, double* Theta, int64_t n, int nrhs,
                       void* stream);
 
+/* One fused pass over A (FP64, n x n, leading dimension lda) that prepares every
+ * mixed-precision operand: the bf16 hi/lo split of each element (as ns_k_split,
+ * leading dimension ld, a multiple of 8), its two f32 limbs a1 = RN32(a),
+ * a2 = RN32(a - a1) (leading dimension ld), and, when non-NULL, the device doubles
+ * ss_out[0] = sum a_ij^2 (for G0 = I/||A||_F, Section 2) and
+ * rowabs_out[0] = max_i sum_j |a_ij| (= ||A||_inf, Section 2). */
+ns_status ns_k_prep_a(const double* A, int64_t lda, int64_t n, void* hi, void* lo, float* a1, float* a2,
+                      int64_t ld, double* ss_out, double* rowabs_out, void* stream);
+
+/* Richardson residual R = B - A Theta (FP64 result) evaluated from A's f32 limbs
+ * (a1, a2 from ns_k_prep_a; ld a multiple of 4, 16-byte aligned) and Theta's limbs,
+ * with exact f32 products and paired-f32 accumulation: each row sum carries about
+ * 48 significant bits, the accuracy of an FP64 GEMV at these sizes.  rsq_out
+ * (device, nrhs doubles, may be NULL) receives ||R_c||^2.  This is the residual the
+ * mixed-precision solve uses (FP64 arithmetic is rate-limited on GB300). */
+ns_status ns_k_resid_x2(const float* a1, const float* a2, int64_t ld, const double* Theta, const double* B,
+                        double* R, int64_t n, int nrhs, double* rsq_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

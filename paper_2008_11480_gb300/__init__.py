@@ -26,7 +26,7 @@ __all__ = [
     "NSError", "ns_options", "ns_stats", "lib", "lib_path", "header_path", "default_options",
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
-    "ns_k_update", "Context",
+    "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "Context",
 ]
 
 NS_OK, NS_NOT_CONVERGED = 0, 1
@@ -126,6 +126,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_double, _vp, _i64, _vp, _vp]),
         "ns_k_resid": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
         "ns_k_update": (_int, [_vp, _int, _i64, _vp, _vp, _i64, _int, _vp]),
+        "ns_k_prep_a": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "ns_k_resid_x2": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -281,6 +283,18 @@ def ns_k_update(G, ldg: int, R, theta, n: int, nrhs: int, stream=None) -> None:
     dt = {torch.float64: 0, torch.float32: 1}[G.dtype]
     _raise(lib().ns_k_update(G.data_ptr(), dt, ldg, _ptr(R), _ptr(theta), n, nrhs, _stream_ptr(stream)),
            "ns_k_update")
+
+
+def ns_k_prep_a(A, lda: int, n: int, hi, lo, a1, a2, ld: int, ss_out=None, rowabs_out=None, stream=None) -> None:
+    bf = torch.bfloat16
+    _raise(lib().ns_k_prep_a(_ptr(A), lda, n, _ptr(hi, bf), _ptr(lo, bf), _ptr(a1, torch.float32),
+                             _ptr(a2, torch.float32), ld, _ptr(ss_out), _ptr(rowabs_out), _stream_ptr(stream)),
+           "ns_k_prep_a")
+
+
+def ns_k_resid_x2(a1, a2, ld: int, theta, B, R, n: int, nrhs: int, rsq_out=None, stream=None) -> None:
+    _raise(lib().ns_k_resid_x2(_ptr(a1, torch.float32), _ptr(a2, torch.float32), ld, _ptr(theta), _ptr(B), _ptr(R),
+                               n, nrhs, _ptr(rsq_out), _stream_ptr(stream)), "ns_k_resid_x2")
 
 
 # ---------------------------------------------------------------- convenience

@@ -102,4 +102,18 @@ cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, d
 cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
                             cudaStream_t s);
 
+// ---- split-f32 Richardson path (mixed precision)
+// One pass over A: sum a^2 / max row |a| partials, bf16 hi/lo, f32 limbs a1/a2.
+cudaError_t launch_prep_a(const double* A, int64_t lda, int n, bf16* hi, bf16* lo, float* a1, float* a2, int64_t ld,
+                          double* ss_part, double* rm_part, int* nblocks_out, cudaStream_t s);
+// theta (n x nrhs) -> f32 limbs T1/T2 stored per right-hand side (leading dimension ldt).
+cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, float* T2, int64_t ldt, cudaStream_t s);
+// R = B - A theta from the limbs; R (FP64, n x nrhs), R32T (f32, per rhs), partial R^2.
+cudaError_t launch_resid_x2(const float* A1, const float* A2, int64_t ld, const float* T1, const float* T2,
+                            int64_t ldt, const double* B, double* R, float* R32T, int n, int nrhs,
+                            double* partials, int* nblocks_out, cudaStream_t s);
+// Theta += G R32 (G f32), writing the new theta's limbs.
+cudaError_t launch_update_x2(const float* G, int64_t ldg, const float* R32T, int64_t ldt, double* Th, float* T1,
+                             float* T2, int n, int nrhs, cudaStream_t s);
+
 }  // namespace nsgb

@@ -75,12 +75,14 @@ struct ns_ctx {
   size_t partials_cap = 0;
   double* Astage = nullptr;
   double *Bd = nullptr, *Thd = nullptr, *Rd = nullptr;
+  float *T1 = nullptr, *T2 = nullptr, *R32T = nullptr;  // f32 limbs of theta, f32 R (per rhs, ld)
   int nrhs_cap = 0;
   int* derr = nullptr;
 
   // mixed precision
   bool mp_ready = false;
   MpMat A, G[2], X[2], F, P[2];
+  float *A1 = nullptr, *A2 = nullptr;  // f32 limbs of A for the residual
   // composite
   bool comp_ready = false;
   std::vector<MpMat> T[2];  // per rate, ping-pong
@@ -157,6 +159,9 @@ ns_status ensure_common(ns_ctx* ctx, int nrhs) {
     NS_TRY(alloc(ctx, &ctx->Rd, static_cast<size_t>(ctx->n) * cap));
     NS_TRY(alloc(ctx, &ctx->Bd, static_cast<size_t>(ctx->n) * cap));
     NS_TRY(alloc(ctx, &ctx->Thd, static_cast<size_t>(ctx->n) * cap));
+    NS_TRY(alloc(ctx, &ctx->T1, static_cast<size_t>(ctx->ld) * cap));
+    NS_TRY(alloc(ctx, &ctx->T2, static_cast<size_t>(ctx->ld) * cap));
+    NS_TRY(alloc(ctx, &ctx->R32T, static_cast<size_t>(ctx->ld) * cap));
     ctx->nrhs_cap = cap;
     ctx->derr = reinterpret_cast<int*>(ctx->dscal + 3);
     // partial sums: GEMM tiles (4 per tile at the smallest tile width), fp64
@@ -182,6 +187,8 @@ ns_status ensure_mp(ns_ctx* ctx) {
     NS_TRY(alloc_mp(ctx, ctx->P[i], false));
   }
   NS_TRY(alloc_mp(ctx, ctx->F, true));
+  NS_TRY(alloc(ctx, &ctx->A1, static_cast<size_t>(ctx->n) * ctx->ld));
+  NS_TRY(alloc(ctx, &ctx->A2, static_cast<size_t>(ctx->n) * ctx->ld));
   ctx->mp_ready = true;
   return NS_OK;
 }
@@ -494,6 +501,32 @@ bool order_ok(int order, int form) {
   return (order & (order - 1)) == 0;
 }
 
+// Cost model of the controller (seconds): one Newton-Schulz step is its
+// products at the tensor-core (or FP64) rate; one Richardson sweep reads A's
+// limbs (or A in FP64) and G once, plus fixed launch and sync overhead.
+int products_per_step(const ns_ctx* ctx) {
+  int m = 0;
+  if (ctx->opt.form == 1 || ctx->order == 3) {
+    m = ctx->opt.form == 1 ? ctx->order : 3;
+  } else {
+    int levels = 0;
+    while ((1 << levels) < ctx->order) ++levels;
+    m = 2 * levels;
+  }
+  for (int r : ctx->rates) m += (r > 1 ? 2 * r : 0) + 3;
+  return m;
+}
+double step_cost(const ns_ctx* ctx, bool fp64, int prec) {
+  const double n = static_cast<double>(ctx->n);
+  const double flops = products_per_step(ctx) * 2.0 * n * n * n * (prec == NS_BF16X3 ? 3.0 : 1.0);
+  return flops / (fp64 ? 1.1e12 : 1.0e15) + 3e-6 * products_per_step(ctx);
+}
+double sweep_cost(const ns_ctx* ctx, bool fp64, int nrhs) {
+  const double n = static_cast<double>(ctx->n);
+  if (fp64) return std::max(12.0 * n * n / 5.0e12, 4.0 * n * n * nrhs / 1.1e12) + 3e-5;
+  return std::max(12.0 * n * n / 5.0e12, 22.0 * n * n * nrhs / 3.0e13) + 3e-5;
+}
+
 // Everything one solve needs, shared by ns_invert and ns_richardson_solve.
 struct Solve {
   const double* A = nullptr;  // device, lda = ld_a
@@ -520,9 +553,13 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
 
   // ---- prep: norms of A, operand splits, G0, ||B_c||
   int nb = 0;
-  NS_CK(launch_matnorms(S.A, S.lda, n, ctx->partials, ctx->partials + ((n + 7) / 8) + 1, &nb, s));
+  double* rm_part = ctx->partials + ((n + 7) / 8) + 1;
+  if (fp64)
+    NS_CK(launch_matnorms(S.A, S.lda, n, ctx->partials, rm_part, &nb, s));
+  else
+    NS_CK(launch_prep_a(S.A, S.lda, n, ctx->A.hi, ctx->A.lo, ctx->A1, ctx->A2, ld, ctx->partials, rm_part, &nb, s));
   NS_CK(launch_reduce_sum(ctx->partials, nb, 1, ss, s));
-  NS_CK(launch_reduce_max(ctx->partials + nb + 1, nb, ctx->dscal + 1, s));
+  NS_CK(launch_reduce_max(rm_part, nb, ctx->dscal + 1, s));
   ctx->launches += 3;
   if (fp64) {
     // the fp64 products read A with leading dimension ld: copy if needed
@@ -537,16 +574,19 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       NS_CK(launch_init_g0_f64(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G64[0], s));
     ctx->launches++;
   } else {
-    NS_CK(launch_split_f64(S.A, S.lda, n, n, ctx->A.hi, ctx->A.lo, nullptr, ld, s));
     if (G0)
       NS_CK(launch_split_f64(G0, n, n, n, ctx->G[0].hi, ctx->G[0].lo, ctx->G[0].m32, ld, s));
     else
       NS_CK(launch_init_g0_mp(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G[0].m32, ctx->G[0].hi, ctx->G[0].lo, s));
-    ctx->launches += 2;
+    ctx->launches += 1;
   }
   if (richardson) {
     NS_CK(launch_colsumsq(S.B, S.nrhs, n, S.nrhs, bsq, nullptr, s));
     ctx->launches++;
+    if (!fp64) {
+      NS_CK(launch_split_theta(S.Th, n, S.nrhs, ctx->T1, ctx->T2, ld, s));
+      ctx->launches++;
+    }
   }
   S.cur = 0;
 
@@ -572,6 +612,8 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   int sweeps_left = ctx->opt.max_sweeps;
   bool ns_active = iters > 0;
   double prev_frob = INFINITY;
+  double prev_ratio = INFINITY;
+  double last_rr = INFINITY;
   bool converged = false;
   int aux_steps = 0;
 
@@ -673,9 +715,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
 
   for (;;) {
     if (richardson) {
-      NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
+      if (fp64) {
+        NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
+        ctx->launches += (S.nrhs + 7) / 8;
+      } else {
+        NS_CK(launch_resid_x2(ctx->A1, ctx->A2, ld, ctx->T1, ctx->T2, ld, S.B, ctx->Rd, ctx->R32T, n, S.nrhs,
+                              ctx->partials, &nb, s));
+        ctx->launches += (S.nrhs + 3) / 4;
+      }
       NS_CK(launch_reduce_sum(ctx->partials, nb, S.nrhs, rsq, s));
-      ctx->launches += 2 + (S.nrhs + 7) / 8;
+      ctx->launches += 1;
     }
     double frob = 0.0;
   recompute_F:
@@ -694,6 +743,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         const double q = b > 0 ? std::sqrt(r / b) : std::sqrt(r);
         rr = std::max(rr, std::isnan(q) ? INFINITY : q);
       }
+      last_rr = rr;
       if (st) {
         st->rel_res = rr;
         if (st->n_res < NS_MAX_HIST) st->rel_res_hist[st->n_res++] = rr;
@@ -708,6 +758,15 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       frob = std::sqrt(ctx->hscal[2]);
       push_frob(frob, prec);
       if (!std::isfinite(frob)) return fail(ctx, NS_ERR_NONFINITE, "||F||_F is not finite");
+      const double ratio = frob / prev_frob;
+      if (autop && prec == NS_BF16 && done >= 2 && frob < prev_frob && ratio > prev_ratio + 0.02) {
+        // the contraction of ||F||_F got worse: bf16 rounding noise is becoming
+        // comparable to the error being removed.  Keep G_k, but F_k itself was
+        // formed in bf16 and carries that noise: form it again in bf16x3.
+        prec = NS_BF16X3;
+        prev_ratio = INFINITY;
+        goto recompute_F;
+      }
       if (autop && prec == NS_BF16 && done > 0 && frob >= prev_frob) {
         // bf16 rounding has stopped the contraction: redo the last step in bf16x3
         S.cur ^= 1;
@@ -722,6 +781,15 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         return fail(ctx, NS_ERR_DIVERGED, "Newton-Schulz diverged (||F||_F grew past sqrt(n))");
       if (ctx->opt.ns_stop && (!autop || prec != NS_BF16)) {
         bool stop = frob <= ctx->opt.ns_stop_frob;
+        if (!stop && richardson && frob < 1.0 && tol > 0 && last_rr > tol) {
+          // rho(I - A G_k) <= ||F_k||_F < 1 bounds the Richardson contraction:
+          // stop when the sweeps that bound implies cost less than one more
+          // Newton-Schulz step (which at best leaves ~one sweep to do)
+          const double need = std::ceil(std::log(tol / last_rr) / std::log(frob));
+          const double t_sweep = sweep_cost(ctx, fp64, S.nrhs);
+          const double t_step = step_cost(ctx, fp64, prec);
+          if (need <= sweeps_left && need * t_sweep <= t_step + 2.0 * t_sweep) stop = true;
+        }
         if (!stop && prev_frob < 1.0 && frob >= 0.5 * prev_frob) {
           stop = true;  // quadratic contraction has stalled at the precision floor
           if (frob > prev_frob) {
@@ -741,11 +809,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         if (fp64)
           NS_CK(launch_update_f64(ctx->G64[gi], ld, ctx->Rd, S.Th, n, S.nrhs, s));
         else
-          NS_CK(launch_update_f32(ctx->G[gi].m32, ld, ctx->Rd, S.Th, n, S.nrhs, s));
+          NS_CK(launch_update_x2(ctx->G[gi].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, s));
         ctx->launches += (S.nrhs + 7) / 8;
         if (st) st->sweeps++;
       }
       S.cur = g_next;
+      prev_ratio = (done > 0 && std::isfinite(prev_frob)) ? frob / prev_frob : INFINITY;
       prev_frob = frob;
       done++;
       if (st) st->ns_iters = done;
@@ -756,7 +825,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     if (fp64)
       NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, s));
     else
-      NS_CK(launch_update_f32(ctx->G[S.cur].m32, ld, ctx->Rd, S.Th, n, S.nrhs, s));
+      NS_CK(launch_update_x2(ctx->G[S.cur].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, s));
     ctx->launches += (S.nrhs + 7) / 8;
     sweeps_left--;
     if (st) st->sweeps++;
@@ -1188,6 +1257,54 @@ ns_status ns_k_update(const void* G, int g_dtype, int64_t ldg, const double* R, 
   cudaError_t e = g_dtype == 1
                       ? launch_update_f32(static_cast<const float*>(G), ldg, R, Theta, static_cast<int>(n), nrhs, st)
                       : launch_update_f64(static_cast<const double*>(G), ldg, R, Theta, static_cast<int>(n), nrhs, st);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_prep_a(const double* A, int64_t lda, int64_t n, void* hi, void* lo, float* a1, float* a2,
+                      int64_t ld, double* ss_out, double* rowabs_out, void* stream) {
+  if (!A || !hi || !lo || !a1 || !a2 || n <= 0 || lda < n || ld < n || ld % 8) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = static_cast<int>((n + 7) / 8);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, sizeof(double) * 2 * nb, st) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  double* ssp = static_cast<double*>(scratch);
+  double* rmp = ssp + nb;
+  int nbo = 0;
+  cudaError_t e = launch_prep_a(A, lda, static_cast<int>(n), static_cast<bf16*>(hi), static_cast<bf16*>(lo), a1, a2,
+                                ld, ssp, rmp, &nbo, st);
+  if (e == cudaSuccess && ss_out) e = launch_reduce_sum(ssp, nbo, 1, ss_out, st);
+  if (e == cudaSuccess && rowabs_out) e = launch_reduce_max(rmp, nbo, rowabs_out, st);
+  cudaFreeAsync(scratch, st);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_resid_x2(const float* a1, const float* a2, int64_t ld, const double* Theta, const double* B,
+                        double* R, int64_t n, int nrhs, double* rsq_out, void* stream) {
+  if (!a1 || !a2 || !Theta || !B || !R || n <= 0 || nrhs <= 0 || ld < n || ld % 4 || !al16(a1) || !al16(a2))
+    return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ni = static_cast<int>(n);
+  const int64_t ldt = round_up(n, 4);
+  const int nb = resid_blocks(ni);
+  const size_t limb = static_cast<size_t>(ldt) * nrhs;
+  void* scratch = nullptr;
+  const size_t bytes = sizeof(float) * 3 * limb + sizeof(double) * nb * nrhs + 64;
+  if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  float* T1 = static_cast<float*>(scratch);
+  float* T2 = T1 + limb;
+  float* R32T = T2 + limb;
+  double* part = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(R32T + limb + 8) & ~uintptr_t(15));
+  int nbo = 0;
+  cudaError_t e = launch_split_theta(Theta, ni, nrhs, T1, T2, ldt, st);
+  if (e == cudaSuccess) e = launch_resid_x2(a1, a2, ld, T1, T2, ldt, B, R, R32T, ni, nrhs, part, &nbo, st);
+  if (e == cudaSuccess && rsq_out) e = launch_reduce_sum(part, nbo, nrhs, rsq_out, st);
+  cudaFreeAsync(scratch, st);
   return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 

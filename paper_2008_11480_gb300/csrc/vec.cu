@@ -531,4 +531,297 @@ cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, do
   return cudaGetLastError();
 }
 
+
+// ==================================================================== split-f32 Richardson kernels
+// GB300 executes FP64 at ~1/60 of its f32 rate, so an FP64 residual GEMV is
+// compute-bound.  The mixed-precision solve instead keeps A as two f32 limbs
+// a1 = RN32(a), a2 = RN32(a - a1) (|a - a1 - a2| <= 2^-48 |a|) and theta as
+// t1, t2 likewise, and forms each product a*theta as the exact f32 product
+// a1*t1 = p + e (TwoProd through fma) plus the f32 corrections e + a1 t2 +
+// a2 t1.  p is accumulated with TwoSum into an f32 pair (hi, lo), so each
+// lane's partial sum carries ~48 significant bits; lane sums are combined in
+// FP64.  The result matches an FP64 GEMV to within a few units of 2^-48
+// relative to sum |a||theta| -- the same order as FP64's own accumulation error
+// at these sizes.
+namespace {
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err;
+}
+
+// Fused preparation pass over A (FP64): partial sums of a^2 and of |a| per
+// row block, the bf16 hi/lo operands of the tensor-core products, and the two
+// f32 limbs used by the residual.
+__global__ void __launch_bounds__(256) k_prep_a(const double* __restrict__ A, int64_t lda, int n,
+                                                bf16* __restrict__ hi, bf16* __restrict__ lo, float* __restrict__ a1,
+                                                float* __restrict__ a2, int64_t ld, double* __restrict__ ss_part,
+                                                double* __restrict__ rm_part) {
+  __shared__ double ss[8], ra[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  double s = 0.0, a = 0.0;
+  if (row < n) {
+    const double* p = A + static_cast<int64_t>(row) * lda;
+    const int64_t o = static_cast<int64_t>(row) * ld;
+    for (int k = lane; k < n; k += 32) {
+      const double v = p[k];
+      s += v * v;
+      a += fabs(v);
+      const float f1 = static_cast<float>(v);
+      const float f2 = static_cast<float>(v - static_cast<double>(f1));
+      a1[o + k] = f1;
+      a2[o + k] = f2;
+      const bf16 h = __float2bfloat16_rn(f1);
+      hi[o + k] = h;
+      lo[o + k] = __float2bfloat16_rn(f1 - __bfloat162float(h));
+    }
+  }
+  s = warp_sum(s);
+  a = warp_sum(a);
+  if (lane == 0) {
+    ss[warp] = s;
+    ra[warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tm = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      ts += ss[w];
+      tm = fmax(tm, ra[w]);
+    }
+    ss_part[blockIdx.x] = ts;
+    rm_part[blockIdx.x] = tm;
+  }
+}
+
+// theta (n x nrhs, FP64, row-major) -> limbs T1[c][k], T2[c][k] (ldt per rhs).
+__global__ void k_split_theta(const double* __restrict__ Th, int n, int nrhs, float* __restrict__ T1,
+                              float* __restrict__ T2, int64_t ldt) {
+  const int64_t total = static_cast<int64_t>(n) * nrhs;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t k = e / nrhs, c = e % nrhs;
+    const double v = Th[e];
+    const float f1 = static_cast<float>(v);
+    T1[c * ldt + k] = f1;
+    T2[c * ldt + k] = static_cast<float>(v - static_cast<double>(f1));
+  }
+}
+
+// R = B - A Theta from the f32 limbs; also R32T[c][row] = RN32(R) (the
+// operand of the update) and per-block partial sums of R^2.  Rows are
+// 16-byte aligned (ld % 4 == 0), lanes stride k by 4.
+template <int NR>
+__global__ void __launch_bounds__(256) k_resid_x2(const float* __restrict__ A1, const float* __restrict__ A2,
+                                                  int64_t ld, const float* __restrict__ T1,
+                                                  const float* __restrict__ T2, int64_t ldt,
+                                                  const double* __restrict__ B, double* __restrict__ R,
+                                                  float* __restrict__ R32T, int n, int nrhs, int c0,
+                                                  double* __restrict__ partials) {
+  __shared__ double sq[kWarps][NR];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const bool r0 = row0 < n, r1 = row0 + 1 < n;
+  const int64_t o0 = static_cast<int64_t>(r0 ? row0 : 0) * ld;
+  const int64_t o1 = static_cast<int64_t>(r1 ? row0 + 1 : 0) * ld;
+  float hi[kRowsPerWarp][NR], lo[kRowsPerWarp][NR];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) hi[r][c] = lo[r][c] = 0.f;
+  const int n4 = n & ~3;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int k = 4 * lane; k < n4; k += 128) {
+    const float4 x0 = r0 ? *reinterpret_cast<const float4*>(A1 + o0 + k) : z4;
+    const float4 y0 = r0 ? *reinterpret_cast<const float4*>(A2 + o0 + k) : z4;
+    const float4 x1 = r1 ? *reinterpret_cast<const float4*>(A1 + o1 + k) : z4;
+    const float4 y1 = r1 ? *reinterpret_cast<const float4*>(A2 + o1 + k) : z4;
+    const float a1v[2][4] = {{x0.x, x0.y, x0.z, x0.w}, {x1.x, x1.y, x1.z, x1.w}};
+    const float a2v[2][4] = {{y0.x, y0.y, y0.z, y0.w}, {y1.x, y1.y, y1.z, y1.w}};
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const float4 u = *reinterpret_cast<const float4*>(T1 + (c0 + c) * ldt + k);
+      const float4 w = *reinterpret_cast<const float4*>(T2 + (c0 + c) * ldt + k);
+      const float t1v[4] = {u.x, u.y, u.z, u.w};
+      const float t2v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float p = a1v[r][j] * t1v[j];
+          const float e = fmaf(a1v[r][j], t1v[j], -p);
+          two_sum_acc(hi[r][c], lo[r][c], p);
+          lo[r][c] += fmaf(a1v[r][j], t2v[j], fmaf(a2v[r][j], t1v[j], e));
+        }
+    }
+  }
+  for (int k = n4 + lane; k < n; k += 32) {
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) {
+      const bool ok = r == 0 ? r0 : r1;
+      const int64_t o = r == 0 ? o0 : o1;
+      const float x = ok ? A1[o + k] : 0.f, y = ok ? A2[o + k] : 0.f;
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const float t1 = T1[(c0 + c) * ldt + k], t2 = T2[(c0 + c) * ldt + k];
+        const float p = x * t1;
+        const float e = fmaf(x, t1, -p);
+        two_sum_acc(hi[r][c], lo[r][c], p);
+        lo[r][c] += fmaf(x, t2, fmaf(y, t1, e));
+      }
+    }
+  }
+  double mysq[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) mysq[c] = 0.0;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double s = warp_sum(static_cast<double>(hi[r][c]) + static_cast<double>(lo[r][c]));
+      const int row = row0 + r;
+      if (lane == 0 && row < n) {
+        const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+        const double v = B[o] - s;
+        R[o] = v;
+        R32T[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v);
+        mysq[c] += v * v;
+      }
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) sq[warp][c] = mysq[c];
+  __syncthreads();
+  if (threadIdx.x < NR) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += sq[w][threadIdx.x];
+    partials[static_cast<int64_t>(blockIdx.x) * nrhs + c0 + threadIdx.x] = t;
+  }
+}
+
+// Theta += G R with G f32 (ld % 4 == 0) and R given as f32 R32T[c][k]; the new
+// theta is also written as its f32 limbs for the next residual.
+template <int NR>
+__global__ void __launch_bounds__(256) k_update_x2(const float* __restrict__ G, int64_t ldg,
+                                                   const float* __restrict__ R32T, int64_t ldt,
+                                                   double* __restrict__ Th, float* __restrict__ T1,
+                                                   float* __restrict__ T2, int n, int nrhs, int c0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const bool r0 = row0 < n, r1 = row0 + 1 < n;
+  const float* g0 = G + static_cast<int64_t>(r0 ? row0 : 0) * ldg;
+  const float* g1 = G + static_cast<int64_t>(r1 ? row0 + 1 : 0) * ldg;
+  float acc[kRowsPerWarp][NR];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[r][c] = 0.f;
+  const int n4 = n & ~3;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+  for (int k = 4 * lane; k < n4; k += 128) {
+    const float4 x0 = r0 ? *reinterpret_cast<const float4*>(g0 + k) : z4;
+    const float4 x1 = r1 ? *reinterpret_cast<const float4*>(g1 + k) : z4;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const float4 t = *reinterpret_cast<const float4*>(R32T + (c0 + c) * ldt + k);
+      acc[0][c] = fmaf(x0.x, t.x, fmaf(x0.y, t.y, fmaf(x0.z, t.z, fmaf(x0.w, t.w, acc[0][c]))));
+      acc[1][c] = fmaf(x1.x, t.x, fmaf(x1.y, t.y, fmaf(x1.z, t.z, fmaf(x1.w, t.w, acc[1][c]))));
+    }
+  }
+  for (int k = n4 + lane; k < n; k += 32) {
+    const float x0 = r0 ? g0[k] : 0.f;
+    const float x1 = r1 ? g1[k] : 0.f;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const float t = R32T[(c0 + c) * ldt + k];
+      acc[0][c] = fmaf(x0, t, acc[0][c]);
+      acc[1][c] = fmaf(x1, t, acc[1][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double s = warp_sum(static_cast<double>(acc[r][c]));
+      const int row = row0 + r;
+      if (lane == 0 && row < n) {
+        const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+        const double v = Th[o] + s;
+        Th[o] = v;
+        const float f1 = static_cast<float>(v);
+        T1[static_cast<int64_t>(c0 + c) * ldt + row] = f1;
+        T2[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v - static_cast<double>(f1));
+      }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prep_a(const double* A, int64_t lda, int n, bf16* hi, bf16* lo, float* a1, float* a2, int64_t ld,
+                          double* ss_part, double* rm_part, int* nblocks_out, cudaStream_t s) {
+  const int nb = (n + 7) / 8;
+  if (nblocks_out) *nblocks_out = nb;
+  if (n <= 0) return cudaSuccess;
+  k_prep_a<<<nb, 256, 0, s>>>(A, lda, n, hi, lo, a1, a2, ld, ss_part, rm_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, float* T2, int64_t ldt, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * nrhs;
+  if (total <= 0) return cudaSuccess;
+  k_split_theta<<<ew_grid(total), 256, 0, s>>>(Th, n, nrhs, T1, T2, ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_x2(const float* A1, const float* A2, int64_t ld, const float* T1, const float* T2,
+                            int64_t ldt, const double* B, double* R, float* R32T, int n, int nrhs,
+                            double* partials, int* nblocks_out, cudaStream_t s) {
+  const int nb = resid_blocks(n);
+  if (nblocks_out) *nblocks_out = nb;
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  if (ld % 4 || ldt % 4 || !aligned16(A1) || !aligned16(A2) || !aligned16(T1) || !aligned16(T2))
+    return cudaErrorInvalidValue;
+  int c0 = 0;
+  while (c0 < nrhs) {
+    const int left = nrhs - c0;
+    const int nr = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    if (nr == 4)
+      k_resid_x2<4><<<nb, 256, 0, s>>>(A1, A2, ld, T1, T2, ldt, B, R, R32T, n, nrhs, c0, partials);
+    else if (nr == 2)
+      k_resid_x2<2><<<nb, 256, 0, s>>>(A1, A2, ld, T1, T2, ldt, B, R, R32T, n, nrhs, c0, partials);
+    else
+      k_resid_x2<1><<<nb, 256, 0, s>>>(A1, A2, ld, T1, T2, ldt, B, R, R32T, n, nrhs, c0, partials);
+    c0 += nr;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_x2(const float* G, int64_t ldg, const float* R32T, int64_t ldt, double* Th, float* T1,
+                             float* T2, int n, int nrhs, cudaStream_t s) {
+  const int nb = resid_blocks(n);
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  if (ldg % 4 || ldt % 4 || !aligned16(G) || !aligned16(R32T)) return cudaErrorInvalidValue;
+  int c0 = 0;
+  while (c0 < nrhs) {
+    const int left = nrhs - c0;
+    const int nr = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    if (nr == 8)
+      k_update_x2<8><<<nb, 256, 0, s>>>(G, ldg, R32T, ldt, Th, T1, T2, n, nrhs, c0);
+    else if (nr == 4)
+      k_update_x2<4><<<nb, 256, 0, s>>>(G, ldg, R32T, ldt, Th, T1, T2, n, nrhs, c0);
+    else if (nr == 2)
+      k_update_x2<2><<<nb, 256, 0, s>>>(G, ldg, R32T, ldt, Th, T1, T2, n, nrhs, c0);
+    else
+      k_update_x2<1><<<nb, 256, 0, s>>>(G, ldg, R32T, ldt, Th, T1, T2, n, nrhs, c0);
+    c0 += nr;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace nsgb

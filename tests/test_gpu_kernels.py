@@ -190,3 +190,60 @@ def test_resid_and_update(n, nrhs):
     terms = -(-n // 32) + 2
     tol2 = terms * 2.0 ** -23 * (np.abs(G32) @ np.abs(Rn)) + 2.0 ** -52 * np.abs(ref2)
     assert np.all(np.abs(th2.cpu().numpy() - ref2) <= tol2)
+
+
+@pytest.mark.parametrize("n", [1, 7, 130, 1000])
+def test_prep_a_bit_exact(n):
+    """Fused pass over A: bf16 hi/lo and f32 limbs equal the oracle's
+    definitions bit for bit; the norms match to rounding."""
+    A = rnd((n, n), 21) * np.exp(np.random.default_rng(22).uniform(-5, 5, (n, n)))
+    ld = rup(n, 8)
+    Ad = torch.from_numpy(A).to(dev)
+    hi = torch.zeros((n, ld), dtype=torch.bfloat16, device=dev)
+    lo = torch.zeros_like(hi)
+    a1 = torch.zeros((n, ld), dtype=torch.float32, device=dev)
+    a2 = torch.zeros_like(a1)
+    ss = torch.zeros(1, dtype=torch.float64, device=dev)
+    rm = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_prep_a(Ad, n, n, hi, lo, a1, a2, ld, ss, rm)
+    torch.cuda.synchronize()
+    rh, rl = O.split_bf16(A)
+    assert np.array_equal(hi.float().cpu().numpy()[:, :n].astype(np.float64), rh)
+    assert np.array_equal(lo.float().cpu().numpy()[:, :n].astype(np.float64), rl)
+    r1 = O.round_f32(A)
+    r2 = O.round_f32(A - r1)
+    assert np.array_equal(a1.cpu().numpy()[:, :n].astype(np.float64), r1)
+    assert np.array_equal(a2.cpu().numpy()[:, :n].astype(np.float64), r2)
+    assert float(ss.item()) == pytest.approx(float(np.sum(A * A)), rel=1e-13)
+    assert float(rm.item()) == pytest.approx(float(np.max(np.sum(np.abs(A), axis=1))), rel=1e-13)
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (64, 1), (130, 3), (257, 9), (1000, 4), (4096, 4)])
+def test_resid_x2(n, nrhs):
+    """R = B - A Theta from f32 limbs (double-f32 accumulation).  Bound: split
+    and product corrections <= 2^-45 sum|a||theta| per row, the f32 'lo'
+    accumulator over m = ceil(n/32) terms per lane <= 2 m^2 2^-48 sum|a||theta|,
+    FP64 combination <= 2^-50 (|B| + sum|a||theta|)."""
+    rng = np.random.default_rng(n + nrhs)
+    A = rng.standard_normal((n, n))
+    Th = rng.standard_normal((n, nrhs))
+    B = A @ Th + 1e-6 * rng.standard_normal((n, nrhs))   # near-cancelling residual
+    ld = rup(n, 8)
+    Ad = torch.from_numpy(A).to(dev)
+    hi = torch.zeros((n, ld), dtype=torch.bfloat16, device=dev)
+    lo = torch.zeros_like(hi)
+    a1 = torch.zeros((n, ld), dtype=torch.float32, device=dev)
+    a2 = torch.zeros_like(a1)
+    nsgb.ns_k_prep_a(Ad, n, n, hi, lo, a1, a2, ld)
+    R = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
+    rsq = torch.zeros(nrhs, dtype=torch.float64, device=dev)
+    nsgb.ns_k_resid_x2(a1, a2, ld, torch.from_numpy(Th).to(dev), torch.from_numpy(B).to(dev), R, n, nrhs, rsq)
+    torch.cuda.synchronize()
+    ref = B - A @ Th
+    absp = np.abs(A) @ np.abs(Th)
+    m = -(-n // 32)
+    tol = (2.0 ** -45 + 2 * m * m * 2.0 ** -48 + 2.0 ** -50) * absp + 2.0 ** -50 * np.abs(B)
+    err = np.abs(R.cpu().numpy() - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    assert np.median(err / absp) <= 2.0 ** -44
+    assert np.allclose(rsq.cpu().numpy(), np.sum(ref * ref, axis=0), rtol=1e-6)
