@@ -213,6 +213,25 @@ ns_status ns_k_prep_a(const double* A, int64_t lda, int64_t n, void* hi, void* l
 ns_status ns_k_resid_x2(const float* a1, const float* a2, int64_t ld, const double* Theta, const double* B,
                         double* R, int64_t n, int nrhs, double* rsq_out, void* stream);
 
+/* Same computation as ns_k_resid, but it allocates nothing: for callers that cannot
+ * allocate device memory at call time (a serving loop whose device memory is all
+ * reserved up front by its admission budget, a latency-critical loop that must not
+ * enter the allocator, which can synchronise the device, or a process that forbids
+ * allocation after start-up).  The paper has no counterpart; this is an interface
+ * convenience.
+ *   - Its scratch (partial sums of ||R_c||^2) is one fixed 256 KiB device array that
+ *     every GPU which loads the library keeps until the process exits.
+ *   - Limits: n <= 32768 and nrhs <= 16; larger sizes return NS_ERR_ARG.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call before
+ *     any stream capture.
+ *   - All calls share the array, which keeps the last call's contents (nothing in it
+ *     needs to start at zero).  Calls whose work overlaps on the GPU (different
+ *     streams, or different host threads on one device) race on it: serialise them.
+ * Returns NS_OK, NS_ERR_ARG, or NS_ERR_CUDA. */
+ns_status ns_k_resid_noalloc(const double* A, int64_t lda, const double* Theta, const double* B, double* R,
+                             int64_t n, int nrhs, double* rsq_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

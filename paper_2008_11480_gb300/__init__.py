@@ -26,7 +26,7 @@ __all__ = [
     "NSError", "ns_options", "ns_stats", "lib", "lib_path", "header_path", "default_options",
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
-    "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "Context",
+    "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
 ]
 
 NS_OK, NS_NOT_CONVERGED = 0, 1
@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
         "ns_k_update": (_int, [_vp, _int, _i64, _vp, _vp, _i64, _int, _vp]),
         "ns_k_prep_a": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
         "ns_k_resid_x2": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
+        "ns_k_resid_noalloc": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -277,6 +278,16 @@ def ns_k_gemm_f64(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float, C,
 def ns_k_resid(A, lda: int, theta, B, R, n: int, nrhs: int, rsq_out=None, stream=None) -> None:
     _raise(lib().ns_k_resid(_ptr(A), lda, _ptr(theta), _ptr(B), _ptr(R), n, nrhs, _ptr(rsq_out),
                             _stream_ptr(stream)), "ns_k_resid")
+
+
+def ns_k_resid_noalloc(A, lda: int, theta, B, R, n: int, nrhs: int, rsq_out=None, stream=None) -> int:
+    """ns_k_resid without any device allocation (fixed scratch; n <= 32768,
+    nrhs <= 16).  Returns the status instead of raising on NS_ERR_ARG."""
+    s = lib().ns_k_resid_noalloc(_ptr(A), lda, _ptr(theta), _ptr(B), _ptr(R), n, nrhs, _ptr(rsq_out),
+                                 _stream_ptr(stream))
+    if s not in (NS_OK, NS_ERR_ARG):
+        raise NSError(s, "ns_k_resid_noalloc")
+    return s
 
 
 def ns_k_update(G, ldg: int, R, theta, n: int, nrhs: int, stream=None) -> None:
