@@ -297,6 +297,43 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_kernel_gemm(a):
+    """Single-product microbenchmark of the tcgen05 GEMM (D = I - L R on
+    n x n bf16 splits), the launch configuration the solve uses; intended as
+    the target of ncu captures.  Prints one JSON line with the per-launch time
+    (CUDA events around `steps` back-to-back calls, each of which also reads
+    back the kernel's error word)."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    dev = torch.device("cuda:0")
+    n = a.n
+    g = torch.Generator(device=dev).manual_seed(7)
+    L = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g) * 0.02
+    mk = lambda dt=torch.bfloat16: torch.zeros((n, n), dtype=dt, device=dev)  # noqa: E731
+    Lh, Ll = mk(), mk()
+    nsgb.ns_k_split(L, Lh, Ll, n, n, n, n)
+    D32, Dh, Dl = mk(torch.float32), mk(), mk()
+    prec = nsgb.NS_BF16X3 if a.precision == "bf16x3" else nsgb.NS_BF16
+
+    def call():
+        nsgb.ns_k_gemm_bf16(prec, n, n, n, Lh, Ll, n, Lh, Ll, n, -1.0, None, 0, 0.0, 1.0, D32, n, Dh, Dl, n,
+                            None, a.bn, a.cm)
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        call()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    passes = 3 if prec == nsgb.NS_BF16X3 else 1
+    print(json.dumps({"kernel": "k_gemm_tc", "n": n, "precision": a.precision, "bn": a.bn, "cm": a.cm,
+                      "ms_per_call": ms, "tflops_incl_call_overhead": passes * 2 * n ** 3 / (ms * 1e-3) / 1e12}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,7 +349,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-ns-iters", type=int, default=8)
     ap.add_argument("--ref-sweeps", type=int, default=9)
+    ap.add_argument("--kernel", default="", choices=["", "gemm"],
+                    help="microbenchmark one kernel instead of the solve")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3"])
+    ap.add_argument("--bn", type=int, default=256)
+    ap.add_argument("--cm", type=int, default=0)
     a = ap.parse_args()
+    if a.kernel == "gemm":
+        run_kernel_gemm(a)
+        return
     if a.warmup < 3 and a.impl == "ours":
         a.warmup = 3
     if a.impl == "reference":

@@ -70,11 +70,13 @@ typedef struct ns_options {
   int max_sweeps;      /* Richardson-only sweeps allowed after NS stops; default 200 */
   int use_updated_G;   /* 1: theta_{k+1} = theta_k + G_{k+1} r_k (ordering of eq. ttk1) */
   int profile;         /* 1: time each GEMM launch with CUDA events (ns_stats.gemm_ms) */
-  int gemm_bn;         /* 0: automatic; else 64, 128 or 256 output columns per tile */
+  int gemm_bn;         /* 0: automatic; else 64, 128, 192 or 256 output columns per tile */
   double timeout_s;    /* bound on every device-side wait; default 2 s */
   int aux_ahead;       /* composite only: 1 starts the auxiliary loops one step ahead,
                           T_i = NS_{m_i}(G0), so rates = {n} gives the double Newton-Schulz
                           method of Section 5.1 (eqs. gamk11-fks1); 0: T_i start at G0 */
+  int gemm_cluster;    /* CTAs per cluster sharing each R tile by TMA multicast: 0 automatic,
+                          1 none, 2 or 4 (with 192- or 256-column tiles) */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -174,11 +176,13 @@ ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int
  * be NULL.  Outputs (each may be NULL): D32 f32 (ldd32), Dhi/Dlo bf16 split of D
  * (ldd16), frob_out a device double receiving sum(D^2).  Leading dimensions of bf16
  * arrays must be multiples of 8 and of f32 arrays multiples of 4; base pointers
- * 16-byte aligned.  bn = 0 picks the tile width.  Returns NS_ERR_ARG on violations. */
+ * 16-byte aligned.  bn = 0 picks the tile width (64, 128, 192 or 256 columns);
+ * cluster_m = 0 picks how many CTAs (1, 2 or 4; 2 and 4 need bn >= 192) share each
+ * R tile through TMA multicast.  Returns NS_ERR_ARG on violations. */
 ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
-                         int64_t ldd16, double* frob_out, int bn, void* stream);
+                         int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream);
 
 /* FP64 product with the same epilogue: D = s L R + beta C + gamma I (C may be NULL). */
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,

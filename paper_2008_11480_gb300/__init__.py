@@ -60,6 +60,7 @@ class ns_options(ctypes.Structure):
         ("gemm_bn", ctypes.c_int),
         ("timeout_s", ctypes.c_double),
         ("aux_ahead", ctypes.c_int),
+        ("gemm_cluster", ctypes.c_int),
     ]
 
 
@@ -121,7 +122,7 @@ def lib() -> ctypes.CDLL:
         "ns_status_string": (ctypes.c_char_p, [_int]),
         "ns_k_split": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
         "ns_k_gemm_bf16": (_int, [_int, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, _vp, _i64,
-                                  ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, _int, _vp]),
+                                  ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, _int, _int, _vp]),
         "ns_k_gemm_f64": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
                                  ctypes.c_double, _vp, _i64, _vp, _vp]),
         "ns_k_resid": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
@@ -260,11 +261,12 @@ def ns_k_split(X: torch.Tensor, hi: torch.Tensor, lo: torch.Tensor, rows: int, c
 
 def ns_k_gemm_bf16(precision: int, M: int, N: int, K: int, Lhi, Llo, ldl: int, Rhi, Rlo, ldr: int, s: float = 1.0,
                    C=None, ldc: int = 0, beta: float = 0.0, gamma: float = 0.0, D32=None, ldd32: int = 0,
-                   Dhi=None, Dlo=None, ldd16: int = 0, frob_out=None, bn: int = 0, stream=None) -> None:
+                   Dhi=None, Dlo=None, ldd16: int = 0, frob_out=None, bn: int = 0, cluster_m: int = 0,
+                   stream=None) -> None:
     bf = torch.bfloat16
     r = lib().ns_k_gemm_bf16(precision, M, N, K, _ptr(Lhi, bf), _ptr(Llo, bf), ldl, _ptr(Rhi, bf), _ptr(Rlo, bf), ldr,
                              s, _ptr(C, torch.float32), ldc, beta, gamma, _ptr(D32, torch.float32), ldd32,
-                             _ptr(Dhi, bf), _ptr(Dlo, bf), ldd16, _ptr(frob_out), bn, _stream_ptr(stream))
+                             _ptr(Dhi, bf), _ptr(Dlo, bf), ldd16, _ptr(frob_out), bn, cluster_m, _stream_ptr(stream))
     _raise(r, "ns_k_gemm_bf16")
 
 

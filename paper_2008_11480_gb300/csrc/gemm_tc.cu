@@ -16,11 +16,25 @@
 // The accumulator is double-buffered in TMEM (2 x BN columns), so the
 // epilogue of tile i overlaps the MMAs of tile i+1.
 //
+// Clusters (CM = 2 or 4 CTAs along M): the CM CTAs of a cluster compute the
+// tiles (m, n) ... (m + CM - 1, n), which share their R tile.  Each CTA loads
+// its own L tile and 1/CM of the R tile, multicast into every CTA of the
+// cluster, so each SM pulls 16 + 32/CM KiB per stage from L2 instead of 48.
+// A stage may be refilled only when all CM CTAs have consumed it: every MMA
+// commit arrives on the `empty` barrier of all CTAs (count CM).
+//
 // Shared-memory layouts (both 128-byte swizzled, atoms of 8 rows x 128 B):
 //   L tile 128 x 64 (K-major):  row r at r*128 B; MMA K-slice k at +32k B.
 //   R tile 64 x BN (N-major):   BN/64 chunks of 64 K-rows x 64 N-columns,
 //                               chunk j at j*8 KiB (LBO), 8-row groups at 1 KiB
 //                               (SBO); MMA K-slice k at +2 KiB*k.
+//
+// Split products (X3): one stage holds all four operand parts of a 32-deep K
+// slice -- L_hi, L_lo (128 x 32 each, 64-byte swizzle, 8-row atoms of 512 B)
+// and R_hi, R_lo (32 x BN each: BN/64 chunks of 32 K-rows x 128 B at 4 KiB) --
+// and issues the 6 products L_hi R_hi, L_hi R_lo, L_lo R_hi of its two K=16
+// slices.  Same bytes per stage as one plain pass, 1.5x the tensor work, so
+// the ring covers 1.5x more load latency and L2 is read 1/3 less per product.
 #include <cstdio>
 
 #include "internal.h"
@@ -34,26 +48,29 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr int kThreads = 192;
 
+constexpr uint32_t pow2_cols(int c) { return c <= 32 ? 32u : (c <= 64 ? 64u : (c <= 128 ? 128u : (c <= 256 ? 256u : 512u))); }
+
 template <int BN>
 struct TcCfg {
   static constexpr int kABytes = kBM * kBK * 2;  // 16 KiB
   static constexpr int kBBytes = BN * kBK * 2;   // BN * 128 B
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = BN == 256 ? 4 : (BN == 128 ? 6 : 8);
-  static constexpr uint32_t kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
+  static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
+  static constexpr uint32_t kTmemCols = pow2_cols(2 * BN);
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
 };
 
-__device__ __forceinline__ void decode_tile(const TcParams& p, int t, int& pi, int& m0, int& n0, int BN) {
+// Work item w of this CTA (cluster rank `rank`): problem, tile row and column.
+__device__ __forceinline__ void decode_item(const TcParams& p, int w, int rank, int CM, int& pi, int& mt, int& nt) {
   pi = 0;
 #pragma unroll 1
   for (int i = 1; i < p.nprob; ++i)
-    if (t >= p.prob[i].tile_begin) pi = i;
+    if (w >= p.prob[i].tile_begin) pi = i;
   const TcProblem& P = p.prob[pi];
-  const int local = t - P.tile_begin;
-  m0 = (local / P.tiles_n) * kBM;
-  n0 = (local % P.tiles_n) * BN;
+  const int local = w - P.tile_begin;
+  mt = (local / P.tiles_n) * CM + rank;
+  nt = local % P.tiles_n;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -61,9 +78,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int BN>
+template <int BN, int CM, bool X3>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
   using Cfg = TcCfg<BN>;
+  const int rank = CM > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int first = blockIdx.x / CM;   // this cluster's first work item
+  const int stride = gridDim.x / CM;   // clusters in the grid
+  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CM) - 1u);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -83,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CM);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -100,6 +121,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   }
   tc_fence_before();
   __syncthreads();
+  // no CTA of the cluster may multicast into a peer before its barriers exist
+  if (CM > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const uint64_t tlim = p.timeout_ns;
@@ -120,18 +143,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     uint32_t phase = 0;
     int it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-      int pi, m0, n0;
-      decode_tile(p, t, pi, m0, n0, BN);
+    for (int w = first; w < p.total_tiles && ok; w += stride) {
+      int pi, mt, nt;
+      decode_item(p, w, rank, CM, pi, mt, nt);
       const TcProblem& P = p.prob[pi];
-      const int nkb = (P.K + kBK - 1) / kBK;
+      const int m0 = mt * kBM, n0 = nt * BN;
+      const int kstep = X3 ? kBK / 2 : kBK;
+      const int nkb = (P.K + kstep - 1) / kstep;
+      const int npass = X3 ? 1 : p.npass;
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        for (int ps = 0; ps < p.npass; ++ps) {
+        for (int ps = 0; ps < npass; ++ps) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, tlim, abort_flag)) {
             ok = false;
             break;
           }
-          if (it != p.debug_stall_iter) {
+          if (X3 && it != p.debug_stall_iter) {
+            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+            armed[stage] = static_cast<int>(phase);
+            uint8_t* a = sA + stage * Cfg::kABytes;
+            uint8_t* b = sB + stage * Cfg::kBBytes;
+            const int x = kb * (kBK / 2);
+            tma_load_2d(a, &P.L[0], &full[stage], x, m0);
+            tma_load_2d(a + 4096, &P.L[0], &full[stage], x, m0 + 64);
+            tma_load_2d(a + 8192, &P.L[1], &full[stage], x, m0);
+            tma_load_2d(a + 12288, &P.L[1], &full[stage], x, m0 + 64);
+#pragma unroll
+            for (int j = 0; j < 2 * (BN / 64); ++j) {
+              const int part = j / (BN / 64), c = j % (BN / 64);
+              uint8_t* dst = b + part * (BN * 64) + c * 4096;
+              if (CM == 1)
+                tma_load_2d(dst, &P.R[part], &full[stage], n0 + 64 * c, x);
+              else if (j % CM == rank)
+                tma_load_2d_mc(dst, &P.R[part], &full[stage], n0 + 64 * c, x, kMask);
+            }
+          } else if (!X3 && it != p.debug_stall_iter) {
             const CUtensorMap* ml = &P.L[ps == 2 ? 1 : 0];
             const CUtensorMap* mr = &P.R[ps == 1 ? 1 : 0];
             mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
@@ -141,7 +186,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             tma_load_2d(a, ml, &full[stage], kb * kBK, m0);
             tma_load_2d(a + 8192, ml, &full[stage], kb * kBK, m0 + 64);
 #pragma unroll
-            for (int j = 0; j < BN / 64; ++j) tma_load_2d(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK);
+            for (int j = 0; j < BN / 64; ++j) {
+              if (CM == 1)
+                tma_load_2d(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK);
+              else if (j % CM == rank)
+                tma_load_2d_mc(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK, kMask);
+            }
           }
           ++it;
           if (++stage == Cfg::kStages) {
@@ -168,11 +218,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     uint32_t acc_phase = 0;
     bool ok = true;
     bool issued = false;
-    for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-      int pi, m0, n0;
-      decode_tile(p, t, pi, m0, n0, BN);
+    for (int w = first; w < p.total_tiles && ok; w += stride) {
+      int pi, mt, nt;
+      decode_item(p, w, rank, CM, pi, mt, nt);
       const TcProblem& P = p.prob[pi];
-      const int nkb = (P.K + kBK - 1) / kBK;
+      const int kstep = X3 ? kBK / 2 : kBK;
+      const int nkb = (P.K + kstep - 1) / kstep;
+      const int npass = X3 ? 1 : p.npass;
       if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, tlim, abort_flag)) {
         ok = false;
         break;
@@ -181,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
       uint32_t accumulate = 0;
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        for (int ps = 0; ps < p.npass; ++ps) {
+        for (int ps = 0; ps < npass; ++ps) {
           if (!mbar_wait(&full[stage], phase, tlim, abort_flag)) {
             ok = false;
             break;
@@ -189,15 +241,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           tc_fence_after();
           const uint32_t a_base = smem_u32(sA + stage * Cfg::kABytes);
           const uint32_t b_base = smem_u32(sB + stage * Cfg::kBBytes);
+          if (X3) {
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) {
-            const uint64_t ad = make_sdesc(a_base + 32u * k, 16u, 1024u);
-            const uint64_t bd = make_sdesc(b_base + 2048u * k, 8192u, 1024u);
-            tc_mma_bf16(d_tmem, ad, bd, idesc, accumulate);
-            accumulate = 1;
+            for (int k = 0; k < 2; ++k) {
+              const uint64_t ah = make_sdesc(a_base + 32u * k, 16u, 512u, kSwz64);
+              const uint64_t al = make_sdesc(a_base + 8192u + 32u * k, 16u, 512u, kSwz64);
+              const uint64_t bh = make_sdesc(b_base + 2048u * k, 4096u, 1024u);
+              const uint64_t bl = make_sdesc(b_base + static_cast<uint32_t>(BN * 64) + 2048u * k, 4096u, 1024u);
+              tc_mma_bf16(d_tmem, ah, bh, idesc, accumulate);
+              accumulate = 1;
+              tc_mma_bf16(d_tmem, ah, bl, idesc, 1u);
+              tc_mma_bf16(d_tmem, al, bh, idesc, 1u);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+              const uint64_t ad = make_sdesc(a_base + 32u * k, 16u, 1024u);
+              const uint64_t bd = make_sdesc(b_base + 2048u * k, 8192u, 1024u);
+              tc_mma_bf16(d_tmem, ad, bd, idesc, accumulate);
+              accumulate = 1;
+            }
           }
           issued = true;
-          tc_commit(&empty[stage]);
+          if (CM == 1)
+            tc_commit(&empty[stage]);
+          else
+            tc_commit_mc(&empty[stage], kMask);
           if (++stage == Cfg::kStages) {
             stage = 0;
             phase ^= 1u;
@@ -226,10 +295,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
-      int pi, m0, n0;
-      decode_tile(p, t, pi, m0, n0, BN);
+    for (int w = first; w < p.total_tiles; w += stride) {
+      int pi, mt, nt;
+      decode_item(p, w, rank, CM, pi, mt, nt);
       const TcProblem& P = p.prob[pi];
+      const int m0 = mt * kBM, n0 = nt * BN;
       bool ok = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -324,11 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
-      if (P.frob_partials != nullptr) {
+      if (P.frob_partials != nullptr && mt < P.tiles_m) {
         double f = static_cast<double>(frob);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-        if (lane == 0) P.frob_partials[(t - P.tile_begin) * 4 + q] = f;
+        if (lane == 0) P.frob_partials[(mt * P.tiles_n + nt) * 4 + q] = f;
       }
       if (++acc == 2) {
         acc = 0;
@@ -343,37 +413,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
+  // peers may still arrive on this CTA's barriers until they are done too
+  if (CM > 1) cluster_sync_all();
 }
 
-template <int BN>
+template <int BN, int CM, bool X3>
 cudaError_t launch_bn(const TcParams& p, int num_sms, cudaStream_t s) {
   using Cfg = TcCfg<BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  static int max_clusters = -1;
+  if (max_clusters < 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, CM, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    max_clusters = num_sms;
+    if (CM > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CM;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(CM * (num_sms / CM));
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = Cfg::kSmem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN, CM, X3>, &cfg);
+      if (e != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = num_sms / CM;
+      }
+      max_clusters = n;
+    }
   }
-  const int grid = p.total_tiles < num_sms ? p.total_tiles : num_sms;
-  if (grid <= 0) return cudaSuccess;
-  k_gemm_tc<BN><<<grid, kThreads, Cfg::kSmem, s>>>(p);
-  return cudaGetLastError();
+  const int clusters = p.total_tiles < max_clusters ? p.total_tiles : max_clusters;
+  if (clusters <= 0) return cudaSuccess;
+  if (CM == 1) {
+    k_gemm_tc<BN, 1, X3><<<clusters, kThreads, Cfg::kSmem, s>>>(p);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CM;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(clusters * CM);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = Cfg::kSmem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN, CM, X3>, p);
 }
 
 }  // namespace
 
 int tc_tiles(int M, int N, int BN) { return ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN); }
 
-cudaError_t launch_gemm_tc(const TcParams& p, int BN, int num_sms, cudaStream_t s) {
-  switch (BN) {
-    case 64:
-      return launch_bn<64>(p, num_sms, s);
-    case 128:
-      return launch_bn<128>(p, num_sms, s);
-    case 256:
-      return launch_bn<256>(p, num_sms, s);
-    default:
-      return cudaErrorInvalidValue;
+int tc_items(int M, int N, int BN, int CM) {
+  const int tiles_m = (M + kBM - 1) / kBM;
+  return ((tiles_m + CM - 1) / CM) * ((N + BN - 1) / BN);
+}
+
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s) {
+  const int key = BN * 10 + CM;
+  if (x3) {
+    switch (key) {
+      case 641: return launch_bn<64, 1, true>(p, num_sms, s);
+      case 1281: return launch_bn<128, 1, true>(p, num_sms, s);
+      case 2561: return launch_bn<256, 1, true>(p, num_sms, s);
+      case 2562: return launch_bn<256, 2, true>(p, num_sms, s);
+      case 2564: return launch_bn<256, 4, true>(p, num_sms, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (key) {
+    case 641: return launch_bn<64, 1, false>(p, num_sms, s);
+    case 1281: return launch_bn<128, 1, false>(p, num_sms, s);
+    case 1921: return launch_bn<192, 1, false>(p, num_sms, s);
+    case 1922: return launch_bn<192, 2, false>(p, num_sms, s);
+    case 1924: return launch_bn<192, 4, false>(p, num_sms, s);
+    case 2561: return launch_bn<256, 1, false>(p, num_sms, s);
+    case 2562: return launch_bn<256, 2, false>(p, num_sms, s);
+    case 2564: return launch_bn<256, 4, false>(p, num_sms, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -395,17 +519,20 @@ EncodeFn get_encode() {
 }
 }  // namespace
 
-bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld) {
+bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int role) {
   EncodeFn enc = get_encode();
   if (enc == nullptr) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 2) % 16 != 0) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * 2)};
-  cuuint32_t box[2] = {64, 64};
+  // role 0: 64 x 64 box, 128-byte swizzle (either operand, one product pass)
+  // role 1: 32 (K) x 64 (rows) box, 64-byte swizzle (L operand of split products)
+  // role 2: 64 (N) x 32 (K) box, 128-byte swizzle (R operand of split products)
+  cuuint32_t box[2] = {role == 1 ? 32u : 64u, role == 2 ? 32u : 64u};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, role == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

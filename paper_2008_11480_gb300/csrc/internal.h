@@ -25,34 +25,43 @@ struct TcProblem {
   CUtensorMap L[2];
   CUtensorMap R[2];
   int M, N, K;
+  int tiles_m;     // ceil(M / 128)
   int tiles_n;     // ceil(N / BN)
-  int tile_begin;  // first global tile index of this problem
-  int tile_count;
+  int tile_begin;  // first global work item of this problem (a work item is
+                   // CM vertically adjacent tiles, one per CTA of a cluster)
+  int tile_count;  // work items of this problem
+  
   float s, beta, gamma;
   int ldc, ldd32, ldd16;
   const float* C;
   float* D32;
   bf16* Dhi;
   bf16* Dlo;
-  double* frob_partials;  // tile_count * 4 values
+  double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4)
 };
 
 struct TcParams {
   TcProblem prob[kTcMaxProblems];
   int nprob;
-  int total_tiles;
+  int total_tiles;  // work items over all problems
   int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3)
   int debug_stall_iter;  // -1 for none; else the producer withholds that load
   unsigned long long timeout_ns;
   int* err;
 };
 
-// Launch a grouped tcgen05 GEMM; BN in {64, 128, 256}.
-cudaError_t launch_gemm_tc(const TcParams& p, int BN, int num_sms, cudaStream_t s);
+// Launch a grouped tcgen05 GEMM: BN in {64, 128, 192, 256} output columns per
+// tile, CM in {1, 2, 4} CTAs per cluster along M (2 and 4 only with BN 192/256).
+// x3 selects the split-product kernel (L/R maps of roles 1/2 below; BN 64, 128
+// or 256; p.npass ignored); otherwise p.npass passes over role-0 maps.
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
+int tc_items(int M, int N, int BN, int CM);
 
 // Encode a 2-D bf16 tensor map (rows x cols, leading dimension ld elements).
-bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld);
+// role 0: 64x64 box, 128 B swizzle; role 1: 32(K)x64 box, 64 B swizzle (L of
+// split products); role 2: 64x32(K) box, 128 B swizzle (R of split products).
+bool encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int role = 0);
 
 // ---- FP64 CUDA-core GEMM with the same epilogue (plain FP64 path)
 struct F64Gemm {

@@ -35,7 +35,9 @@ struct MpMat {
   float* m32 = nullptr;
   bf16* hi = nullptr;
   bf16* lo = nullptr;
-  CUtensorMap map_hi, map_lo;
+  CUtensorMap map_hi, map_lo;    // one-pass products (either operand)
+  CUtensorMap l3_hi, l3_lo;      // split products, as the L operand
+  CUtensorMap r3_hi, r3_lo;      // split products, as the R operand
 };
 
 struct GemmSpec {
@@ -143,8 +145,10 @@ ns_status alloc_mp(ns_ctx* ctx, MpMat& m, bool with32) {
   if (with32) NS_TRY(alloc(ctx, &m.m32, cnt));
   NS_TRY(alloc(ctx, &m.hi, cnt));
   NS_TRY(alloc(ctx, &m.lo, cnt));
-  if (!encode_bf16_map(&m.map_hi, m.hi, ctx->ld, ctx->ld, ctx->ld) ||
-      !encode_bf16_map(&m.map_lo, m.lo, ctx->ld, ctx->ld, ctx->ld))
+  const int64_t ld = ctx->ld;
+  if (!encode_bf16_map(&m.map_hi, m.hi, ld, ld, ld, 0) || !encode_bf16_map(&m.map_lo, m.lo, ld, ld, ld, 0) ||
+      !encode_bf16_map(&m.l3_hi, m.hi, ld, ld, ld, 1) || !encode_bf16_map(&m.l3_lo, m.lo, ld, ld, ld, 1) ||
+      !encode_bf16_map(&m.r3_hi, m.hi, ld, ld, ld, 2) || !encode_bf16_map(&m.r3_lo, m.lo, ld, ld, ld, 2))
     return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return NS_OK;
 }
@@ -267,29 +271,52 @@ void ev_collect(ns_ctx* ctx) {
   cudaGetLastError();
 }
 
-int pick_bn(const ns_ctx* ctx, int nprob) {
-  if (ctx->opt.gemm_bn == 64 || ctx->opt.gemm_bn == 128 || ctx->opt.gemm_bn == 256) return ctx->opt.gemm_bn;
+// Tile width and cluster size for n x n products, nprob of them in one launch:
+// maximise (filled fraction of the last wave) x (useful columns) x (relative
+// efficiency of the tile shape, which falls with the L2 bytes per flop).
+void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
   const int n = static_cast<int>(ctx->n);
-  const int bns[3] = {256, 128, 64};
-  const double eff[3] = {1.0, 0.93, 0.80};
-  int best = 256;
-  double best_e = -1.0;
-  for (int i = 0; i < 3; ++i) {
-    const int tiles = nprob * tc_tiles(n, n, bns[i]);
-    const int waves = (tiles + ctx->num_sms - 1) / ctx->num_sms;
-    const double e = static_cast<double>(tiles) / (static_cast<double>(waves) * ctx->num_sms) * eff[i];
-    if (e > best_e + 1e-9) {
-      best_e = e;
-      best = bns[i];
+  const int tiles_m = (n + 127) / 128;
+  auto cm_for = [&](int bn) {
+    if (ctx->opt.gemm_cluster == 1 || bn < 192) return 1;
+    if (ctx->opt.gemm_cluster == 2 || ctx->opt.gemm_cluster == 4)
+      return tiles_m % ctx->opt.gemm_cluster == 0 ? ctx->opt.gemm_cluster : 1;
+    // two CTAs per cluster measured best at n = 4096: four-CTA clusters
+    // leave SMs idle (fewer co-resident clusters)
+    if (tiles_m % 2 == 0) return 2;
+    return 1;
+  };
+  const int fixed = ctx->opt.gemm_bn;
+  const int bns[4] = {256, 192, 128, 64};
+  const double shape_eff[4] = {1.0, 0.92, 0.80, 0.65};
+  int best_bn = 256, best_cm = 1;
+  double best = -1.0;
+  for (int i = 0; i < 4; ++i) {
+    const int bn = bns[i];
+    if (fixed != 0 && bn != fixed) continue;
+    const int cm = cm_for(bn);
+    const int items = nprob * tc_items(n, n, bn, cm);
+    const int slots = std::max(1, ctx->num_sms / cm);
+    const int waves = (items + slots - 1) / slots;
+    const double fill = static_cast<double>(items) / (static_cast<double>(waves) * slots);
+    const double cols = static_cast<double>(n) / (static_cast<double>((n + bn - 1) / bn) * bn);
+    const double e = fill * cols * shape_eff[i] * (cm == 1 ? 0.93 : 1.0);
+    if (e > best + 1e-9) {
+      best = e;
+      best_bn = bn;
+      best_cm = cm;
     }
   }
-  return best;
+  *bn_out = best_bn;
+  *cm_out = best_cm;
 }
 
 // One grouped tcgen05 launch of up to kTcMaxProblems products of n x n matrices.
 ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   const int n = static_cast<int>(ctx->n);
-  const int bn = pick_bn(ctx, nspec);
+  int bn = 256, cm = 1;
+  pick_tile(ctx, nspec, &bn, &cm);
+  const bool x3 = prec == NS_BF16X3 && bn != 192;
   TcParams p;
   memset(&p, 0, sizeof(p));
   p.nprob = nspec;
@@ -303,17 +330,26 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   for (int i = 0; i < nspec; ++i) {
     const GemmSpec& g = specs[i];
     TcProblem& P = p.prob[i];
-    P.L[0] = g.L->map_hi;
-    P.L[1] = g.L->map_lo;
-    P.R[0] = g.R->map_hi;
-    P.R[1] = g.R->map_lo;
+    if (x3) {
+      P.L[0] = g.L->l3_hi;
+      P.L[1] = g.L->l3_lo;
+      P.R[0] = g.R->r3_hi;
+      P.R[1] = g.R->r3_lo;
+    } else {
+      P.L[0] = g.L->map_hi;
+      P.L[1] = g.L->map_lo;
+      P.R[0] = g.R->map_hi;
+      P.R[1] = g.R->map_lo;
+    }
     P.M = n;
     P.N = n;
     P.K = n;
+    P.tiles_m = (n + 127) / 128;
     P.tiles_n = (n + bn - 1) / bn;
     P.tile_begin = tile;
-    P.tile_count = tc_tiles(n, n, bn);
+    P.tile_count = tc_items(n, n, bn, cm);
     tile += P.tile_count;
+    const int ntiles = tc_tiles(n, n, bn);
     P.s = g.s;
     P.beta = g.beta;
     P.gamma = g.gamma;
@@ -325,11 +361,11 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
     P.Dlo = g.D->lo;
     P.ldd16 = static_cast<int>(ctx->ld);
     if (g.frob_dst != nullptr) {
-      if (poff + static_cast<size_t>(P.tile_count) * 4 > ctx->partials_cap)
+      if (poff + static_cast<size_t>(ntiles) * 4 > ctx->partials_cap)
         return fail(ctx, NS_ERR_ARG, "partials workspace too small");
       P.frob_partials = ctx->partials + poff;
-      reduces.emplace_back(g.frob_dst, P.tile_count * 4);
-      poff += static_cast<size_t>(P.tile_count) * 4;
+      reduces.emplace_back(g.frob_dst, ntiles * 4);
+      poff += static_cast<size_t>(ntiles) * 4;
     }
     if (ctx->st) {
       const double f = 2.0 * n * static_cast<double>(n) * n * p.npass;
@@ -339,7 +375,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   }
   p.total_tiles = tile;
   EventPair* e = ev_begin(ctx, true);
-  NS_CK(launch_gemm_tc(p, bn, ctx->num_sms, ctx->stream));
+  NS_CK(launch_gemm_tc(p, bn, cm, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
   ctx->launches++;
   if (ctx->st) {
@@ -879,6 +915,7 @@ void ns_default_options(ns_options* o) {
   o->gemm_bn = 0;
   o->timeout_s = 2.0;
   o->aux_ahead = 0;
+  o->gemm_cluster = 0;
 }
 
 const char* ns_status_string(ns_status s) {
@@ -1129,7 +1166,7 @@ ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int
 ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
-                         int64_t ldd16, double* frob_out, int bn, void* stream) {
+                         int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream) {
   if (precision != NS_BF16 && precision != NS_BF16X3) return NS_ERR_ARG;
   if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
   if (!Lhi || !Rhi || (precision == NS_BF16X3 && (!Llo || !Rlo))) return NS_ERR_ARG;
@@ -1140,7 +1177,12 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   if ((Dhi || Dlo) && (ldd16 < N || ldd16 % 8)) return NS_ERR_ARG;
   if ((Dhi && !al16(Dhi)) || (Dlo && !al16(Dlo)) || (Dlo && !Dhi)) return NS_ERR_ARG;
   if (bn == 0) bn = N >= 2048 ? 256 : (N > 64 ? 128 : 64);
-  if (bn != 64 && bn != 128 && bn != 256) return NS_ERR_ARG;
+  if (bn != 64 && bn != 128 && bn != 192 && bn != 256) return NS_ERR_ARG;
+  const int tiles_m = static_cast<int>((M + 127) / 128);
+  if (cluster_m == 0) cluster_m = bn < 192 ? 1 : (tiles_m % 2 == 0 ? 2 : 1);
+  if (precision == NS_BF16X3 && bn == 192 && cluster_m > 1) cluster_m = 1;
+  if (cluster_m != 1 && cluster_m != 2 && cluster_m != 4) return NS_ERR_ARG;
+  if (cluster_m > 1 && bn < 192) return NS_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1152,8 +1194,12 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   p.debug_stall_iter = -1;
   p.timeout_ns = 2000000000ull;
   TcProblem& P = p.prob[0];
-  if (!encode_bf16_map(&P.L[0], Lhi, M, K, ldl) || !encode_bf16_map(&P.R[0], Rhi, K, N, ldr)) return NS_ERR_ARG;
-  if (p.npass == 3 && (!encode_bf16_map(&P.L[1], Llo, M, K, ldl) || !encode_bf16_map(&P.R[1], Rlo, K, N, ldr)))
+  const bool x3 = p.npass == 3 && bn != 192;
+  const int lr = x3 ? 1 : 0, rr = x3 ? 2 : 0;
+  if (!encode_bf16_map(&P.L[0], Lhi, M, K, ldl, lr) || !encode_bf16_map(&P.R[0], Rhi, K, N, ldr, rr))
+    return NS_ERR_ARG;
+  if (p.npass == 3 &&
+      (!encode_bf16_map(&P.L[1], Llo, M, K, ldl, lr) || !encode_bf16_map(&P.R[1], Rlo, K, N, ldr, rr)))
     return NS_ERR_ARG;
   if (p.npass == 1) {
     P.L[1] = P.L[0];
@@ -1162,9 +1208,11 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   P.M = static_cast<int>(M);
   P.N = static_cast<int>(N);
   P.K = static_cast<int>(K);
+  P.tiles_m = tiles_m;
   P.tiles_n = static_cast<int>((N + bn - 1) / bn);
   P.tile_begin = 0;
-  P.tile_count = tc_tiles(P.M, P.N, bn);
+  P.tile_count = tc_items(P.M, P.N, bn, cluster_m);
+  const int ntiles = tc_tiles(P.M, P.N, bn);
   P.s = s;
   P.beta = beta;
   P.gamma = gamma;
@@ -1177,7 +1225,7 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   P.ldd16 = static_cast<int>(ldd16);
   p.total_tiles = P.tile_count;
   void* scratch = nullptr;
-  const size_t scratch_bytes = sizeof(int) * 4 + (frob_out ? sizeof(double) * P.tile_count * 4 : 0);
+  const size_t scratch_bytes = sizeof(int) * 4 + (frob_out ? sizeof(double) * ntiles * 4 : 0);
   if (cudaMallocAsync(&scratch, scratch_bytes + 256, st) != cudaSuccess) {
     cudaGetLastError();
     return NS_ERR_OOM;
@@ -1185,8 +1233,8 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   cudaMemsetAsync(scratch, 0, sizeof(int) * 4, st);
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
-  cudaError_t e = launch_gemm_tc(p, bn, sms, st);
-  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, P.tile_count * 4, 1, frob_out, st);
+  cudaError_t e = launch_gemm_tc(p, bn, cluster_m, x3, sms, st);
+  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * 4, 1, frob_out, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(scratch, st);

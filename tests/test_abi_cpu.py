@@ -100,11 +100,16 @@ def test_kernel_entry_points_validate_before_launch(L):
     # wrong precision, non-positive sizes and unaligned leading dimensions are
     # rejected on the host
     assert L.ns_k_gemm_bf16(7, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0, None, None, 0,
-                            None, 0, None) == nsgb.NS_ERR_ARG
+                            None, 0, 0, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 0, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
-                            None, None, 0, None, 0, None) == nsgb.NS_ERR_ARG
+                            None, None, 0, None, 0, 0, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 60, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
-                            None, None, 0, None, 0, None) == nsgb.NS_ERR_ARG
+                            None, None, 0, None, 0, 0, None) == nsgb.NS_ERR_ARG
+    # cluster sizes other than 1, 2, 4, and clusters with narrow tiles, are rejected
+    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
+                            None, None, 0, None, 256, 3, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
+                            None, None, 0, None, 128, 2, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_resid(None, 4, None, None, None, 4, 1, None, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_update(16, 2, 4, 16, 16, 4, 1, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_split(16, 3, 4, 4, 4, 16, 16, 8, None) == nsgb.NS_ERR_ARG

@@ -60,7 +60,7 @@ def test_split_bit_exact(rows, cols):
     assert not torch.any(hi[:, cols:].float() != 0)
 
 
-def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0, scale=1.0):
+def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0, scale=1.0, cm=0):
     L = rnd((M, K), seed, scale)
     R = rnd((K, N), seed + 1, scale)
     C = rnd((M, N), seed + 2) if with_c else None
@@ -73,7 +73,7 @@ def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0
     Dl = torch.zeros((M, ldd), dtype=torch.bfloat16, device=dev)
     fro = torch.zeros(1, dtype=torch.float64, device=dev)
     nsgb.ns_k_gemm_bf16(prec, M, N, K, Lh, Ll, ldl, Rh, Rl, ldr, s, Cd, ldd if with_c else 0, beta, gamma,
-                        D32, ldd, Dh, Dl, ldd, fro, bn)
+                        D32, ldd, Dh, Dl, ldd, fro, bn, cm)
     torch.cuda.synchronize()
     pname = "bf16" if prec == nsgb.NS_BF16 else "bf16x3"
     prod = O.split_product(L, R, pname)
@@ -108,6 +108,15 @@ def test_gemm_tc_tile_widths(prec, bn):
     run_gemm(prec, 390, 520, 200, seed=11, bn=bn)
 
 
+@pytest.mark.parametrize("bn,cm", [(192, 1), (192, 2), (192, 4), (256, 2), (256, 4)])
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+@pytest.mark.parametrize("M,N,K", [(512, 520, 200), (300, 400, 129), (1024, 1024, 1024)])
+def test_gemm_tc_clusters(prec, bn, cm, M, N, K):
+    """Cluster variants: the R tile is shared by TMA multicast among cm CTAs;
+    M = 300 leaves cluster ranks whose tile row lies past the matrix."""
+    run_gemm(prec, M, N, K, seed=M + bn + cm, bn=bn, cm=cm, s=-1.0, gamma=1.0, scale=0.05)
+
+
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 def test_gemm_tc_residual_epilogue(prec):
     """F = I - A G form: s = -1, gamma = 1 on a square problem."""
@@ -131,7 +140,7 @@ def test_gemm_tc_full_size_sampled():
     Rh, Rl = gpu_split(R, n)
     D32 = torch.zeros((n, n), dtype=torch.float32, device=dev)
     nsgb.ns_k_gemm_bf16(nsgb.NS_BF16X3, n, n, n, Lh, Ll, n, Rh, Rl, n, -1.0, None, 0, 0.0, 1.0, D32, n,
-                        None, None, 0, None, 256)
+                        None, None, 0, None, 256, 4)
     torch.cuda.synchronize()
     idx = rng.integers(0, n, (96, 2))
     idx[:8, 1] = idx[:8, 0]   # include diagonal entries (identity term)
