@@ -172,7 +172,7 @@ ns_status ensure_common(ns_ctx* ctx, int nrhs) {
     // tiles, residual blocks x nrhs, norm blocks
     const int n = static_cast<int>(ctx->n);
     size_t need = std::max<size_t>(static_cast<size_t>(tc_tiles(n, n, 64)) * 4, f64_tiles(n, n));
-    need = std::max<size_t>(need, static_cast<size_t>(resid_blocks(n)) * cap);
+    need = std::max<size_t>(need, static_cast<size_t>(std::max(resid_blocks(n), resid_x2_blocks(n))) * cap);
     need = std::max<size_t>(need, 2 * static_cast<size_t>((n + 7) / 8) + 2);
     if (need > ctx->partials_cap) {
       NS_TRY(alloc(ctx, &ctx->partials, need));
@@ -1336,7 +1336,7 @@ ns_status ns_k_resid_x2(const float* a1, const float* a2, int64_t ld, const doub
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ni = static_cast<int>(n);
   const int64_t ldt = round_up(n, 4);
-  const int nb = resid_blocks(ni);
+  const int nb = resid_x2_blocks(ni);
   const size_t limb = static_cast<size_t>(ldt) * nrhs;
   void* scratch = nullptr;
   const size_t bytes = sizeof(float) * 3 * limb + sizeof(double) * nb * nrhs + 64;

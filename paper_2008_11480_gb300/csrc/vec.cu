@@ -567,7 +567,48 @@ __global__ void __launch_bounds__(256) k_prep_a(const double* __restrict__ A, in
   if (row < n) {
     const double* p = A + static_cast<int64_t>(row) * lda;
     const int64_t o = static_cast<int64_t>(row) * ld;
-    for (int k = lane; k < n; k += 32) {
+    int kbeg = 0;
+    // 16-byte vector path: four double pairs per lane in flight (needs even
+    // lda and ld and a 16-byte aligned A)
+    if ((lda & 1) == 0 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+      const int n2 = n & ~1;
+      for (int k0 = 2 * lane; k0 < n2; k0 += 256) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 64 * u;
+          v[u] = k < n2 ? __ldcs(reinterpret_cast<const double2*>(p + k)) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 64 * u;
+          if (k >= n2) continue;
+          const double e[2] = {v[u].x, v[u].y};
+          float f1[2], f2[2];
+          bf16 h[2], l[2];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            s += e[t] * e[t];
+            a += fabs(e[t]);
+            f1[t] = static_cast<float>(e[t]);
+            f2[t] = static_cast<float>(e[t] - static_cast<double>(f1[t]));
+            h[t] = __float2bfloat16_rn(f1[t]);
+            l[t] = __float2bfloat16_rn(f1[t] - __bfloat162float(h[t]));
+          }
+          *reinterpret_cast<float2*>(a1 + o + k) = make_float2(f1[0], f1[1]);
+          *reinterpret_cast<float2*>(a2 + o + k) = make_float2(f2[0], f2[1]);
+          __nv_bfloat162 hh, ll;
+          hh.x = h[0];
+          hh.y = h[1];
+          ll.x = l[0];
+          ll.y = l[1];
+          *reinterpret_cast<__nv_bfloat162*>(hi + o + k) = hh;
+          *reinterpret_cast<__nv_bfloat162*>(lo + o + k) = ll;
+        }
+      }
+      kbeg = n2;
+    }
+    for (int k = kbeg + lane; k < n; k += 32) {
       const double v = p[k];
       s += v * v;
       a += fabs(v);
@@ -612,35 +653,85 @@ __global__ void k_split_theta(const double* __restrict__ Th, int n, int nrhs, fl
   }
 }
 
+// Lane reduction of a paired-f32 value (hi, lo) across the warp with TwoSum at
+// every step, so the ~48-bit partial sums stay ~48-bit (FP64 instructions are
+// rate-limited on this GPU; this uses the f32 pipes and shuffles only).
+__device__ __forceinline__ void warp_sum_x2(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = hi + oh;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (oh - bb);
+    const float l = lo + ol + err;
+    hi = s + l;  // renormalise (FastTwoSum; |s| >= |l|)
+    lo = l - (hi - s);
+  }
+}
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Residual and update kernels: a block of 256 threads covers 8 rows; warp w
+// takes the row pair (w & 3) and the half (w >> 2) of the k range (128-column
+// steps interleaved), so 4096 warps are in flight at n = 4096.  The two halves
+// meet in shared memory.
+constexpr int kXRows = 8;
+
 // R = B - A Theta from the f32 limbs; also R32T[c][row] = RN32(R) (the
-// operand of the update) and per-block partial sums of R^2.  Rows are
-// 16-byte aligned (ld % 4 == 0), lanes stride k by 4.
+// operand of the update) and per-block partial sums of R^2.  ld % 4 == 0.
 template <int NR>
-__global__ void __launch_bounds__(256) k_resid_x2(const float* __restrict__ A1, const float* __restrict__ A2,
-                                                  int64_t ld, const float* __restrict__ T1,
-                                                  const float* __restrict__ T2, int64_t ldt,
-                                                  const double* __restrict__ B, double* __restrict__ R,
-                                                  float* __restrict__ R32T, int n, int nrhs, int c0,
-                                                  double* __restrict__ partials) {
-  __shared__ double sq[kWarps][NR];
+__global__ void __launch_bounds__(256, 3) k_resid_x2(const float* __restrict__ A1, const float* __restrict__ A2,
+                                                     int64_t ld, const float* __restrict__ T1,
+                                                     const float* __restrict__ T2, int64_t ldt,
+                                                     const double* __restrict__ B, double* __restrict__ R,
+                                                     float* __restrict__ R32T, int n, int nrhs, int c0,
+                                                     double* __restrict__ partials) {
+  __shared__ float red_hi[4][2][NR][2], red_lo[4][2][NR][2];
+  __shared__ double sq[kXRows][NR];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const int pair = warp & 3, half = warp >> 2;
+  const int row0 = blockIdx.x * kXRows + pair * 2;
   const bool r0 = row0 < n, r1 = row0 + 1 < n;
   const int64_t o0 = static_cast<int64_t>(r0 ? row0 : 0) * ld;
   const int64_t o1 = static_cast<int64_t>(r1 ? row0 + 1 : 0) * ld;
-  float hi[kRowsPerWarp][NR], lo[kRowsPerWarp][NR];
+  float hi[2][NR], lo[2][NR];
 #pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < NR; ++c) hi[r][c] = lo[r][c] = 0.f;
   const int n4 = n & ~3;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int kfirst = 4 * lane + 128 * half;
+  float4 nx0 = z4, ny0 = z4, nx1 = z4, ny1 = z4;
+  if (kfirst < n4) {
+    if (r0) {
+      nx0 = __ldcs(reinterpret_cast<const float4*>(A1 + o0 + kfirst));
+      ny0 = __ldcs(reinterpret_cast<const float4*>(A2 + o0 + kfirst));
+    }
+    if (r1) {
+      nx1 = __ldcs(reinterpret_cast<const float4*>(A1 + o1 + kfirst));
+      ny1 = __ldcs(reinterpret_cast<const float4*>(A2 + o1 + kfirst));
+    }
+  }
 #pragma unroll 1
-  for (int k = 4 * lane; k < n4; k += 128) {
-    const float4 x0 = r0 ? *reinterpret_cast<const float4*>(A1 + o0 + k) : z4;
-    const float4 y0 = r0 ? *reinterpret_cast<const float4*>(A2 + o0 + k) : z4;
-    const float4 x1 = r1 ? *reinterpret_cast<const float4*>(A1 + o1 + k) : z4;
-    const float4 y1 = r1 ? *reinterpret_cast<const float4*>(A2 + o1 + k) : z4;
+  for (int k = kfirst; k < n4; k += 256) {
+    const float4 x0 = nx0, y0 = ny0, x1 = nx1, y1 = ny1;
+    const int kn = k + 256;
+    if (kn < n4) {
+      if (r0) {
+        nx0 = __ldcs(reinterpret_cast<const float4*>(A1 + o0 + kn));
+        ny0 = __ldcs(reinterpret_cast<const float4*>(A2 + o0 + kn));
+      }
+      if (r1) {
+        nx1 = __ldcs(reinterpret_cast<const float4*>(A1 + o1 + kn));
+        ny1 = __ldcs(reinterpret_cast<const float4*>(A2 + o1 + kn));
+      }
+    }
     const float a1v[2][4] = {{x0.x, x0.y, x0.z, x0.w}, {x1.x, x1.y, x1.z, x1.w}};
     const float a2v[2][4] = {{y0.x, y0.y, y0.z, y0.w}, {y1.x, y1.y, y1.z, y1.w}};
 #pragma unroll
@@ -650,7 +741,7 @@ __global__ void __launch_bounds__(256) k_resid_x2(const float* __restrict__ A1, 
       const float t1v[4] = {u.x, u.y, u.z, u.w};
       const float t2v[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
+      for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float p = a1v[r][j] * t1v[j];
@@ -660,73 +751,97 @@ __global__ void __launch_bounds__(256) k_resid_x2(const float* __restrict__ A1, 
         }
     }
   }
-  for (int k = n4 + lane; k < n; k += 32) {
+  if (half == 0) {
+    for (int k = n4 + lane; k < n; k += 32) {
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
-      const bool ok = r == 0 ? r0 : r1;
-      const int64_t o = r == 0 ? o0 : o1;
-      const float x = ok ? A1[o + k] : 0.f, y = ok ? A2[o + k] : 0.f;
+      for (int r = 0; r < 2; ++r) {
+        const bool ok = r == 0 ? r0 : r1;
+        const int64_t o = r == 0 ? o0 : o1;
+        const float x = ok ? A1[o + k] : 0.f, y = ok ? A2[o + k] : 0.f;
 #pragma unroll
-      for (int c = 0; c < NR; ++c) {
-        const float t1 = T1[(c0 + c) * ldt + k], t2 = T2[(c0 + c) * ldt + k];
-        const float p = x * t1;
-        const float e = fmaf(x, t1, -p);
-        two_sum_acc(hi[r][c], lo[r][c], p);
-        lo[r][c] += fmaf(x, t2, fmaf(y, t1, e));
+        for (int c = 0; c < NR; ++c) {
+          const float t1 = T1[(c0 + c) * ldt + k], t2 = T2[(c0 + c) * ldt + k];
+          const float p = x * t1;
+          const float e = fmaf(x, t1, -p);
+          two_sum_acc(hi[r][c], lo[r][c], p);
+          lo[r][c] += fmaf(x, t2, fmaf(y, t1, e));
+        }
       }
     }
   }
-  double mysq[NR];
 #pragma unroll
-  for (int c = 0; c < NR; ++c) mysq[c] = 0.0;
-#pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-      const double s = warp_sum(static_cast<double>(hi[r][c]) + static_cast<double>(lo[r][c]));
-      const int row = row0 + r;
-      if (lane == 0 && row < n) {
-        const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
-        const double v = B[o] - s;
-        R[o] = v;
-        R32T[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v);
-        mysq[c] += v * v;
+      warp_sum_x2(hi[r][c], lo[r][c]);
+      if (lane == 0) {
+        red_hi[pair][half][c][r] = hi[r][c];
+        red_lo[pair][half][c][r] = lo[r][c];
       }
     }
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < NR; ++c) sq[warp][c] = mysq[c];
+  __syncthreads();
+  // one thread per (row, rhs) of the block combines the two halves in FP64
+  if (threadIdx.x < kXRows * NR) {
+    const int rr = threadIdx.x / NR, c = threadIdx.x % NR;
+    const int pr = rr >> 1, r = rr & 1;
+    const int row = blockIdx.x * kXRows + rr;
+    double v2 = 0.0;
+    if (row < n) {
+      const double sdot = (static_cast<double>(red_hi[pr][0][c][r]) + static_cast<double>(red_lo[pr][0][c][r])) +
+                          (static_cast<double>(red_hi[pr][1][c][r]) + static_cast<double>(red_lo[pr][1][c][r]));
+      const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+      const double v = B[o] - sdot;
+      R[o] = v;
+      R32T[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v);
+      v2 = v * v;
+    }
+    sq[rr][c] = v2;
+  }
   __syncthreads();
   if (threadIdx.x < NR) {
     double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += sq[w][threadIdx.x];
+    for (int w = 0; w < kXRows; ++w) t += sq[w][threadIdx.x];
     partials[static_cast<int64_t>(blockIdx.x) * nrhs + c0 + threadIdx.x] = t;
   }
 }
 
 // Theta += G R with G f32 (ld % 4 == 0) and R given as f32 R32T[c][k]; the new
-// theta is also written as its f32 limbs for the next residual.
+// theta is also written as its f32 limbs for the next residual.  Products and
+// sums are f32 (G is itself an f32 approximation of the inverse, so this adds
+// an error well below G's own); the new theta is formed in FP64.
 template <int NR>
-__global__ void __launch_bounds__(256) k_update_x2(const float* __restrict__ G, int64_t ldg,
-                                                   const float* __restrict__ R32T, int64_t ldt,
-                                                   double* __restrict__ Th, float* __restrict__ T1,
-                                                   float* __restrict__ T2, int n, int nrhs, int c0) {
+__global__ void __launch_bounds__(256, 4) k_update_x2(const float* __restrict__ G, int64_t ldg,
+                                                      const float* __restrict__ R32T, int64_t ldt,
+                                                      double* __restrict__ Th, float* __restrict__ T1,
+                                                      float* __restrict__ T2, int n, int nrhs, int c0) {
+  __shared__ float red[4][2][NR][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * kRowsPerBlock + warp * kRowsPerWarp;
+  const int pair = warp & 3, half = warp >> 2;
+  const int row0 = blockIdx.x * kXRows + pair * 2;
   const bool r0 = row0 < n, r1 = row0 + 1 < n;
   const float* g0 = G + static_cast<int64_t>(r0 ? row0 : 0) * ldg;
   const float* g1 = G + static_cast<int64_t>(r1 ? row0 + 1 : 0) * ldg;
-  float acc[kRowsPerWarp][NR];
+  float acc[2][NR];
 #pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[r][c] = 0.f;
   const int n4 = n & ~3;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
-  for (int k = 4 * lane; k < n4; k += 128) {
-    const float4 x0 = r0 ? *reinterpret_cast<const float4*>(g0 + k) : z4;
-    const float4 x1 = r1 ? *reinterpret_cast<const float4*>(g1 + k) : z4;
+  const int kfirst = 4 * lane + 128 * half;
+  float4 nx0 = z4, nx1 = z4;
+  if (kfirst < n4) {
+    if (r0) nx0 = __ldcs(reinterpret_cast<const float4*>(g0 + kfirst));
+    if (r1) nx1 = __ldcs(reinterpret_cast<const float4*>(g1 + kfirst));
+  }
+#pragma unroll 1
+  for (int k = kfirst; k < n4; k += 256) {
+    const float4 x0 = nx0, x1 = nx1;
+    const int kn = k + 256;
+    if (kn < n4) {
+      if (r0) nx0 = __ldcs(reinterpret_cast<const float4*>(g0 + kn));
+      if (r1) nx1 = __ldcs(reinterpret_cast<const float4*>(g1 + kn));
+    }
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
       const float4 t = *reinterpret_cast<const float4*>(R32T + (c0 + c) * ldt + k);
@@ -734,31 +849,39 @@ __global__ void __launch_bounds__(256) k_update_x2(const float* __restrict__ G, 
       acc[1][c] = fmaf(x1.x, t.x, fmaf(x1.y, t.y, fmaf(x1.z, t.z, fmaf(x1.w, t.w, acc[1][c]))));
     }
   }
-  for (int k = n4 + lane; k < n; k += 32) {
-    const float x0 = r0 ? g0[k] : 0.f;
-    const float x1 = r1 ? g1[k] : 0.f;
+  if (half == 0) {
+    for (int k = n4 + lane; k < n; k += 32) {
+      const float x0 = r0 ? g0[k] : 0.f;
+      const float x1 = r1 ? g1[k] : 0.f;
 #pragma unroll
-    for (int c = 0; c < NR; ++c) {
-      const float t = R32T[(c0 + c) * ldt + k];
-      acc[0][c] = fmaf(x0, t, acc[0][c]);
-      acc[1][c] = fmaf(x1, t, acc[1][c]);
+      for (int c = 0; c < NR; ++c) {
+        const float t = R32T[(c0 + c) * ldt + k];
+        acc[0][c] = fmaf(x0, t, acc[0][c]);
+        acc[1][c] = fmaf(x1, t, acc[1][c]);
+      }
     }
   }
 #pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-      const double s = warp_sum(static_cast<double>(acc[r][c]));
-      const int row = row0 + r;
-      if (lane == 0 && row < n) {
-        const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
-        const double v = Th[o] + s;
-        Th[o] = v;
-        const float f1 = static_cast<float>(v);
-        T1[static_cast<int64_t>(c0 + c) * ldt + row] = f1;
-        T2[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v - static_cast<double>(f1));
-      }
+      const float sred = warp_sum_f32(acc[r][c]);
+      if (lane == 0) red[pair][half][c][r] = sred;
     }
+  __syncthreads();
+  if (threadIdx.x < kXRows * NR) {
+    const int rr = threadIdx.x / NR, c = threadIdx.x % NR;
+    const int pr = rr >> 1, r = rr & 1;
+    const int row = blockIdx.x * kXRows + rr;
+    if (row < n) {
+      const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+      const double v = Th[o] + (static_cast<double>(red[pr][0][c][r]) + static_cast<double>(red[pr][1][c][r]));
+      Th[o] = v;
+      const float f1 = static_cast<float>(v);
+      T1[static_cast<int64_t>(c0 + c) * ldt + row] = f1;
+      T2[static_cast<int64_t>(c0 + c) * ldt + row] = static_cast<float>(v - static_cast<double>(f1));
+    }
+  }
 }
 
 }  // namespace
@@ -779,10 +902,12 @@ cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, flo
   return cudaGetLastError();
 }
 
+int resid_x2_blocks(int n) { return (n + kXRows - 1) / kXRows; }
+
 cudaError_t launch_resid_x2(const float* A1, const float* A2, int64_t ld, const float* T1, const float* T2,
                             int64_t ldt, const double* B, double* R, float* R32T, int n, int nrhs,
                             double* partials, int* nblocks_out, cudaStream_t s) {
-  const int nb = resid_blocks(n);
+  const int nb = resid_x2_blocks(n);
   if (nblocks_out) *nblocks_out = nb;
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (ld % 4 || ldt % 4 || !aligned16(A1) || !aligned16(A2) || !aligned16(T1) || !aligned16(T2))
@@ -804,7 +929,7 @@ cudaError_t launch_resid_x2(const float* A1, const float* A2, int64_t ld, const 
 
 cudaError_t launch_update_x2(const float* G, int64_t ldg, const float* R32T, int64_t ldt, double* Th, float* T1,
                              float* T2, int n, int nrhs, cudaStream_t s) {
-  const int nb = resid_blocks(n);
+  const int nb = resid_x2_blocks(n);
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (ldg % 4 || ldt % 4 || !aligned16(G) || !aligned16(R32T)) return cudaErrorInvalidValue;
   int c0 = 0;
