@@ -156,6 +156,52 @@ const char* ns_last_error(const ns_ctx* ctx);
 const char* ns_status_string(ns_status s);
 
 /* ---------------------------------------------------------------------------
+ * Batched solves: many independent SPD systems A_i theta_i = B_i of uneven size
+ * advanced together, each by the method of ns_richardson_solve (factorized order
+ * 2^m or 3, precision controller per instance, split-f32 Richardson).  Each pass
+ * issues one list-driven tensor-core launch per product level (per tile width
+ * and precision) for all instances, and one launch per batched row kernel.
+ * An instance's arithmetic does not depend on the other instances (tile width
+ * from its own size, fixed-order reductions inside its own blocks), so its
+ * result is bitwise the same alone or in any mix.
+ * ------------------------------------------------------------------------- */
+typedef struct ns_batch ns_batch;
+
+typedef struct ns_batch_stats {
+  int passes;                       /* controller passes (one device sync each) */
+  int converged;                    /* instances that met tol */
+  int not_converged;                /* instances that did not (diverged, floor, budget) */
+  long long gemm_launches;
+  long long kernel_launches;
+  double gemm_flops;                /* executed: 2 n^3 per product pass (bf16x3 = 3 passes) */
+  double gemm_ms;                   /* summed product-launch durations (opt.profile = 1) */
+  double useful_flops_per_product;  /* sum over instances of 2 n_i^3 */
+  double wall_ms;
+} ns_batch_stats;
+
+/* Create a batch of `count` systems; n[i] in [1, 16384], nrhs[i] in [1, 1024].
+ * order: 3 or a power of two.  opt: precision NS_AUTO, NS_BF16 or NS_BF16X3,
+ * form 0, pow_mode 0 (others return NS_ERR_UNSUPPORTED).  Allocates all workspace
+ * (one device allocation) and the per-instance product descriptors. */
+ns_status ns_batch_create(int count, const int64_t* n, const int* nrhs, int order, const ns_options* opt,
+                          ns_batch** out);
+ns_status ns_batch_destroy(ns_batch* b);
+ns_status ns_batch_set_stream(ns_batch* b, void* cuda_stream);
+const char* ns_batch_last_error(const ns_batch* b);
+
+/* Solve all systems from Theta = 0.  A[i] (n_i x n_i), B[i] (n_i x nrhs_i) and
+ * Theta[i] (n_i x nrhs_i, output) are DEVICE pointers, row-major FP64; the
+ * arrays of pointers are host arrays.  iters caps the NS steps per instance;
+ * tol the relative residual.  Returns NS_OK when every instance met tol,
+ * NS_NOT_CONVERGED otherwise (per-instance status via ns_batch_result), or an
+ * error for the whole call. */
+ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* const* B, double* const* Theta,
+                         int iters, double tol, ns_batch_stats* stats);
+
+/* Per-instance outcome of the last ns_batch_solve. */
+ns_status ns_batch_result(const ns_batch* b, int i, int* status, int* ns_iters, int* sweeps, double* rel_res);
+
+/* ---------------------------------------------------------------------------
  * Single-kernel entry points.  Device pointers only; `stream` is a cudaStream_t
  * (NULL = legacy default).  Each returns after launching, without synchronising,
  * except where a result is returned through a host pointer.  Scratch memory they

@@ -27,6 +27,7 @@ __all__ = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
+    "ns_batch_stats", "Batch",
 ]
 
 NS_OK, NS_NOT_CONVERGED = 0, 1
@@ -96,6 +97,20 @@ class ns_stats(ctypes.Structure):
         return [self.rel_res_hist[i] for i in range(self.n_res)]
 
 
+class ns_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("passes", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("not_converged", ctypes.c_int),
+        ("gemm_launches", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("gemm_flops", ctypes.c_double),
+        ("gemm_ms", ctypes.c_double),
+        ("useful_flops_per_product", ctypes.c_double),
+        ("wall_ms", ctypes.c_double),
+    ]
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -130,6 +145,15 @@ def lib() -> ctypes.CDLL:
         "ns_k_prep_a": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
         "ns_k_resid_x2": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
         "ns_k_resid_noalloc": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _int, _vp, _vp]),
+        "ns_batch_create": (_int, [_int, ctypes.POINTER(_i64), ctypes.POINTER(_int), _int, ctypes.POINTER(ns_options),
+                                   ctypes.POINTER(_vp)]),
+        "ns_batch_destroy": (_int, [_vp]),
+        "ns_batch_set_stream": (_int, [_vp, _vp]),
+        "ns_batch_last_error": (ctypes.c_char_p, [_vp]),
+        "ns_batch_solve": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _int,
+                                  ctypes.c_double, ctypes.POINTER(ns_batch_stats)]),
+        "ns_batch_result": (_int, [_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                   ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -362,3 +386,67 @@ class Context:
 
     def residual(self, A, theta, B) -> list[float]:
         return ns_residual(self.handle, A, theta, B)
+
+
+class Batch:
+    """Many independent SPD systems solved together (``ns_batch_*``).
+
+    ``Batch(ns, nrhs, order=4, **options)`` allocates the workspace; ``solve``
+    takes lists of device FP64 tensors A_i (n_i x n_i), B_i (n_i x nrhs_i) and
+    returns the Theta_i (device tensors) with the per-instance outcomes."""
+
+    def __init__(self, ns, nrhs, order: int = 4, stream=None, **options):
+        self.count = len(ns)
+        self.ns = [int(x) for x in ns]
+        self.nrhs = [int(x) for x in nrhs]
+        self.opt = default_options(**options)
+        h = _vp()
+        n_arr = (_i64 * self.count)(*self.ns)
+        r_arr = (_int * self.count)(*self.nrhs)
+        s = lib().ns_batch_create(self.count, n_arr, r_arr, int(order), ctypes.byref(self.opt), ctypes.byref(h))
+        if s != NS_OK:
+            raise NSError(s, "ns_batch_create")
+        self.handle = h.value
+        if stream is not None:
+            lib().ns_batch_set_stream(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ns_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, As, Bs, iters: int = 64, tol: float = 1e-10, outs=None):
+        if outs is None:
+            outs = [torch.empty_like(Bi) for Bi in Bs]
+        for i, (Ai, Bi, Ti) in enumerate(zip(As, Bs, outs)):
+            if not (Ai.is_cuda and Bi.is_cuda and Ti.is_cuda):
+                raise ValueError("batched solves take device tensors")
+            _ptr(Ai), _ptr(Bi), _ptr(Ti)
+            if Ai.shape != (self.ns[i], self.ns[i]) or Bi.shape != (self.ns[i], self.nrhs[i]):
+                raise ValueError(f"instance {i}: shape mismatch")
+        a = (_vp * self.count)(*[t.data_ptr() for t in As])
+        b = (_vp * self.count)(*[t.data_ptr() for t in Bs])
+        o = (_vp * self.count)(*[t.data_ptr() for t in outs])
+        st = ns_batch_stats()
+        s = lib().ns_batch_solve(self.handle, a, b, o, int(iters), float(tol), ctypes.byref(st))
+        if s not in (NS_OK, NS_NOT_CONVERGED):
+            raise NSError(s, lib().ns_batch_last_error(self.handle).decode())
+        return outs, s, st
+
+    def result(self, i: int):
+        st, it, sw = _int(), _int(), _int()
+        rr = ctypes.c_double()
+        lib().ns_batch_result(self.handle, i, ctypes.byref(st), ctypes.byref(it), ctypes.byref(sw), ctypes.byref(rr))
+        return {"status": st.value, "ns_iters": it.value, "sweeps": sw.value, "rel_res": rr.value}

@@ -1,0 +1,48 @@
+// Batched solves: per-instance descriptors shared by the batched kernels and
+// the batch runtime.
+#pragma once
+#include "internal.h"
+
+namespace nsgb {
+
+// Scalar block of one instance: [0] ||A||_F^2, [1] ||A||_inf, [2] ||F||_F^2,
+// [3] unused, [kScalR + c] ||r_c||^2, [kScalR + nrhs + c] ||b_c||^2.
+constexpr int kScalR = 4;
+
+struct BInst {
+  int n, nrhs, ld, nfrob;  // nfrob: partial sums of ||F||^2 written by the product kernel
+  const double* A;         // caller's A (n x n, leading dimension n)
+  const double* B;         // caller's B (n x nrhs)
+  double* Th;              // theta (n x nrhs), the caller's output buffer
+  double* R;               // residual (n x nrhs)
+  bf16* Ahi;               // ld x ld
+  bf16* Alo;
+  float* A1;               // n x ld
+  float* A2;
+  float* G32[2];           // f32 masters of the two G buffers (ld x ld)
+  bf16* Ghi[2];
+  bf16* Glo[2];
+  float* T1;               // theta limbs, nrhs x ld
+  float* T2;
+  float* R32T;             // f32 residual, nrhs x ld
+  double* part;            // row-block partials
+  double* fpart;           // product-kernel partials of ||F||^2
+  double* scal;            // scalar block
+};
+
+// Work item of a batched row kernel: 8 rows [row0, row0 + 8) and 4 right-hand
+// sides [c0, c0 + 4) of one instance; cur selects the G buffer.
+struct BItem {
+  int inst, row0, c0, cur;
+};
+
+cudaError_t launch_bprep(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
+cudaError_t launch_bnorms(const BInst* insts, const int* list, int ninst, cudaStream_t s);
+cudaError_t launch_bg0(const BInst* insts, const BItem* items, int nitems, int mode, int zero_theta,
+                       cudaStream_t s);
+cudaError_t launch_bresid(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
+cudaError_t launch_brsq(const BInst* insts, const int* list, int ninst, cudaStream_t s);
+cudaError_t launch_bupdate(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
+cudaError_t launch_bfrob(const BInst* insts, const int* list, int ninst, cudaStream_t s);
+
+}  // namespace nsgb

@@ -63,6 +63,13 @@ struct TcCfg {
 
 // Work item w of this CTA (cluster rank `rank`): problem, tile row and column.
 __device__ __forceinline__ void decode_item(const TcParams& p, int w, int rank, int CM, int& pi, int& mt, int& nt) {
+  if (p.gprob != nullptr) {
+    const TcItem it = p.items[w];
+    pi = it.prob;
+    mt = it.mt;
+    nt = it.nt;
+    return;
+  }
   pi = 0;
 #pragma unroll 1
   for (int i = 1; i < p.nprob; ++i)
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
-    for (int i = 0; i < p.nprob; ++i) {
+    for (int i = 0; p.gprob == nullptr && i < p.nprob; ++i) {
       tma_prefetch_desc(&p.prob[i].L[0]);
       tma_prefetch_desc(&p.prob[i].R[0]);
       if (p.npass > 1) {
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     for (int w = first; w < p.total_tiles && ok; w += stride) {
       int pi, mt, nt;
       decode_item(p, w, rank, CM, pi, mt, nt);
-      const TcProblem& P = p.prob[pi];
+      const TcProblem& P = p.gprob != nullptr ? p.gprob[pi] : p.prob[pi];
       const int m0 = mt * kBM, n0 = nt * BN;
       const int kstep = X3 ? kBK / 2 : kBK;
       const int nkb = (P.K + kstep - 1) / kstep;
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     for (int w = first; w < p.total_tiles && ok; w += stride) {
       int pi, mt, nt;
       decode_item(p, w, rank, CM, pi, mt, nt);
-      const TcProblem& P = p.prob[pi];
+      const TcProblem& P = p.gprob != nullptr ? p.gprob[pi] : p.prob[pi];
       const int kstep = X3 ? kBK / 2 : kBK;
       const int nkb = (P.K + kstep - 1) / kstep;
       const int npass = X3 ? 1 : p.npass;
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     for (int w = first; w < p.total_tiles; w += stride) {
       int pi, mt, nt;
       decode_item(p, w, rank, CM, pi, mt, nt);
-      const TcProblem& P = p.prob[pi];
+      const TcProblem& P = p.gprob != nullptr ? p.gprob[pi] : p.prob[pi];
       const int m0 = mt * kBM, n0 = nt * BN;
       bool ok = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
       ok = __all_sync(0xffffffffu, ok);

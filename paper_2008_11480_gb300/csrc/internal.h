@@ -40,10 +40,20 @@ struct TcProblem {
   double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4)
 };
 
+// A work item of a list-driven launch: problem index and tile coordinates.
+struct TcItem {
+  int prob, mt, nt, pad;
+};
+
 struct TcParams {
   TcProblem prob[kTcMaxProblems];
   int nprob;
   int total_tiles;  // work items over all problems
+  // List-driven mode (batched / served solves): when gprob is non-null, the
+  // problems live in device memory (64-byte aligned, tensor maps included) and
+  // work item w is items[w]; prob[] and nprob are unused and CM must be 1.
+  const TcProblem* gprob;
+  const TcItem* items;
   int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3)
   int debug_stall_iter;  // -1 for none; else the producer withholds that load
   unsigned long long timeout_ns;
