@@ -650,6 +650,8 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   double prev_frob = INFINITY;
   double prev_ratio = INFINITY;
   double last_rr = INFINITY;
+  double prev_sweep_rr = INFINITY, best_rr = INFINITY;
+  int stall = 0;
   bool converged = false;
   int aux_steps = 0;
 
@@ -858,6 +860,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       continue;
     }
     if (!richardson || sweeps_left <= 0) break;
+    // Richardson alone no longer contracts (rho(I - A G) ~ 1 at this precision):
+    // stop instead of spending the whole sweep budget
+    if (std::isfinite(prev_sweep_rr)) stall = last_rr > 0.95 * prev_sweep_rr ? stall + 1 : 0;
+    prev_sweep_rr = last_rr;
+    best_rr = std::min(best_rr, last_rr);
+    if (stall >= 4 || last_rr > 10.0 * best_rr) break;
     if (fp64)
       NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, s));
     else
