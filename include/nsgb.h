@@ -202,6 +202,76 @@ ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* cons
 ns_status ns_batch_result(const ns_batch* b, int i, int* status, int* ns_iters, int* sweeps, double* rel_res);
 
 /* ---------------------------------------------------------------------------
+ * Continuous-batching server.  Requests (independent SPD systems, each solved
+ * by the method of ns_batch_solve) join and leave between scheduling ticks.
+ * A tick (1) admits queued requests first come, first served while a request
+ * slot is free and its workspace fits the memory budget (first-fit arena,
+ * zeroed on admission), copying A and B into the slot; (2) runs ONE
+ * controller pass over every request on the device: its residual, and while
+ * its Newton-Schulz loop runs, F = I - A G, then its Richardson update and
+ * next product chain, with the launches of the batched solve; (3) retires each
+ * finished request on its own (theta copied to the caller's buffer; the
+ * request is reported done once that copy has landed).  A request's
+ * arithmetic is that of the same system solved alone (own tile width, own
+ * fixed-order reductions), so its theta is bitwise independent of the mix.
+ * The paper has no serving loop; this is the batched path run continuously.
+ * ------------------------------------------------------------------------- */
+typedef struct ns_server ns_server;
+
+typedef struct ns_request {
+  int64_t n;            /* system size, 1..16384 */
+  int nrhs;             /* 1..max_nrhs of the server */
+  int iters;            /* cap on Newton-Schulz steps */
+  double tol;           /* relative residual target (max over right-hand sides) */
+  const double* A;      /* n x n row-major FP64, host (pinned or pageable) or device */
+  const double* B;      /* n x nrhs row-major FP64 */
+  double* Theta;        /* n x nrhs output; written when the request is done */
+} ns_request;           /* A, B and Theta stay owned by the caller and valid until done */
+
+typedef struct ns_result {
+  int status;           /* NS_OK converged, NS_NOT_CONVERGED, NS_ERR_DIVERGED / NONFINITE, NS_ERR_OOM (never fits) */
+  int done;             /* 1 once Theta holds the result */
+  int ns_iters;
+  int sweeps;
+  double rel_res;       /* last measured max_c ||B_c - A theta_c|| / ||B_c|| */
+  double queue_ms;      /* submit -> admission */
+  double latency_ms;    /* submit -> done */
+} ns_result;
+
+typedef struct ns_server_stats {
+  long long submitted, admitted, completed, converged, rejected;
+  long long ticks, passes;
+  int active;           /* requests holding a slot after the last tick */
+  int queued;           /* requests waiting for admission */
+  int last_error;       /* error of the background thread (0 if none) */
+} ns_server_stats;
+
+/* mem_budget_bytes: device arena for request workspaces (slot footprint of a
+ * request about 68 ld^2 + 36 ld nrhs bytes, ld = n rounded up to 64); tables
+ * and staging are allocated beside it.  max_requests: slots.
+ * order and opt as for ns_batch_create.  The server owns a non-blocking stream. */
+ns_status ns_server_create(size_t mem_budget_bytes, int max_requests, int max_nrhs, int order,
+                           const ns_options* opt, ns_server** out);
+/* Stops the background thread (after the queue drains) and frees everything. */
+ns_status ns_server_destroy(ns_server* srv);
+ns_status ns_server_set_stream(ns_server* srv, void* cuda_stream /* NULL: the server's own */);
+const char* ns_server_last_error(const ns_server* srv);
+/* Thread-safe.  Device buffers must hold their data when submit is called. */
+ns_status ns_server_submit(ns_server* srv, const ns_request* req, uint64_t* ticket);
+/* Non-blocking, thread-safe.  NS_ERR_ARG for an unknown ticket. */
+ns_status ns_server_poll(ns_server* srv, uint64_t ticket, ns_result* out);
+/* Forget a finished request's record (NS_ERR_ARG if not done). */
+ns_status ns_server_release(ns_server* srv, uint64_t ticket);
+/* One scheduling tick on the calling thread (synchronises the stream once
+ * per pass).  *active = requests holding a slot afterwards. */
+ns_status ns_server_tick(ns_server* srv, int* active);
+/* Run ticks on a background thread until ns_server_stop (which waits for
+ * every submitted request to finish).  Do not call ns_server_tick meanwhile. */
+ns_status ns_server_start(ns_server* srv);
+ns_status ns_server_stop(ns_server* srv);
+ns_status ns_server_get_stats(ns_server* srv, ns_server_stats* out);
+
+/* ---------------------------------------------------------------------------
  * Single-kernel entry points.  Device pointers only; `stream` is a cudaStream_t
  * (NULL = legacy default).  Each returns after launching, without synchronising,
  * except where a result is returned through a host pointer.  Scratch memory they

@@ -111,6 +111,45 @@ class ns_batch_stats(ctypes.Structure):
     ]
 
 
+class ns_request(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("nrhs", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("A", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("Theta", ctypes.c_void_p),
+    ]
+
+
+class ns_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("done", ctypes.c_int),
+        ("ns_iters", ctypes.c_int),
+        ("sweeps", ctypes.c_int),
+        ("rel_res", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+        ("latency_ms", ctypes.c_double),
+    ]
+
+
+class ns_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong),
+        ("admitted", ctypes.c_longlong),
+        ("completed", ctypes.c_longlong),
+        ("converged", ctypes.c_longlong),
+        ("rejected", ctypes.c_longlong),
+        ("ticks", ctypes.c_longlong),
+        ("passes", ctypes.c_longlong),
+        ("active", ctypes.c_int),
+        ("queued", ctypes.c_int),
+        ("last_error", ctypes.c_int),
+    ]
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -154,6 +193,18 @@ def lib() -> ctypes.CDLL:
                                   ctypes.c_double, ctypes.POINTER(ns_batch_stats)]),
         "ns_batch_result": (_int, [_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int),
                                    ctypes.POINTER(ctypes.c_double)]),
+        "ns_server_create": (_int, [ctypes.c_size_t, _int, _int, _int, ctypes.POINTER(ns_options),
+                                    ctypes.POINTER(_vp)]),
+        "ns_server_destroy": (_int, [_vp]),
+        "ns_server_set_stream": (_int, [_vp, _vp]),
+        "ns_server_last_error": (ctypes.c_char_p, [_vp]),
+        "ns_server_submit": (_int, [_vp, ctypes.POINTER(ns_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "ns_server_poll": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(ns_result)]),
+        "ns_server_release": (_int, [_vp, ctypes.c_uint64]),
+        "ns_server_tick": (_int, [_vp, ctypes.POINTER(_int)]),
+        "ns_server_start": (_int, [_vp]),
+        "ns_server_stop": (_int, [_vp]),
+        "ns_server_get_stats": (_int, [_vp, ctypes.POINTER(ns_server_stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -450,3 +501,95 @@ class Batch:
         rr = ctypes.c_double()
         lib().ns_batch_result(self.handle, i, ctypes.byref(st), ctypes.byref(it), ctypes.byref(sw), ctypes.byref(rr))
         return {"status": st.value, "ns_iters": it.value, "sweeps": sw.value, "rel_res": rr.value}
+
+
+class Server:
+    """Continuous-batching server (``ns_server_*``).
+
+    ``Server(mem_budget_bytes, max_requests, max_nrhs, order=4, **options)``;
+    ``submit(A, B, Theta, iters, tol)`` returns a ticket (the tensors must stay
+    alive until the request is done); ``tick()`` runs one scheduling tick on
+    the calling thread, or ``start()`` / ``stop()`` run ticks on a background
+    thread; ``poll(ticket)`` returns the request's ``ns_result`` as a dict."""
+
+    def __init__(self, mem_budget_bytes: int, max_requests: int, max_nrhs: int, order: int = 4, stream=None,
+                 **options):
+        self.opt = default_options(**options)
+        h = _vp()
+        s = lib().ns_server_create(int(mem_budget_bytes), int(max_requests), int(max_nrhs), int(order),
+                                   ctypes.byref(self.opt), ctypes.byref(h))
+        if s != NS_OK:
+            raise NSError(s, "ns_server_create")
+        self.handle = h.value
+        self._keep: dict[int, tuple] = {}
+        if stream is not None:
+            lib().ns_server_set_stream(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ns_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _err(self, s: int, what: str):
+        raise NSError(s, f"{what}: {lib().ns_server_last_error(self.handle).decode()}")
+
+    def submit(self, A: torch.Tensor, B: torch.Tensor, Theta: torch.Tensor, iters: int = 64,
+               tol: float = 1e-10) -> int:
+        n = A.shape[0]
+        if A.shape != (n, n) or B.dim() != 2 or B.shape[0] != n or Theta.shape != B.shape:
+            raise ValueError("A must be n x n, B and Theta n x nrhs")
+        req = ns_request(n, B.shape[1], int(iters), float(tol), _ptr(A), _ptr(B), _ptr(Theta))
+        t = ctypes.c_uint64()
+        s = lib().ns_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if s != NS_OK:
+            self._err(s, "ns_server_submit")
+        self._keep[t.value] = (A, B, Theta)
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        r = ns_result()
+        s = lib().ns_server_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if s != NS_OK:
+            self._err(s, "ns_server_poll")
+        return {k: getattr(r, k) for k, _ in ns_result._fields_}
+
+    def release(self, ticket: int) -> None:
+        s = lib().ns_server_release(self.handle, ctypes.c_uint64(ticket))
+        if s != NS_OK:
+            self._err(s, "ns_server_release")
+        self._keep.pop(ticket, None)
+
+    def tick(self) -> int:
+        a = _int()
+        s = lib().ns_server_tick(self.handle, ctypes.byref(a))
+        if s != NS_OK:
+            self._err(s, "ns_server_tick")
+        return a.value
+
+    def start(self) -> None:
+        s = lib().ns_server_start(self.handle)
+        if s != NS_OK:
+            self._err(s, "ns_server_start")
+
+    def stop(self) -> None:
+        s = lib().ns_server_stop(self.handle)
+        if s != NS_OK:
+            self._err(s, "ns_server_stop")
+
+    def stats(self) -> dict:
+        st = ns_server_stats()
+        lib().ns_server_get_stats(self.handle, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in ns_server_stats._fields_}

@@ -1,29 +1,44 @@
-// Batched solves of many independent SPD systems of uneven size (the batched
-// mode of Newton-Schulz coupled to Richardson).  Every instance runs the same
-// method as ns_richardson_solve -- factorized product chain of order 2^m or 3,
-// bf16 / split-bf16 products with the per-instance precision controller,
-// split-f32 Richardson -- but each pass advances all instances with a handful
-// of launches: one list-driven tcgen05 launch per product level (per tile
-// width and precision group) and one launch per batched row kernel.
+// Many independent SPD systems of uneven size advanced together: the batched
+// solve (a fixed set of systems) and the continuous-batching server (systems
+// arrive and leave).  Every system runs the method of ns_richardson_solve --
+// factorized product chain of order 2^m or 3, bf16 / split-bf16 products with
+// its own precision controller, split-f32 Richardson -- but one controller
+// pass advances all of them with a handful of launches: one list-driven
+// tcgen05 launch per product level (per tile width and precision group) and
+// one launch per batched row kernel.
 //
-// Batch invariance: an instance's tile width depends only on its own size and
-// all its reductions run in a fixed order inside its own blocks, so its result
-// is the same whether it is solved alone or in any mix.
+// Systems live in slots.  A slot's workspace is carved from one device arena
+// (first fit, zeroed on admission); its tcgen05 problem descriptors (every
+// product type x current G buffer x precision) and its row-kernel descriptor
+// sit at the slot's index in device tables, so admitting or retiring a system
+// touches only its own slot.
+//
+// Invariance: a system's tile width depends only on its own size and all of
+// its reductions run in a fixed order inside its own blocks, so its result is
+// bitwise the same whether it is solved alone or together with any others.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/nsgb.h"
+#include "arena.h"
 #include "batch.h"
 
 using namespace nsgb;
 
 namespace {
 
-int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+size_t rup(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 struct BMat {
   float* m32 = nullptr;
@@ -41,46 +56,95 @@ struct InstState {
   bool converged = false;
   bool recompute = false;
   int sweeps_left = 0;
-  double prev_frob = INFINITY, prev_ratio = INFINITY, last_rr = INFINITY, frob_now = INFINITY;
+  double prev_frob = INFINITY, prev_ratio = INFINITY, frob_now = INFINITY;
+  double best_rr = INFINITY;        // smallest residual of the Richardson-only phase
+  double last_rr_sweep = INFINITY;  // residual of the previous Richardson-only pass
+  int stall = 0;                    // consecutive Richardson-only passes with < 5 % progress
   int status = NS_OK;
   int sweeps = 0;
   int rollbacks = 0;
   double rel_res = INFINITY;
+  int iters = 0;      // cap on Newton-Schulz steps
+  double tol = 0.0;   // relative residual target
 };
 
-// Matrices of one instance, in the order the problem table uses.
+// Matrices of one system, in the order the problem table uses.
 enum { MA = 0, MG0, MG1, MX0, MX1, MF, MP0, MP1, kNumMats };
+
+// Layout of one slot's workspace (offsets from the slot's arena region).
+struct SlotLayout {
+  size_t mat[kNumMats][3];  // f32 master (or SIZE_MAX), hi, lo
+  size_t a1, a2, t1, t2, r32t, r, part, fpart, acopy, bcopy, tcopy;
+  size_t bytes;
+};
+
+int tile_width(int n) { return n <= 512 ? 128 : 256; }
+
+SlotLayout slot_layout(int n, int nrhs, bool copies) {
+  SlotLayout L;
+  size_t total = 0;
+  auto take = [&](size_t bytes) {
+    const size_t off = rup(total, 256);
+    total = off + bytes;
+    return off;
+  };
+  const size_t ld = rup(n, 64);
+  const size_t sq = ld * ld;
+  for (int m = 0; m < kNumMats; ++m) {
+    const bool with32 = m == MG0 || m == MG1 || m == MX0 || m == MX1 || m == MF;
+    L.mat[m][0] = with32 ? take(sq * 4) : SIZE_MAX;
+    L.mat[m][1] = take(sq * 2);
+    L.mat[m][2] = take(sq * 2);
+  }
+  const size_t nrb = (n + 7) / 8;
+  const int bnv = tile_width(n);
+  const size_t tiles = static_cast<size_t>((n + 127) / 128) * ((n + bnv - 1) / bnv);
+  L.a1 = take(n * ld * 4);
+  L.a2 = take(n * ld * 4);
+  L.t1 = take(nrhs * ld * 4);
+  L.t2 = take(nrhs * ld * 4);
+  L.r32t = take(nrhs * ld * 4);
+  L.r = take(static_cast<size_t>(n) * nrhs * 8);
+  L.part = take(std::max(2 * nrb, nrb * nrhs) * 8);
+  L.fpart = take(tiles * 4 * 8);
+  L.acopy = copies ? take(static_cast<size_t>(n) * n * 8) : SIZE_MAX;
+  L.bcopy = copies ? take(static_cast<size_t>(n) * nrhs * 8) : SIZE_MAX;
+  L.tcopy = copies ? take(static_cast<size_t>(n) * nrhs * 8) : SIZE_MAX;
+  L.bytes = rup(total, 256);
+  return L;
+}
 
 }  // namespace
 
 struct ns_batch {
-  int count = 0;
-  int order = 4;
-  int levels = 2;  // order 2^levels, or 0 for order 3
-  int ntypes = 0;
+  int cap = 0;  // slots
+  int order = 4, levels = 2, ntypes = 0;
+  int max_nrhs = 1, scal_stride = 0;
   ns_options opt;
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 148;
   std::string err;
   void* dmem = nullptr;
-  size_t dbytes = 0;
-  std::vector<int> n, nrhs, ld, bn, tiles_m, tiles_n;
-  std::vector<std::vector<BMat>> mats;  // [inst][kNumMats]
-  std::vector<BInst> hinst;
-  BInst* dinst = nullptr;
+  char* abase = nullptr;
+  size_t asize = 0;
+  nsgb::Arena arena;
   TcProblem* dprob = nullptr;
+  BInst* dinst = nullptr;
   double* dscal = nullptr;
-  double* hscal = nullptr;
-  std::vector<size_t> scal_off;
-  size_t scal_total = 0;
-  char* hstage = nullptr;
-  char* dstage = nullptr;
-  size_t stage_cap = 0, stage_used = 0;
   int* derr = nullptr;
+  char* dstage = nullptr;
+  char* hstage = nullptr;
+  size_t stage_cap = 0, stage_used = 0;
+  double* hscal = nullptr;
+  std::vector<char> used;
+  std::vector<size_t> reg_off;
+  std::vector<SlotLayout> lay;
+  std::vector<int> n, nrhs, ld, bn, tiles_m, tiles_n;
+  std::vector<std::array<BMat, kNumMats>> mats;
+  std::vector<BInst> hinst;
   std::vector<InstState> st;
-  std::vector<const double*> A, B;
-  std::vector<double*> Th;
   ns_batch_stats* stats = nullptr;
+  int fixed_count = 0;  // systems of a fixed batch (slots 0 .. fixed_count - 1)
 };
 
 namespace {
@@ -90,24 +154,23 @@ ns_status bfail(ns_batch* b, ns_status s, const std::string& m) {
   return s;
 }
 
-#define B_CK(call)                                                                              \
-  do {                                                                                          \
-    cudaError_t e_ = (call);                                                                    \
+#define B_CK(call)                                                                                          \
+  do {                                                                                                      \
+    cudaError_t e_ = (call);                                                                                \
     if (e_ != cudaSuccess) return bfail(b, NS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-#define B_TRY(expr)           \
-  do {                        \
-    ns_status s_ = (expr);    \
-    if (s_ < 0) return s_;    \
+#define B_TRY(expr)        \
+  do {                     \
+    ns_status s_ = (expr); \
+    if (s_ < 0) return s_; \
   } while (0)
 
-// Copy `bytes` from host memory into the device staging area (stream ordered);
-// returns the device address.  The host side is a pinned mirror of the same
-// offsets, so a region is never rewritten before its copy has run: the bump
-// pointer is reset only after a stream synchronisation.
+// Copy host bytes into the device staging area (stream ordered); the host side
+// is a pinned mirror at the same offsets and the bump pointer is reset only
+// after a stream synchronisation, so no region is rewritten before its copy.
 void* stage(ns_batch* b, const void* src, size_t bytes) {
   const size_t off = rup(b->stage_used, 256);
-  if (off + bytes > b->stage_cap) return nullptr;
+  if (off + bytes > b->stage_cap - 256) return nullptr;
   memcpy(b->hstage + off, src, bytes);
   if (cudaMemcpyAsync(b->dstage + off, b->hstage + off, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return nullptr;
@@ -115,11 +178,15 @@ void* stage(ns_batch* b, const void* src, size_t bytes) {
   return b->dstage + off;
 }
 
+size_t prob_index(const ns_batch* b, int i, int type, int cur, int x3) {
+  return ((static_cast<size_t>(i) * b->ntypes + type) * 2 + cur) * 2 + x3;
+}
+
 // Product types of one step: order 2^m -> 0: F = I - A G; 1 + 2j: X_{j+1} =
 // X_j + X_j P_j; 2 + 2j: P_{j+1} = P_j P_j (j < m - 1).  Order 3 -> 0: F
 // (with f32 master), 1: W = F + F F, 2: G' = G + G W.
 TcProblem make_problem(const ns_batch* b, int i, int type, int cur, int x3) {
-  const std::vector<BMat>& M = b->mats[i];
+  const auto& M = b->mats[i];
   const BMat& Gc = M[cur ? MG1 : MG0];
   const BMat& Gn = M[cur ? MG0 : MG1];
   const BMat *L = nullptr, *R = nullptr, *D = nullptr;
@@ -188,10 +255,6 @@ TcProblem make_problem(const ns_batch* b, int i, int type, int cur, int x3) {
   return P;
 }
 
-size_t prob_index(const ns_batch* b, int i, int type, int cur, int x3) {
-  return ((static_cast<size_t>(i) * b->ntypes + type) * 2 + cur) * 2 + x3;
-}
-
 double step_cost_i(const ns_batch* b, int i, int prec) {
   const double n = b->n[i];
   const int prods = b->levels == 0 ? 3 : 2 * b->levels;
@@ -202,8 +265,104 @@ double sweep_cost_i(const ns_batch* b, int i) {
   return std::max(12.0 * n * n / 5.0e12, 22.0 * n * n * b->nrhs[i] / 3.0e13) + 3e-5;
 }
 
-// Launch the products of `types` for the instances in `ids` (each with its own
-// current G and precision), one list-driven launch per (tile width, precision).
+// Allocate and build a slot for (n, nrhs); -1 when no slot or memory is free.
+// With `copies` the slot also holds A, B and theta (a server request); else
+// the caller's buffers are attached by attach_fixed().
+int add_slot(ns_batch* b, int n, int nrhs, bool copies) {
+  int i = -1;
+  for (int k = 0; k < b->cap; ++k)
+    if (!b->used[k]) {
+      i = k;
+      break;
+    }
+  if (i < 0) return -1;
+  const SlotLayout L = slot_layout(n, nrhs, copies);
+  const size_t off = b->arena.alloc(L.bytes);
+  if (off == SIZE_MAX) return -1;
+  char* base = b->abase + off;
+  if (cudaMemsetAsync(base, 0, L.bytes, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    b->arena.release(off, L.bytes);
+    return -1;
+  }
+  b->used[i] = 1;
+  b->reg_off[i] = off;
+  b->lay[i] = L;
+  b->n[i] = n;
+  b->nrhs[i] = nrhs;
+  b->ld[i] = static_cast<int>(rup(n, 64));
+  b->bn[i] = tile_width(n);
+  b->tiles_m[i] = (n + 127) / 128;
+  b->tiles_n[i] = (n + b->bn[i] - 1) / b->bn[i];
+  const int64_t ldi = b->ld[i];
+  for (int m = 0; m < kNumMats; ++m) {
+    BMat& M = b->mats[i][m];
+    M.m32 = L.mat[m][0] == SIZE_MAX ? nullptr : reinterpret_cast<float*>(base + L.mat[m][0]);
+    M.hi = reinterpret_cast<bf16*>(base + L.mat[m][1]);
+    M.lo = reinterpret_cast<bf16*>(base + L.mat[m][2]);
+    encode_bf16_map(&M.map_hi, M.hi, ldi, ldi, ldi, 0);
+    encode_bf16_map(&M.map_lo, M.lo, ldi, ldi, ldi, 0);
+    encode_bf16_map(&M.l3_hi, M.hi, ldi, ldi, ldi, 1);
+    encode_bf16_map(&M.l3_lo, M.lo, ldi, ldi, ldi, 1);
+    encode_bf16_map(&M.r3_hi, M.hi, ldi, ldi, ldi, 2);
+    encode_bf16_map(&M.r3_lo, M.lo, ldi, ldi, ldi, 2);
+  }
+  BInst& I = b->hinst[i];
+  memset(&I, 0, sizeof(I));
+  I.n = n;
+  I.nrhs = nrhs;
+  I.ld = b->ld[i];
+  I.nfrob = b->tiles_m[i] * b->tiles_n[i] * 4;
+  I.Ahi = b->mats[i][MA].hi;
+  I.Alo = b->mats[i][MA].lo;
+  I.A1 = reinterpret_cast<float*>(base + L.a1);
+  I.A2 = reinterpret_cast<float*>(base + L.a2);
+  I.T1 = reinterpret_cast<float*>(base + L.t1);
+  I.T2 = reinterpret_cast<float*>(base + L.t2);
+  I.R32T = reinterpret_cast<float*>(base + L.r32t);
+  I.R = reinterpret_cast<double*>(base + L.r);
+  I.part = reinterpret_cast<double*>(base + L.part);
+  I.fpart = reinterpret_cast<double*>(base + L.fpart);
+  I.scal = b->dscal + static_cast<size_t>(i) * b->scal_stride;
+  if (copies) {
+    I.A = reinterpret_cast<const double*>(base + L.acopy);
+    I.B = reinterpret_cast<const double*>(base + L.bcopy);
+    I.Th = reinterpret_cast<double*>(base + L.tcopy);
+  }
+  for (int c = 0; c < 2; ++c) {
+    const BMat& G = b->mats[i][c ? MG1 : MG0];
+    I.G32[c] = G.m32;
+    I.Ghi[c] = G.hi;
+    I.Glo[c] = G.lo;
+  }
+  b->st[i] = InstState();
+  return i;
+}
+
+void free_slot(ns_batch* b, int i) {
+  if (i < 0 || i >= b->cap || !b->used[i]) return;
+  b->arena.release(b->reg_off[i], b->lay[i].bytes);
+  b->used[i] = 0;
+}
+
+// Upload a slot's row-kernel descriptor and all its product descriptors.
+ns_status publish_slot(ns_batch* b, int i, bool problems) {
+  if (problems) {
+    std::vector<TcProblem> probs(static_cast<size_t>(b->ntypes) * 4);
+    for (int t = 0; t < b->ntypes; ++t)
+      for (int c = 0; c < 2; ++c)
+        for (int x = 0; x < 2; ++x) probs[(static_cast<size_t>(t) * 2 + c) * 2 + x] = make_problem(b, i, t, c, x);
+    const void* dp = stage(b, probs.data(), probs.size() * sizeof(TcProblem));
+    if (!dp) return bfail(b, NS_ERR_OOM, "staging area exhausted");
+    B_CK(cudaMemcpyAsync(b->dprob + prob_index(b, i, 0, 0, 0), dp, probs.size() * sizeof(TcProblem),
+                         cudaMemcpyDeviceToDevice, b->stream));
+  }
+  const void* di = stage(b, &b->hinst[i], sizeof(BInst));
+  if (!di) return bfail(b, NS_ERR_OOM, "staging area exhausted");
+  B_CK(cudaMemcpyAsync(b->dinst + i, di, sizeof(BInst), cudaMemcpyDeviceToDevice, b->stream));
+  return NS_OK;
+}
+
 ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::vector<int>& types) {
   for (int bnv : {128, 256}) {
     for (int x3 = 0; x3 < 2; ++x3) {
@@ -220,7 +379,7 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
       }
       if (items.empty()) continue;
       const TcItem* ditems = static_cast<const TcItem*>(stage(b, items.data(), items.size() * sizeof(TcItem)));
-      if (!ditems) return bfail(b, NS_ERR_OOM, "batch staging area exhausted");
+      if (!ditems) return bfail(b, NS_ERR_OOM, "staging area exhausted");
       TcParams p;
       memset(&p, 0, sizeof(p));
       p.gprob = b->dprob;
@@ -267,11 +426,18 @@ std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids, boo
 }
 
 ns_status sync_read(ns_batch* b) {
-  B_CK(cudaMemcpyAsync(b->hscal, b->dscal, b->scal_total * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-  int herr = 0;
-  B_CK(cudaMemcpyAsync(&herr, b->derr, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  int hi_slot = 0;
+  for (int k = 0; k < b->cap; ++k)
+    if (b->used[k]) hi_slot = k + 1;
+  if (hi_slot > 0)
+    B_CK(cudaMemcpyAsync(b->hscal, b->dscal, static_cast<size_t>(hi_slot) * b->scal_stride * sizeof(double),
+                         cudaMemcpyDeviceToHost, b->stream));
+  char* herr_slot = b->hstage + b->stage_cap - 64;
+  B_CK(cudaMemcpyAsync(herr_slot, b->derr, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   B_CK(cudaStreamSynchronize(b->stream));
   b->stage_used = 0;
+  int herr = 0;
+  memcpy(&herr, herr_slot, sizeof(int));
   if (herr != DEV_OK) {
     cudaMemsetAsync(b->derr, 0, sizeof(int), b->stream);
     cudaStreamSynchronize(b->stream);
@@ -284,7 +450,7 @@ template <typename F>
 ns_status run_rows(ns_batch* b, const std::vector<BItem>& items, F launch) {
   if (items.empty()) return NS_OK;
   const BItem* d = static_cast<const BItem*>(stage(b, items.data(), items.size() * sizeof(BItem)));
-  if (!d) return bfail(b, NS_ERR_OOM, "batch staging area exhausted");
+  if (!d) return bfail(b, NS_ERR_OOM, "staging area exhausted");
   B_CK(launch(d, static_cast<int>(items.size())));
   if (b->stats) b->stats->kernel_launches++;
   return NS_OK;
@@ -294,17 +460,18 @@ ns_status run_list(ns_batch* b, const std::vector<int>& ids,
                    cudaError_t (*launch)(const BInst*, const int*, int, cudaStream_t)) {
   if (ids.empty()) return NS_OK;
   const int* d = static_cast<const int*>(stage(b, ids.data(), ids.size() * sizeof(int)));
-  if (!d) return bfail(b, NS_ERR_OOM, "batch staging area exhausted");
+  if (!d) return bfail(b, NS_ERR_OOM, "staging area exhausted");
   B_CK(launch(b->dinst, d, static_cast<int>(ids.size()), b->stream));
   if (b->stats) b->stats->kernel_launches++;
   return NS_OK;
 }
 
-// One controller decision for instance i after its residual (and ||F||, when
-// its Newton-Schulz loop is active) were read.  Mirrors the single-system run.
-void decide(ns_batch* b, int i, double tol) {
+// One controller decision for system i after its residual (and ||F||, while
+// its Newton-Schulz loop runs) were read.  Same rules as the single-system run.
+void decide(ns_batch* b, int i) {
   InstState& s = b->st[i];
-  const double* sc = b->hscal + b->scal_off[i];
+  const double tol = s.tol;
+  const double* sc = b->hscal + static_cast<size_t>(i) * b->scal_stride;
   const int nr = b->nrhs[i];
   double rr = 0.0;
   for (int c = 0; c < nr; ++c) {
@@ -313,7 +480,6 @@ void decide(ns_batch* b, int i, double tol) {
     rr = std::max(rr, std::isnan(q) ? INFINITY : q);
   }
   s.rel_res = rr;
-  s.last_rr = rr;
   s.recompute = false;
   if (!std::isfinite(rr)) {
     s.finished = true;
@@ -326,7 +492,19 @@ void decide(ns_batch* b, int i, double tol) {
     s.status = NS_OK;
     return;
   }
-  if (!s.ns_active) return;
+  if (!s.ns_active) {
+    // Richardson alone: stop when it no longer contracts (rho(I - A G) ~ 1 at
+    // this precision) instead of spending the whole sweep budget
+    const double prev = s.last_rr_sweep;
+    s.last_rr_sweep = rr;
+    if (std::isfinite(prev)) s.stall = rr > 0.95 * prev ? s.stall + 1 : 0;
+    s.best_rr = std::min(s.best_rr, rr);
+    if (s.stall >= 4 || rr > 10.0 * s.best_rr) {
+      s.finished = true;
+      s.status = NS_NOT_CONVERGED;
+    }
+    return;
+  }
   const double frob = std::sqrt(sc[2]);
   if (!std::isfinite(frob)) {
     s.finished = true;
@@ -369,177 +547,271 @@ void decide(ns_batch* b, int i, double tol) {
     }
     if (stop) s.ns_active = false;
   }
-  s.frob_now = frob;  // bookkeeping of the step that follows
+  s.frob_now = frob;
 }
 
-}  // namespace
-
-extern "C" {
-
-ns_status ns_batch_create(int count, const int64_t* n, const int* nrhs, int order, const ns_options* opt,
-                          ns_batch** out) {
-  if (!out || count <= 0 || !n || !nrhs) return NS_ERR_ARG;
-  ns_options o;
-  if (opt)
-    o = *opt;
-  else
-    ns_default_options(&o);
-  if (o.form != 0 || o.pow_mode != 0) return NS_ERR_UNSUPPORTED;
-  if (o.precision != NS_AUTO && o.precision != NS_BF16 && o.precision != NS_BF16X3) return NS_ERR_UNSUPPORTED;
-  if (order != 3 && (order < 2 || (order & (order - 1)) != 0)) return NS_ERR_ARG;
-  for (int i = 0; i < count; ++i)
-    if (n[i] <= 0 || n[i] > 16384 || nrhs[i] <= 0 || nrhs[i] > 1024) return NS_ERR_ARG;
-  if (o.timeout_s <= 0) o.timeout_s = 2.0;
-  ns_batch* b = new ns_batch();
-  b->count = count;
-  b->order = order;
-  b->levels = 0;
-  if (order != 3)
-    while ((1 << b->levels) < order) ++b->levels;
-  b->ntypes = order == 3 ? 3 : 2 * b->levels;
-  b->opt = o;
-  if (cudaGetDevice(&b->device) != cudaSuccess) {
-    cudaGetLastError();
-    delete b;
-    return NS_ERR_CUDA;
+// Preparation of newly admitted systems: norms, splits and limbs of A, G0,
+// theta = 0 and its limbs.  iters[k] / tol[k] belong to ids[k].
+ns_status prep_slots(ns_batch* b, const std::vector<int>& ids, const std::vector<int>& iters,
+                     const std::vector<double>& tol) {
+  if (ids.empty()) return NS_OK;
+  for (size_t k = 0; k < ids.size(); ++k) {
+    const int i = ids[k];
+    InstState s;
+    s.prec = b->opt.precision == NS_AUTO ? NS_BF16 : b->opt.precision;
+    s.sweeps_left = b->opt.max_sweeps;
+    s.ns_active = iters[k] > 0;
+    s.iters = iters[k];
+    s.tol = tol[k];
+    b->st[i] = s;
   }
-  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
-  b->n.assign(n, n + count);
-  b->nrhs.assign(nrhs, nrhs + count);
-  b->ld.resize(count);
-  b->bn.resize(count);
-  b->tiles_m.resize(count);
-  b->tiles_n.resize(count);
-  // ---- sizes and offsets of every per-instance region inside one allocation
-  struct Reg {
-    size_t off, bytes;
-  };
+  B_TRY(run_rows(b, row_items(b, ids, false),
+                 [&](const BItem* d, int k) { return launch_bprep(b->dinst, d, k, b->stream); }));
+  B_TRY(run_list(b, ids, launch_bnorms));
+  B_TRY(run_rows(b, row_items(b, ids, false), [&](const BItem* d, int k) {
+    return launch_bg0(b->dinst, d, k, b->opt.g0_mode, 1, b->stream);
+  }));
+  return NS_OK;
+}
+
+// One controller pass over the active systems: residual (+ ||F|| while NS
+// runs) -> one device sync -> decisions -> Richardson update and next NS step.
+ns_status pass(ns_batch* b, const std::vector<int>& act) {
+  std::vector<int> nsact;
+  for (int i : act)
+    if (b->st[i].ns_active) nsact.push_back(i);
+  B_TRY(run_rows(b, row_items(b, act, true),
+                 [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+  B_TRY(run_list(b, act, launch_brsq));
+  if (!nsact.empty()) {
+    B_TRY(launch_products(b, nsact, {0}));
+    B_TRY(run_list(b, nsact, launch_bfrob));
+  }
+  B_TRY(sync_read(b));
+  for (int i : act) decide(b, i);
+  for (int guard = 0; guard < 4; ++guard) {
+    std::vector<int> redo;
+    for (int i : act)
+      if (b->st[i].recompute && !b->st[i].finished) redo.push_back(i);
+    if (redo.empty()) break;
+    B_TRY(launch_products(b, redo, {0}));
+    B_TRY(run_list(b, redo, launch_bfrob));
+    B_TRY(sync_read(b));
+    for (int i : redo) decide(b, i);
+  }
+  std::vector<int> step, upd;
+  for (int i : act) {
+    InstState& s = b->st[i];
+    if (s.finished) continue;
+    if (s.ns_active) {
+      step.push_back(i);
+      upd.push_back(i);
+    } else if (s.sweeps_left > 0) {
+      upd.push_back(i);
+      s.sweeps_left--;
+    } else {
+      s.finished = true;
+      s.status = NS_NOT_CONVERGED;
+    }
+  }
+  // the update applies G_k (current buffer); the chain writes the other one
+  if (!upd.empty())
+    B_TRY(run_rows(b, row_items(b, upd, true),
+                   [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
+  if (!step.empty()) {
+    if (b->levels == 0) {
+      B_TRY(launch_products(b, step, {1}));
+      B_TRY(launch_products(b, step, {2}));
+    } else {
+      for (int j = 0; j < b->levels; ++j) {
+        if (j + 1 < b->levels)
+          B_TRY(launch_products(b, step, {1 + 2 * j, 2 + 2 * j}));
+        else
+          B_TRY(launch_products(b, step, {1 + 2 * j}));
+      }
+    }
+  }
+  for (int i : upd) b->st[i].sweeps++;
+  for (int i : step) {
+    InstState& s = b->st[i];
+    s.prev_ratio = (s.done > 0 && std::isfinite(s.prev_frob)) ? s.frob_now / s.prev_frob : INFINITY;
+    s.prev_frob = s.frob_now;
+    s.cur ^= 1;
+    s.done++;
+    if (s.done >= s.iters) s.ns_active = false;
+  }
+  return NS_OK;
+}
+
+// Options the batched path supports, checked for both the batch and the server.
+ns_status check_opts(ns_options* o, const ns_options* opt, int order) {
+  if (opt)
+    *o = *opt;
+  else
+    ns_default_options(o);
+  if (o->form != 0 || o->pow_mode != 0) return NS_ERR_UNSUPPORTED;
+  if (o->precision != NS_AUTO && o->precision != NS_BF16 && o->precision != NS_BF16X3) return NS_ERR_UNSUPPORTED;
+  if (order != 3 && (order < 2 || order > 64 || (order & (order - 1)) != 0)) return NS_ERR_ARG;
+  if (o->timeout_s <= 0) o->timeout_s = 2.0;
+  return NS_OK;
+}
+
+// Tables, staging and arena in one device allocation.
+ns_status alloc_batch(ns_batch* b, int cap, int max_nrhs, size_t arena_bytes) {
+  b->cap = cap;
+  b->max_nrhs = max_nrhs;
+  b->scal_stride = kScalR + 2 * max_nrhs;
+  b->stage_cap = std::max<size_t>(16u << 20, static_cast<size_t>(cap) * 48 * 1024);
   size_t total = 0;
   auto take = [&](size_t bytes) {
     const size_t off = rup(total, 256);
     total = off + bytes;
     return off;
   };
-  std::vector<std::vector<size_t>> off(count);
-  b->scal_off.resize(count);
-  size_t scal_total = 0;
-  for (int i = 0; i < count; ++i) {
-    const int ni = static_cast<int>(n[i]);
-    const int64_t ldi = rup(ni, 64);
-    b->ld[i] = static_cast<int>(ldi);
-    b->bn[i] = ni <= 512 ? 128 : 256;
-    b->tiles_m[i] = (ni + 127) / 128;
-    b->tiles_n[i] = (ni + b->bn[i] - 1) / b->bn[i];
-    const size_t sq = static_cast<size_t>(ldi) * ldi;
-    std::vector<size_t>& o2 = off[i];
-    for (int m = 0; m < kNumMats; ++m) {
-      const bool with32 = m == MG0 || m == MG1 || m == MX0 || m == MX1 || m == MF;
-      o2.push_back(with32 ? take(sq * 4) : SIZE_MAX);
-      o2.push_back(take(sq * 2));
-      o2.push_back(take(sq * 2));
-    }
-    const int nrb = (ni + 7) / 8;
-    o2.push_back(take(static_cast<size_t>(ni) * ldi * 4));                        // A1
-    o2.push_back(take(static_cast<size_t>(ni) * ldi * 4));                        // A2
-    o2.push_back(take(static_cast<size_t>(nrhs[i]) * ldi * 4));                   // T1
-    o2.push_back(take(static_cast<size_t>(nrhs[i]) * ldi * 4));                   // T2
-    o2.push_back(take(static_cast<size_t>(nrhs[i]) * ldi * 4));                   // R32T
-    o2.push_back(take(static_cast<size_t>(ni) * nrhs[i] * 8));                    // R
-    o2.push_back(take(static_cast<size_t>(std::max(2 * nrb, nrb * nrhs[i])) * 8));  // part
-    o2.push_back(take(static_cast<size_t>(b->tiles_m[i]) * b->tiles_n[i] * 4 * 8));  // fpart
-    b->scal_off[i] = scal_total;
-    scal_total += kScalR + 2 * static_cast<size_t>(nrhs[i]);
-  }
-  b->scal_total = scal_total;
-  const size_t probs_off = take(sizeof(TcProblem) * static_cast<size_t>(count) * b->ntypes * 4 + 64);
-  const size_t inst_off = take(sizeof(BInst) * static_cast<size_t>(count));
-  const size_t scal_off = take(scal_total * 8);
-  const size_t err_off = take(64);
-  b->stage_cap = std::max<size_t>(16u << 20, static_cast<size_t>(count) * 64 * 1024);
-  const size_t stage_off = take(b->stage_cap);
-  b->dbytes = total;
+  const size_t o_prob = take(sizeof(TcProblem) * static_cast<size_t>(cap) * b->ntypes * 4 + 64);
+  const size_t o_inst = take(sizeof(BInst) * static_cast<size_t>(cap));
+  const size_t o_scal = take(sizeof(double) * static_cast<size_t>(cap) * b->scal_stride);
+  const size_t o_err = take(64);
+  const size_t o_stage = take(b->stage_cap);
+  const size_t o_arena = take(arena_bytes);
   if (cudaMalloc(&b->dmem, total) != cudaSuccess) {
     cudaGetLastError();
-    delete b;
     return NS_ERR_OOM;
   }
   char* base = static_cast<char*>(b->dmem);
-  if (cudaMemset(base, 0, total) != cudaSuccess || cudaMallocHost(&b->hscal, scal_total * 8) != cudaSuccess ||
+  if (cudaMemset(base, 0, o_arena) != cudaSuccess || cudaMallocHost(&b->hscal, sizeof(double) * cap * b->scal_stride) !=
+                                                         cudaSuccess ||
       cudaMallocHost(&b->hstage, b->stage_cap) != cudaSuccess) {
     cudaGetLastError();
-    ns_batch_destroy(b);
     return NS_ERR_OOM;
   }
-  b->dprob = reinterpret_cast<TcProblem*>(rup(reinterpret_cast<uintptr_t>(base + probs_off), 64));
-  b->dinst = reinterpret_cast<BInst*>(base + inst_off);
-  b->dscal = reinterpret_cast<double*>(base + scal_off);
-  b->derr = reinterpret_cast<int*>(base + err_off);
-  b->dstage = base + stage_off;
-  // ---- matrices, tensor maps, instance descriptors
-  b->mats.assign(count, std::vector<BMat>(kNumMats));
-  b->hinst.resize(count);
-  for (int i = 0; i < count; ++i) {
-    const int64_t ldi = b->ld[i];
-    const std::vector<size_t>& o2 = off[i];
-    for (int m = 0; m < kNumMats; ++m) {
-      BMat& M = b->mats[i][m];
-      M.m32 = o2[3 * m] == SIZE_MAX ? nullptr : reinterpret_cast<float*>(base + o2[3 * m]);
-      M.hi = reinterpret_cast<bf16*>(base + o2[3 * m + 1]);
-      M.lo = reinterpret_cast<bf16*>(base + o2[3 * m + 2]);
-      if (!encode_bf16_map(&M.map_hi, M.hi, ldi, ldi, ldi, 0) || !encode_bf16_map(&M.map_lo, M.lo, ldi, ldi, ldi, 0) ||
-          !encode_bf16_map(&M.l3_hi, M.hi, ldi, ldi, ldi, 1) || !encode_bf16_map(&M.l3_lo, M.lo, ldi, ldi, ldi, 1) ||
-          !encode_bf16_map(&M.r3_hi, M.hi, ldi, ldi, ldi, 2) || !encode_bf16_map(&M.r3_lo, M.lo, ldi, ldi, ldi, 2)) {
-        ns_batch_destroy(b);
-        return NS_ERR_CUDA;
-      }
-    }
-    const size_t k0 = 3 * kNumMats;
-    BInst& I = b->hinst[i];
-    memset(&I, 0, sizeof(I));
-    I.n = b->n[i];
-    I.nrhs = b->nrhs[i];
-    I.ld = b->ld[i];
-    I.nfrob = b->tiles_m[i] * b->tiles_n[i] * 4;
-    I.Ahi = b->mats[i][MA].hi;
-    I.Alo = b->mats[i][MA].lo;
-    I.A1 = reinterpret_cast<float*>(base + o2[k0]);
-    I.A2 = reinterpret_cast<float*>(base + o2[k0 + 1]);
-    I.T1 = reinterpret_cast<float*>(base + o2[k0 + 2]);
-    I.T2 = reinterpret_cast<float*>(base + o2[k0 + 3]);
-    I.R32T = reinterpret_cast<float*>(base + o2[k0 + 4]);
-    I.R = reinterpret_cast<double*>(base + o2[k0 + 5]);
-    I.part = reinterpret_cast<double*>(base + o2[k0 + 6]);
-    I.fpart = reinterpret_cast<double*>(base + o2[k0 + 7]);
-    I.scal = b->dscal + b->scal_off[i];
-    for (int c = 0; c < 2; ++c) {
-      const BMat& G = b->mats[i][c ? MG1 : MG0];
-      I.G32[c] = G.m32;
-      I.Ghi[c] = G.hi;
-      I.Glo[c] = G.lo;
-    }
-  }
-  std::vector<TcProblem> probs(static_cast<size_t>(count) * b->ntypes * 4);
-  for (int i = 0; i < count; ++i)
-    for (int t = 0; t < b->ntypes; ++t)
-      for (int c = 0; c < 2; ++c)
-        for (int x = 0; x < 2; ++x) probs[prob_index(b, i, t, c, x)] = make_problem(b, i, t, c, x);
-  if (cudaMemcpy(b->dprob, probs.data(), probs.size() * sizeof(TcProblem), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaGetLastError();
-    ns_batch_destroy(b);
-    return NS_ERR_CUDA;
-  }
-  b->st.assign(count, InstState());
-  *out = b;
+  b->dprob = reinterpret_cast<TcProblem*>(rup(reinterpret_cast<uintptr_t>(base + o_prob), 64));
+  b->dinst = reinterpret_cast<BInst*>(base + o_inst);
+  b->dscal = reinterpret_cast<double*>(base + o_scal);
+  b->derr = reinterpret_cast<int*>(base + o_err);
+  b->dstage = base + o_stage;
+  b->abase = base + o_arena;
+  b->asize = arena_bytes;
+  b->arena.init(arena_bytes);
+  b->used.assign(cap, 0);
+  b->reg_off.assign(cap, 0);
+  b->lay.assign(cap, SlotLayout());
+  b->n.assign(cap, 0);
+  b->nrhs.assign(cap, 0);
+  b->ld.assign(cap, 0);
+  b->bn.assign(cap, 0);
+  b->tiles_m.assign(cap, 0);
+  b->tiles_n.assign(cap, 0);
+  b->mats.assign(cap, std::array<BMat, kNumMats>());
+  b->hinst.assign(cap, BInst());
+  b->st.assign(cap, InstState());
   return NS_OK;
 }
 
-ns_status ns_batch_destroy(ns_batch* b) {
-  if (!b) return NS_OK;
+ns_status init_batch(ns_batch* b, int order, const ns_options* opt) {
+  ns_status s = check_opts(&b->opt, opt, order);
+  if (s != NS_OK) return s;
+  b->order = order;
+  b->levels = 0;
+  if (order != 3)
+    while ((1 << b->levels) < order) ++b->levels;
+  b->ntypes = order == 3 ? 3 : 2 * b->levels;
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  return NS_OK;
+}
+
+void release_batch(ns_batch* b) {
+  if (!b) return;
   cudaStreamSynchronize(b->stream);
   if (b->dmem) cudaFree(b->dmem);
   if (b->hscal) cudaFreeHost(b->hscal);
   if (b->hstage) cudaFreeHost(b->hstage);
   delete b;
+}
+
+}  // namespace
+
+// ============================================================== server state
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  ns_request r;
+  Clock::time_point t_submit, t_admit;
+  bool done = false;
+  ns_result res;
+};
+
+}  // namespace
+
+struct ns_server {
+  ns_batch* b = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::mutex mu;       // queue, request records, slot tickets, statistics
+  std::mutex tick_mu;  // one tick at a time
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Req> reqs;
+  std::vector<uint64_t> slot_ticket;  // 0: slot free or not yet owned
+  std::vector<int> retiring;          // slots whose theta copy is in flight
+  uint64_t next_ticket = 1;
+  std::thread worker;
+  bool running = false, stopping = false;
+  ns_server_stats stats;
+  std::string err;
+};
+
+// ====================================================================== ABI
+extern "C" {
+
+ns_status ns_batch_create(int count, const int64_t* n, const int* nrhs, int order, const ns_options* opt,
+                          ns_batch** out) {
+  if (!out || count <= 0 || !n || !nrhs) return NS_ERR_ARG;
+  int max_nrhs = 1;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] <= 0 || n[i] > 16384 || nrhs[i] <= 0 || nrhs[i] > 1024) return NS_ERR_ARG;
+    max_nrhs = std::max(max_nrhs, nrhs[i]);
+  }
+  ns_batch* b = new ns_batch();
+  ns_status s = init_batch(b, order, opt);
+  if (s != NS_OK) {
+    delete b;
+    return s;
+  }
+  size_t arena = 0;
+  for (int i = 0; i < count; ++i) arena += slot_layout(static_cast<int>(n[i]), nrhs[i], false).bytes;
+  s = alloc_batch(b, count, max_nrhs, arena);
+  if (s != NS_OK) {
+    release_batch(b);
+    return s;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (add_slot(b, static_cast<int>(n[i]), nrhs[i], false) != i || publish_slot(b, i, true) != NS_OK) {
+      release_batch(b);
+      return NS_ERR_OOM;
+    }
+    if (b->stage_used > b->stage_cap / 2) {
+      cudaStreamSynchronize(b->stream);
+      b->stage_used = 0;
+    }
+  }
+  b->fixed_count = count;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    release_batch(b);
+    return NS_ERR_CUDA;
+  }
+  b->stage_used = 0;
+  *out = b;
+  return NS_OK;
+}
+
+ns_status ns_batch_destroy(ns_batch* b) {
+  release_batch(b);
   return NS_OK;
 }
 
@@ -553,130 +825,52 @@ const char* ns_batch_last_error(const ns_batch* b) { return b ? b->err.c_str() :
 
 ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* const* B, double* const* Theta,
                          int iters, double tol, ns_batch_stats* stats) {
-  if (!b || !A || !B || !Theta || iters < 0) return NS_ERR_ARG;
-  auto t0 = std::chrono::steady_clock::now();
+  if (!b || !A || !B || !Theta || iters < 0 || b->fixed_count <= 0) return NS_ERR_ARG;
+  const auto t0 = Clock::now();
   b->err.clear();
   b->stats = stats;
   if (stats) memset(stats, 0, sizeof(*stats));
   B_CK(cudaSetDevice(b->device));
-  const int count = b->count;
+  const int count = b->fixed_count;
+  b->stage_used = 0;
+  std::vector<int> all(count);
   for (int i = 0; i < count; ++i) {
     if (!A[i] || !B[i] || !Theta[i]) return bfail(b, NS_ERR_ARG, "null instance pointer");
+    all[i] = i;
     b->hinst[i].A = A[i];
     b->hinst[i].B = B[i];
     b->hinst[i].Th = Theta[i];
   }
   B_CK(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, b->stream));
-  b->stage_used = 0;
-  std::vector<int> all(count);
-  for (int i = 0; i < count; ++i) {
-    all[i] = i;
-    InstState s;
-    s.prec = b->opt.precision == NS_AUTO ? NS_BF16 : b->opt.precision;
-    s.sweeps_left = b->opt.max_sweeps;
-    s.ns_active = iters > 0;
-    b->st[i] = s;
-  }
-  // ---- preparation: norms, operand splits, G0, theta = 0 and its limbs
-  B_TRY(run_rows(b, row_items(b, all, false),
-                 [&](const BItem* d, int k) { return launch_bprep(b->dinst, d, k, b->stream); }));
-  B_TRY(run_list(b, all, launch_bnorms));
-  B_TRY(run_rows(b, row_items(b, all, false), [&](const BItem* d, int k) {
-    return launch_bg0(b->dinst, d, k, b->opt.g0_mode, 1, b->stream);
-  }));
+  B_TRY(prep_slots(b, all, std::vector<int>(count, iters), std::vector<double>(count, tol)));
   int passes = 0;
   for (;;) {
-    std::vector<int> act, nsact;
-    for (int i = 0; i < count; ++i) {
-      if (b->st[i].finished) continue;
-      act.push_back(i);
-      if (b->st[i].ns_active) nsact.push_back(i);
-    }
+    std::vector<int> act;
+    for (int i = 0; i < count; ++i)
+      if (!b->st[i].finished) act.push_back(i);
     if (act.empty()) break;
     ++passes;
-    B_TRY(run_rows(b, row_items(b, act, true),
-                   [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
-    B_TRY(run_list(b, act, launch_brsq));
-    if (!nsact.empty()) {
-      B_TRY(launch_products(b, nsact, {0}));
-      B_TRY(run_list(b, nsact, launch_bfrob));
-    }
-    B_TRY(sync_read(b));
-    for (int i : act) decide(b, i, tol);
-    // instances whose F must be formed again (precision switch / rollback)
-    for (int guard = 0; guard < 4; ++guard) {
-      std::vector<int> redo;
-      for (int i : act)
-        if (b->st[i].recompute && !b->st[i].finished) redo.push_back(i);
-      if (redo.empty()) break;
-      B_TRY(launch_products(b, redo, {0}));
-      B_TRY(run_list(b, redo, launch_bfrob));
-      B_TRY(sync_read(b));
-      for (int i : redo) decide(b, i, tol);
-    }
-    // actions: next NS step (+ coupled sweep) or plain sweeps
-    std::vector<int> step, upd;
-    std::vector<int> gused(count, 0);
-    for (int i : act) {
-      InstState& s = b->st[i];
-      if (s.finished) continue;
-      if (s.ns_active) {
-        step.push_back(i);
-        upd.push_back(i);
-        gused[i] = s.cur;
-      } else if (s.sweeps_left > 0) {
-        upd.push_back(i);
-        gused[i] = s.cur;
-        s.sweeps_left--;
-      } else {
-        s.finished = true;
-        s.status = NS_NOT_CONVERGED;
-      }
-    }
-    if (!step.empty()) {
-      if (b->levels == 0) {
-        B_TRY(launch_products(b, step, {1}));
-        B_TRY(launch_products(b, step, {2}));
-      } else {
-        for (int j = 0; j < b->levels; ++j) {
-          if (j + 1 < b->levels)
-            B_TRY(launch_products(b, step, {1 + 2 * j, 2 + 2 * j}));
-          else
-            B_TRY(launch_products(b, step, {1 + 2 * j}));
-        }
-      }
-    }
-    if (!upd.empty()) {
-      std::vector<BItem> it = row_items(b, upd, true);
-      for (BItem& x : it) x.cur = gused[x.inst];
-      B_TRY(run_rows(b, it, [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
-    }
-    for (int i : upd) b->st[i].sweeps++;
-    for (int i : step) {
-      InstState& s = b->st[i];
-      const double frob = s.frob_now;
-      s.prev_ratio = (s.done > 0 && std::isfinite(s.prev_frob)) ? frob / s.prev_frob : INFINITY;
-      s.prev_frob = frob;
-      s.cur ^= 1;
-      s.done++;
-      if (s.done >= iters) s.ns_active = false;
-    }
+    B_TRY(pass(b, act));
     if (passes > iters + b->opt.max_sweeps + 8) break;
   }
   B_CK(cudaStreamSynchronize(b->stream));
+  b->stage_used = 0;
   int nconv = 0, nfail = 0;
   for (int i = 0; i < count; ++i) {
+    if (!b->st[i].finished) {
+      b->st[i].finished = true;
+      b->st[i].status = NS_NOT_CONVERGED;
+    }
     if (b->st[i].converged)
       nconv++;
     else
       nfail++;
-    if (!b->st[i].finished) b->st[i].status = NS_NOT_CONVERGED;
   }
   if (stats) {
     stats->passes = passes;
     stats->converged = nconv;
     stats->not_converged = nfail;
-    stats->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->wall_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
     double useful = 0.0;
     for (int i = 0; i < count; ++i) useful += 2.0 * b->n[i] * static_cast<double>(b->n[i]) * b->n[i];
     stats->useful_flops_per_product = useful;
@@ -686,12 +880,255 @@ ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* cons
 }
 
 ns_status ns_batch_result(const ns_batch* b, int i, int* status, int* ns_iters, int* sweeps, double* rel_res) {
-  if (!b || i < 0 || i >= b->count) return NS_ERR_ARG;
+  if (!b || i < 0 || i >= b->fixed_count) return NS_ERR_ARG;
   const InstState& s = b->st[i];
   if (status) *status = s.status;
   if (ns_iters) *ns_iters = s.done;
   if (sweeps) *sweeps = s.sweeps;
   if (rel_res) *rel_res = s.rel_res;
+  return NS_OK;
+}
+
+// ------------------------------------------------------------------ server
+ns_status ns_server_create(size_t mem_budget_bytes, int max_requests, int max_nrhs, int order,
+                           const ns_options* opt, ns_server** out) {
+  if (!out || mem_budget_bytes < (1u << 20) || max_requests <= 0 || max_requests > 65536 || max_nrhs <= 0 ||
+      max_nrhs > 1024)
+    return NS_ERR_ARG;
+  ns_server* sv = new ns_server();
+  sv->b = new ns_batch();
+  ns_status s = init_batch(sv->b, order, opt);
+  if (s == NS_OK && cudaStreamCreateWithFlags(&sv->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s = NS_ERR_CUDA;
+  }
+  sv->b->stream = sv->own_stream;
+  if (s == NS_OK) s = alloc_batch(sv->b, max_requests, max_nrhs, mem_budget_bytes);
+  if (s != NS_OK) {
+    release_batch(sv->b);
+    if (sv->own_stream) cudaStreamDestroy(sv->own_stream);
+    delete sv;
+    return s;
+  }
+  sv->slot_ticket.assign(max_requests, 0);
+  memset(&sv->stats, 0, sizeof(sv->stats));
+  *out = sv;
+  return NS_OK;
+}
+
+ns_status ns_server_set_stream(ns_server* sv, void* stream) {
+  if (!sv) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> tk(sv->tick_mu);
+  cudaStreamSynchronize(sv->b->stream);
+  sv->b->stream = stream ? static_cast<cudaStream_t>(stream) : sv->own_stream;
+  return NS_OK;
+}
+
+const char* ns_server_last_error(const ns_server* sv) {
+  if (!sv) return "null server";
+  return sv->err.empty() ? sv->b->err.c_str() : sv->err.c_str();
+}
+
+ns_status ns_server_submit(ns_server* sv, const ns_request* rq, uint64_t* ticket) {
+  if (!sv || !rq || !ticket || rq->n <= 0 || rq->n > 16384 || rq->nrhs <= 0 || rq->nrhs > sv->b->max_nrhs ||
+      rq->iters < 0 || !(rq->tol >= 0.0) || !rq->A || !rq->B || !rq->Theta)
+    return NS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const uint64_t t = sv->next_ticket++;
+  Req& r = sv->reqs[t];
+  r.r = *rq;
+  r.t_submit = Clock::now();
+  memset(&r.res, 0, sizeof(r.res));
+  r.res.status = NS_NOT_CONVERGED;
+  sv->queue.push_back(t);
+  sv->stats.submitted++;
+  *ticket = t;
+  sv->cv.notify_all();
+  return NS_OK;
+}
+
+ns_status ns_server_poll(ns_server* sv, uint64_t ticket, ns_result* out) {
+  if (!sv || !out) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return NS_ERR_ARG;
+  *out = it->second.res;
+  out->done = it->second.done ? 1 : 0;
+  return NS_OK;
+}
+
+ns_status ns_server_release(ns_server* sv, uint64_t ticket) {
+  if (!sv) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end() || !it->second.done) return NS_ERR_ARG;
+  sv->reqs.erase(it);
+  return NS_OK;
+}
+
+ns_status ns_server_tick(ns_server* sv, int* active_out) {
+  if (!sv) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> tk(sv->tick_mu);
+  ns_batch* b = sv->b;
+  if (cudaSetDevice(b->device) != cudaSuccess) return NS_ERR_CUDA;
+  // ---- admission, first come first served, while a slot and memory are free
+  std::vector<int> fresh;
+  std::vector<std::pair<int, ns_request>> copies;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    while (!sv->queue.empty() && b->stage_used < b->stage_cap / 2) {
+      const uint64_t t = sv->queue.front();
+      Req& r = sv->reqs[t];
+      if (slot_layout(static_cast<int>(r.r.n), r.r.nrhs, true).bytes > b->asize) {  // never fits
+        sv->queue.pop_front();
+        r.done = true;
+        r.res.status = NS_ERR_OOM;
+        sv->stats.rejected++;
+        continue;
+      }
+      const int slot = add_slot(b, static_cast<int>(r.r.n), r.r.nrhs, true);
+      if (slot < 0) break;
+      sv->queue.pop_front();
+      r.t_admit = Clock::now();
+      sv->slot_ticket[slot] = t;
+      copies.emplace_back(slot, r.r);
+      fresh.push_back(slot);
+      sv->stats.admitted++;
+    }
+  }
+  for (size_t k = 0; k < copies.size(); ++k) {
+    const int slot = copies[k].first;
+    const ns_request& q = copies[k].second;
+    const BInst& I = b->hinst[slot];
+    B_CK(cudaMemcpyAsync(const_cast<double*>(I.A), q.A, static_cast<size_t>(q.n) * q.n * sizeof(double),
+                         cudaMemcpyDefault, b->stream));
+    B_CK(cudaMemcpyAsync(const_cast<double*>(I.B), q.B, static_cast<size_t>(q.n) * q.nrhs * sizeof(double),
+                         cudaMemcpyDefault, b->stream));
+    B_TRY(publish_slot(b, slot, true));
+  }
+  {
+    std::vector<int> it;
+    std::vector<double> tl;
+    for (const auto& c : copies) {
+      it.push_back(c.second.iters);
+      tl.push_back(c.second.tol);
+    }
+    B_TRY(prep_slots(b, fresh, it, tl));
+  }
+  // ---- one controller pass over every request on the device
+  std::vector<int> act;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int k = 0; k < b->cap; ++k)
+      if (sv->slot_ticket[k] != 0 && !b->st[k].finished) act.push_back(k);
+  }
+  if (!act.empty()) {
+    B_TRY(pass(b, act));
+  } else if (!sv->retiring.empty() || !fresh.empty()) {
+    B_TRY(sync_read(b));
+  }
+  // ---- retirement: copies started by the previous tick have landed (the
+  // pass above synchronised the stream after them); start the copies of the
+  // requests that finished in this pass
+  std::vector<int> finishing;
+  for (int k : act)
+    if (b->st[k].finished) finishing.push_back(k);
+  for (int k : finishing) {
+    Req* r = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      r = &sv->reqs[sv->slot_ticket[k]];
+    }
+    const size_t nb = static_cast<size_t>(b->n[k]) * b->nrhs[k] * sizeof(double);
+    B_CK(cudaMemcpyAsync(r->r.Theta, b->hinst[k].Th, nb, cudaMemcpyDefault, b->stream));
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const auto now = Clock::now();
+    for (int k : sv->retiring) {
+      Req& r = sv->reqs[sv->slot_ticket[k]];
+      const InstState& st = b->st[k];
+      r.res.status = st.status;
+      r.res.ns_iters = st.done;
+      r.res.sweeps = st.sweeps;
+      r.res.rel_res = st.rel_res;
+      r.res.latency_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+      r.res.queue_ms = std::chrono::duration<double, std::milli>(r.t_admit - r.t_submit).count();
+      r.done = true;
+      if (st.converged) sv->stats.converged++;
+      sv->stats.completed++;
+      sv->slot_ticket[k] = 0;
+      free_slot(b, k);
+    }
+    sv->retiring = finishing;
+    int on_device = 0;
+    for (int k = 0; k < b->cap; ++k)
+      if (sv->slot_ticket[k] != 0) on_device++;
+    sv->stats.active = on_device;
+    sv->stats.queued = static_cast<int>(sv->queue.size());
+    sv->stats.ticks++;
+    if (!act.empty()) sv->stats.passes++;
+    if (active_out) *active_out = on_device;
+  }
+  return NS_OK;
+}
+
+ns_status ns_server_start(ns_server* sv) {
+  if (!sv) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->running) return NS_OK;
+  sv->running = true;
+  sv->stopping = false;
+  sv->worker = std::thread([sv]() {
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        bool busy = !sv->retiring.empty();
+        for (uint64_t t : sv->slot_ticket) busy = busy || t != 0;
+        if (!busy && sv->queue.empty()) {
+          if (sv->stopping) break;
+          sv->cv.wait_for(lk, std::chrono::milliseconds(5));
+          continue;
+        }
+      }
+      const ns_status s = ns_server_tick(sv, nullptr);
+      if (s < 0) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->err = sv->b->err.empty() ? std::string("server tick failed: ") + ns_status_string(s) : sv->b->err;
+        sv->stats.last_error = s;
+        break;
+      }
+    }
+  });
+  return NS_OK;
+}
+
+ns_status ns_server_stop(ns_server* sv) {
+  if (!sv) return NS_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->running) return NS_OK;
+    sv->stopping = true;
+    sv->cv.notify_all();
+  }
+  sv->worker.join();
+  sv->running = false;
+  return sv->stats.last_error < 0 ? static_cast<ns_status>(sv->stats.last_error) : NS_OK;
+}
+
+ns_status ns_server_get_stats(ns_server* sv, ns_server_stats* out) {
+  if (!sv || !out) return NS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *out = sv->stats;
+  return NS_OK;
+}
+
+ns_status ns_server_destroy(ns_server* sv) {
+  if (!sv) return NS_OK;
+  ns_server_stop(sv);
+  release_batch(sv->b);
+  if (sv->own_stream) cudaStreamDestroy(sv->own_stream);
+  delete sv;
   return NS_OK;
 }
 

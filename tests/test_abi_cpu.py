@@ -41,6 +41,13 @@ int main(void) {
          offsetof(ns_options, timeout_s), offsetof(ns_options, aux_ahead), sizeof(ns_stats));
   printf("%zu %zu %zu %zu\n", offsetof(ns_stats, frob_F), offsetof(ns_stats, rel_res_hist),
          offsetof(ns_stats, gemm_launches), offsetof(ns_stats, wall_ms));
+  printf("%zu %zu %zu\n", sizeof(ns_batch_stats), offsetof(ns_batch_stats, gemm_launches),
+         offsetof(ns_batch_stats, wall_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(ns_request), offsetof(ns_request, tol), offsetof(ns_request, A),
+         offsetof(ns_request, Theta));
+  printf("%zu %zu %zu\n", sizeof(ns_result), offsetof(ns_result, rel_res), offsetof(ns_result, latency_ms));
+  printf("%zu %zu %zu\n", sizeof(ns_server_stats), offsetof(ns_server_stats, active),
+         offsetof(ns_server_stats, last_error));
   return 0;
 }
 """
@@ -52,8 +59,13 @@ int main(void) {
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     got = [int(x) for x in out]
     O, S = nsgb.ns_options, nsgb.ns_stats
+    BS, Q, R, SS = nsgb.ns_batch_stats, nsgb.ns_request, nsgb.ns_result, nsgb.ns_server_stats
     want = [ctypes.sizeof(O), O.ns_stop_frob.offset, O.timeout_s.offset, O.aux_ahead.offset, ctypes.sizeof(S),
-            S.frob_F.offset, S.rel_res_hist.offset, S.gemm_launches.offset, S.wall_ms.offset]
+            S.frob_F.offset, S.rel_res_hist.offset, S.gemm_launches.offset, S.wall_ms.offset,
+            ctypes.sizeof(BS), BS.gemm_launches.offset, BS.wall_ms.offset,
+            ctypes.sizeof(Q), Q.tol.offset, Q.A.offset, Q.Theta.offset,
+            ctypes.sizeof(R), R.rel_res.offset, R.latency_ms.offset,
+            ctypes.sizeof(SS), SS.active.offset, SS.last_error.offset]
     assert got == want
 
 
@@ -120,3 +132,63 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(nsgb, "lib_path", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         nsgb.lib()
+
+
+def test_batch_and_server_validate_before_cuda(L):
+    h = ctypes.c_void_p()
+    opt = nsgb.default_options()
+    n = (ctypes.c_int64 * 2)(16, 0)
+    r = (ctypes.c_int * 2)(1, 1)
+    assert L.ns_batch_create(2, n, r, 4, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    assert L.ns_batch_create(0, n, r, 4, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    # budget below 1 MiB, no slots, nrhs out of range
+    assert L.ns_server_create(1 << 10, 8, 4, 4, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    assert L.ns_server_create(1 << 30, 0, 4, 4, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    assert L.ns_server_create(1 << 30, 8, 0, 4, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    # the batched path supports the factorized form, orders 3 and 2^m, bf16 precisions
+    bad = nsgb.default_options(form=1)
+    assert L.ns_server_create(1 << 30, 8, 4, 4, ctypes.byref(bad), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
+    bad = nsgb.default_options(precision=nsgb.NS_FP64)
+    assert L.ns_server_create(1 << 30, 8, 4, 4, ctypes.byref(bad), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
+    assert L.ns_server_create(1 << 30, 8, 4, 6, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    # null handles
+    t = ctypes.c_uint64()
+    q = nsgb.ns_request(16, 1, 8, 1e-10, 1, 1, 1)
+    assert L.ns_server_submit(None, ctypes.byref(q), ctypes.byref(t)) == nsgb.NS_ERR_ARG
+    assert L.ns_server_tick(None, None) == nsgb.NS_ERR_ARG
+    assert L.ns_server_destroy(None) == nsgb.NS_OK
+
+
+def test_arena_first_fit_and_merge():
+    """The server's workspace allocator: first fit, 256-byte granules, and
+    freed neighbours merge back into one range."""
+    gxx = shutil.which("g++") or shutil.which("c++")
+    if gxx is None:
+        pytest.skip("no C++ compiler")
+    src = r"""
+#include <cstdio>
+#include "arena.h"
+int main() {
+  nsgb::Arena a;
+  a.init(4096);
+  size_t x = a.alloc(100), y = a.alloc(256), z = a.alloc(1000), w = a.alloc(4096);
+  std::printf("%zu %zu %zu %zu %zu\n", x, y, z, w == SIZE_MAX, a.free_bytes());
+  a.release(y, 256);                      // hole of 256 between x and z
+  size_t u = a.alloc(300);                // does not fit the hole: goes after z
+  size_t v = a.alloc(200);                // first fit: the hole
+  std::printf("%zu %zu %zu\n", u, v, a.free_.size());
+  a.release(x, 100); a.release(v, 200); a.release(z, 1000); a.release(u, 300);
+  std::printf("%zu %zu %zu\n", a.free_.size(), a.free_.begin()->first, a.free_.begin()->second);
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "arena.cc")
+        exe = os.path.join(d, "arena")
+        open(c, "w").write(src)
+        subprocess.run([gxx, "-std=c++17", "-I", os.path.join(ROOT, "paper_2008_11480_gb300", "csrc"), c, "-o", exe],
+                       check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    assert [int(v) for v in lines[0].split()] == [0, 256, 512, 1, 4096 - 1536]
+    assert [int(v) for v in lines[1].split()] == [1536, 256, 1]
+    assert [int(v) for v in lines[2].split()] == [1, 0, 4096]

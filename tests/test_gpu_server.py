@@ -1,0 +1,187 @@
+"""Continuous-batching server through the C ABI: requests arrive between
+ticks, are admitted by slot and memory budget, advance one controller pass per
+tick and retire on their own.  Every result is checked in FP64 by the oracle's
+residual, and each request's theta must be bitwise the same as the same system
+solved alone (and as the batched solve of it), whatever else was in flight."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2008_11480_gb300 as nsgb
+from workloads import make_serving_trace, make_spd
+
+pytestmark = pytest.mark.gpu
+dev = torch.device("cuda:0")
+GiB = 1 << 30
+
+
+def tens(x, pin=False):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    return t.pin_memory() if pin else t.to(dev)
+
+
+def mix(seed=0, count=10):
+    """A small stand-in for the serving mix: n log-uniform in [16, 400],
+    kappa log-uniform in [1e2, 1e5], 1..6 right-hand sides."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(16), np.log(400)))))
+        kappa = float(np.exp(rng.uniform(np.log(1e2), np.log(1e5))))
+        out.append(make_spd(n, kappa, nrhs=int(rng.integers(1, 7)), seed=500 + 17 * seed + i))
+    return out
+
+
+def run_ticks(srv, arrivals, iters=60, tol=1e-10, pin=False):
+    """arrivals: list of (tick index, problem).  Submits each problem before
+    the tick it arrives at, ticks until everything is done; returns the theta
+    tensors, results and the largest number of requests seen on the device."""
+    pending = sorted(arrivals, key=lambda a: a[0])
+    tickets, thetas, bufs = [], [], []
+    tick, most = 0, 0
+    while pending or any(not srv.poll(t)["done"] for t in tickets):
+        while pending and pending[0][0] <= tick:
+            _, p = pending.pop(0)
+            A, B = tens(p.A, pin), tens(p.B, pin)
+            th = torch.full_like(B, float("nan"))
+            tickets.append(srv.submit(A, B, th, iters=iters, tol=tol))
+            thetas.append(th)
+            bufs.append((A, B))
+        most = max(most, srv.tick())
+        tick += 1
+        assert tick < 5000
+    return thetas, [srv.poll(t) for t in tickets], most
+
+
+def check_solution(p, th, r, tol=1e-10):
+    assert r["done"] == 1 and r["status"] == nsgb.NS_OK, r
+    x = th.cpu().numpy()
+    assert float(np.max(O.rel_residual(p.A, x, p.B))) <= tol, r
+    assert r["latency_ms"] >= r["queue_ms"] >= 0.0
+
+
+def test_server_staggered_arrivals_converge_and_match_alone():
+    probs = mix(0, 10)
+    arrivals = [(2 * i, p) for i, p in enumerate(probs)]  # one new request every other tick
+    with nsgb.Server(4 * GiB, 16, 8, order=4) as srv:
+        thetas, res, most = run_ticks(srv, arrivals)
+        st = srv.stats()
+    assert most >= 2, "requests never overlapped"
+    assert st["completed"] == len(probs) and st["converged"] == len(probs) and st["rejected"] == 0
+    for p, th, r in zip(probs, thetas, res):
+        check_solution(p, th, r)
+    # the same systems one at a time, each in a fresh server
+    for k in (0, 3, 6, 9):
+        with nsgb.Server(4 * GiB, 4, 8, order=4) as one:
+            alone, res1, _ = run_ticks(one, [(0, probs[k])])
+        assert torch.equal(alone[0], thetas[k]), f"request {k} differs alone vs in the mix"
+        assert res1[0]["ns_iters"] == res[k]["ns_iters"] and res1[0]["sweeps"] == res[k]["sweeps"]
+
+
+def test_server_matches_batched_solve_bitwise():
+    probs = mix(1, 6)
+    with nsgb.Server(4 * GiB, 8, 8, order=8) as srv:
+        thetas, res, _ = run_ticks(srv, [(i, p) for i, p in enumerate(probs)])
+    with nsgb.Batch([p.n for p in probs], [p.nrhs for p in probs], order=8) as bt:
+        outs, status, _ = bt.solve([tens(p.A) for p in probs], [tens(p.B) for p in probs], iters=60, tol=1e-10)
+        bres = [bt.result(i) for i in range(len(probs))]
+    assert status == nsgb.NS_OK
+    for k in range(len(probs)):
+        assert torch.equal(outs[k], thetas[k]), k
+        assert bres[k]["ns_iters"] == res[k]["ns_iters"] and bres[k]["sweeps"] == res[k]["sweeps"]
+
+
+def test_server_admission_by_memory_budget():
+    """A budget that holds two n = 384 requests at a time: the rest wait in
+    the queue, everything completes, and a request larger than the whole
+    budget is rejected with NS_ERR_OOM instead of blocking the queue."""
+    probs = [make_spd(384, 1e3, nrhs=2, seed=900 + i) for i in range(5)]
+    ld = 384
+    foot = 68 * ld * ld + 36 * ld * 2
+    budget = int(2.4 * foot)
+    big = make_spd(1024, 1e2, nrhs=1, seed=999)
+    with nsgb.Server(budget, 16, 4, order=4) as srv:
+        arrivals = [(0, p) for p in probs[:3]] + [(0, big)] + [(1, p) for p in probs[3:]]
+        thetas, res, most = run_ticks(srv, arrivals)
+        st = srv.stats()
+    assert most <= 2
+    assert st["rejected"] == 1 and st["completed"] == 5
+    assert res[3]["status"] == nsgb.NS_ERR_OOM and res[3]["done"] == 1
+    for p, th, r in zip(probs[:3] + probs[3:], thetas[:3] + thetas[4:], res[:3] + res[4:]):
+        check_solution(p, th, r)
+    # the third request was admitted only after one of the first two retired
+    # (all three were submitted within a millisecond)
+    assert res[2]["queue_ms"] >= min(res[0]["latency_ms"], res[1]["latency_ms"]) - 1.0
+
+
+def test_server_slot_limit_and_reuse():
+    probs = mix(2, 9)
+    with nsgb.Server(4 * GiB, 3, 8, order=4) as srv:
+        thetas, res, most = run_ticks(srv, [(0, p) for p in probs])
+        st = srv.stats()
+    assert most <= 3 and st["completed"] == 9
+    for p, th, r in zip(probs, thetas, res):
+        check_solution(p, th, r)
+
+
+def test_server_host_buffers_match_device_buffers():
+    probs = mix(3, 5)
+    with nsgb.Server(4 * GiB, 8, 8, order=4) as srv:
+        dev_th, _, _ = run_ticks(srv, [(i, p) for i, p in enumerate(probs)])
+    with nsgb.Server(4 * GiB, 8, 8, order=4) as srv:
+        host_th, res, _ = run_ticks(srv, [(i, p) for i, p in enumerate(probs)], pin=True)
+    for k, p in enumerate(probs):
+        assert not host_th[k].is_cuda
+        assert torch.equal(host_th[k], dev_th[k].cpu())
+        check_solution(p, host_th[k], res[k])
+
+
+def test_server_background_thread():
+    probs = mix(4, 8)
+    with nsgb.Server(4 * GiB, 8, 8, order=4) as srv:
+        ref, _, _ = run_ticks(srv, [(0, p) for p in probs])
+    with nsgb.Server(4 * GiB, 8, 8, order=4) as srv:
+        srv.start()
+        tickets, thetas, keep = [], [], []
+        for p in probs:
+            A, B = tens(p.A), tens(p.B)
+            torch.cuda.synchronize()
+            th = torch.empty_like(B)
+            tickets.append(srv.submit(A, B, th, iters=60, tol=1e-10))
+            thetas.append(th)
+            keep.append((A, B))
+            time.sleep(0.003)
+        t0 = time.time()
+        while not all(srv.poll(t)["done"] for t in tickets):
+            assert time.time() - t0 < 60
+            time.sleep(0.002)
+        srv.stop()
+        res = [srv.poll(t) for t in tickets]
+        for t in tickets:
+            srv.release(t)
+        with pytest.raises(nsgb.NSError):
+            srv.poll(tickets[0])
+    for k, p in enumerate(probs):
+        check_solution(p, thetas[k], res[k])
+        assert torch.equal(thetas[k], ref[k])
+
+
+def test_server_serving_trace_sample():
+    """A short slice of the serving workload's request mix (n log-uniform,
+    kappa up to 1e6, up to 64 right-hand sides), scaled down in n so the
+    oracle check stays quick."""
+    trace = make_serving_trace(2000.0, 0.006, seed=7, n_lo=32, n_hi=512, nrhs_hi=64)
+    assert len(trace) >= 5
+    probs = [make_spd(r.n, r.kappa, nrhs=r.nrhs, seed=r.seed) for r in trace]
+    with nsgb.Server(8 * GiB, 64, 64, order=4) as srv:
+        thetas, res, _ = run_ticks(srv, [(i, p) for i, p in enumerate(probs)], iters=80)
+    for p, th, r in zip(probs, thetas, res):
+        if r["status"] == nsgb.NS_OK:
+            check_solution(p, th, r)
+        else:  # never reported as converged when it is not
+            assert r["status"] in (nsgb.NS_NOT_CONVERGED, nsgb.NS_ERR_DIVERGED, nsgb.NS_ERR_NONFINITE)
+            assert float(np.max(O.rel_residual(p.A, th.cpu().numpy(), p.B))) > 1e-10
+    assert sum(r["status"] == nsgb.NS_OK for r in res) >= len(res) - 1
