@@ -48,6 +48,7 @@ def workload_config(a):
         "precision": "auto: bf16 products while ||F||_F falls, then bf16x3; f32 accumulate; FP64 residual "
                      "and Richardson",
         "tol": 1e-10, "l2": "flushed between timed steps (512 MiB write)", "seed": 1,
+        "couple_frob": a.couple,
     }
 
 
@@ -182,7 +183,7 @@ def run_ours(a):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1)
+    ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1, couple_frob=a.couple)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
     assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
@@ -224,7 +225,7 @@ def run_ours(a):
     Ah = torch.from_numpy(p.A).pin_memory()
     Bh = torch.from_numpy(p.B).pin_memory()
     Th = torch.empty_like(Bh).pin_memory()
-    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream)
+    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple)
     ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
     e2e_steps = max(1, min(a.steps, 5))
     barrier()
@@ -245,7 +246,7 @@ def run_ours(a):
     # plain FP64 Newton-Schulz + FP64 Richardson on the GPU (same algorithm, same stopping rule)
     fp64 = None
     if not a.no_fp64:
-        ctx64 = nsgb.Context(a.n, order=a.order, stream=stream, precision=nsgb.NS_FP64)
+        ctx64 = nsgb.Context(a.n, order=a.order, stream=stream, precision=nsgb.NS_FP64, couple_frob=a.couple)
         small = make_spd(256, a.kappa, nrhs=a.nrhs, seed=2)
         with nsgb.Context(256, order=a.order, precision=nsgb.NS_FP64) as cw:
             cw.solve(torch.from_numpy(small.A).to(dev), torch.from_numpy(small.B).to(dev), iters=a.iters, tol=1e-10)
@@ -351,7 +352,8 @@ def run_batched(a):
     Bs = [torch.from_numpy(p.B).to(dev) for p in probs]
     outs = [torch.empty_like(b) for b in Bs]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    bt = nsgb.Batch([p.n for p in probs], [1] * len(probs), order=a.order, stream=stream, profile=1)
+    bt = nsgb.Batch([p.n for p in probs], [1] * len(probs), order=a.order, stream=stream, profile=1,
+                    couple_frob=a.couple)
     for _ in range(max(3, a.warmup)):
         _, status, st = bt.solve(As, Bs, iters=a.iters, tol=1e-10, outs=outs)
     sampler = ClockSampler(0)
@@ -383,7 +385,7 @@ def run_batched(a):
         "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"{a.count} harmonic-regressor Gram systems, m ~ U{{8..128}}, n = 2m, T = 4n, "
-                               f"ridge 1e-6, b = A theta*, 1 RHS", "order": a.order, "tol": 1e-10,
+                               f"ridge 1e-6, b = A theta*, 1 RHS", "order": a.order, "tol": 1e-10, "couple_frob": a.couple,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "instances": a.count, "converged_per_step": statistics.mean(conv),
         "not_converged_per_step": a.count - statistics.mean(conv),
@@ -395,6 +397,114 @@ def run_batched(a):
                      "note": "executed (tile-padded) product flops of the list-driven launches / their event time"},
         "useful_flops_per_product_level": st.useful_flops_per_product, "clocks": clocks}), flush=True)
     bt.close()
+
+
+def run_serving(a):
+    """Continuous-batching serving: Poisson arrivals at `a.rate` req/s for
+    `a.duration` s; each request an SPD system Q diag(lambda) Q^T with n
+    log-uniform in [32, 2048], kappa log-uniform in [1e2, 1e6], 1..64 RHS,
+    solved to a 1e-10 relative residual by order-4 Newton-Schulz (bf16 /
+    bf16x3 products) coupled to Richardson.  The A matrices come from a pool
+    of `a.pool` systems drawn from that distribution (request i uses pool entry
+    i mod pool); every request has its own B.  The server runs on its own
+    thread; requests are submitted at their arrival times from this thread.
+    value = converged requests / (last completion - first arrival)."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_serving_trace, make_spd_device
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    defs = make_serving_trace(1e6, 2.0 * a.pool / 1e6 + 1e-3, seed=11)[:a.pool]
+    pool = [make_spd_device(r.n, r.kappa, nrhs=1, seed=r.seed, device=dev, qr_on_host=a.pool_qr_host)[0]
+            for r in defs]
+    trace = make_serving_trace(a.rate, a.duration, seed=a.seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(a.seed)
+    reqs = []
+    for i, r in enumerate(trace):
+        A = pool[i % len(pool)]
+        B = torch.randn(A.shape[0], r.nrhs, generator=gen, device=dev, dtype=torch.float64)
+        reqs.append((r.arrival_s, A, B, torch.empty_like(B)))
+    warm = [(pool[j], torch.randn(pool[j].shape[0], 8, generator=gen, device=dev, dtype=torch.float64))
+            for j in range(min(len(pool), max(3, a.warmup) * 8))]
+    torch.cuda.synchronize()
+    srv = nsgb.Server(int(a.budget_gb * (1 << 30)), a.max_requests, 64, order=a.order, couple_frob=a.couple)
+    srv.start()
+    wt = [srv.submit(A, B, torch.empty_like(B), iters=a.iters, tol=1e-10) for A, B in warm]
+    while not all(srv.poll(t)["done"] for t in wt):
+        time.sleep(0.01)
+    st0 = srv.stats()
+    sampler = ClockSampler(0)
+    sampler.start()
+    tickets, t_sub = [], []
+    t0 = time.perf_counter()
+    for arr, A, B, T in reqs:
+        while True:
+            dt = t0 + arr - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 2e-4:
+                time.sleep(dt - 1e-4)
+        t_sub.append(time.perf_counter() - t0)
+        tickets.append(srv.submit(A, B, T, iters=a.iters, tol=1e-10))
+    deadline = time.perf_counter() + 4 * a.duration + 60
+    res = [None] * len(tickets)
+    left = list(range(len(tickets)))
+    while left and time.perf_counter() < deadline:
+        nxt = []
+        for k in left:
+            r = srv.poll(tickets[k])
+            if r["done"]:
+                res[k] = r
+            else:
+                nxt.append(k)
+        left = nxt
+        if left:
+            time.sleep(0.005)
+    clocks = sampler.stop()
+    st1 = srv.stats()
+    done = [(k, r) for k, r in enumerate(res) if r is not None]
+    conv = [(k, r) for k, r in done if r["status"] == nsgb.NS_OK]
+    t_end = max(t_sub[k] + r["latency_ms"] / 1e3 for k, r in done) if done else float("nan")
+    lat = np.array([r["latency_ms"] for _, r in conv]) if conv else np.array([float("nan")])
+    qms = np.array([r["queue_ms"] for _, r in conv]) if conv else np.array([float("nan")])
+    # spot-check converged results in FP64 on the device
+    worst = 0.0
+    for k, r in conv[:: max(1, len(conv) // 64)]:
+        _, A, B, T = reqs[k]
+        rr = torch.linalg.vector_norm(B - A @ T, dim=0) / torch.linalg.vector_norm(B, dim=0)
+        worst = max(worst, float(rr.max()))
+    flops = st1["gemm_flops"] - st0["gemm_flops"]
+    pk, pk_kind = peaks()
+    ach = flops / t_end / 1e12 if done else None
+    print(json.dumps({
+        "metric": METRIC + " (serving)", "value": len(conv) / t_end if done else 0.0, "unit": UNIT,
+        "n_gpus": 1, "steps": 1, "warmup": a.warmup, "ms_per_step": t_end * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"serving trace: Poisson arrivals {a.rate:g} req/s for {a.duration:g} s; n log-uniform "
+                               f"[32, 2048], kappa log-uniform [1e2, 1e6], nrhs U{{1..64}}; A from a pool of "
+                               f"{a.pool} systems, own B per request", "order": a.order, "tol": 1e-10, "couple_frob": a.couple,
+                   "budget_gb": a.budget_gb, "max_requests": a.max_requests, "buffers": "device (HBM)",
+                   "l2": "inputs of the whole trace exceed L2"},
+        "requests": len(reqs), "completed": len(done), "converged": len(conv),
+        "not_converged": len(done) - len(conv), "unfinished": len(left),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
+        "offered_rate": len(reqs) / a.duration, "passes": st1["passes"] - st0["passes"],
+        "worst_sampled_rel_res": worst,
+        "server_host_ms": st1["tick_ms"] - st0["tick_ms"], "server_wait_ms": st1["wait_ms"] - st0["wait_ms"],
+        "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                     "frac": ach / pk["bf16_tflops_sustained"] if ach else None, "traffic": None,
+                     "note": "executed product flops over the whole serving wall time (a lower bound on the "
+                             f"product kernels' rate); peak {pk_kind} sustained bf16"},
+        "clocks": clocks}), flush=True)
+    if left:  # requests still running: do not wait for them on the way out
+        os._exit(0)
+    srv.stop()
+    srv.close()
 
 
 def main():
@@ -417,10 +527,28 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
-                    help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+                    help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems; "
+                         "serving: continuous batching of a Poisson request trace")
     ap.add_argument("--count", type=int, default=2048)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--pool", type=int, default=256)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-requests", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--couple", type=float, default=1.0,
+                    help="couple_frob: Richardson starts once ||F_{k-1}||_F <= this (0: from the first step)")
+    ap.add_argument("--pool-qr-host", action="store_true",
+                    help="draw the serving pool's orthogonal factors with a host QR (e.g. under a profiler)")
     a = ap.parse_args()
+    if a.workload == "serving" and a.impl == "ours":
+        if a.order == 8 and "--order" not in sys.argv:
+            a.order = 4
+        if a.iters == 60 and "--iters" not in sys.argv:
+            a.iters = 80
+        run_serving(a)
+        return
     if a.workload == "batched" and a.impl == "ours":
         if a.order == 8 and "--order" not in sys.argv:
             a.order = 4

@@ -77,6 +77,13 @@ typedef struct ns_options {
                           method of Section 5.1 (eqs. gamk11-fks1); 0: T_i start at G0 */
   int gemm_cluster;    /* CTAs per cluster sharing each R tile by TMA multicast: 0 automatic,
                           1 none, 2 or 4 (with 192- or 256-column tiles) */
+  double couple_frob;  /* 0 (default): the Richardson branch (residual, test, update) runs on
+                          every NS step, as in Section 6.  > 0: it starts with the first
+                          G_k whose ||I - A G_k||_F <= couple_frob and stays on.  Earlier G_k
+                          need not contract (rho(I - A G_k) may be ~1) and, with
+                          F_k = F_0^{n^k}, the residual factor they contribute is negligible
+                          next to the last step's.  1.0 skips exactly the sweeps without a
+                          contraction bound (costs one extra device sync where it starts). */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -244,6 +251,11 @@ typedef struct ns_server_stats {
   int active;           /* requests holding a slot after the last tick */
   int queued;           /* requests waiting for admission */
   int last_error;       /* error of the background thread (0 if none) */
+  long long gemm_launches;   /* tensor-core product launches so far */
+  long long kernel_launches; /* all kernel launches so far */
+  double gemm_flops;         /* product flops so far (2 n^3 per product; bf16x3 = 3 passes) */
+  double tick_ms;            /* host time spent inside ticks */
+  double wait_ms;            /* ... of which blocked waiting for the device */
 } ns_server_stats;
 
 /* mem_budget_bytes: device arena for request workspaces (slot footprint of a

@@ -500,7 +500,7 @@ def ns_richardson_solve(A: np.ndarray, B: np.ndarray, order: int = 4, ns_iters: 
                         tol: float | None = None, max_sweeps: int = 0,
                         theta0: np.ndarray | None = None, G0: np.ndarray | None = None,
                         form: str = "factorized", pow_mode: str = "square",
-                        use_updated_G: bool = False) -> SolveResult:
+                        use_updated_G: bool = False, couple_frob: float = 0.0) -> SolveResult:
     """Newton-Schulz inversion coupled to Richardson iteration.
 
     Each pass first forms r = B - A theta and its relative residual
@@ -510,14 +510,31 @@ def ns_richardson_solve(A: np.ndarray, B: np.ndarray, order: int = 4, ns_iters: 
     (``use_updated_G`` applies G_{k+1} instead, the ordering of eq. ttk1 where
     the newest operator is applied); afterwards up to ``max_sweeps`` plain
     sweeps theta <- theta + G r with the last G.  The returned theta is always
-    the one whose residual was recorded last."""
+    the one whose residual was recorded last.
+
+    ``couple_frob`` > 0 delays the coupling (a library option; the paper
+    couples from the first step): passes take the NS step alone until the
+    first G_k with ||I - A G_k||_F <= ``couple_frob``; from that pass on (and
+    once Newton-Schulz has stopped) every pass forms the residual and updates
+    theta as above."""
     G = G0 if G0 is not None else alpha_frobenius(A) * _eye_like(A)
     theta = np.zeros_like(B) if theta0 is None else theta0.copy()
     bn = np.sqrt(np.sum(B * B, axis=0))
     res = SolveResult(theta=theta, G=G, ns_iters=0, sweeps=0, converged=False)
     cnt = MMCount()
     sweeps_left = max_sweeps
+    coupled = couple_frob <= 0.0
     while True:
+        if not coupled and res.ns_iters < ns_iters:
+            # the norm of the F the coming step forms (not a separate mmm)
+            E = residual_right(A, G)
+            coupled = float(np.sqrt(np.sum(E * E))) <= couple_frob
+        if not coupled and res.ns_iters < ns_iters:
+            G_new, F = ns_step(A, G, order, form, pow_mode, cnt)
+            res.frob_E.append(float(np.sqrt(np.sum(F * F))))
+            G = G_new
+            res.ns_iters += 1
+            continue
         R = B - A @ theta
         rr = float(np.max(np.sqrt(np.sum(R * R, axis=0)) / bn))
         res.rel_res.append(rr)

@@ -62,6 +62,7 @@ class ns_options(ctypes.Structure):
         ("timeout_s", ctypes.c_double),
         ("aux_ahead", ctypes.c_int),
         ("gemm_cluster", ctypes.c_int),
+        ("couple_frob", ctypes.c_double),
     ]
 
 
@@ -147,6 +148,11 @@ class ns_server_stats(ctypes.Structure):
         ("active", ctypes.c_int),
         ("queued", ctypes.c_int),
         ("last_error", ctypes.c_int),
+        ("gemm_launches", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("gemm_flops", ctypes.c_double),
+        ("tick_ms", ctypes.c_double),
+        ("wait_ms", ctypes.c_double),
     ]
 
 

@@ -64,6 +64,9 @@ struct InstState {
   int sweeps = 0;
   int rollbacks = 0;
   double rel_res = INFINITY;
+  bool has_res = false;   // this pass formed the residual (the Richardson branch ran)
+  bool coupled = false;   // delayed coupling has started (opt.couple_frob > 0)
+  bool need_res = false;  // coupling starts with this pass's G_k: form its residual
   int iters = 0;      // cap on Newton-Schulz steps
   double tol = 0.0;   // relative residual target
 };
@@ -121,7 +124,9 @@ struct ns_batch {
   int order = 4, levels = 2, ntypes = 0;
   int max_nrhs = 1, scal_stride = 0;
   ns_options opt;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // row kernels (residual, update, preparation) and copies
+  cudaStream_t pstream = nullptr;  // tensor-core products (owned); joins `stream` once per pass
+  cudaEvent_t ev_r = nullptr, ev_p = nullptr;
   int device = 0, num_sms = 148;
   std::string err;
   void* dmem = nullptr;
@@ -144,6 +149,7 @@ struct ns_batch {
   std::vector<BInst> hinst;
   std::vector<InstState> st;
   ns_batch_stats* stats = nullptr;
+  double wait_ms = 0.0;  // host time blocked in the per-pass stream synchronisation
   int fixed_count = 0;  // systems of a fixed batch (slots 0 .. fixed_count - 1)
 };
 
@@ -168,11 +174,11 @@ ns_status bfail(ns_batch* b, ns_status s, const std::string& m) {
 // Copy host bytes into the device staging area (stream ordered); the host side
 // is a pinned mirror at the same offsets and the bump pointer is reset only
 // after a stream synchronisation, so no region is rewritten before its copy.
-void* stage(ns_batch* b, const void* src, size_t bytes) {
+void* stage(ns_batch* b, const void* src, size_t bytes, cudaStream_t st) {
   const size_t off = rup(b->stage_used, 256);
   if (off + bytes > b->stage_cap - 256) return nullptr;
   memcpy(b->hstage + off, src, bytes);
-  if (cudaMemcpyAsync(b->dstage + off, b->hstage + off, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(b->dstage + off, b->hstage + off, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return nullptr;
   b->stage_used = off + bytes;
   return b->dstage + off;
@@ -352,12 +358,12 @@ ns_status publish_slot(ns_batch* b, int i, bool problems) {
     for (int t = 0; t < b->ntypes; ++t)
       for (int c = 0; c < 2; ++c)
         for (int x = 0; x < 2; ++x) probs[(static_cast<size_t>(t) * 2 + c) * 2 + x] = make_problem(b, i, t, c, x);
-    const void* dp = stage(b, probs.data(), probs.size() * sizeof(TcProblem));
+    const void* dp = stage(b, probs.data(), probs.size() * sizeof(TcProblem), b->stream);
     if (!dp) return bfail(b, NS_ERR_OOM, "staging area exhausted");
     B_CK(cudaMemcpyAsync(b->dprob + prob_index(b, i, 0, 0, 0), dp, probs.size() * sizeof(TcProblem),
                          cudaMemcpyDeviceToDevice, b->stream));
   }
-  const void* di = stage(b, &b->hinst[i], sizeof(BInst));
+  const void* di = stage(b, &b->hinst[i], sizeof(BInst), b->stream);
   if (!di) return bfail(b, NS_ERR_OOM, "staging area exhausted");
   B_CK(cudaMemcpyAsync(b->dinst + i, di, sizeof(BInst), cudaMemcpyDeviceToDevice, b->stream));
   return NS_OK;
@@ -378,7 +384,8 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
         }
       }
       if (items.empty()) continue;
-      const TcItem* ditems = static_cast<const TcItem*>(stage(b, items.data(), items.size() * sizeof(TcItem)));
+      const TcItem* ditems =
+          static_cast<const TcItem*>(stage(b, items.data(), items.size() * sizeof(TcItem), b->pstream));
       if (!ditems) return bfail(b, NS_ERR_OOM, "staging area exhausted");
       TcParams p;
       memset(&p, 0, sizeof(p));
@@ -393,16 +400,16 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
       if (b->opt.profile) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        cudaEventRecord(e0, b->stream);
+        cudaEventRecord(e0, b->pstream);
       }
-      B_CK(launch_gemm_tc(p, bnv, 1, x3 == 1, b->num_sms, b->stream));
+      B_CK(launch_gemm_tc(p, bnv, 1, x3 == 1, b->num_sms, b->pstream));
       if (b->stats) {
         b->stats->gemm_launches++;
         b->stats->kernel_launches++;
         b->stats->gemm_flops += flops;
       }
       if (b->opt.profile) {
-        cudaEventRecord(e1, b->stream);
+        cudaEventRecord(e1, b->pstream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -420,12 +427,23 @@ std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids, boo
   for (int i : ids) {
     const int cmax = with_rhs ? b->nrhs[i] : 1;
     for (int r = 0; r < b->n[i]; r += 8)
-      for (int c = 0; c < cmax; c += 4) it.push_back(BItem{i, r, c, b->st[i].cur});
+      for (int c = 0; c < cmax; c += kBRhs) it.push_back(BItem{i, r, c, b->st[i].cur});
   }
   return it;
 }
 
+// Make `to` wait for everything enqueued on `from` so far.
+ns_status join(ns_batch* b, cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t ev = from == b->stream ? b->ev_r : b->ev_p;
+  B_CK(cudaEventRecord(ev, from));
+  B_CK(cudaStreamWaitEvent(to, ev, 0));
+  return NS_OK;
+}
+
+// Read every slot's scalars and the device error word: the product stream
+// joins the row stream, which is then synchronised.
 ns_status sync_read(ns_batch* b) {
+  B_TRY(join(b, b->pstream, b->stream));
   int hi_slot = 0;
   for (int k = 0; k < b->cap; ++k)
     if (b->used[k]) hi_slot = k + 1;
@@ -434,7 +452,9 @@ ns_status sync_read(ns_batch* b) {
                          cudaMemcpyDeviceToHost, b->stream));
   char* herr_slot = b->hstage + b->stage_cap - 64;
   B_CK(cudaMemcpyAsync(herr_slot, b->derr, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  const auto w0 = std::chrono::steady_clock::now();
   B_CK(cudaStreamSynchronize(b->stream));
+  b->wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   b->stage_used = 0;
   int herr = 0;
   memcpy(&herr, herr_slot, sizeof(int));
@@ -449,7 +469,7 @@ ns_status sync_read(ns_batch* b) {
 template <typename F>
 ns_status run_rows(ns_batch* b, const std::vector<BItem>& items, F launch) {
   if (items.empty()) return NS_OK;
-  const BItem* d = static_cast<const BItem*>(stage(b, items.data(), items.size() * sizeof(BItem)));
+  const BItem* d = static_cast<const BItem*>(stage(b, items.data(), items.size() * sizeof(BItem), b->stream));
   if (!d) return bfail(b, NS_ERR_OOM, "staging area exhausted");
   B_CK(launch(d, static_cast<int>(items.size())));
   if (b->stats) b->stats->kernel_launches++;
@@ -457,11 +477,11 @@ ns_status run_rows(ns_batch* b, const std::vector<BItem>& items, F launch) {
 }
 
 ns_status run_list(ns_batch* b, const std::vector<int>& ids,
-                   cudaError_t (*launch)(const BInst*, const int*, int, cudaStream_t)) {
+                   cudaError_t (*launch)(const BInst*, const int*, int, cudaStream_t), cudaStream_t st) {
   if (ids.empty()) return NS_OK;
-  const int* d = static_cast<const int*>(stage(b, ids.data(), ids.size() * sizeof(int)));
+  const int* d = static_cast<const int*>(stage(b, ids.data(), ids.size() * sizeof(int), st));
   if (!d) return bfail(b, NS_ERR_OOM, "staging area exhausted");
-  B_CK(launch(b->dinst, d, static_cast<int>(ids.size()), b->stream));
+  B_CK(launch(b->dinst, d, static_cast<int>(ids.size()), st));
   if (b->stats) b->stats->kernel_launches++;
   return NS_OK;
 }
@@ -473,24 +493,31 @@ void decide(ns_batch* b, int i) {
   const double tol = s.tol;
   const double* sc = b->hscal + static_cast<size_t>(i) * b->scal_stride;
   const int nr = b->nrhs[i];
-  double rr = 0.0;
-  for (int c = 0; c < nr; ++c) {
-    const double bb = sc[kScalR + nr + c], r = sc[kScalR + c];
-    const double q = bb > 0 ? std::sqrt(r / bb) : std::sqrt(r);
-    rr = std::max(rr, std::isnan(q) ? INFINITY : q);
-  }
-  s.rel_res = rr;
+  double rr = INFINITY;
   s.recompute = false;
-  if (!std::isfinite(rr)) {
-    s.finished = true;
-    s.status = NS_ERR_NONFINITE;
+  if (!s.has_res && s.ns_active && b->opt.couple_frob > 0.0 && std::sqrt(sc[2]) <= b->opt.couple_frob) {
+    s.need_res = true;  // the first G_k with ||I - A G_k||_F <= couple_frob
     return;
   }
-  if (tol > 0 && rr <= tol) {
-    s.finished = true;
-    s.converged = true;
-    s.status = NS_OK;
-    return;
+  if (s.has_res) {
+    rr = 0.0;
+    for (int c = 0; c < nr; ++c) {
+      const double bb = sc[kScalR + nr + c], r = sc[kScalR + c];
+      const double q = bb > 0 ? std::sqrt(r / bb) : std::sqrt(r);
+      rr = std::max(rr, std::isnan(q) ? INFINITY : q);
+    }
+    s.rel_res = rr;
+    if (!std::isfinite(rr)) {
+      s.finished = true;
+      s.status = NS_ERR_NONFINITE;
+      return;
+    }
+    if (tol > 0 && rr <= tol) {
+      s.finished = true;
+      s.converged = true;
+      s.status = NS_OK;
+      return;
+    }
   }
   if (!s.ns_active) {
     // Richardson alone: stop when it no longer contracts (rho(I - A G) ~ 1 at
@@ -536,7 +563,7 @@ void decide(ns_batch* b, int i) {
   }
   if (b->opt.ns_stop && (!autop || s.prec != NS_BF16)) {
     bool stop = frob <= b->opt.ns_stop_frob;
-    if (!stop && frob < 1.0 && tol > 0 && rr > tol) {
+    if (!stop && s.has_res && frob < 1.0 && tol > 0 && rr > tol) {
       const double need = std::ceil(std::log(tol / rr) / std::log(frob));
       if (need <= s.sweeps_left && need * sweep_cost_i(b, i) <= step_cost_i(b, i, s.prec) + 2.0 * sweep_cost_i(b, i))
         stop = true;
@@ -567,36 +594,67 @@ ns_status prep_slots(ns_batch* b, const std::vector<int>& ids, const std::vector
   }
   B_TRY(run_rows(b, row_items(b, ids, false),
                  [&](const BItem* d, int k) { return launch_bprep(b->dinst, d, k, b->stream); }));
-  B_TRY(run_list(b, ids, launch_bnorms));
+  B_TRY(run_list(b, ids, launch_bnorms, b->stream));
   B_TRY(run_rows(b, row_items(b, ids, false), [&](const BItem* d, int k) {
     return launch_bg0(b->dinst, d, k, b->opt.g0_mode, 1, b->stream);
   }));
-  return NS_OK;
+  // the products read the splits of A and G0 (and the tables just published)
+  return join(b, b->stream, b->pstream);
 }
 
-// One controller pass over the active systems: residual (+ ||F|| while NS
-// runs) -> one device sync -> decisions -> Richardson update and next NS step.
+// One controller pass over the active systems.  Two streams: the product
+// stream forms F = I - A G (and ||F||) for the systems whose Newton-Schulz
+// loop runs while the row stream forms the residuals (Richardson branch); one
+// join and device sync; host decisions; then the product chain and the
+// Richardson update, again on the two streams.  With opt.couple_frob > 0 a
+// system's Richardson branch starts with its first G_k whose ||I - A G_k||_F
+// is at most that (its residual is then formed after the sync).
 ns_status pass(ns_batch* b, const std::vector<int>& act) {
-  std::vector<int> nsact;
-  for (int i : act)
-    if (b->st[i].ns_active) nsact.push_back(i);
-  B_TRY(run_rows(b, row_items(b, act, true),
-                 [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
-  B_TRY(run_list(b, act, launch_brsq));
+  const double couple = b->opt.couple_frob;
+  std::vector<int> nsact, rich;
+  for (int i : act) {
+    InstState& s = b->st[i];
+    if (s.ns_active) nsact.push_back(i);
+    s.has_res = !s.ns_active || couple <= 0.0 || s.coupled;
+    if (s.has_res) rich.push_back(i);
+  }
   if (!nsact.empty()) {
     B_TRY(launch_products(b, nsact, {0}));
-    B_TRY(run_list(b, nsact, launch_bfrob));
+    B_TRY(run_list(b, nsact, launch_bfrob, b->pstream));
   }
+  B_TRY(run_rows(b, row_items(b, rich, true),
+                 [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+  B_TRY(run_list(b, rich, launch_brsq, b->stream));
   B_TRY(sync_read(b));
   for (int i : act) decide(b, i);
-  for (int guard = 0; guard < 4; ++guard) {
-    std::vector<int> redo;
-    for (int i : act)
-      if (b->st[i].recompute && !b->st[i].finished) redo.push_back(i);
-    if (redo.empty()) break;
-    B_TRY(launch_products(b, redo, {0}));
-    B_TRY(run_list(b, redo, launch_bfrob));
+  // follow-ups, then decide again: systems whose coupling starts with this
+  // pass's G_k need their residual; systems that switched precision or rolled
+  // back need F formed again
+  for (int guard = 0; guard < 8; ++guard) {
+    std::vector<int> late, redo;
+    for (int i : act) {
+      InstState& s = b->st[i];
+      if (s.finished) continue;
+      if (s.need_res) {
+        s.need_res = false;
+        s.has_res = s.coupled = true;
+        late.push_back(i);
+      } else if (s.recompute) {
+        redo.push_back(i);
+      }
+    }
+    if (late.empty() && redo.empty()) break;
+    if (!redo.empty()) {
+      B_TRY(launch_products(b, redo, {0}));
+      B_TRY(run_list(b, redo, launch_bfrob, b->pstream));
+    }
+    if (!late.empty()) {
+      B_TRY(run_rows(b, row_items(b, late, true),
+                     [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+      B_TRY(run_list(b, late, launch_brsq, b->stream));
+    }
     B_TRY(sync_read(b));
+    for (int i : late) decide(b, i);
     for (int i : redo) decide(b, i);
   }
   std::vector<int> step, upd;
@@ -605,7 +663,9 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
     if (s.finished) continue;
     if (s.ns_active) {
       step.push_back(i);
-      upd.push_back(i);
+      if (s.has_res) upd.push_back(i);
+    } else if (!s.has_res) {
+      // Newton-Schulz stopped on a pass without a residual: the next pass forms it
     } else if (s.sweeps_left > 0) {
       upd.push_back(i);
       s.sweeps_left--;
@@ -614,10 +674,7 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
       s.status = NS_NOT_CONVERGED;
     }
   }
-  // the update applies G_k (current buffer); the chain writes the other one
-  if (!upd.empty())
-    B_TRY(run_rows(b, row_items(b, upd, true),
-                   [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
+  // the chain reads G_k and writes the other G buffer; the update applies G_k
   if (!step.empty()) {
     if (b->levels == 0) {
       B_TRY(launch_products(b, step, {1}));
@@ -631,6 +688,9 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
       }
     }
   }
+  if (!upd.empty())
+    B_TRY(run_rows(b, row_items(b, upd, true),
+                   [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
   for (int i : upd) b->st[i].sweeps++;
   for (int i : step) {
     InstState& s = b->st[i];
@@ -721,12 +781,24 @@ ns_status init_batch(ns_batch* b, int order, const ns_options* opt) {
     return NS_ERR_CUDA;
   }
   cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (cudaStreamCreateWithFlags(&b->pstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_r, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_p, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_CUDA;
+  }
   return NS_OK;
 }
 
 void release_batch(ns_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  if (b->pstream) {
+    cudaStreamSynchronize(b->pstream);
+    cudaStreamDestroy(b->pstream);
+  }
+  if (b->ev_r) cudaEventDestroy(b->ev_r);
+  if (b->ev_p) cudaEventDestroy(b->ev_p);
   if (b->dmem) cudaFree(b->dmem);
   if (b->hscal) cudaFreeHost(b->hscal);
   if (b->hstage) cudaFreeHost(b->hstage);
@@ -763,6 +835,7 @@ struct ns_server {
   std::thread worker;
   bool running = false, stopping = false;
   ns_server_stats stats;
+  ns_batch_stats bst;  // launch and flop counters of the passes (tick thread only)
   std::string err;
 };
 
@@ -851,8 +924,9 @@ ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* cons
     if (act.empty()) break;
     ++passes;
     B_TRY(pass(b, act));
-    if (passes > iters + b->opt.max_sweeps + 8) break;
+    if (passes > 2 * iters + b->opt.max_sweeps + 8) break;
   }
+  B_TRY(join(b, b->pstream, b->stream));
   B_CK(cudaStreamSynchronize(b->stream));
   b->stage_used = 0;
   int nconv = 0, nfail = 0;
@@ -912,6 +986,8 @@ ns_status ns_server_create(size_t mem_budget_bytes, int max_requests, int max_nr
   }
   sv->slot_ticket.assign(max_requests, 0);
   memset(&sv->stats, 0, sizeof(sv->stats));
+  memset(&sv->bst, 0, sizeof(sv->bst));
+  sv->b->stats = &sv->bst;
   *out = sv;
   return NS_OK;
 }
@@ -920,6 +996,7 @@ ns_status ns_server_set_stream(ns_server* sv, void* stream) {
   if (!sv) return NS_ERR_ARG;
   std::lock_guard<std::mutex> tk(sv->tick_mu);
   cudaStreamSynchronize(sv->b->stream);
+  cudaStreamSynchronize(sv->b->pstream);
   sv->b->stream = stream ? static_cast<cudaStream_t>(stream) : sv->own_stream;
   return NS_OK;
 }
@@ -969,6 +1046,7 @@ ns_status ns_server_release(ns_server* sv, uint64_t ticket) {
 ns_status ns_server_tick(ns_server* sv, int* active_out) {
   if (!sv) return NS_ERR_ARG;
   std::lock_guard<std::mutex> tk(sv->tick_mu);
+  const auto t_tick = Clock::now();
   ns_batch* b = sv->b;
   if (cudaSetDevice(b->device) != cudaSuccess) return NS_ERR_CUDA;
   // ---- admission, first come first served, while a slot and memory are free
@@ -1068,6 +1146,11 @@ ns_status ns_server_tick(ns_server* sv, int* active_out) {
     sv->stats.queued = static_cast<int>(sv->queue.size());
     sv->stats.ticks++;
     if (!act.empty()) sv->stats.passes++;
+    sv->stats.gemm_launches = sv->bst.gemm_launches;
+    sv->stats.kernel_launches = sv->bst.kernel_launches;
+    sv->stats.gemm_flops = sv->bst.gemm_flops;
+    sv->stats.wait_ms = b->wait_ms;
+    sv->stats.tick_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_tick).count();
     if (active_out) *active_out = on_device;
   }
   return NS_OK;

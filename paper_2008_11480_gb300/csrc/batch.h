@@ -30,8 +30,11 @@ struct BInst {
   double* scal;            // scalar block
 };
 
-// Work item of a batched row kernel: 8 rows [row0, row0 + 8) and 4 right-hand
-// sides [c0, c0 + 4) of one instance; cur selects the G buffer.
+// Right-hand sides per block of the batched residual and update kernels.
+constexpr int kBRhs = 8;
+
+// Work item of a batched row kernel: 8 rows [row0, row0 + 8) and kBRhs
+// right-hand sides [c0, c0 + kBRhs) of one instance; cur selects the G buffer.
 struct BItem {
   int inst, row0, c0, cur;
 };

@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(256) k_bg0(const BInst* __restrict__ insts, co
 
 // ---------------------------------------------------------------- residual
 // Same arithmetic as the single-system split-f32 residual: warp = (row pair,
-// half of the k range), 4 right-hand sides [c0, c0 + 4) masked to nrhs.
-__global__ void __launch_bounds__(256, 3) k_bresid(const BInst* __restrict__ insts, const BItem* __restrict__ items) {
-  constexpr int NR = 4;
+// half of the k range), kBRhs right-hand sides [c0, c0 + kBRhs) masked to nrhs.
+__global__ void __launch_bounds__(256, 2) k_bresid(const BInst* __restrict__ insts, const BItem* __restrict__ items) {
+  constexpr int NR = kBRhs;
   __shared__ float red_hi[4][2][NR][2], red_lo[4][2][NR][2];
   __shared__ double sq[kRows][NR];
   const BItem it = items[blockIdx.x];
@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(256) k_brsq(const BInst* __restrict__ insts, c
 }
 
 // Theta += G R (G = the instance's f32 master G[cur]); new theta's limbs too.
-__global__ void __launch_bounds__(256, 4) k_bupdate(const BInst* __restrict__ insts,
+__global__ void __launch_bounds__(256, 3) k_bupdate(const BInst* __restrict__ insts,
                                                     const BItem* __restrict__ items) {
-  constexpr int NR = 4;
+  constexpr int NR = kBRhs;
   __shared__ float red[4][2][NR][2];
   const BItem it = items[blockIdx.x];
   const BInst& I = insts[it.inst];

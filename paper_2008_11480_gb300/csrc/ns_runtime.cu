@@ -751,19 +751,28 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
   };
 
-  for (;;) {
-    if (richardson) {
-      if (fp64) {
-        NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
-        ctx->launches += (S.nrhs + 7) / 8;
-      } else {
-        NS_CK(launch_resid_x2(ctx->A1, ctx->A2, ld, ctx->T1, ctx->T2, ld, S.B, ctx->Rd, ctx->R32T, n, S.nrhs,
-                              ctx->partials, &nb, s));
-        ctx->launches += (S.nrhs + 3) / 4;
-      }
-      NS_CK(launch_reduce_sum(ctx->partials, nb, S.nrhs, rsq, s));
-      ctx->launches += 1;
+  // Richardson branch of a pass: r = B - A theta and its per-rhs norms
+  auto launch_residual = [&]() -> ns_status {
+    if (fp64) {
+      NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
+      ctx->launches += (S.nrhs + 7) / 8;
+    } else {
+      NS_CK(launch_resid_x2(ctx->A1, ctx->A2, ld, ctx->T1, ctx->T2, ld, S.B, ctx->Rd, ctx->R32T, n, S.nrhs,
+                            ctx->partials, &nb, s));
+      ctx->launches += (S.nrhs + 3) / 4;
     }
+    NS_CK(launch_reduce_sum(ctx->partials, nb, S.nrhs, rsq, s));
+    ctx->launches += 1;
+    return NS_OK;
+  };
+  // couple_frob > 0 delays the coupling: it starts with the first G_k whose
+  // ||I - A G_k||_F is at most couple_frob (and stays on)
+  const double couple = ctx->opt.couple_frob;
+  bool coupled = couple <= 0.0;
+  for (;;) {
+    bool rich = richardson && (!ns_active || coupled);
+    bool rr_read = false;
+    if (rich) NS_TRY(launch_residual());
     double frob = 0.0;
   recompute_F:
     if (ns_active) {
@@ -773,7 +782,14 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         NS_TRY(mp_residual_F(ctx, ctx->G[S.cur], prec, ctx->order == 3 || ctx->opt.form == 1));
     }
     NS_TRY(sync_scalars(ctx, S.nrhs));
-    if (richardson) {
+    if (ns_active && richardson && !rich && std::sqrt(ctx->hscal[2]) <= couple) {
+      NS_TRY(launch_residual());
+      NS_TRY(sync_scalars(ctx, S.nrhs));
+      rich = true;
+      coupled = true;
+    }
+    if (rich && !rr_read) {
+      rr_read = true;
       double rr = 0.0;
       for (int c = 0; c < S.nrhs; ++c) {
         const double b = ctx->hscal[8 + ctx->scal_cap + c];
@@ -819,7 +835,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         return fail(ctx, NS_ERR_DIVERGED, "Newton-Schulz diverged (||F||_F grew past sqrt(n))");
       if (ctx->opt.ns_stop && (!autop || prec != NS_BF16)) {
         bool stop = frob <= ctx->opt.ns_stop_frob;
-        if (!stop && richardson && frob < 1.0 && tol > 0 && last_rr > tol) {
+        if (!stop && rich && frob < 1.0 && tol > 0 && last_rr > tol) {
           // rho(I - A G_k) <= ||F_k||_F < 1 bounds the Richardson contraction:
           // stop when the sweeps that bound implies cost less than one more
           // Newton-Schulz step (which at best leaves ~one sweep to do)
@@ -842,7 +858,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       const int g_used = S.cur;
       NS_TRY(ns_update(prec));
       const int g_next = S.cur ^ 1;
-      if (richardson) {
+      if (rich) {
         const int gi = ctx->opt.use_updated_G ? g_next : g_used;
         if (fp64)
           NS_CK(launch_update_f64(ctx->G64[gi], ld, ctx->Rd, S.Th, n, S.nrhs, s));
@@ -860,6 +876,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       continue;
     }
     if (!richardson || sweeps_left <= 0) break;
+    if (!rich) continue;  // no residual was formed this pass: the next one forms it
     // Richardson alone no longer contracts (rho(I - A G) ~ 1 at this precision):
     // stop instead of spending the whole sweep budget
     if (std::isfinite(prev_sweep_rr)) stall = last_rr > 0.95 * prev_sweep_rr ? stall + 1 : 0;
@@ -924,6 +941,7 @@ void ns_default_options(ns_options* o) {
   o->timeout_s = 2.0;
   o->aux_ahead = 0;
   o->gemm_cluster = 0;
+  o->couple_frob = 0.0;
 }
 
 const char* ns_status_string(ns_status s) {

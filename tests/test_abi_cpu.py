@@ -46,8 +46,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(ns_request), offsetof(ns_request, tol), offsetof(ns_request, A),
          offsetof(ns_request, Theta));
   printf("%zu %zu %zu\n", sizeof(ns_result), offsetof(ns_result, rel_res), offsetof(ns_result, latency_ms));
-  printf("%zu %zu %zu\n", sizeof(ns_server_stats), offsetof(ns_server_stats, active),
-         offsetof(ns_server_stats, last_error));
+  printf("%zu %zu %zu %zu\n", sizeof(ns_server_stats), offsetof(ns_server_stats, active),
+         offsetof(ns_server_stats, last_error), offsetof(ns_server_stats, wait_ms));
   return 0;
 }
 """
@@ -65,7 +65,7 @@ int main(void) {
             ctypes.sizeof(BS), BS.gemm_launches.offset, BS.wall_ms.offset,
             ctypes.sizeof(Q), Q.tol.offset, Q.A.offset, Q.Theta.offset,
             ctypes.sizeof(R), R.rel_res.offset, R.latency_ms.offset,
-            ctypes.sizeof(SS), SS.active.offset, SS.last_error.offset]
+            ctypes.sizeof(SS), SS.active.offset, SS.last_error.offset, SS.wait_ms.offset]
     assert got == want
 
 

@@ -117,6 +117,18 @@ def test_server_admission_by_memory_budget():
     assert res[2]["queue_ms"] >= min(res[0]["latency_ms"], res[1]["latency_ms"]) - 1.0
 
 
+def test_server_delayed_coupling_matches_batch():
+    probs = mix(5, 6)
+    with nsgb.Server(4 * GiB, 8, 8, order=4, couple_frob=1.0) as srv:
+        thetas, res, _ = run_ticks(srv, [(2 * i, p) for i, p in enumerate(probs)])
+    with nsgb.Batch([p.n for p in probs], [p.nrhs for p in probs], order=4, couple_frob=1.0) as bt:
+        outs, status, _ = bt.solve([tens(p.A) for p in probs], [tens(p.B) for p in probs], iters=60, tol=1e-10)
+    assert status == nsgb.NS_OK
+    for k, p in enumerate(probs):
+        check_solution(p, thetas[k], res[k])
+        assert torch.equal(outs[k], thetas[k])
+
+
 def test_server_slot_limit_and_reuse():
     probs = mix(2, 9)
     with nsgb.Server(4 * GiB, 3, 8, order=4) as srv:

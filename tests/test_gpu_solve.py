@@ -131,6 +131,33 @@ def test_fp64_richardson_orderings(updated):
     assert r.stats.sweeps == ref.sweeps
 
 
+@pytest.mark.parametrize("c", [1.0, 0.25])
+def test_fp64_delayed_coupling_matches_oracle(c):
+    """couple_frob > 0: the Richardson branch starts once ||F_{k-1}||_F <= c;
+    iterates, residual record and sweep count follow the oracle's."""
+    n = 60
+    p = make_spd(n, 80.0, nrhs=2, seed=14)
+    ref = O.ns_richardson_solve(p.A, p.B, order=4, ns_iters=7, max_sweeps=3, couple_frob=c)
+    with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=3, couple_frob=c) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=7, tol=0.0)
+    assert rel(r.theta.cpu().numpy(), ref.theta) <= 1e-12
+    assert r.stats.sweeps == ref.sweeps and r.stats.ns_iters == ref.ns_iters
+    assert np.allclose(r.stats.res_history(), ref.rel_res, rtol=1e-9, atol=1e-14)
+
+
+def test_mixed_delayed_coupling_saves_sweeps():
+    p = make_spd(384, 1e4, nrhs=3, seed=15)
+    out = {}
+    for c in (0.0, 1.0):
+        with nsgb.Context(384, order=4, couple_frob=c) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+        assert r.status == nsgb.NS_OK
+        assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10
+        out[c] = r.stats
+    assert out[1.0].sweeps < out[0.0].sweeps
+    assert out[1.0].ns_iters <= out[0.0].ns_iters + 1
+
+
 @pytest.mark.parametrize("n,kappa,order,nrhs", [(64, 100.0, 4, 1), (256, 1e3, 4, 3), (200, 1e4, 8, 4),
                                                 (130, 1e2, 3, 2), (512, 1e4, 2, 5)])
 def test_mixed_precision_solve_reaches_tolerance(n, kappa, order, nrhs):

@@ -380,6 +380,33 @@ def test_richardson_error_model(order, updated):
         assert fro((r.theta - tstar) - ref) <= 1e-11 * max(1, fro(tstar))
 
 
+@pytest.mark.parametrize("order", [2, 4])
+def test_delayed_coupling_error_model(order):
+    """With the coupling delayed until the first G_k with ||I - A G_k||_F <= c,
+    only the coupled steps k contribute their factor I - G_k A = F_0^{n^k}: the
+    error after K steps is F_0^e theta~_0 with e the sum of n^k over the
+    coupled k, and the steps before leave theta (and the residual record)
+    alone."""
+    pr = spd(16, 30.0, nrhs=2, seed=23)
+    a = O.alpha_frobenius(pr.A)
+    tstar = np.linalg.solve(pr.A, pr.B)
+    K = 12 if order == 2 else 6
+    for c in (1.0, 0.3):
+        r = O.ns_richardson_solve(pr.A, pr.B, order=order, ns_iters=K, couple_frob=c)
+        k0 = next(k for k in range(K) if r.frob_E[k] <= c)
+        coupled = list(range(k0, K))
+        assert 0 < len(coupled) < K
+        e = sum(order ** k for k in coupled)
+        ref = eig_power(pr, a, e) @ (0 - tstar)
+        assert fro((r.theta - tstar) - ref) <= 1e-11 * max(1, fro(tstar))
+        # one residual per coupled step plus the final one
+        assert len(r.rel_res) == len(coupled) + 1 and r.sweeps == len(coupled)
+    # c = 0 is the paper's coupling from the first step
+    r0 = O.ns_richardson_solve(pr.A, pr.B, order=order, ns_iters=K, couple_frob=0.0)
+    r1 = O.ns_richardson_solve(pr.A, pr.B, order=order, ns_iters=K)
+    assert np.array_equal(r0.theta, r1.theta)
+
+
 def test_richardson_converges_to_cholesky():
     pr = spd(32, 100.0, nrhs=3, seed=20)
     r = O.ns_richardson_solve(pr.A, pr.B, order=4, ns_iters=8, tol=1e-12, max_sweeps=50)

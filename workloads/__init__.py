@@ -18,6 +18,7 @@ stand in for those:
 * ``make_harmonic_batch`` -- many such instances with m ~ U{8..128}.
 * ``make_serving_trace``  -- Poisson arrival times with per-request (n, kappa,
                          nrhs) drawn as described in each docstring.
+* ``make_spd_device``     -- make_spd's system built with torch on a device.
 
 Draw order inside one generator is fixed (Q, then lambda, then B) so that a
 seed always yields the same system.
@@ -35,6 +36,7 @@ __all__ = [
     "make_harmonic",
     "make_harmonic_batch",
     "make_serving_trace",
+    "make_spd_device",
     "ServingRequest",
 ]
 
@@ -159,3 +161,27 @@ def make_serving_trace(rate_per_s: float, duration_s: float, seed: int = 0,
         out.append(ServingRequest(t, n, kappa, nrhs, seed * 1_000_003 + i))
         i += 1
     return out
+
+
+def make_spd_device(n: int, kappa: float, nrhs: int = 1, seed: int = 0, device="cuda", qr_on_host: bool = False):
+    """The system ``make_spd(n, kappa, nrhs, seed)`` describes, built on a torch
+    device: the same Gaussian draws, spectrum and B from the same seed, with
+    the QR and Q diag(lam) Q^T done in FP64 by torch on ``device`` (so large
+    pools of systems can be drawn quickly; A agrees with make_spd's to
+    rounding).  ``qr_on_host`` does the QR with torch on the CPU instead.
+    Returns (A, B) as device tensors."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    Z = torch.from_numpy(rng.standard_normal((n, n)))
+    lam = torch.from_numpy(_log_uniform_spectrum(n, kappa, rng)).to(device)
+    B = torch.from_numpy(rng.standard_normal((n, nrhs))).to(device)
+    if qr_on_host:
+        Q, R = torch.linalg.qr(Z)
+        Q, R = Q.to(device), R.to(device)
+    else:
+        Q, R = torch.linalg.qr(Z.to(device))
+    Q = Q * torch.sign(torch.diagonal(R))[None, :]
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    return A.contiguous(), B.contiguous()
