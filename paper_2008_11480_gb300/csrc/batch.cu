@@ -369,11 +369,7 @@ ns_status publish_slot(ns_batch* b, int i, bool problems) {
   return NS_OK;
 }
 
-ns_status launch_products(ns_batch* b, const std::vector<int>& ids_in, const std::vector<int>& types) {
-  // largest systems first: the persistent kernel deals tiles out round-robin,
-  // so a descending cost order balances the CTAs (largest-first scheduling)
-  std::vector<int> ids(ids_in);
-  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::vector<int>& types) {
   for (int bnv : {128, 256}) {
     for (int x3 = 0; x3 < 2; ++x3) {
       std::vector<TcItem> items;
@@ -426,9 +422,7 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids_in, const std
   return NS_OK;
 }
 
-std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids_in, bool with_rhs) {
-  std::vector<int> ids(ids_in);  // largest systems first, as for the products
-  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids, bool with_rhs) {
   std::vector<BItem> it;
   for (int i : ids) {
     const int cmax = with_rhs ? b->nrhs[i] : 1;
