@@ -60,6 +60,7 @@ struct InstState {
   double best_rr = INFINITY;        // smallest residual of the Richardson-only phase
   double last_rr_sweep = INFINITY;  // residual of the previous Richardson-only pass
   int stall = 0;                    // consecutive Richardson-only passes with < 5 % progress
+  double prev_sweep_ratio = INFINITY;  // previous contraction ratio of the Richardson-only phase
   int status = NS_OK;
   int sweeps = 0;
   int rollbacks = 0;
@@ -526,7 +527,17 @@ void decide(ns_batch* b, int i) {
     s.last_rr_sweep = rr;
     if (std::isfinite(prev)) s.stall = rr > 0.95 * prev ? s.stall + 1 : 0;
     s.best_rr = std::min(s.best_rr, rr);
-    if (s.stall >= 4 || rr > 10.0 * s.best_rr) {
+    bool stop = s.stall >= 4 || rr > 10.0 * s.best_rr;
+    // ... or when even the better of the last two contraction ratios cannot
+    // reach tol within the sweeps left (an optimistic projection)
+    if (std::isfinite(prev) && prev > 0.0) {
+      const double ratio = rr / prev;
+      const double rho = std::min(ratio, s.prev_sweep_ratio);
+      s.prev_sweep_ratio = ratio;
+      if (tol > 0 && rho < 1.0 && std::log(tol / rr) / std::log(rho) > static_cast<double>(s.sweeps_left))
+        stop = true;
+    }
+    if (stop) {
       s.finished = true;
       s.status = NS_NOT_CONVERGED;
     }

@@ -650,7 +650,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   double prev_frob = INFINITY;
   double prev_ratio = INFINITY;
   double last_rr = INFINITY;
-  double prev_sweep_rr = INFINITY, best_rr = INFINITY;
+  double prev_sweep_rr = INFINITY, best_rr = INFINITY, prev_sweep_ratio = INFINITY;
   int stall = 0;
   bool converged = false;
   int aux_steps = 0;
@@ -880,9 +880,20 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     // Richardson alone no longer contracts (rho(I - A G) ~ 1 at this precision):
     // stop instead of spending the whole sweep budget
     if (std::isfinite(prev_sweep_rr)) stall = last_rr > 0.95 * prev_sweep_rr ? stall + 1 : 0;
-    prev_sweep_rr = last_rr;
     best_rr = std::min(best_rr, last_rr);
     if (stall >= 4 || last_rr > 10.0 * best_rr) break;
+    // ... or when even the better of the last two contraction ratios cannot
+    // reach tol within the sweeps left (the ratio settles towards rho(I - A G)
+    // from below, so this projection is optimistic)
+    if (std::isfinite(prev_sweep_rr) && prev_sweep_rr > 0.0) {
+      const double ratio = last_rr / prev_sweep_rr;
+      const double rho = std::min(ratio, prev_sweep_ratio);
+      prev_sweep_ratio = ratio;
+      if (tol > 0 && rho < 1.0 && last_rr > tol &&
+          std::log(tol / last_rr) / std::log(rho) > static_cast<double>(sweeps_left))
+        break;
+    }
+    prev_sweep_rr = last_rr;
     if (fp64)
       NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, s));
     else
