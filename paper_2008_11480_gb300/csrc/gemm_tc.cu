@@ -12,7 +12,8 @@
 // Roles (192 threads, one CTA per SM):
 //   warp 0 lane 0   TMA producer: fills a ring of shared-memory stages
 //   warp 1          TMEM allocator; lane 0 issues tcgen05.mma for a tile
-//   warps 2..5      epilogue: TMEM -> registers -> fused math -> global
+//   warps 2..5      epilogue: TMEM -> registers -> shared-memory transpose ->
+//                   fused math -> coalesced global stores (whole 128-B rows)
 // The accumulator is double-buffered in TMEM (2 x BN columns), so the
 // epilogue of tile i overlaps the MMAs of tile i+1.
 //
@@ -55,10 +56,14 @@ struct TcCfg {
   static constexpr int kABytes = kBM * kBK * 2;  // 16 KiB
   static constexpr int kBBytes = BN * kBK * 2;   // BN * 128 B
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
+  static constexpr int kStages = (196 * 1024) / kStageBytes > 8 ? 8 : (196 * 1024) / kStageBytes;
   static constexpr uint32_t kTmemCols = pow2_cols(2 * BN);
   static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
+  // epilogue transpose buffers: 4 warps x 32 rows x 36 floats (rows padded to
+  // 144 B so that the float4 writes and reads of a quarter-warp hit distinct banks)
+  static constexpr int kEpiStride = 36;
+  static constexpr int kEpiBytes = 4 * 32 * kEpiStride * 4;
+  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
 };
 
 // Work item w of this CTA (cluster rank `rank`): problem, tile row and column.
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ebuf = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + Cfg::kBarBytes);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -315,89 +321,112 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         break;
       }
       tc_fence_after();
-      const int row = m0 + q * 32 + lane;
-      const bool row_ok = row < P.M;
+      // Each 32-column chunk: tcgen05.ld gives lane l row (q*32 + l); the warp
+      // transposes it through shared memory so that every global access below
+      // covers whole 128-byte row segments (8 lanes x 16 B per row, 4 rows per
+      // instruction) instead of one 16-byte piece of 32 different rows.
+      float* wb = ebuf + q * 32 * Cfg::kEpiStride;
+      const int sub_r = lane >> 3;       // row within a group of 4
+      const int sub_c = (lane & 7) * 4;  // first of this lane's 4 columns
+      // the problem's fields in registers: the stores below could alias the
+      // problem table as far as the compiler knows, which would force a reload
+      // of every field after every store
+      const float e_s = P.s, e_beta = P.beta, e_gamma = P.gamma;
+      const int e_M = P.M, e_N = P.N;
+      const int64_t e_ldc = P.ldc, e_ld32 = P.ldd32, e_ld16 = P.ldd16;
+      const float* __restrict__ e_C = e_beta != 0.f ? P.C : nullptr;
+      float* __restrict__ e_D32 = P.D32;
+      bf16* __restrict__ e_Dhi = P.Dhi;
+      bf16* __restrict__ e_Dlo = P.Dlo;
       float frob = 0.f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
+        const int col0 = n0 + c0;
+        if (col0 >= e_N) break;  // warp-uniform: no later chunk has columns either
+        const int col = col0 + sub_c;
+        const bool cols4 = col + 4 <= e_N;
+        // the beta C term of all 8 row groups first, so that the loads overlap
+        // one another and the TMEM load below
+        float4 cv[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          cv[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const int row = m0 + q * 32 + 4 * g + sub_r;
+          if (e_C == nullptr || row >= e_M || col >= e_N) continue;
+          const float* crow = e_C + static_cast<int64_t>(row) * e_ldc + col;
+          if (cols4) {
+            cv[g] = *reinterpret_cast<const float4*>(crow);
+          } else {
+            cv[g].x = crow[0];
+            if (col + 1 < e_N) cv[g].y = crow[1];
+            if (col + 2 < e_N) cv[g].z = crow[2];
+          }
+        }
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN + c0),
                            r);
         tmem_wait_ld();
-        const int col0 = n0 + c0;
-        if (!row_ok || col0 >= P.N) continue;
-        float v[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = P.s * __uint_as_float(r[i]);
-        const bool full_chunk = col0 + 32 <= P.N;
-        if (P.C != nullptr && P.beta != 0.f) {
-          const float* crow = P.C + static_cast<int64_t>(row) * P.ldc + col0;
-          if (full_chunk) {
+        for (int i = 0; i < 32; i += 4)
+          *reinterpret_cast<float4*>(wb + lane * Cfg::kEpiStride + i) =
+              make_float4(e_s * __uint_as_float(r[i]), e_s * __uint_as_float(r[i + 1]),
+                          e_s * __uint_as_float(r[i + 2]), e_s * __uint_as_float(r[i + 3]));
+        __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              const float4 c = *reinterpret_cast<const float4*>(crow + i);
-              v[i] += P.beta * c.x;
-              v[i + 1] += P.beta * c.y;
-              v[i + 2] += P.beta * c.z;
-              v[i + 3] += P.beta * c.w;
+        for (int g = 0; g < 8; ++g) {
+          const int rr = 4 * g + sub_r;
+          const int row = m0 + q * 32 + rr;
+          const float4 x4 = *reinterpret_cast<const float4*>(wb + rr * Cfg::kEpiStride + sub_c);
+          if (row >= e_M || col >= e_N) continue;
+          float v[4] = {x4.x, x4.y, x4.z, x4.w};
+          if (e_C != nullptr) {
+            v[0] += e_beta * cv[g].x;
+            v[1] += e_beta * cv[g].y;
+            v[2] += e_beta * cv[g].z;
+            v[3] += e_beta * cv[g].w;
+          }
+          if (e_gamma != 0.f) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] += (row == col + t) ? e_gamma : 0.f;
+          }
+          if (cols4) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) frob += v[t] * v[t];
+            if (e_D32 != nullptr)
+              *reinterpret_cast<float4*>(e_D32 + static_cast<int64_t>(row) * e_ld32 + col) =
+                  make_float4(v[0], v[1], v[2], v[3]);
+            if (e_Dhi != nullptr) {
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+              const __nv_bfloat16 h2 = __float2bfloat16_rn(v[2]), h3 = __float2bfloat16_rn(v[3]);
+              __nv_bfloat162 ha, hb;
+              ha.x = h0;
+              ha.y = h1;
+              hb.x = h2;
+              hb.y = h3;
+              const int64_t o16 = static_cast<int64_t>(row) * e_ld16 + col;
+              *reinterpret_cast<uint2*>(e_Dhi + o16) =
+                  make_uint2(*reinterpret_cast<uint32_t*>(&ha), *reinterpret_cast<uint32_t*>(&hb));
+              if (e_Dlo != nullptr)
+                *reinterpret_cast<uint2*>(e_Dlo + o16) =
+                    make_uint2(pack_bf16x2(v[0] - __bfloat162float(h0), v[1] - __bfloat162float(h1)),
+                               pack_bf16x2(v[2] - __bfloat162float(h2), v[3] - __bfloat162float(h3)));
             }
           } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (col0 + i < P.N) v[i] += P.beta * crow[i];
-          }
-        }
-        if (P.gamma != 0.f) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += (row == col0 + i) ? P.gamma : 0.f;
-        }
-        if (full_chunk) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) frob += v[i] * v[i];
-          if (P.D32 != nullptr) {
-            float* drow = P.D32 + static_cast<int64_t>(row) * P.ldd32 + col0;
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(drow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-          }
-          if (P.Dhi != nullptr) {
-            uint32_t hi[16], lo[16];
-#pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[i]);
-              const __nv_bfloat16 h1 = __float2bfloat16_rn(v[i + 1]);
-              __nv_bfloat162 hh;
-              hh.x = h0;
-              hh.y = h1;
-              hi[i / 2] = *reinterpret_cast<uint32_t*>(&hh);
-              lo[i / 2] = pack_bf16x2(v[i] - __bfloat162float(h0), v[i + 1] - __bfloat162float(h1));
-            }
-            bf16* hrow = P.Dhi + static_cast<int64_t>(row) * P.ldd16 + col0;
-#pragma unroll
-            for (int i = 0; i < 16; i += 4)
-              *reinterpret_cast<uint4*>(hrow + 2 * i) = make_uint4(hi[i], hi[i + 1], hi[i + 2], hi[i + 3]);
-            if (P.Dlo != nullptr) {
-              bf16* lrow = P.Dlo + static_cast<int64_t>(row) * P.ldd16 + col0;
-#pragma unroll
-              for (int i = 0; i < 16; i += 4)
-                *reinterpret_cast<uint4*>(lrow + 2 * i) = make_uint4(lo[i], lo[i + 1], lo[i + 2], lo[i + 3]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (col0 + i >= P.N) continue;
-            frob += v[i] * v[i];
-            const int64_t o32 = static_cast<int64_t>(row) * P.ldd32 + col0 + i;
-            const int64_t o16 = static_cast<int64_t>(row) * P.ldd16 + col0 + i;
-            if (P.D32 != nullptr) P.D32[o32] = v[i];
-            if (P.Dhi != nullptr) {
-              const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
-              P.Dhi[o16] = h;
-              if (P.Dlo != nullptr) P.Dlo[o16] = __float2bfloat16_rn(v[i] - __bfloat162float(h));
+            for (int t = 0; t < 4; ++t) {
+              if (col + t >= e_N) continue;
+              frob += v[t] * v[t];
+              if (e_D32 != nullptr) e_D32[static_cast<int64_t>(row) * e_ld32 + col + t] = v[t];
+              if (e_Dhi != nullptr) {
+                const int64_t o16 = static_cast<int64_t>(row) * e_ld16 + col + t;
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[t]);
+                e_Dhi[o16] = h;
+                if (e_Dlo != nullptr) e_Dlo[o16] = __float2bfloat16_rn(v[t] - __bfloat162float(h));
+              }
             }
           }
         }
+        __syncwarp();  // the buffer is rewritten by the next chunk
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
