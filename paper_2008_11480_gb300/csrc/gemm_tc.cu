@@ -160,6 +160,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       int pi, mt, nt;
       decode_item(p, w, rank, CM, pi, mt, nt);
       const TcProblem& P = p.gprob != nullptr ? p.gprob[pi] : p.prob[pi];
+      if (p.gprob != nullptr && w + stride < p.total_tiles) {
+        // list mode: every item may name another problem, i.e. other tensor
+        // maps; warm the descriptors of this CTA's next item
+        const TcProblem& Q = p.gprob[p.items[w + stride].prob];
+        tma_prefetch_desc(&Q.L[0]);
+        tma_prefetch_desc(&Q.R[0]);
+        if (X3 || p.npass > 1) {
+          tma_prefetch_desc(&Q.L[1]);
+          tma_prefetch_desc(&Q.R[1]);
+        }
+      }
       const int m0 = mt * kBM, n0 = nt * BN;
       const int kstep = X3 ? kBK / 2 : kBK;
       const int nkb = (P.K + kstep - 1) / kstep;

@@ -75,6 +75,12 @@ struct ns_ctx {
   int scal_cap = 0;
   double* partials = nullptr;
   size_t partials_cap = 0;
+  // Richardson branch (residual, update) on its own stream, concurrent with
+  // the products; it joins the main stream at every scalar read
+  cudaStream_t rstream = nullptr;
+  cudaEvent_t ev_join[2] = {nullptr, nullptr};
+  double* rpartials = nullptr;
+  size_t rpartials_cap = 0;
   double* Astage = nullptr;
   double *Bd = nullptr, *Thd = nullptr, *Rd = nullptr;
   float *T1 = nullptr, *T2 = nullptr, *R32T = nullptr;  // f32 limbs of theta, f32 R (per rhs, ld)
@@ -177,6 +183,16 @@ ns_status ensure_common(ns_ctx* ctx, int nrhs) {
     if (need > ctx->partials_cap) {
       NS_TRY(alloc(ctx, &ctx->partials, need));
       ctx->partials_cap = need;
+    }
+    const size_t rneed = static_cast<size_t>(std::max(resid_blocks(n), resid_x2_blocks(n))) * cap;
+    if (rneed > ctx->rpartials_cap) {
+      NS_TRY(alloc(ctx, &ctx->rpartials, rneed));
+      ctx->rpartials_cap = rneed;
+    }
+    if (ctx->rstream == nullptr) {
+      NS_CK(cudaStreamCreateWithFlags(&ctx->rstream, cudaStreamNonBlocking));
+      NS_CK(cudaEventCreateWithFlags(&ctx->ev_join[0], cudaEventDisableTiming));
+      NS_CK(cudaEventCreateWithFlags(&ctx->ev_join[1], cudaEventDisableTiming));
     }
   }
   return NS_OK;
@@ -425,7 +441,17 @@ ns_status f64_gemm(ns_ctx* ctx, const double* L, const double* R, double s, cons
 
 // Read the scalar block back (one small D2H copy + stream sync) and check the
 // device error word.
+// Make `to` wait for the work enqueued on `from` so far.
+ns_status join_streams(ns_ctx* ctx, cudaStream_t from, cudaStream_t to) {
+  if (from == to) return NS_OK;
+  cudaEvent_t ev = ctx->ev_join[from == ctx->rstream ? 1 : 0];
+  NS_CK(cudaEventRecord(ev, from));
+  NS_CK(cudaStreamWaitEvent(to, ev, 0));
+  return NS_OK;
+}
+
 ns_status sync_scalars(ns_ctx* ctx, int nrhs) {
+  if (ctx->rstream) NS_TRY(join_streams(ctx, ctx->rstream, ctx->stream));
   const size_t bytes = (8 + 2 * static_cast<size_t>(ctx->scal_cap)) * sizeof(double);
   NS_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   NS_CK(cudaStreamSynchronize(ctx->stream));
@@ -751,17 +777,20 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
   };
 
-  // Richardson branch of a pass: r = B - A theta and its per-rhs norms
+  // Richardson branch of a pass on its own stream: r = B - A theta and its
+  // per-rhs norms (the operands prepared above are visible to it)
+  cudaStream_t rs = ctx->rstream ? ctx->rstream : s;
+  if (richardson) NS_TRY(join_streams(ctx, s, rs));
   auto launch_residual = [&]() -> ns_status {
     if (fp64) {
-      NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->partials, &nb, s));
+      NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->rpartials, &nb, rs));
       ctx->launches += (S.nrhs + 7) / 8;
     } else {
       NS_CK(launch_resid_x2(ctx->A1, ctx->A2, ld, ctx->T1, ctx->T2, ld, S.B, ctx->Rd, ctx->R32T, n, S.nrhs,
-                            ctx->partials, &nb, s));
+                            ctx->rpartials, &nb, rs));
       ctx->launches += (S.nrhs + 3) / 4;
     }
-    NS_CK(launch_reduce_sum(ctx->partials, nb, S.nrhs, rsq, s));
+    NS_CK(launch_reduce_sum(ctx->rpartials, nb, S.nrhs, rsq, rs));
     ctx->launches += 1;
     return NS_OK;
   };
@@ -860,10 +889,11 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       const int g_next = S.cur ^ 1;
       if (rich) {
         const int gi = ctx->opt.use_updated_G ? g_next : g_used;
+        if (ctx->opt.use_updated_G) NS_TRY(join_streams(ctx, s, rs));  // G_{k+1} comes from the chain
         if (fp64)
-          NS_CK(launch_update_f64(ctx->G64[gi], ld, ctx->Rd, S.Th, n, S.nrhs, s));
+          NS_CK(launch_update_f64(ctx->G64[gi], ld, ctx->Rd, S.Th, n, S.nrhs, rs));
         else
-          NS_CK(launch_update_x2(ctx->G[gi].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, s));
+          NS_CK(launch_update_x2(ctx->G[gi].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, rs));
         ctx->launches += (S.nrhs + 7) / 8;
         if (st) st->sweeps++;
       }
@@ -895,14 +925,15 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
     prev_sweep_rr = last_rr;
     if (fp64)
-      NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, s));
+      NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, rs));
     else
-      NS_CK(launch_update_x2(ctx->G[S.cur].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, s));
+      NS_CK(launch_update_x2(ctx->G[S.cur].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, rs));
     ctx->launches += (S.nrhs + 7) / 8;
     sweeps_left--;
     if (st) st->sweeps++;
   }
   (void)aux_steps;
+  if (richardson) NS_TRY(join_streams(ctx, rs, s));  // theta is final on the main stream
   if (richardson) return converged || tol <= 0 ? NS_OK : NS_NOT_CONVERGED;
   return NS_OK;
 }
@@ -920,6 +951,7 @@ ns_status begin_call(ns_ctx* ctx, ns_stats* st) {
 }
 
 ns_status end_call(ns_ctx* ctx, ns_status r, std::chrono::steady_clock::time_point t0) {
+  if (ctx->rstream) cudaStreamSynchronize(ctx->rstream);
   cudaStreamSynchronize(ctx->stream);
   ev_collect(ctx);
   if (ctx->st) {
@@ -1002,6 +1034,12 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
 ns_status ns_destroy(ns_ctx* ctx) {
   if (!ctx) return NS_OK;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->rstream) {
+    cudaStreamSynchronize(ctx->rstream);
+    cudaStreamDestroy(ctx->rstream);
+  }
+  for (cudaEvent_t e : ctx->ev_join)
+    if (e) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->hscal) cudaFreeHost(ctx->hscal);
   for (auto& e : ctx->ev_pool) {
