@@ -5,6 +5,7 @@
 // instance's arithmetic (row blocks, k split, reduction order) is the same as
 // when it is alone in the batch, so results do not depend on the mix.
 #include "batch.h"
+#include "split.cuh"
 
 namespace nsgb {
 namespace {
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(256) k_bprep(const BInst* __restrict__ insts, 
       const double v = p[k];
       s += v * v;
       a += fabs(v);
-      const float f1 = static_cast<float>(v);
-      const float f2 = static_cast<float>(v - static_cast<double>(f1));
+      float f1, f2;
+      split_f64_f32(v, f1, f2);
       I.A1[o + k] = f1;
       I.A2[o + k] = f2;
       const bf16 h = __float2bfloat16_rn(f1);

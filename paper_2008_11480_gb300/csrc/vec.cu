@@ -2,6 +2,7 @@
 // R = B - A Theta (FP64), the update Theta += G R, matrix/column norms,
 // fixed-order (deterministic) reductions, the bf16 hi/lo splits and G0.
 #include "internal.h"
+#include "split.cuh"
 
 namespace nsgb {
 namespace {
@@ -590,8 +591,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const double* __restrict__ A, in
           for (int t = 0; t < 2; ++t) {
             s += e[t] * e[t];
             a += fabs(e[t]);
-            f1[t] = static_cast<float>(e[t]);
-            f2[t] = static_cast<float>(e[t] - static_cast<double>(f1[t]));
+            split_f64_f32(e[t], f1[t], f2[t]);
             h[t] = __float2bfloat16_rn(f1[t]);
             l[t] = __float2bfloat16_rn(f1[t] - __bfloat162float(h[t]));
           }
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(256) k_prep_a(const double* __restrict__ A, in
       const double v = p[k];
       s += v * v;
       a += fabs(v);
-      const float f1 = static_cast<float>(v);
-      const float f2 = static_cast<float>(v - static_cast<double>(f1));
+      float f1, f2;
+      split_f64_f32(v, f1, f2);
       a1[o + k] = f1;
       a2[o + k] = f2;
       const bf16 h = __float2bfloat16_rn(f1);

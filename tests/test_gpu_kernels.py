@@ -227,6 +227,42 @@ def test_prep_a_bit_exact(n):
     assert float(rm.item()) == pytest.approx(float(np.max(np.sum(np.abs(A), axis=1))), rel=1e-13)
 
 
+def test_prep_a_split_edge_cases():
+    """The two-limb split on values chosen to hit its corner cases: ties at
+    the 24-bit rounding point (both parities), significands of all ones
+    (rounding carries into the exponent), both ends of the integer fast path
+    (|v| near 2^-74 and 2^127) and beyond, doubles that are exactly floats,
+    zeros and negative values; limbs equal RN32(v) and RN32(v - RN32(v))."""
+    rng = np.random.default_rng(31)
+    vals = []
+    for e in (-80, -75, -74, -73, -30, -1, 0, 1, 30, 100, 126, 127):
+        for sig in (0x0000000000000, 0xFFFFFFFFFFFFF, 0x0000010000000, 0x0000030000000, 0x0000010000001,
+                    0x000002FFFFFFF, 0x8000010000000):
+            bits = ((e + 1023) << 52) | sig
+            vals.append(np.array([bits], dtype=np.uint64).view(np.float64)[0])
+    vals += [0.0, -0.0, 1.0, -1.0, 3.0e38, -3.0e38, 1e-300, -1e-300, 5e-324, 2.0 ** -126, 1.5 * 2.0 ** -149]
+    vals = np.array(vals)
+    vals = vals[np.isfinite(O.round_f32(vals))]  # leave out values whose f32 rounding overflows
+    vals = np.concatenate([vals, -vals, rng.standard_normal(8) * 2.0 ** rng.integers(-70, 120, 8)])
+    n = 64
+    A = np.resize(vals, (n, n)).copy()
+    hi = torch.zeros((n, n), dtype=torch.bfloat16, device=dev)
+    lo = torch.zeros_like(hi)
+    a1 = torch.zeros((n, n), dtype=torch.float32, device=dev)
+    a2 = torch.zeros_like(a1)
+    nsgb.ns_k_prep_a(torch.from_numpy(A).to(dev), n, n, hi, lo, a1, a2, n)
+    torch.cuda.synchronize()
+    r1 = O.round_f32(A)
+    r2 = O.round_f32(A - r1)
+    g1 = a1.cpu().numpy().astype(np.float64)
+    g2 = a2.cpu().numpy().astype(np.float64)
+    assert np.array_equal(g1, r1)
+    assert np.array_equal(g2, r2)
+    rh, rl = O.split_bf16(A)
+    assert np.array_equal(hi.float().cpu().numpy().astype(np.float64), rh)
+    assert np.array_equal(lo.float().cpu().numpy().astype(np.float64), rl)
+
+
 @pytest.mark.parametrize("n,nrhs", [(1, 1), (64, 1), (130, 3), (257, 9), (1000, 4), (4096, 4)])
 def test_resid_x2(n, nrhs):
     """R = B - A Theta from f32 limbs (double-f32 accumulation).  Bound: split
