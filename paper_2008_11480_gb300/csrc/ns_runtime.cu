@@ -3,6 +3,7 @@
 // composite mixed-rate and double-loop variants (Section 5, 5.1), the coupled
 // Richardson iteration (Section 6) and the precision controller.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1268,6 +1269,15 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   p.npass = precision == NS_BF16X3 ? 3 : 1;
   p.debug_stall_iter = -1;
   p.timeout_ns = 2000000000ull;
+  // host-side fault injection for the failure-detection tests: the producer
+  // withholds one stage load (a flag that nothing sets), and the bound on
+  // every device wait can be shortened; the kernel then reports
+  // NS_ERR_TIMEOUT and the context stays usable
+  if (const char* v = std::getenv("NSGB_INJECT_WITHHOLD_LOAD")) p.debug_stall_iter = std::atoi(v);
+  if (const char* v = std::getenv("NSGB_WAIT_LIMIT_MS")) {
+    const long ms = std::atol(v);
+    if (ms > 0 && ms <= 10000) p.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
+  }
   TcProblem& P = p.prob[0];
   const bool x3 = p.npass == 3 && bn != 192;
   const int lr = x3 ? 1 : 0, rr = x3 ? 2 : 0;
