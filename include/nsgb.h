@@ -84,6 +84,14 @@ typedef struct ns_options {
                           F_k = F_0^{n^k}, the residual factor they contribute is negligible
                           next to the last step's.  1.0 skips exactly the sweeps without a
                           contraction bound (costs one extra device sync where it starts). */
+  int accel_richardson; /* 1: accelerated Richardson of Section 6 (eq. ttk1 with q = n): while
+                          Newton-Schulz runs, theta_k = theta_{k-1} + omega_k r with
+                          omega_k = L_k + Gamma_k^n {sum_{j<n} F_k^j} G_k from the double
+                          Newton-Schulz state (eqs. gamk11-fks1), so the error follows
+                          (S^{-1}D)^{gamma_k} of eq. riem6; theta starts at L_0 b unless
+                          Theta0 is given.  Needs rates = {order} and aux_ahead = 1 (the
+                          double NS method); ns_create returns NS_ERR_ARG otherwise.  omega_k r
+                          is applied as u = X_k r, u += L_k (r - A u) without forming omega_k. */
 } ns_options;
 
 #define NS_MAX_HIST 256

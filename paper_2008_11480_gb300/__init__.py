@@ -63,6 +63,7 @@ class ns_options(ctypes.Structure):
         ("aux_ahead", ctypes.c_int),
         ("gemm_cluster", ctypes.c_int),
         ("couple_frob", ctypes.c_double),
+        ("accel_richardson", ctypes.c_int),
     ]
 
 

@@ -127,6 +127,8 @@ cudaError_t launch_prep_a(const double* A, int64_t lda, int n, bf16* hi, bf16* l
                           double* ss_part, double* rm_part, int* nblocks_out, cudaStream_t s);
 // theta (n x nrhs) -> f32 limbs T1/T2 stored per right-hand side (leading dimension ldt).
 cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, float* T2, int64_t ldt, cudaStream_t s);
+cudaError_t launch_axpy_theta(double* Th, const double* U, int n, int nrhs, float* T1, float* T2, int64_t ldt,
+                              cudaStream_t s);
 // R = B - A theta from the limbs; R (FP64, n x nrhs), R32T (f32, per rhs), partial R^2
 // (resid_x2_blocks(n) blocks x nrhs partials).
 int resid_x2_blocks(int n);

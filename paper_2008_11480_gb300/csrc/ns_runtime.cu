@@ -80,6 +80,10 @@ struct ns_ctx {
   // the products; it joins the main stream at every scalar read
   cudaStream_t rstream = nullptr;
   cudaEvent_t ev_join[2] = {nullptr, nullptr};
+  // accelerated Richardson: u = X_k r, v = r - A u (FP64 and f32 forms)
+  double *AccU = nullptr, *AccV = nullptr;
+  float *AccU1 = nullptr, *AccU2 = nullptr, *AccV32T = nullptr;
+  int acc_cap = 0;
   double* rpartials = nullptr;
   size_t rpartials_cap = 0;
   double* Astage = nullptr;
@@ -598,6 +602,7 @@ struct Solve {
   double* Th = nullptr;       // device n x nrhs
   int nrhs = 0;
   bool fp64 = false;
+  bool theta0_given = false;  // Theta0 came from the caller (else theta starts at 0)
   int prec = NS_BF16X3;
   int cur = 0;  // G buffer holding G_k
   int ccur = 0; // composite buffers holding T_i
@@ -716,6 +721,28 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     NS_TRY(composite_aux_step(prec));
     aux_steps++;
   }
+  const bool accel = richardson && ctx->opt.accel_richardson != 0;
+  if (accel) {
+    // workspace of omega_k r, and theta_0 = L_0 b (Section 6) unless given
+    if (ctx->acc_cap < S.nrhs) {
+      const size_t c = static_cast<size_t>(S.nrhs);
+      NS_TRY(alloc(ctx, &ctx->AccU, static_cast<size_t>(n) * c));
+      NS_TRY(alloc(ctx, &ctx->AccV, static_cast<size_t>(n) * c));
+      NS_TRY(alloc(ctx, &ctx->AccU1, static_cast<size_t>(ld) * c));
+      NS_TRY(alloc(ctx, &ctx->AccU2, static_cast<size_t>(ld) * c));
+      NS_TRY(alloc(ctx, &ctx->AccV32T, static_cast<size_t>(ld) * c));
+      ctx->acc_cap = S.nrhs;
+    }
+    if (!S.theta0_given) {
+      if (fp64) {
+        NS_CK(launch_update_f64(ctx->T64[S.ccur][0], ld, S.B, S.Th, n, S.nrhs, s));
+      } else {
+        NS_CK(launch_update_f32(ctx->T[S.ccur][0].m32, ld, S.B, S.Th, n, S.nrhs, s));
+        NS_CK(launch_split_theta(S.Th, n, S.nrhs, ctx->T1, ctx->T2, ld, s));
+      }
+      ctx->launches += 2;
+    }
+  }
 
   // G_{k+1} = T_c + Gamma_c X with X the NS step of G_k (eq. gkgen1); the
   // plain NS product chain when there are no rates.
@@ -793,6 +820,30 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
     NS_CK(launch_reduce_sum(ctx->rpartials, nb, S.nrhs, rsq, rs));
     ctx->launches += 1;
+    return NS_OK;
+  };
+  // omega_k r applied without forming omega_k: u = X_k r, v = r - A u,
+  // u += L_k v, theta += u (L_k in composite buffer `lbuf`, X_k in Xs[0])
+  auto accel_update = [&](int lbuf) -> ns_status {
+    const size_t nb2 = static_cast<size_t>(n) * S.nrhs;
+    NS_CK(cudaMemsetAsync(ctx->AccU, 0, nb2 * sizeof(double), rs));
+    int nbv = 0;
+    if (fp64) {
+      NS_CK(launch_update_f64(ctx->Xs64[0], ld, ctx->Rd, ctx->AccU, n, S.nrhs, rs));
+      NS_CK(launch_resid(S.A, S.lda, ctx->AccU, ctx->Rd, ctx->AccV, n, S.nrhs, ctx->rpartials, &nbv, rs));
+      NS_CK(launch_update_f64(ctx->T64[lbuf][0], ld, ctx->AccV, ctx->AccU, n, S.nrhs, rs));
+      NS_CK(launch_axpy_theta(S.Th, ctx->AccU, n, S.nrhs, nullptr, nullptr, ld, rs));
+    } else {
+      NS_CK(cudaMemsetAsync(ctx->AccU1, 0, static_cast<size_t>(ld) * S.nrhs * sizeof(float), rs));
+      NS_CK(cudaMemsetAsync(ctx->AccU2, 0, static_cast<size_t>(ld) * S.nrhs * sizeof(float), rs));
+      NS_CK(launch_update_x2(ctx->Xs[0].m32, ld, ctx->R32T, ld, ctx->AccU, ctx->AccU1, ctx->AccU2, n, S.nrhs, rs));
+      NS_CK(launch_resid_x2(ctx->A1, ctx->A2, ld, ctx->AccU1, ctx->AccU2, ld, ctx->Rd, ctx->AccV, ctx->AccV32T, n,
+                            S.nrhs, ctx->rpartials, &nbv, rs));
+      NS_CK(launch_update_x2(ctx->T[lbuf][0].m32, ld, ctx->AccV32T, ld, ctx->AccU, ctx->AccU1, ctx->AccU2, n,
+                             S.nrhs, rs));
+      NS_CK(launch_axpy_theta(S.Th, ctx->AccU, n, S.nrhs, ctx->T1, ctx->T2, ld, rs));
+    }
+    ctx->launches += 4;
     return NS_OK;
   };
   // couple_frob > 0 delays the coupling: it starts with the first G_k whose
@@ -888,7 +939,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       const int g_used = S.cur;
       NS_TRY(ns_update(prec));
       const int g_next = S.cur ^ 1;
-      if (rich) {
+      if (rich && accel) {
+        // eq. ttk1: theta += omega_k r, omega_k = L_k + (I - L_k A) X_k with X_k the
+        // NS step of G_k (the chain output) and L_k the auxiliary loop before its
+        // advance; the first step only sets up the state (theta_0 = L_0 b)
+        if (done > 0) {
+          NS_TRY(join_streams(ctx, s, rs));
+          NS_TRY(accel_update(S.ccur ^ 1));
+          if (st) st->sweeps++;
+        }
+      } else if (rich) {
         const int gi = ctx->opt.use_updated_G ? g_next : g_used;
         if (ctx->opt.use_updated_G) NS_TRY(join_streams(ctx, s, rs));  // G_{k+1} comes from the chain
         if (fp64)
@@ -986,6 +1046,7 @@ void ns_default_options(ns_options* o) {
   o->aux_ahead = 0;
   o->gemm_cluster = 0;
   o->couple_frob = 0.0;
+  o->accel_richardson = 0;
 }
 
 const char* ns_status_string(ns_status s) {
@@ -1016,6 +1077,8 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
+  // accelerated Richardson runs on the double Newton-Schulz state
+  if (o.accel_richardson && (n_rates != 1 || rates[0] != order || !o.aux_ahead)) return NS_ERR_ARG;
   ns_ctx* c = new ns_ctx();
   c->n = n;
   c->ld = round_up(n, 64);
@@ -1168,6 +1231,7 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   S.Th = Th;
   S.nrhs = nrhs;
   S.fp64 = fp64;
+  S.theta0_given = Theta0 != nullptr;
   r = run(ctx, S, nullptr, iters, tol, true, st);
   if (r >= 0 && !out_dev) {
     e = cudaMemcpyAsync(Theta_out, Th, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);

@@ -653,6 +653,25 @@ __global__ void k_split_theta(const double* __restrict__ Th, int n, int nrhs, fl
   }
 }
 
+// Theta += U (n x nrhs, row-major FP64); with T1 non-null also the f32 limbs
+// of the new theta (T1/T2[c][k], leading dimension ldt).
+__global__ void k_axpy_theta(double* __restrict__ Th, const double* __restrict__ U, int n, int nrhs,
+                             float* __restrict__ T1, float* __restrict__ T2, int64_t ldt) {
+  const int64_t total = static_cast<int64_t>(n) * nrhs;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double v = Th[e] + U[e];
+    Th[e] = v;
+    if (T1 != nullptr) {
+      const int64_t k = e / nrhs, c = e % nrhs;
+      float f1, f2;
+      split_f64_f32(v, f1, f2);
+      T1[c * ldt + k] = f1;
+      T2[c * ldt + k] = f2;
+    }
+  }
+}
+
 // Lane reduction of a paired-f32 value (hi, lo) across the warp with TwoSum at
 // every step, so the ~48-bit partial sums stay ~48-bit (FP64 instructions are
 // rate-limited on this GPU; this uses the f32 pipes and shuffles only).
@@ -899,6 +918,14 @@ cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, flo
   const int64_t total = static_cast<int64_t>(n) * nrhs;
   if (total <= 0) return cudaSuccess;
   k_split_theta<<<ew_grid(total), 256, 0, s>>>(Th, n, nrhs, T1, T2, ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_theta(double* Th, const double* U, int n, int nrhs, float* T1, float* T2, int64_t ldt,
+                              cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * nrhs;
+  if (total <= 0) return cudaSuccess;
+  k_axpy_theta<<<ew_grid(total), 256, 0, s>>>(Th, U, n, nrhs, T1, T2, ldt);
   return cudaGetLastError();
 }
 

@@ -131,6 +131,48 @@ def test_fp64_richardson_orderings(updated):
     assert r.stats.sweeps == ref.sweeps
 
 
+@pytest.mark.parametrize("n_order,K", [(2, 2), (2, 3), (3, 2)])
+def test_fp64_accelerated_richardson_matches_oracle(n_order, K):
+    """Accelerated Richardson of Section 6 (eq. ttk1, q = n) on the double
+    Newton-Schulz state: theta starts at L_0 b and step k applies
+    omega_k = L_k + Gamma_k^n P(F_k) G_k; the iterate equals the oracle's and
+    its error is (S^{-1}D)^{gamma_k} theta~_0 with gamma_k of eq. riem6."""
+    n = 40
+    p = make_spd(n, 20.0, nrhs=2, seed=16)
+    a = O.alpha_frobenius(p.A)
+    st = O.double_ns_init(p.A, a * np.eye(n), n_order)
+    theta = st.L @ p.B
+    tstar = np.linalg.solve(p.A, p.B)
+    t0 = theta - tstar
+    for _ in range(K):
+        st = O.double_ns_iterate(p.A, st, n_order)
+        theta = O.accelerated_richardson_step(p.A, p.B, theta, st, q=n_order)
+    with nsgb.Context(n, order=n_order, rates=(n_order,), precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=0,
+                      aux_ahead=1, accel_richardson=1) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=K + 1, tol=0.0)
+    got = r.theta.cpu().numpy()
+    assert rel(got, theta) <= 1e-12
+    g = int(O.accelerated_richardson_exponent(n_order, 1, K))
+    Fg = (p.Q * (1 - a * p.lam) ** g) @ p.Q.T
+    assert np.linalg.norm((got - tstar) - Fg @ t0) <= 1e-11 * max(1.0, np.linalg.norm(t0))
+    assert r.stats.sweeps == K
+
+
+def test_accelerated_richardson_needs_double_ns():
+    with pytest.raises(nsgb.NSError):
+        nsgb.Context(32, order=4, precision=nsgb.NS_FP64, accel_richardson=1)
+    with pytest.raises(nsgb.NSError):
+        nsgb.Context(32, order=4, rates=(4,), precision=nsgb.NS_FP64, accel_richardson=1)  # aux_ahead = 0
+
+
+def test_mixed_accelerated_richardson_reaches_tolerance():
+    p = make_spd(300, 1e3, nrhs=3, seed=17)
+    with nsgb.Context(300, order=4, rates=(4,), aux_ahead=1, accel_richardson=1) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10
+
+
 @pytest.mark.parametrize("c", [1.0, 0.25])
 def test_fp64_delayed_coupling_matches_oracle(c):
     """couple_frob > 0: the Richardson branch starts once ||F_{k-1}||_F <= c;
