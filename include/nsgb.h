@@ -62,9 +62,14 @@ typedef enum ns_precision {
 
 typedef struct ns_options {
   int precision;       /* ns_precision; default NS_AUTO */
-  int form;            /* 0 factorized (orders 3 and 2^m), 1 unfactorized Horner (any order) */
+  int form;            /* 0 factorized (orders 3 and 2^m), 1 unfactorized Horner (any order),
+                          2 the Appendix tool-kit (Tables t1-t3) for orders 2..19 (p + w + 1
+                          products, +1 for the eq. ztab2 rows), 3 nested order 45 in ten
+                          products (Section 4, eqs. ex1-ex3; order must be 45) */
   int pow_mode;        /* 0: F^{2^{j+1}} = F^{2^j} F^{2^j}; 1: F^{2^{j+1}} = I - A X_{j+1} (eq. ua1) */
-  int g0_mode;         /* 0: alpha = 1/||A||_F; 1: alpha = 1/(||A||_inf/2 + 1e-8 ||A||_inf) */
+  int g0_mode;         /* 0: alpha = 1/||A||_F; 1: alpha = 1/(||A||_inf/2 + 1e-8 ||A||_inf);
+                          2: Jacobi, G0 = diag(A)^{-1} (Section 2, strictly diagonally dominant A;
+                          single-system path only) */
   int ns_stop;         /* 0: take exactly `iters` NS steps; 1: stop NS at the precision floor */
   double ns_stop_frob; /* with ns_stop = 1, also stop once ||F_k||_F <= this; default 0.02 */
   int max_sweeps;      /* Richardson-only sweeps allowed after NS stops; default 200 */

@@ -720,7 +720,7 @@ ns_status check_opts(ns_options* o, const ns_options* opt, int order) {
     *o = *opt;
   else
     ns_default_options(o);
-  if (o->form != 0 || o->pow_mode != 0) return NS_ERR_UNSUPPORTED;
+  if (o->form != 0 || o->pow_mode != 0 || o->g0_mode < 0 || o->g0_mode > 1) return NS_ERR_UNSUPPORTED;
   if (o->precision != NS_AUTO && o->precision != NS_BF16 && o->precision != NS_BF16X3) return NS_ERR_UNSUPPORTED;
   if (order != 3 && (order < 2 || order > 64 || (order & (order - 1)) != 0)) return NS_ERR_ARG;
   if (o->timeout_s <= 0) o->timeout_s = 2.0;

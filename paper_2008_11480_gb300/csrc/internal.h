@@ -116,6 +116,8 @@ cudaError_t launch_split_f32(const float* X, int64_t ldx, int rows, int cols, bf
 cudaError_t launch_init_g0_mp(const double* scal, int mode, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,
                               cudaStream_t s);
 cudaError_t launch_init_g0_f64(const double* scal, int mode, int n, int64_t ld, double* G, cudaStream_t s);
+cudaError_t launch_init_g0_jacobi(const double* A, int64_t lda, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,
+                                  double* G64, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
                               cudaStream_t s);
 cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
@@ -129,6 +131,8 @@ cudaError_t launch_prep_a(const double* A, int64_t lda, int n, bf16* hi, bf16* l
 cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, float* T2, int64_t ldt, cudaStream_t s);
 cudaError_t launch_axpy_theta(double* Th, const double* U, int n, int nrhs, float* T1, float* T2, int64_t ldt,
                               cudaStream_t s);
+cudaError_t launch_add_split(float* a32, const float* b32, bf16* hi, bf16* lo, int n, int64_t ld, cudaStream_t s);
+cudaError_t launch_add_f64(double* a, const double* b, int n, int64_t ld, cudaStream_t s);
 // R = B - A theta from the limbs; R (FP64, n x nrhs), R32T (f32, per rhs), partial R^2
 // (resid_x2_blocks(n) blocks x nrhs partials).
 int resid_x2_blocks(int n);

@@ -481,7 +481,83 @@ ns_status mp_residual_F(ns_ctx* ctx, const MpMat& Gm, int prec, bool want32) {
 // Remaining products of one NS step of G = Gin (F already formed): result in Gout.
 // Order 2^m: X_{j+1} = X_j + X_j P_j, P_{j+1} = P_j P_j (or I - A X_{j+1}).
 // Order 3: W = F + F F, G' = G + G W.  Horner (form = 1): X = G + X F, n - 1 times.
+// Appendix Tables t1-t3: the unified form of each order h = 2..19, as (z1, p, w):
+// order h = w (p + 1) by eq. ztab1 (z1 = 0) or h = w (p + 1) + 1 by eq. ztab2
+// (z1 = 1); for h = 10 and 11 the first of the two listed forms.
+struct ToolkitRow {
+  int z1, p, w;
+};
+ToolkitRow toolkit_row(int h) {
+  static const ToolkitRow rows[20] = {
+      {0, 0, 0}, {0, 0, 0}, {0, 1, 1}, {1, 1, 1}, {0, 1, 2}, {1, 1, 2}, {0, 2, 2}, {1, 2, 2}, {0, 3, 2}, {0, 2, 3},
+      {1, 2, 3}, {1, 4, 2}, {0, 3, 3}, {1, 3, 3}, {0, 6, 2}, {0, 2, 5}, {0, 3, 4}, {1, 3, 4}, {0, 5, 3}, {1, 5, 3}};
+  return (h >= 2 && h <= 19) ? rows[h] : ToolkitRow{0, 0, 0};
+}
+
+// The right-form mirror of the unified factorization (Section 4, eqs. xa2-z2,
+// ztab2), F = I - A X already formed:
+//   U = X sum_{d<=p} F^d           (p products, Horner: U_i = X + U_{i-1} F)
+//   E = I - A U  (= F^{p+1})       (1 product)
+//   Z = U sum_{j<w} E^j            (w - 1 products, Horner: Z_j = U + Z_{j-1} E)
+//   z1: X + Z F                    (1 product)
+// so one step costs p + w + 1 (+1) products with F, as eq. np1 counts.
+ns_status mp_chain_toolkit(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int h, int prec) {
+  const ToolkitRow t = toolkit_row(h);
+  if (t.p < 1) return fail(ctx, NS_ERR_ARG, "tool-kit order must be 2..19");
+  const bool u_is_last = !t.z1 && t.w == 1;
+  // U: intermediates in P[0]/P[1], the final U in X[0] (its f32 master is a C term below)
+  const MpMat* Uc = &Gin;
+  for (int i = 1; i <= t.p; ++i) {
+    MpMat* out = i == t.p ? (u_is_last ? &Gout : &ctx->X[0]) : &ctx->P[i & 1];
+    GemmSpec g{Uc, &ctx->F, 1.f, Gin.m32, 1.f, 0.f, out, i == t.p, nullptr};
+    NS_TRY(mp_gemm(ctx, &g, 1, prec));
+    Uc = out;
+  }
+  if (u_is_last) return NS_OK;
+  const MpMat* Zc = Uc;  // Z_0 = U
+  if (t.w > 1) {
+    GemmSpec ge{&ctx->A, Uc, -1.f, nullptr, 0.f, 1.f, &ctx->P[0], false, nullptr};
+    NS_TRY(mp_gemm(ctx, &ge, 1, prec));
+    MpMat* zbuf[2] = {&ctx->X[1], &ctx->P[1]};
+    for (int j = 1; j < t.w; ++j) {
+      const bool last = j == t.w - 1 && !t.z1;
+      MpMat* out = last ? &Gout : zbuf[j & 1];
+      GemmSpec g{Zc, &ctx->P[0], 1.f, Uc->m32, 1.f, 0.f, out, last, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, prec));
+      Zc = out;
+    }
+  }
+  if (!t.z1) return NS_OK;
+  GemmSpec g{Zc, &ctx->F, 1.f, Gin.m32, 1.f, 0.f, &Gout, true, nullptr};
+  return mp_gemm(ctx, &g, 1, prec);
+}
+
+// Nested order 45 in ten products (Section 4, eqs. ex1-ex3), right form, F
+// formed (with its f32 master):
+//   S = F + F F; W3 = X + X S; E3 = I - A W3; T = W3 + W3 E3; W9 = W3 + T E3
+//   E9 = I - A W9; E18 = E9 E9; V = E9 + E18 (elementwise); Q = V + E18 V
+//   Z = W9 + W9 Q = W9 sum_{j<5} E9^j, of order 9 x 5 = 45.
+ns_status mp_chain_nested45(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int prec) {
+  MpMat &F = ctx->F, &X0 = ctx->X[0], &X1 = ctx->X[1], &P0 = ctx->P[0], &P1 = ctx->P[1];
+  GemmSpec s1{&F, &F, 1.f, F.m32, 1.f, 0.f, &P0, false, nullptr};         // S
+  GemmSpec s2{&Gin, &P0, 1.f, Gin.m32, 1.f, 0.f, &X0, true, nullptr};     // W3
+  GemmSpec s3{&ctx->A, &X0, -1.f, nullptr, 0.f, 1.f, &P1, false, nullptr};  // E3
+  GemmSpec s4{&X0, &P1, 1.f, X0.m32, 1.f, 0.f, &P0, false, nullptr};      // T
+  GemmSpec s5{&P0, &P1, 1.f, X0.m32, 1.f, 0.f, &X1, true, nullptr};       // W9
+  GemmSpec s6{&ctx->A, &X1, -1.f, nullptr, 0.f, 1.f, &F, true, nullptr};  // E9
+  GemmSpec s7{&F, &F, 1.f, nullptr, 0.f, 0.f, &X0, true, nullptr};        // E18
+  for (GemmSpec* g : {&s1, &s2, &s3, &s4, &s5, &s6, &s7}) NS_TRY(mp_gemm(ctx, g, 1, prec));
+  NS_CK(launch_add_split(F.m32, X0.m32, F.hi, F.lo, static_cast<int>(ctx->n), ctx->ld, ctx->stream));  // V in F
+  ctx->launches++;
+  GemmSpec s8{&X0, &F, 1.f, F.m32, 1.f, 0.f, &P1, false, nullptr};        // Q
+  GemmSpec s9{&X1, &P1, 1.f, X1.m32, 1.f, 0.f, &Gout, true, nullptr};     // Z
+  NS_TRY(mp_gemm(ctx, &s8, 1, prec));
+  return mp_gemm(ctx, &s9, 1, prec);
+}
+
 ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int prec) {
+  if (ctx->opt.form == 2) return mp_chain_toolkit(ctx, Gin, Gout, order, prec);
+  if (ctx->opt.form == 3) return mp_chain_nested45(ctx, Gin, Gout, prec);
   if (ctx->opt.form == 1) {
     const MpMat* Xc = &Gin;
     for (int j = 0; j < order - 1; ++j) {
@@ -526,7 +602,44 @@ ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int pr
 // ---------------------------------------------------------------- fp64 steps
 ns_status f64_chain(ns_ctx* ctx, const double* Gin, double* Gout, int order) {
   const int n = static_cast<int>(ctx->n);
-  (void)n;
+  if (ctx->opt.form == 2) {  // the same tool-kit chain as mp_chain_toolkit, in FP64
+    const ToolkitRow t = toolkit_row(order);
+    if (t.p < 1) return fail(ctx, NS_ERR_ARG, "tool-kit order must be 2..19");
+    const bool u_is_last = !t.z1 && t.w == 1;
+    const double* Uc = Gin;
+    for (int i = 1; i <= t.p; ++i) {
+      double* out = i == t.p ? (u_is_last ? Gout : ctx->X64[0]) : ctx->P64[i & 1];
+      NS_TRY(f64_gemm(ctx, Uc, ctx->F64, 1.0, Gin, 1.0, 0.0, out, nullptr));
+      Uc = out;
+    }
+    if (u_is_last) return NS_OK;
+    const double* Zc = Uc;
+    if (t.w > 1) {
+      NS_TRY(f64_gemm(ctx, ctx->Astage, Uc, -1.0, nullptr, 0.0, 1.0, ctx->P64[0], nullptr));
+      double* zbuf[2] = {ctx->X64[1], ctx->P64[1]};
+      for (int j = 1; j < t.w; ++j) {
+        double* out = (j == t.w - 1 && !t.z1) ? Gout : zbuf[j & 1];
+        NS_TRY(f64_gemm(ctx, Zc, ctx->P64[0], 1.0, Uc, 1.0, 0.0, out, nullptr));
+        Zc = out;
+      }
+    }
+    if (!t.z1) return NS_OK;
+    return f64_gemm(ctx, Zc, ctx->F64, 1.0, Gin, 1.0, 0.0, Gout, nullptr);
+  }
+  if (ctx->opt.form == 3) {  // nested order 45, as mp_chain_nested45
+    double *F = ctx->F64, *X0 = ctx->X64[0], *X1 = ctx->X64[1], *P0 = ctx->P64[0], *P1 = ctx->P64[1];
+    NS_TRY(f64_gemm(ctx, F, F, 1.0, F, 1.0, 0.0, P0, nullptr));                       // S
+    NS_TRY(f64_gemm(ctx, Gin, P0, 1.0, Gin, 1.0, 0.0, X0, nullptr));                  // W3
+    NS_TRY(f64_gemm(ctx, ctx->Astage, X0, -1.0, nullptr, 0.0, 1.0, P1, nullptr));     // E3
+    NS_TRY(f64_gemm(ctx, X0, P1, 1.0, X0, 1.0, 0.0, P0, nullptr));                    // T
+    NS_TRY(f64_gemm(ctx, P0, P1, 1.0, X0, 1.0, 0.0, X1, nullptr));                    // W9
+    NS_TRY(f64_gemm(ctx, ctx->Astage, X1, -1.0, nullptr, 0.0, 1.0, F, nullptr));      // E9
+    NS_TRY(f64_gemm(ctx, F, F, 1.0, nullptr, 0.0, 0.0, X0, nullptr));                 // E18
+    NS_CK(launch_add_f64(F, X0, n, ctx->ld, ctx->stream));                            // V = E9 + E18
+    ctx->launches++;
+    NS_TRY(f64_gemm(ctx, X0, F, 1.0, F, 1.0, 0.0, P1, nullptr));                      // Q
+    return f64_gemm(ctx, X1, P1, 1.0, X1, 1.0, 0.0, Gout, nullptr);                   // Z
+  }
   if (ctx->opt.form == 1) {
     const double* Xc = Gin;
     for (int j = 0; j < order - 1; ++j) {
@@ -562,8 +675,10 @@ ns_status f64_chain(ns_ctx* ctx, const double* Gin, double* Gout, int order) {
 }
 
 bool order_ok(int order, int form) {
-  if (order < 2) return false;
+  if (order < 2 || form < 0 || form > 3) return false;
   if (form == 1) return true;
+  if (form == 2) return order <= 19;
+  if (form == 3) return order == 45;
   if (order == 3) return true;
   return (order & (order - 1)) == 0;
 }
@@ -573,7 +688,12 @@ bool order_ok(int order, int form) {
 // limbs (or A in FP64) and G once, plus fixed launch and sync overhead.
 int products_per_step(const ns_ctx* ctx) {
   int m = 0;
-  if (ctx->opt.form == 1 || ctx->order == 3) {
+  if (ctx->opt.form == 2) {
+    const ToolkitRow t = toolkit_row(ctx->order);
+    m = t.p + t.w + 1 + t.z1;
+  } else if (ctx->opt.form == 3) {
+    m = 10;
+  } else if (ctx->opt.form == 1 || ctx->order == 3) {
     m = ctx->opt.form == 1 ? ctx->order : 3;
   } else {
     int levels = 0;
@@ -638,12 +758,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
     if (G0)
       NS_CK(launch_copy_f64(G0, n, n, n, ctx->G64[0], ld, s));
+    else if (ctx->opt.g0_mode == 2)
+      NS_CK(launch_init_g0_jacobi(S.A, S.lda, n, ld, nullptr, nullptr, nullptr, ctx->G64[0], s));
     else
       NS_CK(launch_init_g0_f64(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G64[0], s));
     ctx->launches++;
   } else {
     if (G0)
       NS_CK(launch_split_f64(G0, n, n, n, ctx->G[0].hi, ctx->G[0].lo, ctx->G[0].m32, ld, s));
+    else if (ctx->opt.g0_mode == 2)
+      NS_CK(launch_init_g0_jacobi(S.A, S.lda, n, ld, ctx->G[0].m32, ctx->G[0].hi, ctx->G[0].lo, nullptr, s));
     else
       NS_CK(launch_init_g0_mp(ctx->dscal, ctx->opt.g0_mode, n, ld, ctx->G[0].m32, ctx->G[0].hi, ctx->G[0].lo, s));
     ctx->launches += 1;
@@ -710,7 +834,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           NS_CK(cudaMemcpyAsync(tout.lo, tin.lo, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
           continue;
         }
-        NS_TRY(mp_residual_F(ctx, tin, p, m == 3));
+        NS_TRY(mp_residual_F(ctx, tin, p, m == 3 || ctx->opt.form == 1 || ctx->opt.form == 3));
         NS_TRY(mp_chain(ctx, tin, tout, m, p));
       }
     }
@@ -860,7 +984,8 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       if (fp64)
         NS_TRY(f64_gemm(ctx, ctx->Astage, ctx->G64[S.cur], -1.0, nullptr, 0.0, 1.0, ctx->F64, ctx->dscal + 2));
       else
-        NS_TRY(mp_residual_F(ctx, ctx->G[S.cur], prec, ctx->order == 3 || ctx->opt.form == 1));
+        NS_TRY(mp_residual_F(ctx, ctx->G[S.cur], prec,
+                             ctx->order == 3 || ctx->opt.form == 1 || ctx->opt.form == 3));
     }
     NS_TRY(sync_scalars(ctx, S.nrhs));
     if (ns_active && richardson && !rich && std::sqrt(ctx->hscal[2]) <= couple) {
@@ -1075,6 +1200,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.precision != NS_FP64 && o.precision != NS_BF16 && o.precision != NS_BF16X3 && o.precision != NS_AUTO)
     return NS_ERR_ARG;
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
+  if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state

@@ -353,6 +353,29 @@ __global__ void k_init_g0_f64(const double* __restrict__ scal, int mode, int n, 
   }
 }
 
+// Jacobi preconditioner S^{-1} = diag(A)^{-1} (Section 2, S = diag(A)) as G0:
+// the f32 master and bf16 split (mixed path) or FP64.
+__global__ void k_init_g0_jacobi(const double* __restrict__ A, int64_t lda, int n, int64_t ld,
+                                 float* __restrict__ G32, bf16* __restrict__ hi, bf16* __restrict__ lo,
+                                 double* __restrict__ G64) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  const bf16 z = __float2bfloat16_rn(0.f);
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n, c = e % n;
+    const double d = r == c ? 1.0 / A[r * lda + r] : 0.0;
+    if (G64 != nullptr) {
+      G64[r * ld + c] = d;
+    } else {
+      const float f = static_cast<float>(d);
+      const bf16 h = __float2bfloat16_rn(f);
+      G32[r * ld + c] = f;
+      hi[r * ld + c] = r == c ? h : z;
+      lo[r * ld + c] = r == c ? __float2bfloat16_rn(f - __bfloat162float(h)) : z;
+    }
+  }
+}
+
 __global__ void k_f32_to_f64(const float* __restrict__ X, int64_t ldx, int rows, int cols, double* __restrict__ Y,
                              int64_t ldy) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
@@ -516,6 +539,14 @@ cudaError_t launch_init_g0_f64(const double* scal, int mode, int n, int64_t ld, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_g0_jacobi(const double* A, int64_t lda, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,
+                                  double* G64, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_init_g0_jacobi<<<ew_grid(total), 256, 0, s>>>(A, lda, n, ld, G32, hi, lo, G64);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
                               cudaStream_t s) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
@@ -650,6 +681,31 @@ __global__ void k_split_theta(const double* __restrict__ Th, int n, int nrhs, fl
     const float f1 = static_cast<float>(v);
     T1[c * ldt + k] = f1;
     T2[c * ldt + k] = static_cast<float>(v - static_cast<double>(f1));
+  }
+}
+
+// A32 += B32 on n x n (leading dimension ld) and the bf16 hi/lo split of the
+// sum (the elementwise sum of two powers inside the nested order-45 chain).
+__global__ void k_add_split(float* __restrict__ a32, const float* __restrict__ b32, bf16* __restrict__ hi,
+                            bf16* __restrict__ lo, int n, int64_t ld) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = (e / n) * ld + e % n;
+    const float v = a32[o] + b32[o];
+    a32[o] = v;
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[o] = h;
+    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+__global__ void k_add_f64(double* __restrict__ a, const double* __restrict__ b, int n, int64_t ld) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = (e / n) * ld + e % n;
+    a[o] += b[o];
   }
 }
 
@@ -918,6 +974,20 @@ cudaError_t launch_split_theta(const double* Th, int n, int nrhs, float* T1, flo
   const int64_t total = static_cast<int64_t>(n) * nrhs;
   if (total <= 0) return cudaSuccess;
   k_split_theta<<<ew_grid(total), 256, 0, s>>>(Th, n, nrhs, T1, T2, ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_split(float* a32, const float* b32, bf16* hi, bf16* lo, int n, int64_t ld, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_add_split<<<ew_grid(total), 256, 0, s>>>(a32, b32, hi, lo, n, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f64(double* a, const double* b, int n, int64_t ld, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_add_f64<<<ew_grid(total), 256, 0, s>>>(a, b, n, ld);
   return cudaGetLastError();
 }
 

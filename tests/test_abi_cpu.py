@@ -92,6 +92,22 @@ def test_create_rejects_bad_arguments(L, n, order, rates):
     assert s == nsgb.NS_ERR_ARG
 
 
+@pytest.mark.parametrize("form,order", [(2, 1), (2, 20), (3, 44), (3, 9), (4, 4)])
+def test_create_rejects_bad_form_orders(L, form, order):
+    opt = nsgb.default_options(form=form)
+    h = ctypes.c_void_p()
+    assert L.ns_create(64, order, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+
+
+def test_create_rejects_bad_g0_mode_and_accel(L):
+    h = ctypes.c_void_p()
+    opt = nsgb.default_options(g0_mode=3)
+    assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+    opt = nsgb.default_options(accel_richardson=1, aux_ahead=1)
+    arr = (ctypes.c_int * 1)(2)
+    assert L.ns_create(64, 4, arr, 1, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
+
+
 def test_create_rejects_bad_precision(L):
     opt = nsgb.default_options(precision=7)
     h = ctypes.c_void_p()

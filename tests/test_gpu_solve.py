@@ -89,6 +89,83 @@ def test_fp64_user_g0_noncommuting():
     assert rel(G.cpu().numpy(), ref) <= 1e-12
 
 
+def diag_dominant(n, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(-1, 1, (n, n))
+    M = 0.5 * (M + M.T)
+    np.fill_diagonal(M, 0)
+    return M + np.diag(np.abs(M).sum(1) + rng.uniform(0.5, 3, n))
+
+
+def test_fp64_jacobi_g0_mode():
+    """g0_mode = 2: the library forms the Jacobi preconditioner S^{-1} =
+    diag(A)^{-1} itself (Section 2); iterates equal the oracle's from the same G0."""
+    n = 72
+    A = diag_dominant(n, 8)
+    B = np.random.default_rng(9).standard_normal((n, 2))
+    G0 = O.jacobi_preconditioner(A)
+    ref = O.ns_richardson_solve(A, B, order=4, ns_iters=4, G0=G0)
+    with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=0, g0_mode=2) as ctx:
+        r = ctx.solve(tens(A), tens(B), iters=4, tol=0.0)
+        G, _ = ctx.invert(tens(A), iters=4)
+    assert rel(r.theta.cpu().numpy(), ref.theta) <= 1e-12
+    assert rel(G.cpu().numpy(), ref.G) <= 1e-12
+
+
+def test_mixed_jacobi_g0_mode_reaches_tolerance():
+    n = 300
+    A = diag_dominant(n, 10)
+    B = np.random.default_rng(11).standard_normal((n, 3))
+    with nsgb.Context(n, order=4, g0_mode=2) as ctx:
+        r = ctx.solve(tens(A), tens(B), iters=40, tol=1e-10)
+    assert r.status == nsgb.NS_OK
+    assert float(np.max(O.rel_residual(A, r.theta.cpu().numpy(), B))) <= 1e-10
+
+
+@pytest.mark.parametrize("h", list(range(2, 20)))
+def test_fp64_toolkit_orders_match_oracle(h):
+    """form = 2: the Appendix tool-kit row for order h (Tables t1-t3) as the
+    NS step; iterates equal the oracle's tool-kit series {sum_{j<h} Y^j} X and
+    each step costs the row's mmm count (eq. np1, +1 for eq. ztab2)."""
+    n = 48
+    p = make_spd(n, 30.0, nrhs=1, seed=40 + h)
+    K = 2
+    ref = O.alpha_frobenius(p.A) * np.eye(n)
+    cnt = O.MMCount()
+    for _ in range(K):
+        ref = O.toolkit(ref, p.A, h, cnt)
+    with nsgb.Context(n, order=h, precision=nsgb.NS_FP64, ns_stop=0, form=2) as ctx:
+        G, st = ctx.invert(tens(p.A), iters=K)
+    assert rel(G.cpu().numpy(), ref) <= 1e-12
+    assert st.gemm_launches == cnt.n
+
+
+def test_fp64_nested_order45_matches_oracle():
+    n = 48
+    p = make_spd(n, 200.0, nrhs=1, seed=45)
+    ref = O.alpha_frobenius(p.A) * np.eye(n)
+    cnt = O.MMCount()
+    for _ in range(2):
+        ref = O.nested_order45(ref, p.A, cnt)
+    with nsgb.Context(n, order=45, precision=nsgb.NS_FP64, ns_stop=0, form=3) as ctx:
+        G, st = ctx.invert(tens(p.A), iters=2)
+    assert rel(G.cpu().numpy(), ref) <= 1e-12
+    assert st.gemm_launches == cnt.n == 20
+    # error model: I - G_2 A = F_0^{45^2}
+    a = O.alpha_frobenius(p.A)
+    F = (p.Q * (1 - a * p.lam) ** (45 ** 2)) @ p.Q.T
+    assert np.linalg.norm(np.eye(n) - G.cpu().numpy() @ p.A - F) <= 1e-10
+
+
+@pytest.mark.parametrize("form,order", [(2, 5), (2, 7), (2, 12), (2, 19), (3, 45)])
+def test_mixed_toolkit_forms_reach_tolerance(form, order):
+    p = make_spd(256, 1e3, nrhs=2, seed=50 + order)
+    with nsgb.Context(256, order=order, form=form) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=40, tol=1e-10)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10
+
+
 @pytest.mark.parametrize("n_order,rates", [(2, [2]), (2, [2, 3]), (3, [2])])
 def test_fp64_composite_matches_oracle(n_order, rates):
     n = 80
