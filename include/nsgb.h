@@ -97,6 +97,9 @@ typedef struct ns_options {
                           Theta0 is given.  Needs rates = {order} and aux_ahead = 1 (the
                           double NS method); ns_create returns NS_ERR_ARG otherwise.  omega_k r
                           is applied as u = X_k r, u += L_k (r - A u) without forming omega_k. */
+  int g0_order;         /* 0 or 1: G0 = S^{-1} (g0_mode); h = 2..19: the initial series of Section 3
+                          (eq. g01), G0 = {sum_{j<h} (S^{-1}D)^j} S^{-1}, by one tool-kit step of
+                          order h from S^{-1} (bf16x3 products on the mixed path) */
 } ns_options;
 
 #define NS_MAX_HIST 256

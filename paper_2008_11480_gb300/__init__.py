@@ -64,6 +64,7 @@ class ns_options(ctypes.Structure):
         ("gemm_cluster", ctypes.c_int),
         ("couple_frob", ctypes.c_double),
         ("accel_richardson", ctypes.c_int),
+        ("g0_order", ctypes.c_int),
     ]
 
 

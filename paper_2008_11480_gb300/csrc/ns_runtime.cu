@@ -782,17 +782,38 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   }
   S.cur = 0;
 
+  // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
+  // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
+  // S^{-1} (F = I - A S^{-1} mirrors S^{-1} D)
+  if (ctx->opt.g0_order >= 2) {
+    const int saved_form = ctx->opt.form;
+    ctx->opt.form = 2;
+    ns_status r0;
+    if (fp64) {
+      r0 = f64_gemm(ctx, ctx->Astage, ctx->G64[0], -1.0, nullptr, 0.0, 1.0, ctx->F64, nullptr);
+      if (r0 == NS_OK) r0 = f64_chain(ctx, ctx->G64[0], ctx->G64[1], ctx->opt.g0_order);
+    } else {
+      const int p0 = ctx->opt.precision == NS_AUTO ? NS_BF16X3 : ctx->opt.precision;
+      r0 = mp_residual_F(ctx, ctx->G[0], p0, false);
+      if (r0 == NS_OK) r0 = mp_chain(ctx, ctx->G[0], ctx->G[1], ctx->opt.g0_order, p0);
+    }
+    ctx->opt.form = saved_form;
+    NS_TRY(r0);
+    S.cur = 1;
+  }
+
   // composite: auxiliary expansions T_i start at G0 (or one NS step ahead)
   if (comp) {
     const size_t w = ctx->rates.size();
     for (size_t i = 0; i < w; ++i) {
       if (fp64) {
-        NS_CK(cudaMemcpyAsync(ctx->T64[0][i], ctx->G64[0], sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(ctx->T64[0][i], ctx->G64[S.cur], sizeof(double) * n * ld, cudaMemcpyDeviceToDevice,
+                              s));
       } else {
         MpMat& t = ctx->T[0][i];
-        NS_CK(cudaMemcpyAsync(t.m32, ctx->G[0].m32, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
-        NS_CK(cudaMemcpyAsync(t.hi, ctx->G[0].hi, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
-        NS_CK(cudaMemcpyAsync(t.lo, ctx->G[0].lo, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(t.m32, ctx->G[S.cur].m32, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(t.hi, ctx->G[S.cur].hi, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
+        NS_CK(cudaMemcpyAsync(t.lo, ctx->G[S.cur].lo, sizeof(bf16) * n * ld, cudaMemcpyDeviceToDevice, s));
       }
     }
     S.ccur = 0;
@@ -1172,6 +1193,7 @@ void ns_default_options(ns_options* o) {
   o->gemm_cluster = 0;
   o->couple_frob = 0.0;
   o->accel_richardson = 0;
+  o->g0_order = 0;
 }
 
 const char* ns_status_string(ns_status s) {
@@ -1201,6 +1223,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
     return NS_ERR_ARG;
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
+  if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state

@@ -112,6 +112,24 @@ def test_fp64_jacobi_g0_mode():
     assert rel(G.cpu().numpy(), ref.G) <= 1e-12
 
 
+@pytest.mark.parametrize("h", [4, 6, 9])
+def test_fp64_initial_series_g0(h):
+    """g0_order = h: G0 is the initial series of eq. g01 from the Jacobi
+    S^{-1} (Section 3), G0 = {sum_{j<h} (S^{-1}D)^j} S^{-1}, built by one
+    tool-kit step; it equals the oracle's initial_series (unified form with
+    the table's (p, w)) and then the iterates follow."""
+    n = 64
+    A = diag_dominant(n, 12)
+    Sinv = O.jacobi_preconditioner(A)
+    _, p, w = O.TOOLKIT_TABLE[h]
+    G0, F0 = O.initial_series(A, Sinv, p, w)
+    assert np.allclose(F0, np.linalg.matrix_power(np.eye(n) - Sinv @ A, h), atol=1e-12)
+    ref, _ = O.ns_invert(A, G0=G0, order=4, iters=2)
+    with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, ns_stop=0, g0_mode=2, g0_order=h) as ctx:
+        G, _ = ctx.invert(tens(A), iters=2)
+    assert rel(G.cpu().numpy(), ref) <= 1e-12
+
+
 def test_mixed_jacobi_g0_mode_reaches_tolerance():
     n = 300
     A = diag_dominant(n, 10)
