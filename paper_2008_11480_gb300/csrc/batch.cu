@@ -61,6 +61,8 @@ struct InstState {
   double last_rr_sweep = INFINITY;  // residual of the previous Richardson-only pass
   int stall = 0;                    // consecutive Richardson-only passes with < 5 % progress
   double prev_sweep_ratio = INFINITY;  // previous contraction ratio of the Richardson-only phase
+  double proj_need = 0.0;  // sweeps still needed after the last measured residual (projection)
+  int k_meas = 1;          // sweeps applied between the previous measured residual and this one
   int status = NS_OK;
   int sweeps = 0;
   int rollbacks = 0;
@@ -152,6 +154,8 @@ struct ns_batch {
   ns_batch_stats* stats = nullptr;
   double wait_ms = 0.0;  // host time blocked in the per-pass stream synchronisation
   int fixed_count = 0;  // systems of a fixed batch (slots 0 .. fixed_count - 1)
+  int max_pre = 0;      // extra Richardson-only sweeps per pass (fixed batches: fewer syncs;
+                        // the server keeps ticks short for latency)
 };
 
 namespace {
@@ -525,17 +529,21 @@ void decide(ns_batch* b, int i) {
     // this precision) instead of spending the whole sweep budget
     const double prev = s.last_rr_sweep;
     s.last_rr_sweep = rr;
-    if (std::isfinite(prev)) s.stall = rr > 0.95 * prev ? s.stall + 1 : 0;
+    // contraction per sweep over the k_meas sweeps since the previous measurement
+    const double ratio = (std::isfinite(prev) && prev > 0.0) ? std::pow(rr / prev, 1.0 / s.k_meas) : INFINITY;
+    if (std::isfinite(prev)) s.stall = ratio > 0.95 ? s.stall + 1 : 0;
     s.best_rr = std::min(s.best_rr, rr);
     bool stop = s.stall >= 4 || rr > 10.0 * s.best_rr;
     // ... or when even the better of the last two contraction ratios cannot
     // reach tol within the sweeps left (an optimistic projection)
-    if (std::isfinite(prev) && prev > 0.0) {
-      const double ratio = rr / prev;
+    s.proj_need = 0.0;
+    if (std::isfinite(ratio)) {
       const double rho = std::min(ratio, s.prev_sweep_ratio);
       s.prev_sweep_ratio = ratio;
-      if (tol > 0 && rho < 1.0 && std::log(tol / rr) / std::log(rho) > static_cast<double>(s.sweeps_left))
-        stop = true;
+      if (tol > 0 && rho < 1.0) {
+        s.proj_need = std::log(tol / rr) / std::log(rho);
+        if (s.proj_need > static_cast<double>(s.sweeps_left)) stop = true;
+      }
     }
     if (stop) {
       s.finished = true;
@@ -623,6 +631,36 @@ ns_status prep_slots(ns_batch* b, const std::vector<int>& ids, const std::vector
 ns_status pass(ns_batch* b, const std::vector<int>& act) {
   const double couple = b->opt.couple_frob;
   std::vector<int> nsact, rich;
+  // Richardson-only systems far from tol take extra sweeps before this pass's
+  // measured residual: at most half of the (optimistic) projected remainder, so
+  // no system is swept past the sweep where it would have met tol
+  std::vector<int> pre(b->cap, 0);
+  int max_pre = 0;
+  for (int i : act) {
+    InstState& s = b->st[i];
+    s.k_meas = 1;
+    if (s.ns_active || s.proj_need < 3.0) continue;
+    int k = static_cast<int>((s.proj_need - 1.0) / 2.0);
+    k = std::min(std::min(k, b->max_pre), s.sweeps_left - 1);
+    if (k < 1) continue;
+    pre[i] = k;
+    max_pre = std::max(max_pre, k);
+  }
+  for (int j = 0; j < max_pre; ++j) {
+    std::vector<int> sw;
+    for (int i : act)
+      if (pre[i] > j) sw.push_back(i);
+    B_TRY(run_rows(b, row_items(b, sw, true),
+                   [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+    B_TRY(run_rows(b, row_items(b, sw, true),
+                   [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
+    for (int i : sw) {
+      InstState& s = b->st[i];
+      s.sweeps++;
+      s.sweeps_left--;
+      s.k_meas++;
+    }
+  }
   for (int i : act) {
     InstState& s = b->st[i];
     if (s.ns_active) nsact.push_back(i);
@@ -885,6 +923,7 @@ ns_status ns_batch_create(int count, const int64_t* n, const int* nrhs, int orde
     }
   }
   b->fixed_count = count;
+  b->max_pre = 7;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
     release_batch(b);
     return NS_ERR_CUDA;
