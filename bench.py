@@ -359,7 +359,7 @@ def run_batched(a):
     sampler = ClockSampler(0)
     torch.cuda.synchronize()
     sampler.start()
-    ms, conv, gflops, gms = [], [], 0.0, 0.0
+    ms, conv, gflops, gms, gbytes = [], [], 0.0, 0.0, 0.0
     for _ in range(a.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -371,6 +371,7 @@ def run_batched(a):
         conv.append(st.converged)
         gflops += st.gemm_flops
         gms += st.gemm_ms
+        gbytes += st.gemm_bytes
     clocks = sampler.stop()
     import oracle as O
     worst = 0.0
@@ -379,6 +380,7 @@ def run_batched(a):
             worst = max(worst, float(np.max(O.rel_residual(p.A, t.cpu().numpy(), p.B))))
     pk, pk_kind = peaks()
     ach = gflops / (gms / 1e3) / 1e12 if gms > 0 else None
+    hbm_gbs = gbytes / (gms / 1e3) / 1e9 if gms > 0 else None
     value = statistics.mean(conv) / (statistics.mean(ms) / 1e3)
     print(json.dumps({
         "metric": METRIC + " (batched harmonic-regressor systems)", "value": value, "unit": UNIT,
@@ -392,9 +394,13 @@ def run_batched(a):
         "worst_verified_rel_res_of_converged": worst, "passes": st.passes,
         "gemm_launches_per_step": st.gemm_launches, "kernel_launches_per_step": st.kernel_launches,
         "gpu_launches": int(st.kernel_launches) * a.steps,
-        "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                     "frac": ach / pk["bf16_tflops_sustained"] if ach else None, "traffic": None,
-                     "note": "executed (tile-padded) product flops of the list-driven launches / their event time"},
+        "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": hbm_gbs / pk["hbm_gbs"] if hbm_gbs else None, "traffic": None,
+                     "note": "list-driven product launches: algorithmic bytes (operands once, C term, f32 and "
+                             "bf16 outputs) / their event time; tiles of K <= 256 have ~30 flop/B, below the "
+                             f"bf16 ridge, so HBM bounds them ({pk_kind} copy peak)",
+                     "tensor_tflops": ach, "tensor_frac_of_sustained": ach / pk["bf16_tflops_sustained"] if ach
+                     else None},
         "useful_flops_per_product_level": st.useful_flops_per_product, "clocks": clocks}), flush=True)
     bt.close()
 

@@ -200,6 +200,8 @@ typedef struct ns_batch_stats {
   double gemm_ms;                   /* summed product-launch durations (opt.profile = 1) */
   double useful_flops_per_product;  /* sum over instances of 2 n_i^3 */
   double wall_ms;
+  double gemm_bytes;                /* algorithmic HBM bytes of the products: operands once
+                                       (hi, or hi and lo), C term, outputs */
 } ns_batch_stats;
 
 /* Create a batch of `count` systems; n[i] in [1, 16384], nrhs[i] in [1, 1024].

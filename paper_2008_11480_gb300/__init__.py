@@ -111,6 +111,7 @@ class ns_batch_stats(ctypes.Structure):
         ("gemm_ms", ctypes.c_double),
         ("useful_flops_per_product", ctypes.c_double),
         ("wall_ms", ctypes.c_double),
+        ("gemm_bytes", ctypes.c_double),
     ]
 
 

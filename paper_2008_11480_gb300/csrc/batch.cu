@@ -374,11 +374,28 @@ ns_status publish_slot(ns_batch* b, int i, bool problems) {
   return NS_OK;
 }
 
+// Algorithmic HBM bytes of one product of system i (type t): its operands once
+// (hi only for a bf16 pass, hi and lo for bf16x3), the C term, and the outputs
+// (f32 master where kept, bf16 hi and lo) -- the flags of make_problem.
+double product_bytes(const ns_batch* b, int i, int t, int x3) {
+  const double e = static_cast<double>(b->n[i]) * b->n[i];
+  bool c = false, d32 = false;
+  if (t == 0) {
+    d32 = b->levels == 0;
+  } else if (b->levels == 0) {
+    c = true;
+    d32 = t == 2;
+  } else {
+    c = d32 = (t - 1) % 2 == 0;
+  }
+  return e * (2.0 * (x3 ? 4.0 : 2.0) + (c ? 4.0 : 0.0) + (d32 ? 4.0 : 0.0) + 4.0);
+}
+
 ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::vector<int>& types) {
   for (int bnv : {128, 256}) {
     for (int x3 = 0; x3 < 2; ++x3) {
       std::vector<TcItem> items;
-      double flops = 0.0;
+      double flops = 0.0, bytes = 0.0;
       for (int i : ids) {
         if (b->bn[i] != bnv || (b->st[i].prec == NS_BF16X3) != (x3 == 1)) continue;
         for (int t : types) {
@@ -386,6 +403,7 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
           for (int mt = 0; mt < b->tiles_m[i]; ++mt)
             for (int nt = 0; nt < b->tiles_n[i]; ++nt) items.push_back(TcItem{pi, mt, nt, 0});
           flops += 2.0 * b->n[i] * static_cast<double>(b->n[i]) * b->n[i] * (x3 ? 3 : 1);
+          bytes += product_bytes(b, i, t, x3);
         }
       }
       if (items.empty()) continue;
@@ -412,6 +430,7 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
         b->stats->gemm_launches++;
         b->stats->kernel_launches++;
         b->stats->gemm_flops += flops;
+        b->stats->gemm_bytes += bytes;
       }
       if (b->opt.profile) {
         cudaEventRecord(e1, b->pstream);

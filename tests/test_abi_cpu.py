@@ -41,8 +41,8 @@ int main(void) {
          offsetof(ns_options, timeout_s), offsetof(ns_options, aux_ahead), sizeof(ns_stats));
   printf("%zu %zu %zu %zu\n", offsetof(ns_stats, frob_F), offsetof(ns_stats, rel_res_hist),
          offsetof(ns_stats, gemm_launches), offsetof(ns_stats, wall_ms));
-  printf("%zu %zu %zu\n", sizeof(ns_batch_stats), offsetof(ns_batch_stats, gemm_launches),
-         offsetof(ns_batch_stats, wall_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(ns_batch_stats), offsetof(ns_batch_stats, gemm_launches),
+         offsetof(ns_batch_stats, wall_ms), offsetof(ns_batch_stats, gemm_bytes));
   printf("%zu %zu %zu %zu\n", sizeof(ns_request), offsetof(ns_request, tol), offsetof(ns_request, A),
          offsetof(ns_request, Theta));
   printf("%zu %zu %zu\n", sizeof(ns_result), offsetof(ns_result, rel_res), offsetof(ns_result, latency_ms));
@@ -62,7 +62,7 @@ int main(void) {
     BS, Q, R, SS = nsgb.ns_batch_stats, nsgb.ns_request, nsgb.ns_result, nsgb.ns_server_stats
     want = [ctypes.sizeof(O), O.ns_stop_frob.offset, O.timeout_s.offset, O.aux_ahead.offset, ctypes.sizeof(S),
             S.frob_F.offset, S.rel_res_hist.offset, S.gemm_launches.offset, S.wall_ms.offset,
-            ctypes.sizeof(BS), BS.gemm_launches.offset, BS.wall_ms.offset,
+            ctypes.sizeof(BS), BS.gemm_launches.offset, BS.wall_ms.offset, BS.gemm_bytes.offset,
             ctypes.sizeof(Q), Q.tol.offset, Q.A.offset, Q.Theta.offset,
             ctypes.sizeof(R), R.rel_res.offset, R.latency_ms.offset,
             ctypes.sizeof(SS), SS.active.offset, SS.last_error.offset, SS.wait_ms.offset]
