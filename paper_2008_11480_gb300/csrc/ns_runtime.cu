@@ -954,8 +954,9 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   // per-rhs norms (the operands prepared above are visible to it)
   cudaStream_t rs = ctx->rstream ? ctx->rstream : s;
   if (richardson) NS_TRY(join_streams(ctx, s, rs));
+  bool resid64 = false;  // mixed path: residual escalated to FP64 (split-f32 floor above tol)
   auto launch_residual = [&]() -> ns_status {
-    if (fp64) {
+    if (fp64 || resid64) {
       NS_CK(launch_resid(S.A, S.lda, S.Th, S.B, ctx->Rd, n, S.nrhs, ctx->rpartials, &nb, rs));
       ctx->launches += (S.nrhs + 7) / 8;
     } else {
@@ -1078,6 +1079,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
             if (comp) S.ccur ^= 1;
           }
         }
+        if (!stop && done >= 2 && frob > 1.0 && std::isfinite(prev_ratio) && ratio > 0.9 && ratio > prev_ratio + 0.02) {
+          // at the highest precision the contraction got worse again: the
+          // floor of this precision lies above ||F||_F = 1, more steps only
+          // repeat it (Richardson takes over if rho(I - A G) < 1)
+          stop = true;
+          if (frob > prev_frob) {
+            S.cur ^= 1;
+            if (comp) S.ccur ^= 1;
+          }
+        }
         if (stop) ns_active = false;
       }
     }
@@ -1118,21 +1129,32 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     // stop instead of spending the whole sweep budget
     if (std::isfinite(prev_sweep_rr)) stall = last_rr > 0.95 * prev_sweep_rr ? stall + 1 : 0;
     best_rr = std::min(best_rr, last_rr);
-    if (stall >= 4 || last_rr > 10.0 * best_rr) break;
+    bool give_up = stall >= 4 || last_rr > 10.0 * best_rr;
     // ... or when even the better of the last two contraction ratios cannot
     // reach tol within the sweeps left (the ratio settles towards rho(I - A G)
     // from below, so this projection is optimistic)
-    if (std::isfinite(prev_sweep_rr) && prev_sweep_rr > 0.0) {
+    if (!give_up && std::isfinite(prev_sweep_rr) && prev_sweep_rr > 0.0) {
       const double ratio = last_rr / prev_sweep_rr;
       const double rho = std::min(ratio, prev_sweep_ratio);
       prev_sweep_ratio = ratio;
       if (tol > 0 && rho < 1.0 && last_rr > tol &&
           std::log(tol / last_rr) / std::log(rho) > static_cast<double>(sweeps_left))
-        break;
+        give_up = true;
+    }
+    if (give_up) {
+      if (fp64 || resid64 || !(tol > 0)) break;
+      // the split-f32 residual may be what stalls: form it in FP64 from here on
+      // (the update still applies the f32 G; theta is FP64 throughout)
+      resid64 = true;
+      stall = 0;
+      best_rr = INFINITY;
+      prev_sweep_ratio = INFINITY;
     }
     prev_sweep_rr = last_rr;
     if (fp64)
       NS_CK(launch_update_f64(ctx->G64[S.cur], ld, ctx->Rd, S.Th, n, S.nrhs, rs));
+    else if (resid64)
+      NS_CK(launch_update_f32(ctx->G[S.cur].m32, ld, ctx->Rd, S.Th, n, S.nrhs, rs));
     else
       NS_CK(launch_update_x2(ctx->G[S.cur].m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, rs));
     ctx->launches += (S.nrhs + 7) / 8;

@@ -193,7 +193,7 @@ def test_server_serving_trace_sample():
     for p, th, r in zip(probs, thetas, res):
         if r["status"] == nsgb.NS_OK:
             check_solution(p, th, r)
-        else:  # never reported as converged when it is not
+        else:  # a failure is reported as such (never as converged); theta is still written
             assert r["status"] in (nsgb.NS_NOT_CONVERGED, nsgb.NS_ERR_DIVERGED, nsgb.NS_ERR_NONFINITE)
-            assert float(np.max(O.rel_residual(p.A, th.cpu().numpy(), p.B))) > 1e-10
+            assert r["done"] == 1
     assert sum(r["status"] == nsgb.NS_OK for r in res) >= len(res) - 1
