@@ -63,6 +63,7 @@ struct InstState {
   double prev_sweep_ratio = INFINITY;  // previous contraction ratio of the Richardson-only phase
   double proj_need = 0.0;  // sweeps still needed after the last measured residual (projection)
   int k_meas = 1;          // sweeps applied between the previous measured residual and this one
+  bool resid64 = false;    // residual escalated to FP64 (the split-f32 one stalled above tol)
   int status = NS_OK;
   int sweeps = 0;
   int rollbacks = 0;
@@ -446,6 +447,21 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
   return NS_OK;
 }
 
+std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids, bool with_rhs);
+template <typename F>
+ns_status run_rows(ns_batch* b, const std::vector<BItem>& items, F launch);
+
+// Residuals of the systems in `ids`: split-f32 for most, FP64 for those escalated.
+ns_status launch_residuals(ns_batch* b, const std::vector<int>& ids) {
+  std::vector<int> x2, f64;
+  for (int i : ids) (b->st[i].resid64 ? f64 : x2).push_back(i);
+  B_TRY(run_rows(b, row_items(b, x2, true),
+                 [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+  B_TRY(run_rows(b, row_items(b, f64, true),
+                 [&](const BItem* d, int k) { return launch_bresid64(b->dinst, d, k, b->stream); }));
+  return NS_OK;
+}
+
 std::vector<BItem> row_items(const ns_batch* b, const std::vector<int>& ids, bool with_rhs) {
   std::vector<BItem> it;
   for (int i : ids) {
@@ -564,6 +580,15 @@ void decide(ns_batch* b, int i) {
         if (s.proj_need > static_cast<double>(s.sweeps_left)) stop = true;
       }
     }
+    if (stop && !s.resid64 && tol > 0 && s.sweeps_left > 0) {
+      // the split-f32 residual may be what stalls: form it in FP64 from here on
+      s.resid64 = true;
+      s.stall = 0;
+      s.best_rr = INFINITY;
+      s.prev_sweep_ratio = INFINITY;
+      s.proj_need = 0.0;
+      stop = false;
+    }
     if (stop) {
       s.finished = true;
       s.status = NS_NOT_CONVERGED;
@@ -669,8 +694,7 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
     std::vector<int> sw;
     for (int i : act)
       if (pre[i] > j) sw.push_back(i);
-    B_TRY(run_rows(b, row_items(b, sw, true),
-                   [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+    B_TRY(launch_residuals(b, sw));
     B_TRY(run_rows(b, row_items(b, sw, true),
                    [&](const BItem* d, int k) { return launch_bupdate(b->dinst, d, k, b->stream); }));
     for (int i : sw) {
@@ -690,8 +714,7 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
     B_TRY(launch_products(b, nsact, {0}));
     B_TRY(run_list(b, nsact, launch_bfrob, b->pstream));
   }
-  B_TRY(run_rows(b, row_items(b, rich, true),
-                 [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+  B_TRY(launch_residuals(b, rich));
   B_TRY(run_list(b, rich, launch_brsq, b->stream));
   B_TRY(sync_read(b));
   for (int i : act) decide(b, i);
@@ -717,8 +740,7 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
       B_TRY(run_list(b, redo, launch_bfrob, b->pstream));
     }
     if (!late.empty()) {
-      B_TRY(run_rows(b, row_items(b, late, true),
-                     [&](const BItem* d, int k) { return launch_bresid(b->dinst, d, k, b->stream); }));
+      B_TRY(launch_residuals(b, late));
       B_TRY(run_list(b, late, launch_brsq, b->stream));
     }
     B_TRY(sync_read(b));

@@ -44,6 +44,7 @@ cudaError_t launch_bnorms(const BInst* insts, const int* list, int ninst, cudaSt
 cudaError_t launch_bg0(const BInst* insts, const BItem* items, int nitems, int mode, int zero_theta,
                        cudaStream_t s);
 cudaError_t launch_bresid(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
+cudaError_t launch_bresid64(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
 cudaError_t launch_brsq(const BInst* insts, const int* list, int ninst, cudaStream_t s);
 cudaError_t launch_bupdate(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
 cudaError_t launch_bfrob(const BInst* insts, const int* list, int ninst, cudaStream_t s);

@@ -272,6 +272,57 @@ __global__ void __launch_bounds__(256, 2) k_bresid(const BInst* __restrict__ ins
   }
 }
 
+// FP64 residual for systems whose split-f32 residual stalled above tol:
+// R = B - A Theta from the caller's FP64 A and the FP64 theta, one warp per row
+// (lanes stride k, fixed-order shuffle reduction), 8 rows x kBRhs RHS per
+// block; also R32T (the update's operand) and the block's sums of R^2.
+__global__ void __launch_bounds__(256) k_bresid64(const BInst* __restrict__ insts, const BItem* __restrict__ items) {
+  constexpr int NR = kBRhs;
+  __shared__ double sq[kRows][NR];
+  const BItem it = items[blockIdx.x];
+  const BInst& I = insts[it.inst];
+  const int n = I.n, nrhs = I.nrhs, c0 = it.c0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = it.row0 + warp;
+  double acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+  if (row < n) {
+    const double* a = I.A + static_cast<int64_t>(row) * n;
+    for (int k = lane; k < n; k += 32) {
+      const double av = a[k];
+      const double* t = I.Th + static_cast<int64_t>(k) * nrhs + c0;
+#pragma unroll
+      for (int c = 0; c < NR; ++c)
+        if (c0 + c < nrhs) acc[c] = fma(av, t[c], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = warp_sum_f64(acc[c]);
+  if (lane < NR) {
+    const int c = lane;
+    double v2 = 0.0;
+    if (row < n && c0 + c < nrhs) {
+      double dot = 0.0;
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        if (j == c) dot = acc[j];
+      const int64_t o = static_cast<int64_t>(row) * nrhs + c0 + c;
+      const double v = I.B[o] - dot;
+      I.R[o] = v;
+      I.R32T[static_cast<int64_t>(c0 + c) * I.ld + row] = static_cast<float>(v);
+      v2 = v * v;
+    }
+    sq[warp][c] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x < NR && c0 + static_cast<int>(threadIdx.x) < nrhs) {
+    double t = 0.0;
+    for (int w = 0; w < kRows; ++w) t += sq[w][threadIdx.x];
+    I.part[static_cast<int64_t>(it.row0 / kRows) * nrhs + c0 + threadIdx.x] = t;
+  }
+}
+
 // Per instance: ||r_c||^2 from the residual's row-block partials (fixed order).
 __global__ void __launch_bounds__(256) k_brsq(const BInst* __restrict__ insts, const int* __restrict__ list) {
   const BInst& I = insts[list[blockIdx.x]];
@@ -395,6 +446,11 @@ cudaError_t launch_bg0(const BInst* insts, const BItem* items, int nitems, int m
 cudaError_t launch_bresid(const BInst* insts, const BItem* items, int nitems, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   k_bresid<<<nitems, 256, 0, s>>>(insts, items);
+  return cudaGetLastError();
+}
+cudaError_t launch_bresid64(const BInst* insts, const BItem* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  k_bresid64<<<nitems, 256, 0, s>>>(insts, items);
   return cudaGetLastError();
 }
 cudaError_t launch_brsq(const BInst* insts, const int* list, int ninst, cudaStream_t s) {
