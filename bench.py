@@ -513,6 +513,120 @@ def run_serving(a):
     srv.close()
 
 
+def run_orders(a):
+    """Order / form comparison on the n = 4096, kappa = 1e4, 4-RHS system (the
+    paper's cost analysis: mmm per step against the order reached): factorized
+    orders 2, 3, 4, 8, 16, tool-kit orders 5, 7, 12, nested order 45, composite
+    rates {2} and {2, 3}, double NS, accelerated Richardson.  Each entry: solves/s
+    (device time, median of a.steps solves), NS steps, sweeps, products per solve.
+    value = the best entry's solves/s."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_spd
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = make_spd(a.n, a.kappa, nrhs=a.nrhs, seed=1)
+    A = torch.from_numpy(p.A).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    out = torch.empty_like(B)
+    variants = [("factorized order 2", 2, (), {}), ("order 3", 3, (), {}), ("factorized order 4", 4, (), {}),
+                ("factorized order 8", 8, (), {}), ("factorized order 16", 16, (), {}),
+                ("tool-kit order 5", 5, (), {"form": 2}), ("tool-kit order 7", 7, (), {"form": 2}),
+                ("tool-kit order 12", 12, (), {"form": 2}), ("nested order 45", 45, (), {"form": 3}),
+                ("composite order 2, rates {2}", 2, (2,), {}), ("composite order 2, rates {2,3}", 2, (2, 3), {}),
+                ("double NS order 4", 4, (4,), {"aux_ahead": 1}),
+                ("accelerated Richardson, double NS order 4", 4, (4,), {"aux_ahead": 1, "accel_richardson": 1})]
+    table = []
+    for name, order, rates, kw in variants:
+        ctx = nsgb.Context(a.n, order=order, rates=rates, stream=stream, couple_frob=a.couple, **kw)
+        for _ in range(2):
+            r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+        ms = []
+        for _ in range(max(3, a.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ctx.close()
+        med = statistics.median(ms)
+        table.append({"variant": name, "status": r.status, "solves_per_s": 1e3 / med, "ms": med,
+                      "ns_iters": r.stats.ns_iters, "sweeps": r.stats.sweeps,
+                      "products": int(r.stats.gemm_launches), "rel_res": r.stats.rel_res})
+    best = max((t for t in table if t["status"] == 0), key=lambda t: t["solves_per_s"])
+    print(json.dumps({
+        "metric": METRIC + " (order and form comparison)", "value": best["solves_per_s"], "unit": UNIT,
+        "n_gpus": 1, "steps": max(3, a.steps), "warmup": 2, "ms_per_step": best["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": dict(workload_config(a), order="per variant"), "best": best["variant"], "variants": table}),
+        flush=True)
+
+
+def run_small(a):
+    """Configuration 1: n = 64, lambda log-uniform in [1, 100], one RHS, order 4,
+    G0 = I/||A||_F, 8 coupled iterations in FP64 (the plain path; the oracle's
+    parity case) and the mixed path to 1e-10: latency of one solve, and
+    throughput of many independent copies solved together as one batch."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_spd
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = make_spd(64, 100.0, nrhs=1, seed=0)
+    A = torch.from_numpy(p.A).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    lat = {}
+    for name, kw, iters, tol in [("fp64, 8 coupled iterations", {"precision": nsgb.NS_FP64, "ns_stop": 0,
+                                                                 "max_sweeps": 0}, 8, 0.0),
+                                 ("mixed, to 1e-10", {}, 60, 1e-10)]:
+        with nsgb.Context(64, order=4, stream=stream, **kw) as ctx:
+            for _ in range(5):
+                r = ctx.solve(A, B, iters=iters, tol=tol)
+            ms = []
+            for _ in range(max(10, a.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = ctx.solve(A, B, iters=iters, tol=tol)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        lat[name] = {"us_per_solve": 1e3 * statistics.median(ms), "status": r.status,
+                     "rel_res": r.stats.rel_res, "ns_iters": r.stats.ns_iters, "sweeps": r.stats.sweeps}
+    copies = a.count
+    probs = [make_spd(64, 100.0, nrhs=1, seed=1000 + i) for i in range(copies)]
+    As = [torch.from_numpy(q.A).to(dev) for q in probs]
+    Bs = [torch.from_numpy(q.B).to(dev) for q in probs]
+    outs = [torch.empty_like(b) for b in Bs]
+    with nsgb.Batch([64] * copies, [1] * copies, order=4, stream=stream, couple_frob=a.couple) as bt:
+        for _ in range(3):
+            _, status, st = bt.solve(As, Bs, iters=60, tol=1e-10, outs=outs)
+        ms = []
+        for _ in range(max(3, a.steps // 4)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, status, st = bt.solve(As, Bs, iters=60, tol=1e-10, outs=outs)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    import oracle as O
+    worst = max(float(np.max(O.rel_residual(q.A, t.cpu().numpy(), q.B))) for q, t in zip(probs[:64], outs[:64]))
+    med = statistics.median(ms)
+    print(json.dumps({
+        "metric": METRIC + " (n = 64 systems)", "value": st.converged / (med / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": len(ms), "warmup": 3, "ms_per_step": med, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"{copies} copies of the n = 64 system (lambda log-uniform [1, 100], 1 RHS, order 4, "
+                               "G0 = I/||A||_F) solved as one batch to 1e-10; single-solve latencies alongside",
+                   "couple_frob": a.couple},
+        "converged": st.converged, "passes": st.passes, "worst_verified_rel_res_first64": worst,
+        "single_solve_latency": lat}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,7 +647,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "orders", "small"],
                     help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems; "
                          "serving: continuous batching of a Poisson request trace")
     ap.add_argument("--count", type=int, default=2048)
@@ -548,6 +662,16 @@ def main():
     ap.add_argument("--pool-qr-host", action="store_true",
                     help="draw the serving pool's orthogonal factors with a host QR (e.g. under a profiler)")
     a = ap.parse_args()
+    if a.workload == "orders" and a.impl == "ours":
+        if "--steps" not in sys.argv:
+            a.steps = 5
+        run_orders(a)
+        return
+    if a.workload == "small" and a.impl == "ours":
+        if "--steps" not in sys.argv:
+            a.steps = 20
+        run_small(a)
+        return
     if a.workload == "serving" and a.impl == "ours":
         if a.order == 8 and "--order" not in sys.argv:
             a.order = 4

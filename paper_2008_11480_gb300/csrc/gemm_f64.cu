@@ -85,14 +85,65 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Gemm g) {
   }
 }
 
+// Small products (fewer 64 x 64 tiles than half the SMs): 16 x 16 output tiles,
+// one output per thread, so that e.g. n = 64 spreads over 16 SMs instead of one.
+constexpr int TS = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_f64_small(F64Gemm g) {
+  __shared__ double sL[TS][TS + 1];
+  __shared__ double sR[TS][TS + 1];
+  __shared__ double red[8];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = blockIdx.y * TS + ty, col = blockIdx.x * TS + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += TS) {
+    const int lk = k0 + tx, rk = k0 + ty;
+    sL[ty][tx] = (row < g.M && lk < g.K) ? g.L[static_cast<int64_t>(row) * g.ldl + lk] : 0.0;
+    sR[ty][tx] = (rk < g.K && col < g.N) ? g.R[static_cast<int64_t>(rk) * g.ldr + col] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TS; ++k) acc = fma(sL[ty][k], sR[k][tx], acc);
+    __syncthreads();
+  }
+  double frob = 0.0;
+  if (row < g.M && col < g.N) {
+    double v = g.s * acc;
+    if (g.C != nullptr && g.beta != 0.0) v += g.beta * g.C[static_cast<int64_t>(row) * g.ldc + col];
+    if (row == col) v += g.gamma;
+    g.D[static_cast<int64_t>(row) * g.ldd + col] = v;
+    frob = v * v;
+  }
+  if (g.frob_partials != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) frob += __shfl_xor_sync(0xffffffffu, frob, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = frob;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      g.frob_partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+bool use_small(int M, int N) { return ((M + TM - 1) / TM) * ((N + TN - 1) / TN) < 76; }
+
 }  // namespace
 
-int f64_tiles(int M, int N) { return ((M + TM - 1) / TM) * ((N + TN - 1) / TN); }
+int f64_tiles(int M, int N) {
+  if (use_small(M, N)) return ((M + TS - 1) / TS) * ((N + TS - 1) / TS);
+  return ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+}
 
 cudaError_t launch_gemm_f64(const F64Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
-  k_gemm_f64<<<grid, 256, 0, s>>>(g);
+  if (use_small(g.M, g.N)) {
+    dim3 grid((g.N + TS - 1) / TS, (g.M + TS - 1) / TS);
+    k_gemm_f64_small<<<grid, 256, 0, s>>>(g);
+  } else {
+    dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+    k_gemm_f64<<<grid, 256, 0, s>>>(g);
+  }
   return cudaGetLastError();
 }
 
