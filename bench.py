@@ -103,6 +103,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+# Batched and served systems are independent: under torchrun each rank takes a
+# share of them (no data-path collective); only timings and counts are
+# reduced, and rank 0 prints.
+def dist_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_balanced(costs, world):
+    """Largest-first greedy split of units with the given costs over `world`
+    ranks (deterministic, ties broken by index); one sorted index list per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(q) for q in parts]
+
+
+def reduce_over_ranks(values, op, device="cpu"):
+    """Element-wise max or sum of a list of floats over all ranks (identity
+    without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+def gather_lists(values):
+    """Concatenation of every rank's list (all ranks receive it)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, list(values))
+    return [v for part in out for v in part]
+
+
 # ------------------------------------------------------------------ oracle (CPU) leg
 def oracle_sample(a, ns_iters: int, sweeps: int, reps: int = 1):
     """Time the FP64 oracle as it stands on the host cores: one Newton-Schulz
@@ -342,12 +386,20 @@ def run_batched(a):
     that reached the tolerance per second (the others are counted, not hidden)."""
     import torch
 
+    import torch.distributed as dist
+
     import paper_2008_11480_gb300 as nsgb
     from workloads import make_harmonic_batch
-    dev = torch.device("cuda:0")
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    probs = make_harmonic_batch(a.count, seed=3)
+    probs_all = make_harmonic_batch(a.count, seed=3)
+    mine = shard_balanced([float(p.n) ** 3 for p in probs_all], world)[rank]
+    probs = [probs_all[i] for i in mine]
     As = [torch.from_numpy(p.A).to(dev) for p in probs]
     Bs = [torch.from_numpy(p.B).to(dev) for p in probs]
     outs = [torch.empty_like(b) for b in Bs]
@@ -356,7 +408,9 @@ def run_batched(a):
                     couple_frob=a.couple)
     for _ in range(max(3, a.warmup)):
         _, status, st = bt.solve(As, Bs, iters=a.iters, tol=1e-10, outs=outs)
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     ms, conv, gflops, gms, gbytes = [], [], 0.0, 0.0, 0.0
@@ -378,19 +432,28 @@ def run_batched(a):
     for p, t, i in zip(probs, outs, range(len(probs))):
         if bt.result(i)["status"] == nsgb.NS_OK:
             worst = max(worst, float(np.max(O.rel_residual(p.A, t.cpu().numpy(), p.B))))
+    if world > 1:
+        dist.barrier()
     pk, pk_kind = peaks()
     ach = gflops / (gms / 1e3) / 1e12 if gms > 0 else None
     hbm_gbs = gbytes / (gms / 1e3) / 1e9 if gms > 0 else None
-    value = statistics.mean(conv) / (statistics.mean(ms) / 1e3)
+    # whole job: converged systems of all ranks over the slowest rank's time
+    t_max = reduce_over_ranks([sum(ms)], "max", dev)[0]
+    conv_all = reduce_over_ranks([float(sum(conv))], "sum", dev)[0]
+    worst = reduce_over_ranks([worst], "max", dev)[0]
+    value = conv_all / (t_max / 1e3)
+    if rank != 0:
+        bt.close()
+        return
     print(json.dumps({
         "metric": METRIC + " (batched harmonic-regressor systems)", "value": value, "unit": UNIT,
-        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(ms),
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"{a.count} harmonic-regressor Gram systems, m ~ U{{8..128}}, n = 2m, T = 4n, "
                                f"ridge 1e-6, b = A theta*, 1 RHS", "order": a.order, "tol": 1e-10, "couple_frob": a.couple,
                    "l2": "flushed between timed steps (512 MiB write)"},
-        "instances": a.count, "converged_per_step": statistics.mean(conv),
-        "not_converged_per_step": a.count - statistics.mean(conv),
+        "instances": a.count, "converged_per_step": conv_all / a.steps,
+        "not_converged_per_step": a.count - conv_all / a.steps,
         "worst_verified_rel_res_of_converged": worst, "passes": st.passes,
         "gemm_launches_per_step": st.gemm_launches, "kernel_launches_per_step": st.kernel_launches,
         "gpu_launches": int(st.kernel_launches) * a.steps,
@@ -417,18 +480,26 @@ def run_serving(a):
     value = converged requests / (last completion - first arrival)."""
     import torch
 
+    import torch.distributed as dist
+
     import paper_2008_11480_gb300 as nsgb
     from workloads import make_serving_trace, make_spd_device
-    dev = torch.device("cuda:0")
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     defs = make_serving_trace(1e6, 2.0 * a.pool / 1e6 + 1e-3, seed=11)[:a.pool]
     pool = [make_spd_device(r.n, r.kappa, nrhs=1, seed=r.seed, device=dev, qr_on_host=a.pool_qr_host)[0]
             for r in defs]
-    trace = make_serving_trace(a.rate, a.duration, seed=a.seed)
+    trace_all = make_serving_trace(a.rate, a.duration, seed=a.seed)
+    # each rank serves every world-th arrival of the one trace on its own GPU
+    trace = [r for i, r in enumerate(trace_all) if i % world == rank]
     gen = torch.Generator(device=dev)
-    gen.manual_seed(a.seed)
+    gen.manual_seed(a.seed + rank)
     reqs = []
-    for i, r in enumerate(trace):
+    for i, r in zip(range(rank, len(trace_all), world), trace):
         A = pool[i % len(pool)]
         B = torch.randn(A.shape[0], r.nrhs, generator=gen, device=dev, dtype=torch.float64)
         reqs.append((r.arrival_s, A, B, torch.empty_like(B)))
@@ -441,9 +512,11 @@ def run_serving(a):
     while not all(srv.poll(t)["done"] for t in wt):
         time.sleep(0.01)
     st0 = srv.stats()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
     sampler.start()
     tickets, t_sub = [], []
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for arr, A, B, T in reqs:
         while True:
@@ -482,23 +555,38 @@ def run_serving(a):
         rr = torch.linalg.vector_norm(B - A @ T, dim=0) / torch.linalg.vector_norm(B, dim=0)
         worst = max(worst, float(rr.max()))
     flops = st1["gemm_flops"] - st0["gemm_flops"]
+    # whole job over ranks: counts summed, the slowest rank's span, latencies pooled
+    if world > 1:
+        dist.barrier()
+    t_end = reduce_over_ranks([t_end], "max", dev)[0]
+    n_req, n_done, n_conv, n_left, flops, worst = (
+        reduce_over_ranks([float(len(reqs)), float(len(done)), float(len(conv)), float(len(left)), flops], "sum",
+                          dev) + reduce_over_ranks([worst], "max", dev))
+    lat = np.array(gather_lists(lat.tolist()))
+    qms = np.array(gather_lists(qms.tolist()))
+    if rank != 0:
+        if left:
+            os._exit(0)
+        srv.stop()
+        srv.close()
+        return
     pk, pk_kind = peaks()
-    ach = flops / t_end / 1e12 if done else None
+    ach = flops / t_end / 1e12 if n_done else None
     print(json.dumps({
-        "metric": METRIC + " (serving)", "value": len(conv) / t_end if done else 0.0, "unit": UNIT,
-        "n_gpus": 1, "steps": 1, "warmup": a.warmup, "ms_per_step": t_end * 1e3,
+        "metric": METRIC + " (serving)", "value": n_conv / t_end if n_done else 0.0, "unit": UNIT,
+        "n_gpus": world, "steps": 1, "warmup": a.warmup, "ms_per_step": t_end * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"serving trace: Poisson arrivals {a.rate:g} req/s for {a.duration:g} s; n log-uniform "
                                f"[32, 2048], kappa log-uniform [1e2, 1e6], nrhs U{{1..64}}; A from a pool of "
                                f"{a.pool} systems, own B per request", "order": a.order, "tol": 1e-10, "couple_frob": a.couple,
                    "budget_gb": a.budget_gb, "max_requests": a.max_requests, "buffers": "device (HBM)",
                    "l2": "inputs of the whole trace exceed L2"},
-        "requests": len(reqs), "completed": len(done), "converged": len(conv),
-        "not_converged": len(done) - len(conv), "unfinished": len(left),
+        "requests": int(n_req), "completed": int(n_done), "converged": int(n_conv),
+        "not_converged": int(n_done - n_conv), "unfinished": int(n_left),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean()), "max": float(lat.max())},
         "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
-        "offered_rate": len(reqs) / a.duration, "passes": st1["passes"] - st0["passes"],
+        "offered_rate": n_req / a.duration, "passes": st1["passes"] - st0["passes"],
         "worst_sampled_rel_res": worst,
         "server_host_ms": st1["tick_ms"] - st0["tick_ms"], "server_wait_ms": st1["wait_ms"] - st0["wait_ms"],
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
