@@ -49,6 +49,7 @@ def workload_config(a):
                      "and Richardson",
         "tol": 1e-10, "l2": "flushed between timed steps (512 MiB write)", "seed": 1,
         "couple_frob": a.couple,
+        **({"gemm_cluster": a.gemm_cluster} if getattr(a, "gemm_cluster", 0) else {}),
     }
 
 
@@ -227,7 +228,8 @@ def run_ours(a):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1, couple_frob=a.couple)
+    ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1, couple_frob=a.couple,
+                       gemm_cluster=a.gemm_cluster)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
     assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
@@ -269,7 +271,7 @@ def run_ours(a):
     Ah = torch.from_numpy(p.A).pin_memory()
     Bh = torch.from_numpy(p.B).pin_memory()
     Th = torch.empty_like(Bh).pin_memory()
-    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple)
+    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple, gemm_cluster=a.gemm_cluster)
     ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
     e2e_steps = max(1, min(a.steps, 5))
     barrier()
@@ -735,6 +737,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
+    ap.add_argument("--gemm-cluster", type=int, default=0,
+                    help="single workload: product-kernel clustering (0 automatic, 1, 2, 4; -2 CTA pairs)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "orders", "small"],
                     help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems; "
                          "serving: continuous batching of a Poisson request trace")

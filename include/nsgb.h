@@ -81,7 +81,10 @@ typedef struct ns_options {
                           T_i = NS_{m_i}(G0), so rates = {n} gives the double Newton-Schulz
                           method of Section 5.1 (eqs. gamk11-fks1); 0: T_i start at G0 */
   int gemm_cluster;    /* CTAs per cluster sharing each R tile by TMA multicast: 0 automatic,
-                          1 none, 2 or 4 (with 192- or 256-column tiles) */
+                          1 none, 2 or 4 (with 192- or 256-column tiles); -2: CTA pairs
+                          sharing each MMA (tcgen05 cta_group::2, 256 x 256 tiles) where
+                          ceil(n / 128) is even, else automatic.  Automatic picks CTA
+                          pairs wherever 256-column tiles are chosen and apply */
   double couple_frob;  /* 0 (default): the Richardson branch (residual, test, update) runs on
                           every NS step, as in Section 6.  > 0: it starts with the first
                           G_k whose ||I - A G_k||_F <= couple_frob and stays on.  Earlier G_k
@@ -323,8 +326,11 @@ ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int
  * (ldd16), frob_out a device double receiving sum(D^2).  Leading dimensions of bf16
  * arrays must be multiples of 8 and of f32 arrays multiples of 4; base pointers
  * 16-byte aligned.  bn = 0 picks the tile width (64, 128, 192 or 256 columns);
- * cluster_m = 0 picks how many CTAs (1, 2 or 4; 2 and 4 need bn >= 192) share each
- * R tile through TMA multicast.  Returns NS_ERR_ARG on violations. */
+ * cluster_m: 1, 2 or 4 CTAs (2 and 4 need bn >= 192) share each R tile through TMA
+ * multicast; -2 runs CTA pairs that share each MMA (tcgen05 cta_group::2, 256 x 256
+ * tiles: bn must be 0 or 256 and ceil(M / 128) even); 0 picks CTA pairs where they
+ * apply (bn = 256, ceil(M / 128) even), else 2 with bn >= 192, else 1.  Returns
+ * NS_ERR_ARG on violations. */
 ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,

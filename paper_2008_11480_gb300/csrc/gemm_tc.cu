@@ -40,6 +40,7 @@
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "tc_common.cuh"
 
 namespace nsgb {
 
@@ -66,29 +67,7 @@ struct TcCfg {
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
 };
 
-// Work item w of this CTA (cluster rank `rank`): problem, tile row and column.
-__device__ __forceinline__ void decode_item(const TcParams& p, int w, int rank, int CM, int& pi, int& mt, int& nt) {
-  if (p.gprob != nullptr) {
-    const TcItem it = p.items[w];
-    pi = it.prob;
-    mt = it.mt;
-    nt = it.nt;
-    return;
-  }
-  pi = 0;
-#pragma unroll 1
-  for (int i = 1; i < p.nprob; ++i)
-    if (w >= p.prob[i].tile_begin) pi = i;
-  const TcProblem& P = p.prob[pi];
-  const int local = w - P.tile_begin;
-  mt = (local / P.tiles_n) * CM + rank;
-  nt = local % P.tiles_n;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
+using tc::decode_item;
 
 template <int BN, int CM, bool X3>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
@@ -332,113 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         break;
       }
       tc_fence_after();
-      // Each 32-column chunk: tcgen05.ld gives lane l row (q*32 + l); the warp
-      // transposes it through shared memory so that every global access below
-      // covers whole 128-byte row segments (8 lanes x 16 B per row, 4 rows per
-      // instruction) instead of one 16-byte piece of 32 different rows.
-      float* wb = ebuf + q * 32 * Cfg::kEpiStride;
-      const int sub_r = lane >> 3;       // row within a group of 4
-      const int sub_c = (lane & 7) * 4;  // first of this lane's 4 columns
-      // the problem's fields in registers: the stores below could alias the
-      // problem table as far as the compiler knows, which would force a reload
-      // of every field after every store
-      const float e_s = P.s, e_beta = P.beta, e_gamma = P.gamma;
-      const int e_M = P.M, e_N = P.N;
-      const int64_t e_ldc = P.ldc, e_ld32 = P.ldd32, e_ld16 = P.ldd16;
-      const float* __restrict__ e_C = e_beta != 0.f ? P.C : nullptr;
-      float* __restrict__ e_D32 = P.D32;
-      bf16* __restrict__ e_Dhi = P.Dhi;
-      bf16* __restrict__ e_Dlo = P.Dlo;
-      float frob = 0.f;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        const int col0 = n0 + c0;
-        if (col0 >= e_N) break;  // warp-uniform: no later chunk has columns either
-        const int col = col0 + sub_c;
-        const bool cols4 = col + 4 <= e_N;
-        // the beta C term of all 8 row groups first, so that the loads overlap
-        // one another and the TMEM load below
-        float4 cv[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          cv[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-          const int row = m0 + q * 32 + 4 * g + sub_r;
-          if (e_C == nullptr || row >= e_M || col >= e_N) continue;
-          const float* crow = e_C + static_cast<int64_t>(row) * e_ldc + col;
-          if (cols4) {
-            cv[g] = *reinterpret_cast<const float4*>(crow);
-          } else {
-            cv[g].x = crow[0];
-            if (col + 1 < e_N) cv[g].y = crow[1];
-            if (col + 2 < e_N) cv[g].z = crow[2];
-          }
-        }
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN + c0),
-                           r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 32; i += 4)
-          *reinterpret_cast<float4*>(wb + lane * Cfg::kEpiStride + i) =
-              make_float4(e_s * __uint_as_float(r[i]), e_s * __uint_as_float(r[i + 1]),
-                          e_s * __uint_as_float(r[i + 2]), e_s * __uint_as_float(r[i + 3]));
-        __syncwarp();
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          const int rr = 4 * g + sub_r;
-          const int row = m0 + q * 32 + rr;
-          const float4 x4 = *reinterpret_cast<const float4*>(wb + rr * Cfg::kEpiStride + sub_c);
-          if (row >= e_M || col >= e_N) continue;
-          float v[4] = {x4.x, x4.y, x4.z, x4.w};
-          if (e_C != nullptr) {
-            v[0] += e_beta * cv[g].x;
-            v[1] += e_beta * cv[g].y;
-            v[2] += e_beta * cv[g].z;
-            v[3] += e_beta * cv[g].w;
-          }
-          if (e_gamma != 0.f) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) v[t] += (row == col + t) ? e_gamma : 0.f;
-          }
-          if (cols4) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) frob += v[t] * v[t];
-            if (e_D32 != nullptr)
-              *reinterpret_cast<float4*>(e_D32 + static_cast<int64_t>(row) * e_ld32 + col) =
-                  make_float4(v[0], v[1], v[2], v[3]);
-            if (e_Dhi != nullptr) {
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
-              const __nv_bfloat16 h2 = __float2bfloat16_rn(v[2]), h3 = __float2bfloat16_rn(v[3]);
-              __nv_bfloat162 ha, hb;
-              ha.x = h0;
-              ha.y = h1;
-              hb.x = h2;
-              hb.y = h3;
-              const int64_t o16 = static_cast<int64_t>(row) * e_ld16 + col;
-              *reinterpret_cast<uint2*>(e_Dhi + o16) =
-                  make_uint2(*reinterpret_cast<uint32_t*>(&ha), *reinterpret_cast<uint32_t*>(&hb));
-              if (e_Dlo != nullptr)
-                *reinterpret_cast<uint2*>(e_Dlo + o16) =
-                    make_uint2(pack_bf16x2(v[0] - __bfloat162float(h0), v[1] - __bfloat162float(h1)),
-                               pack_bf16x2(v[2] - __bfloat162float(h2), v[3] - __bfloat162float(h3)));
-            }
-          } else {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              if (col + t >= e_N) continue;
-              frob += v[t] * v[t];
-              if (e_D32 != nullptr) e_D32[static_cast<int64_t>(row) * e_ld32 + col + t] = v[t];
-              if (e_Dhi != nullptr) {
-                const int64_t o16 = static_cast<int64_t>(row) * e_ld16 + col + t;
-                const __nv_bfloat16 h = __float2bfloat16_rn(v[t]);
-                e_Dhi[o16] = h;
-                if (e_Dlo != nullptr) e_Dlo[o16] = __float2bfloat16_rn(v[t] - __bfloat162float(h));
-              }
-            }
-          }
-        }
-        __syncwarp();  // the buffer is rewritten by the next chunk
-      }
+      const float frob = tc::epilogue_tile<BN, Cfg::kEpiStride>(
+          P, m0, n0, q, lane, ebuf + q * 32 * Cfg::kEpiStride,
+          tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN));
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
       if (P.frob_partials != nullptr && mt < P.tiles_m) {
@@ -519,6 +394,7 @@ cudaError_t launch_bn(const TcParams& p, int num_sms, cudaStream_t s) {
 int tc_tiles(int M, int N, int BN) { return ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN); }
 
 int tc_items(int M, int N, int BN, int CM) {
+  if (CM < 0) CM = -CM;  // -2: CTA pairs, counted like clusters of two
   const int tiles_m = (M + kBM - 1) / kBM;
   return ((tiles_m + CM - 1) / CM) * ((N + BN - 1) / BN);
 }

@@ -65,6 +65,11 @@ struct TcParams {
 // x3 selects the split-product kernel (L/R maps of roles 1/2 below; BN 64, 128
 // or 256; p.npass ignored); otherwise p.npass passes over role-0 maps.
 cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s);
+// CTA-pair variant (cta_group::2): 256 x 256 output tiles, clusters of two
+// CTAs along M, tile bookkeeping of BN = 256, CM = 2 (tc_items(M, N, 256, 2)
+// items, tc_tiles(M, N, 256) partial sums).  Single-problem-table mode only
+// (p.gprob == nullptr); x3 selects split products, otherwise p.npass == 1.
+cudaError_t launch_gemm_tc_pair(const TcParams& p, bool x3, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
 int tc_items(int M, int N, int BN, int CM);
 

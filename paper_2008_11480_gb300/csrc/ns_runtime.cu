@@ -299,11 +299,14 @@ void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
   const int n = static_cast<int>(ctx->n);
   const int tiles_m = (n + 127) / 128;
   auto cm_for = [&](int bn) {
-    if (ctx->opt.gemm_cluster == 1 || bn < 192) return 1;
-    if (ctx->opt.gemm_cluster == 2 || ctx->opt.gemm_cluster == 4)
-      return tiles_m % ctx->opt.gemm_cluster == 0 ? ctx->opt.gemm_cluster : 1;
-    // two CTAs per cluster measured best at n = 4096: four-CTA clusters
-    // leave SMs idle (fewer co-resident clusters)
+    const int gc = ctx->opt.gemm_cluster;
+    if (gc == 1 || bn < 192) return 1;
+    if (gc == 2 || gc == 4) return tiles_m % gc == 0 ? gc : 1;
+    // automatic and -2: CTA pairs sharing each MMA (cta_group::2) where the
+    // tile width and the row-tile count allow (in-solve product rate at
+    // n = 4096: 1609 vs 1441 TFLOP/s for two-CTA multicast clusters); else two
+    // CTAs per cluster (four-CTA clusters leave SMs idle: fewer co-resident)
+    if (bn == 256 && tiles_m % 2 == 0) return -2;
     if (tiles_m % 2 == 0) return 2;
     return 1;
   };
@@ -317,11 +320,11 @@ void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
     if (fixed != 0 && bn != fixed) continue;
     const int cm = cm_for(bn);
     const int items = nprob * tc_items(n, n, bn, cm);
-    const int slots = std::max(1, ctx->num_sms / cm);
+    const int slots = std::max(1, ctx->num_sms / std::abs(cm));
     const int waves = (items + slots - 1) / slots;
     const double fill = static_cast<double>(items) / (static_cast<double>(waves) * slots);
     const double cols = static_cast<double>(n) / (static_cast<double>((n + bn - 1) / bn) * bn);
-    const double e = fill * cols * shape_eff[i] * (cm == 1 ? 0.93 : 1.0);
+    const double e = fill * cols * shape_eff[i] * (cm == 1 ? 0.93 : (cm == -2 ? 1.1 : 1.0));
     if (e > best + 1e-9) {
       best = e;
       best_bn = bn;
@@ -396,7 +399,10 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   }
   p.total_tiles = tile;
   EventPair* e = ev_begin(ctx, true);
-  NS_CK(launch_gemm_tc(p, bn, cm, x3, ctx->num_sms, ctx->stream));
+  if (cm == -2)
+    NS_CK(launch_gemm_tc_pair(p, x3, ctx->num_sms, ctx->stream));
+  else
+    NS_CK(launch_gemm_tc(p, bn, cm, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
   ctx->launches++;
   if (ctx->st) {
@@ -1487,9 +1493,17 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   if (D32 && (ldd32 < N || ldd32 % 4 || !al16(D32))) return NS_ERR_ARG;
   if ((Dhi || Dlo) && (ldd16 < N || ldd16 % 8)) return NS_ERR_ARG;
   if ((Dhi && !al16(Dhi)) || (Dlo && !al16(Dlo)) || (Dlo && !Dhi)) return NS_ERR_ARG;
+  if (cluster_m == -2 && bn == 0) bn = 256;
   if (bn == 0) bn = N >= 2048 ? 256 : (N > 64 ? 128 : 64);
   if (bn != 64 && bn != 128 && bn != 192 && bn != 256) return NS_ERR_ARG;
   const int tiles_m = static_cast<int>((M + 127) / 128);
+  bool pair = cluster_m == -2;
+  if (pair && (bn != 256 || tiles_m % 2 != 0)) return NS_ERR_ARG;
+  if (pair) cluster_m = 2;  // same item and partial-sum bookkeeping as two-CTA clusters
+  if (cluster_m == 0 && !pair && bn == 256 && tiles_m % 2 == 0) {
+    pair = true;  // automatic: CTA pairs where they apply
+    cluster_m = 2;
+  }
   if (cluster_m == 0) cluster_m = bn < 192 ? 1 : (tiles_m % 2 == 0 ? 2 : 1);
   if (precision == NS_BF16X3 && bn == 192 && cluster_m > 1) cluster_m = 1;
   if (cluster_m != 1 && cluster_m != 2 && cluster_m != 4) return NS_ERR_ARG;
@@ -1553,7 +1567,7 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   cudaMemsetAsync(scratch, 0, sizeof(int) * 4, st);
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
-  cudaError_t e = launch_gemm_tc(p, bn, cluster_m, x3, sms, st);
+  cudaError_t e = pair ? launch_gemm_tc_pair(p, x3, sms, st) : launch_gemm_tc(p, bn, cluster_m, x3, sms, st);
   if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * 4, 1, frob_out, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -138,6 +138,13 @@ def test_kernel_entry_points_validate_before_launch(L):
                             None, None, 0, None, 256, 3, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
                             None, None, 0, None, 128, 2, None) == nsgb.NS_ERR_ARG
+    # CTA pairs (cluster_m = -2) need 256-column tiles and an even number of 128-row tiles
+    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 256, 256, 64, 16, 16, 64, 16, 16, 256, 1.0, None, 0, 0.0, 0.0, None,
+                            0, None, None, 0, None, 128, -2, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_bf16(nsgb.NS_BF16X3, 300, 256, 64, 16, 16, 64, 16, 16, 256, 1.0, None, 0, 0.0, 0.0, None,
+                            0, None, None, 0, None, 0, -2, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 256, 256, 64, 16, 16, 64, 16, 16, 256, 1.0, None, 0, 0.0, 0.0, None,
+                            0, None, None, 0, None, 256, -4, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_resid(None, 4, None, None, None, 4, 1, None, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_update(16, 2, 4, 16, 16, 4, 1, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_split(16, 3, 4, 4, 4, 16, 16, 8, None) == nsgb.NS_ERR_ARG

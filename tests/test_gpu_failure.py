@@ -36,10 +36,10 @@ def operands(M, N, K, seed):
     return L, R, out
 
 
-def gemm(prec, M, N, K, parts, D32):
+def gemm(prec, M, N, K, parts, D32, bn=128, cm=1):
     Lh, Ll, Rh, Rl = parts
     nsgb.ns_k_gemm_bf16(prec, M, N, K, Lh, Ll, K, Rh, Rl, N, -1.0, None, 0, 0.0, 1.0, D32, N, None, None, 0,
-                        None, 128, 1)
+                        None, bn, cm)
 
 
 @pytest.fixture
@@ -56,9 +56,13 @@ def inject(monkeypatch):
     off()
 
 
+@pytest.mark.parametrize("bn,cm", [(128, 1), (256, -2)])
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 @pytest.mark.parametrize("k", [0, 5])
-def test_withheld_stage_load_times_out_and_context_recovers(inject, prec, k):
+def test_withheld_stage_load_times_out_and_context_recovers(inject, prec, k, bn, cm):
+    """cm = -2: both CTAs of each MMA pair withhold the load, so the stage
+    barrier of the pair's first CTA is never armed; both CTAs must give up,
+    release the pair's tensor memory together and exit."""
     on, off = inject
     M, N, K = 256, 256, 512
     L, R, parts = operands(M, N, K, seed=60 + k)
@@ -66,13 +70,13 @@ def test_withheld_stage_load_times_out_and_context_recovers(inject, prec, k):
     on(k)
     t0 = time.perf_counter()
     with pytest.raises(nsgb.NSError) as ei:
-        gemm(prec, M, N, K, parts, D32)
+        gemm(prec, M, N, K, parts, D32, bn, cm)
     elapsed = time.perf_counter() - t0
     assert ei.value.status == nsgb.NS_ERR_TIMEOUT
     assert elapsed < 5.0
     off()
     # the same product right after is complete and correct
-    gemm(prec, M, N, K, parts, D32)
+    gemm(prec, M, N, K, parts, D32, bn, cm)
     torch.cuda.synchronize()
     name = "bf16" if prec == nsgb.NS_BF16 else "bf16x3"
     ref = np.eye(M, N) - O.split_product(L, R, name)

@@ -118,6 +118,22 @@ def test_gemm_tc_clusters(prec, bn, cm, M, N, K):
 
 
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (250, 300, 129), (200, 130, 33), (512, 520, 200),
+                                   (1024, 1024, 1024)])
+def test_gemm_tc_pair(prec, M, N, K):
+    """CTA pairs sharing each MMA (cta_group::2): 256 x 256 tiles split as two
+    128-row halves in two TMEMs, R columns split between the two shared
+    memories.  Ragged M, N and K tails; s = -1, gamma = 1 as in F = I - A G."""
+    run_gemm(prec, M, N, K, seed=M + N + K + 7, bn=256, cm=-2, s=-1.0, gamma=1.0, scale=0.05)
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+def test_gemm_tc_pair_accumulate_epilogue(prec):
+    """X + X P form through CTA pairs: C = X, beta = 1."""
+    run_gemm(prec, 500, 333, 333, seed=16, beta=1.0, with_c=True, bn=256, cm=-2)
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 def test_gemm_tc_residual_epilogue(prec):
     """F = I - A G form: s = -1, gamma = 1 on a square problem."""
     run_gemm(prec, 200, 200, 200, seed=5, s=-1.0, gamma=1.0, scale=0.07)
@@ -129,25 +145,28 @@ def test_gemm_tc_accumulate_epilogue(prec):
     run_gemm(prec, 333, 333, 333, seed=6, beta=1.0, with_c=True)
 
 
-def test_gemm_tc_full_size_sampled():
-    """4096^3 bf16x3 (the bench's product size and launch configuration):
+@pytest.mark.parametrize("prec,bn,cm", [(nsgb.NS_BF16X3, 256, 4), (nsgb.NS_BF16X3, 256, -2),
+                                        (nsgb.NS_BF16, 256, 2), (nsgb.NS_BF16, 256, -2)])
+def test_gemm_tc_full_size_sampled(prec, bn, cm):
+    """4096^3 products (the bench's product size and launch configurations):
     sampled outputs recomputed one by one by the oracle."""
     n = 4096
+    pname = "bf16x3" if prec == nsgb.NS_BF16X3 else "bf16"
     rng = np.random.default_rng(40)
     L = rng.standard_normal((n, n)) * 0.02
     R = rng.standard_normal((n, n)) * 0.02
     Lh, Ll = gpu_split(L, n)
     Rh, Rl = gpu_split(R, n)
     D32 = torch.zeros((n, n), dtype=torch.float32, device=dev)
-    nsgb.ns_k_gemm_bf16(nsgb.NS_BF16X3, n, n, n, Lh, Ll, n, Rh, Rl, n, -1.0, None, 0, 0.0, 1.0, D32, n,
-                        None, None, 0, None, 256, 4)
+    nsgb.ns_k_gemm_bf16(prec, n, n, n, Lh, Ll, n, Rh, Rl, n, -1.0, None, 0, 0.0, 1.0, D32, n,
+                        None, None, 0, None, bn, cm)
     torch.cuda.synchronize()
     idx = rng.integers(0, n, (96, 2))
     idx[:8, 1] = idx[:8, 0]   # include diagonal entries (identity term)
     out = D32.cpu().numpy()
     for i, j in idx:
-        p = O.split_product(L[i:i + 1], R[:, j:j + 1], "bf16x3")[0, 0]
-        a = O.split_abs_product(L[i:i + 1], R[:, j:j + 1], "bf16x3")[0, 0]
+        p = O.split_product(L[i:i + 1], R[:, j:j + 1], pname)[0, 0]
+        a = O.split_abs_product(L[i:i + 1], R[:, j:j + 1], pname)[0, 0]
         ref = -p + (1.0 if i == j else 0.0)
         tol = n * 2.0 ** -23 * a + 2.0 ** -22 * (abs(ref) + 1.0)
         assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)

@@ -310,6 +310,25 @@ def test_mixed_precision_solve_reaches_tolerance(n, kappa, order, nrhs):
     assert r.stats.gemm_launches > 0
 
 
+@pytest.mark.parametrize("n,kappa", [(1000, 1e4), (512, 1e3)])
+def test_mixed_solve_through_cta_pairs(n, kappa):
+    """The products of the solve on CTA pairs sharing each MMA (gemm_cluster =
+    -2, 256 x 256 tiles): the tolerance is reached and theta matches the
+    closed-form solution as closely as with one-CTA tiles."""
+    p = make_spd(n, kappa, nrhs=3, seed=17)
+    out = {}
+    for cm in (2, -2):
+        with nsgb.Context(n, order=8, gemm_bn=256, gemm_cluster=cm) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+        th = r.theta.cpu().numpy()
+        assert r.status == nsgb.NS_OK, (cm, r.stats.res_history())
+        assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+        out[cm] = th
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(out[-2], tstar) <= 10 * kappa * 1e-10
+    assert rel(out[-2], out[2]) <= 10 * kappa * 1e-10
+
+
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 def test_fixed_precision_solve(prec):
     p = make_spd(128, 50.0, nrhs=2, seed=13)
