@@ -23,6 +23,12 @@
 // Both CTAs meet at a cluster barrier before the pair's TMEM is released and
 // again before exit, so no arrival or load targets a CTA that has left.
 //
+// Wave balance: with T tiles on C clusters, a last wave of T mod C tiles
+// leaves most clusters idle while it runs.  When 2 (T mod C) <= C those tiles
+// run as two half-width items each (256 x 128, MMA N = 128, 64 R columns per
+// CTA), which halves the last wave.  The partial sums of D^2 keep two slots of
+// four per tile (one per half; a whole tile writes 0 to the second).
+//
 // Shared-memory layouts per CTA are those of the one-CTA kernel with 128 R
 // columns: one pass -- L 128 x 64 (128-byte swizzle), R 64 x 128 as two 8 KiB
 // chunks of 64 columns; split products -- L_hi, L_lo 128 x 32 (64-byte
@@ -54,6 +60,19 @@ constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
 static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
 
+// Work item w: problem, tile row (128-row units, this CTA's half of the pair
+// tile), tile column, and which half of the tile's columns (-1: all 256).
+__device__ __forceinline__ void pair_item(const TcParams& p, int w, int rank, int& pi, int& mt, int& nt, int& half) {
+  const int split_from = p.total_tiles - p.pair_tail;
+  int tile = w;
+  half = -1;
+  if (w >= split_from) {
+    tile = split_from + ((w - split_from) >> 1);
+    half = (w - split_from) & 1;
+  }
+  tc::decode_item(p, tile, rank, 2, pi, mt, nt);
+}
+
 __device__ __forceinline__ void spin_ns(uint64_t ns) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 0; it < 0x10000000u; ++it)
@@ -71,6 +90,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
   const int rank = static_cast<int>(cluster_ctarank());
   const int first = blockIdx.x / 2;
   const int stride = gridDim.x / 2;
+  const int items = p.total_tiles + p.pair_tail;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -133,12 +153,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
     uint32_t phase = 0;
     int it = 0;
     bool ok = true;
-    for (int w = first; w < p.total_tiles && ok; w += stride) {
-      int pi, mt, nt;
-      tc::decode_item(p, w, rank, 2, pi, mt, nt);
+    for (int w = first; w < items && ok; w += stride) {
+      int pi, mt, nt, half;
+      pair_item(p, w, rank, pi, mt, nt, half);
       const TcProblem& P = p.prob[pi];
-      const int m0 = mt * kRows;                   // this CTA's L rows
-      const int nb = nt * kCols + rank * kHalf;    // this CTA's R columns
+      const int m0 = mt * kRows;                       // this CTA's L rows
+      const int cw = half < 0 ? kHalf : kHalf / 2;     // R columns this CTA stages
+      const int nb = nt * kCols + (half > 0 ? kHalf : 0) + rank * cw;
+      const uint32_t tx = 2u * static_cast<uint32_t>(kABytes + cw * kBK * 2);  // both CTAs' bytes
       const int kstep = X3 ? kBK / 2 : kBK;
       const int nkb = (P.K + kstep - 1) / kstep;
       for (int kb = 0; kb < nkb; ++kb) {
@@ -148,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
         }
         if (it != p.debug_stall_iter) {
           if (rank == 0) {
-            mbar_arrive_expect_tx(&full[stage], 2 * kStageBytes);
+            mbar_arrive_expect_tx(&full[stage], tx);
             armed[stage] = static_cast<int>(phase);
           }
           const uint32_t bar = full0 + static_cast<uint32_t>(stage * 8);
@@ -161,16 +183,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
             tma_load_2d_pair(a + 8192, &P.L[1], bar, x, m0);
             tma_load_2d_pair(a + 12288, &P.L[1], bar, x, m0 + 64);
 #pragma unroll
-            for (int part = 0; part < 2; ++part)
-#pragma unroll
-              for (int c = 0; c < 2; ++c)
-                tma_load_2d_pair(b + part * (kHalf * 64) + c * 4096, &P.R[part], bar, nb + 64 * c, x);
+            for (int part = 0; part < 2; ++part) {
+              tma_load_2d_pair(b + part * (kHalf * 64), &P.R[part], bar, nb, x);
+              if (half < 0) tma_load_2d_pair(b + part * (kHalf * 64) + 4096, &P.R[part], bar, nb + 64, x);
+            }
           } else {
             const int x = kb * kBK;
             tma_load_2d_pair(a, &P.L[0], bar, x, m0);
             tma_load_2d_pair(a + 8192, &P.L[0], bar, x, m0 + 64);
             tma_load_2d_pair(b, &P.R[0], bar, nb, x);
-            tma_load_2d_pair(b + 8192, &P.R[0], bar, nb + 64, x);
+            if (half < 0) tma_load_2d_pair(b + 8192, &P.R[0], bar, nb + 64, x);
           }
         }
         ++it;
@@ -196,19 +218,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ------------------------------------------------------------ MMA issuer (CTA 0)
-    constexpr uint32_t idesc = make_idesc_bf16(2 * kRows, kCols, 0, 1);
+    constexpr uint32_t idesc_full = make_idesc_bf16(2 * kRows, kCols, 0, 1);
+    constexpr uint32_t idesc_half = make_idesc_bf16(2 * kRows, kCols / 2, 0, 1);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
     bool issued = false;
-    for (int w = first; w < p.total_tiles && ok; w += stride) {
-      int pi, mt, nt;
-      tc::decode_item(p, w, 0, 2, pi, mt, nt);
+    for (int w = first; w < items && ok; w += stride) {
+      int pi, mt, nt, half;
+      pair_item(p, w, 0, pi, mt, nt, half);
       const TcProblem& P = p.prob[pi];
       const int kstep = X3 ? kBK / 2 : kBK;
       const int nkb = (P.K + kstep - 1) / kstep;
+      const uint32_t idesc = half < 0 ? idesc_full : idesc_half;
       if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, tlim, abort_flag)) {
         ok = false;
         break;
@@ -274,11 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int w = first; w < p.total_tiles; w += stride) {
-      int pi, mt, nt;
-      tc::decode_item(p, w, rank, 2, pi, mt, nt);
+    for (int w = first; w < items; w += stride) {
+      int pi, mt, nt, half;
+      pair_item(p, w, rank, pi, mt, nt, half);
       const TcProblem& P = p.prob[pi];
-      const int m0 = mt * kRows, n0 = nt * kCols;
+      const int m0 = mt * kRows, n0 = nt * kCols + (half > 0 ? kHalf : 0);
+
       bool ok = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -287,9 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
         break;
       }
       tc_fence_after();
-      const float frob = tc::epilogue_tile<kCols, kEpiStride>(
-          P, m0, n0, q, lane, ebuf + q * 32 * kEpiStride,
-          tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kCols));
+      // whole and half-width tiles as separate constant-width instances
+      const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kCols);
+      float* wb = ebuf + q * 32 * kEpiStride;
+      const float frob = half < 0 ? tc::epilogue_tile<kCols, kEpiStride>(P, m0, n0, q, lane, wb, tq)
+                                  : tc::epilogue_tile<kHalf, kEpiStride>(P, m0, n0, q, lane, wb, tq);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty0 + static_cast<uint32_t>(acc * 8));
@@ -297,7 +324,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
         double f = static_cast<double>(frob);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-        if (lane == 0) P.frob_partials[(mt * P.tiles_n + nt) * 4 + q] = f;
+        if (lane == 0) {
+          double* slot = P.frob_partials + (mt * P.tiles_n + nt) * 8 + q;
+          slot[half > 0 ? 4 : 0] = f;
+          if (half < 0) slot[4] = 0.0;
+        }
       }
       if (++acc == 2) {
         acc = 0;
@@ -344,10 +375,18 @@ cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
     }
     max_clusters = n;
   }
-  const int clusters = p.total_tiles < max_clusters ? p.total_tiles : max_clusters;
-  if (clusters <= 0) return cudaSuccess;
+  if (p.total_tiles <= 0) return cudaSuccess;
+  TcParams q = p;
+  // a last wave of `tail` tiles on `max_clusters` clusters runs as 2 tail
+  // half-width items where they still fit in one wave
+  const int tail = p.total_tiles % max_clusters == 0 && p.total_tiles >= max_clusters
+                       ? 0
+                       : (p.total_tiles > max_clusters ? p.total_tiles % max_clusters : p.total_tiles);
+  q.pair_tail = 2 * tail <= max_clusters ? tail : 0;
+  const int items = q.total_tiles + q.pair_tail;
+  const int clusters = items < max_clusters ? items : max_clusters;
   cfg.gridDim = dim3(2 * clusters);
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<X3>, p);
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<X3>, q);
 }
 
 }  // namespace

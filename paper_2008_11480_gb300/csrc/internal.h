@@ -37,7 +37,8 @@ struct TcProblem {
   float* D32;
   bf16* Dhi;
   bf16* Dlo;
-  double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4)
+  double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4); the CTA-pair
+                          // kernel writes 8 (two half-width slots of 4)
 };
 
 // A work item of a list-driven launch: problem index and tile coordinates.
@@ -56,6 +57,8 @@ struct TcParams {
   const TcItem* items;
   int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3)
   int debug_stall_iter;  // -1 for none; else the producer withholds that load
+  int pair_tail;  // CTA-pair kernel: the last pair_tail tiles each run as two
+                  // half-width (256 x 128) items (set by its launcher)
   unsigned long long timeout_ns;
   int* err;
 };
@@ -67,8 +70,10 @@ struct TcParams {
 cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s);
 // CTA-pair variant (cta_group::2): 256 x 256 output tiles, clusters of two
 // CTAs along M, tile bookkeeping of BN = 256, CM = 2 (tc_items(M, N, 256, 2)
-// items, tc_tiles(M, N, 256) partial sums).  Single-problem-table mode only
-// (p.gprob == nullptr); x3 selects split products, otherwise p.npass == 1.
+// tiles, 8 partial sums per tc_tiles(M, N, 256) tile).  Single-problem-table
+// mode only (p.gprob == nullptr); x3 selects split products, otherwise
+// p.npass == 1.  Tiles of a last, partial wave run as two half-width items
+// each when that shortens the wave.
 cudaError_t launch_gemm_tc_pair(const TcParams& p, bool x3, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
 int tc_items(int M, int N, int BN, int CM);

@@ -183,6 +183,8 @@ ns_status ensure_common(ns_ctx* ctx, int nrhs) {
     // tiles, residual blocks x nrhs, norm blocks
     const int n = static_cast<int>(ctx->n);
     size_t need = std::max<size_t>(static_cast<size_t>(tc_tiles(n, n, 64)) * 4, f64_tiles(n, n));
+    // CTA-pair launches: 8 per 256-column tile, for every problem of a launch
+    need = std::max<size_t>(need, static_cast<size_t>(kTcMaxProblems) * tc_tiles(n, n, 256) * 8);
     need = std::max<size_t>(need, static_cast<size_t>(std::max(resid_blocks(n), resid_x2_blocks(n))) * cap);
     need = std::max<size_t>(need, 2 * static_cast<size_t>((n + 7) / 8) + 2);
     if (need > ctx->partials_cap) {
@@ -385,11 +387,12 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
     P.Dlo = g.D->lo;
     P.ldd16 = static_cast<int>(ctx->ld);
     if (g.frob_dst != nullptr) {
-      if (poff + static_cast<size_t>(ntiles) * 4 > ctx->partials_cap)
+      const int per_tile = cm == -2 ? 8 : 4;  // the pair kernel keeps a slot set per half tile
+      if (poff + static_cast<size_t>(ntiles) * per_tile > ctx->partials_cap)
         return fail(ctx, NS_ERR_ARG, "partials workspace too small");
       P.frob_partials = ctx->partials + poff;
-      reduces.emplace_back(g.frob_dst, ntiles * 4);
-      poff += static_cast<size_t>(ntiles) * 4;
+      reduces.emplace_back(g.frob_dst, ntiles * per_tile);
+      poff += static_cast<size_t>(ntiles) * per_tile;
     }
     if (ctx->st) {
       const double f = 2.0 * n * static_cast<double>(n) * n * p.npass;
@@ -1559,7 +1562,8 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   P.ldd16 = static_cast<int>(ldd16);
   p.total_tiles = P.tile_count;
   void* scratch = nullptr;
-  const size_t scratch_bytes = sizeof(int) * 4 + (frob_out ? sizeof(double) * ntiles * 4 : 0);
+  const int per_tile = pair ? 8 : 4;  // the pair kernel keeps a slot set per half tile
+  const size_t scratch_bytes = sizeof(int) * 4 + (frob_out ? sizeof(double) * ntiles * per_tile : 0);
   if (cudaMallocAsync(&scratch, scratch_bytes + 256, st) != cudaSuccess) {
     cudaGetLastError();
     return NS_ERR_OOM;
@@ -1568,7 +1572,7 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
   cudaError_t e = pair ? launch_gemm_tc_pair(p, x3, sms, st) : launch_gemm_tc(p, bn, cluster_m, x3, sms, st);
-  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * 4, 1, frob_out, st);
+  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * per_tile, 1, frob_out, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(scratch, st);

@@ -128,6 +128,16 @@ def test_gemm_tc_pair(prec, M, N, K):
 
 
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
+@pytest.mark.parametrize("M,N,K", [(3072, 2048, 192), (3584, 2304, 128)])
+def test_gemm_tc_pair_waves(prec, M, N, K):
+    """Wave balance of the pair kernel on 152 SMs (76 pairs): 96 tiles leave a
+    last wave of 20, run as 40 half-width items; 126 tiles leave 50, which
+    would not fit one wave as halves and run whole.  (Fewer tiles than pairs,
+    in the cases above, run entirely as halves.)"""
+    run_gemm(prec, M, N, K, seed=M + N + K + 9, bn=256, cm=-2, s=-1.0, gamma=1.0, scale=0.05)
+
+
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 def test_gemm_tc_pair_accumulate_epilogue(prec):
     """X + X P form through CTA pairs: C = X, beta = 1."""
     run_gemm(prec, 500, 333, 333, seed=16, beta=1.0, with_c=True, bn=256, cm=-2)
