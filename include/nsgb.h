@@ -103,6 +103,10 @@ typedef struct ns_options {
   int g0_order;         /* 0 or 1: G0 = S^{-1} (g0_mode); h = 2..19: the initial series of Section 3
                           (eq. g01), G0 = {sum_{j<h} (S^{-1}D)^j} S^{-1}, by one tool-kit step of
                           order h from S^{-1} (bf16x3 products on the mixed path) */
+  int final_check;      /* after ns_invert / ns_richardson_solve: 0 (default) none; -1 ||I - A G||_F of
+                          the final G by one FP64 product; s = 1..4096 Hutchinson's estimate with s
+                          Rademacher probes and seed 0 (see ns_inverse_residual); into
+                          ns_stats.final_frob.  On the mixed path G is the f32 master, widened. */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -126,6 +130,8 @@ typedef struct ns_stats {
   long long tc_gemm_launches;
   double tc_gemm_flops;
   double wall_ms;                    /* host wall time of the call */
+  double final_frob;                 /* ||I - A G||_F of the final G in FP64 (option final_check);
+                                        -1 when not computed */
 } ns_stats;
 
 /* Fill *opt with the defaults documented in ns_options. */
@@ -176,6 +182,21 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
  * (the parameter-estimation error of eq. ttk1 measured through A). */
 ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const double* B, int nrhs,
                       double* rel_res_out);
+
+/* Final check of an inverse estimate (precision control): ||I - A G||_F in FP64 for n x n A and
+ * G (row-major FP64, lda = ldg = n, device or host; the context's n).
+ *   probes = 0: I - A G formed by one FP64 product (2 n^3 flop) with its sum of squares.
+ *   probes = s > 0: Hutchinson's estimate sqrt((1/s) sum_j ||z_j - A (G z_j)||^2) over s
+ *   Rademacher probes (two FP64 products n x n x s): unbiased for ||I - A G||_F^2, exact when
+ *   I - A G is diagonal.  Probe entry (i, j) is -1 when the top bit of SplitMix64 output
+ *   k = j n + i from state `seed` is set, else +1; SplitMix64 (Steele, Lea, Flood 2014):
+ *   output k = mix(seed + (k + 1) * 0x9E3779B97F4A7C15), mix(z): z ^= z >> 30,
+ *   z *= 0xBF58476D1CE4E5B9, z ^= z >> 27, z *= 0x94D049BB133111EB, z ^= z >> 31.
+ * *frob_out (host) receives the value.  Workspace (n^2 or 3 n s doubles) is taken per call
+ * from the stream-ordered allocator; the context's stream is synchronised.
+ * Errors: NS_ERR_ARG (null pointer, probes < 0 or > 4096), NS_ERR_OOM, NS_ERR_CUDA. */
+ns_status ns_inverse_residual(ns_ctx* ctx, const double* A, const double* G, int probes,
+                              unsigned long long seed, double* frob_out);
 
 /* Message for the last failing call on ctx ("" if none; static text for NULL). */
 const char* ns_last_error(const ns_ctx* ctx);

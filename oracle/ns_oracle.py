@@ -483,6 +483,53 @@ def rel_residual(A: np.ndarray, theta: np.ndarray, B: np.ndarray) -> np.ndarray:
     return np.sqrt(np.sum(R * R, axis=0)) / np.sqrt(np.sum(B * B, axis=0))
 
 
+# --------------------------------------------------------------------------
+# Final check of an inverse estimate: ||I - A G||_F, the quantity whose powers
+# bound the Newton-Schulz error (Section 3: F_k = F_0^{n^k}) and whose norm
+# bounds the Richardson contraction (Section 6).  The exact value is one FP64
+# product; Hutchinson's estimator replaces it by products with s random sign
+# vectors z_j: E ||(I - A G) z||^2 = ||I - A G||_F^2 when the entries of z are
+# independent +-1 (E z z^T = I), exactly so for every z when I - A G is
+# diagonal (z_i^2 = 1).
+# --------------------------------------------------------------------------
+
+_U64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k (0-based) of SplitMix64 from state `seed` (Steele, Lea,
+    Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the
+    state advances by the odd constant 0x9E3779B97F4A7C15, and each state is
+    finalised by two xor-shift-multiply rounds and a last xor-shift.  Exact
+    integer arithmetic mod 2^64."""
+    z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & _U64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _U64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _U64
+    return z ^ (z >> 31)
+
+
+def rademacher_probes(n: int, s: int, seed: int) -> np.ndarray:
+    """n x s matrix of +-1: entry (i, j) is -1 when the top bit of SplitMix64
+    output j n + i is set (the library's documented probe layout)."""
+    Z = np.empty((n, s))
+    for j in range(s):
+        for i in range(n):
+            Z[i, j] = -1.0 if splitmix64(seed, j * n + i) >> 63 else 1.0
+    return Z
+
+
+def inverse_residual(A: np.ndarray, G: np.ndarray) -> float:
+    """||I - A G||_F, formed with one product."""
+    return float(np.linalg.norm(_eye_like(A) - A @ G))
+
+
+def inverse_residual_hutchinson(A: np.ndarray, G: np.ndarray, s: int, seed: int) -> float:
+    """sqrt((1/s) sum_j ||z_j - A (G z_j)||^2) over the s probes above."""
+    Z = rademacher_probes(A.shape[0], s, seed)
+    R = Z - A @ (G @ Z)
+    return float(np.sqrt(np.sum(R * R) / s))
+
+
 def ns_invert(A: np.ndarray, G0: np.ndarray | None = None, order: int = 2, iters: int = 10,
               form: str = "factorized", pow_mode: str = "square") -> tuple[np.ndarray, list]:
     """Run ``iters`` Newton-Schulz steps of the given order (Section 3, eq. ns,

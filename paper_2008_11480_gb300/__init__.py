@@ -25,6 +25,7 @@ __all__ = [
     "NS_FP64", "NS_BF16", "NS_BF16X3", "NS_AUTO",
     "NSError", "ns_options", "ns_stats", "lib", "lib_path", "header_path", "default_options",
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
+    "ns_inverse_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
     "ns_batch_stats", "Batch",
@@ -65,6 +66,7 @@ class ns_options(ctypes.Structure):
         ("couple_frob", ctypes.c_double),
         ("accel_richardson", ctypes.c_int),
         ("g0_order", ctypes.c_int),
+        ("final_check", ctypes.c_int),
     ]
 
 
@@ -88,6 +90,7 @@ class ns_stats(ctypes.Structure):
         ("tc_gemm_launches", ctypes.c_longlong),
         ("tc_gemm_flops", ctypes.c_double),
         ("wall_ms", ctypes.c_double),
+        ("final_frob", ctypes.c_double),
     ]
 
     def frob_history(self) -> list[float]:
@@ -181,6 +184,7 @@ def lib() -> ctypes.CDLL:
         "ns_invert": (_int, [_vp, _vp, _vp, _int, _vp, ctypes.POINTER(ns_stats)]),
         "ns_richardson_solve": (_int, [_vp, _vp, _vp, _int, _vp, _int, ctypes.c_double, _vp, ctypes.POINTER(ns_stats)]),
         "ns_residual": (_int, [_vp, _vp, _vp, _vp, _int, _vp]),
+        "ns_inverse_residual": (_int, [_vp, _vp, _vp, _int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
         "ns_last_error": (ctypes.c_char_p, [_vp]),
         "ns_status_string": (ctypes.c_char_p, [_int]),
         "ns_k_split": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
@@ -329,6 +333,15 @@ def ns_residual(ctx: int, A: torch.Tensor, theta: torch.Tensor, B: torch.Tensor)
     return list(out)
 
 
+def ns_inverse_residual(ctx: int, A: torch.Tensor, G: torch.Tensor, probes: int = 0, seed: int = 0) -> float:
+    """||I - A G||_F in FP64: exact (probes = 0) or Hutchinson's estimate with
+    `probes` Rademacher probes drawn from SplitMix64 at `seed`."""
+    out = ctypes.c_double(0.0)
+    s = lib().ns_inverse_residual(ctx, _ptr(A), _ptr(G), int(probes), int(seed) & (2 ** 64 - 1), ctypes.byref(out))
+    _check(ctx, s, (NS_OK,))
+    return out.value
+
+
 # ---------------------------------------------------------------- single kernels
 
 def _raise(s: int, what: str):
@@ -446,6 +459,9 @@ class Context:
 
     def residual(self, A, theta, B) -> list[float]:
         return ns_residual(self.handle, A, theta, B)
+
+    def inverse_residual(self, A, G, probes: int = 0, seed: int = 0) -> float:
+        return ns_inverse_residual(self.handle, A, G, probes, seed)
 
 
 class Batch:

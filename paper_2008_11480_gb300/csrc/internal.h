@@ -132,6 +132,8 @@ cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, d
                               cudaStream_t s);
 cudaError_t launch_copy_f64(const double* X, int64_t ldx, int rows, int cols, double* Y, int64_t ldy,
                             cudaStream_t s);
+// Rademacher probes (rows x probes, ld = probes) from SplitMix64 outputs j rows + i.
+cudaError_t launch_rademacher(double* Z, int rows, int probes, unsigned long long seed, cudaStream_t s);
 
 // ---- split-f32 Richardson path (mixed precision)
 // One pass over A: sum a^2 / max row |a| partials, bf16 hi/lo, f32 limbs a1/a2.

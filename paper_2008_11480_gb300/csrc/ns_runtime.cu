@@ -1183,9 +1183,85 @@ ns_status begin_call(ns_ctx* ctx, ns_stats* st) {
   ctx->launches = 0;
   if (st) {
     memset(st, 0, sizeof(*st));
+    st->final_frob = -1.0;
   }
   NS_CK(cudaSetDevice(ctx->device));
   return NS_OK;
+}
+
+// ||I - A G||_F in FP64 for device A (lda) and G (ldg), the final check of the
+// precision control.  probes = 0: I - A G by one FP64 product with the fused
+// identity term and per-tile sums of squares.  probes = s > 0: Hutchinson's
+// estimate sqrt((1/s) sum_j ||z_j - A (G z_j)||^2) over s Rademacher probes
+// (SplitMix64 from `seed`), two FP64 products n x n x s; unbiased for the
+// squared norm and exact when I - A G is diagonal (z_i^2 = 1).  Workspace is
+// taken per call from the stream-ordered allocator; the stream is synchronised
+// to read the value.
+ns_status inverse_check(ns_ctx* ctx, const double* A, int64_t lda, const double* G, int64_t ldg, int probes,
+                        unsigned long long seed, double* out) {
+  const int n = static_cast<int>(ctx->n);
+  cudaStream_t st = ctx->stream;
+  const size_t elems = probes == 0 ? static_cast<size_t>(n) * n : static_cast<size_t>(n) * probes * 3;
+  const int ntiles = probes == 0 ? f64_tiles(n, n) : f64_tiles(n, probes);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, sizeof(double) * (elems + ntiles + 1), st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, NS_ERR_OOM, "inverse check workspace");
+  }
+  double* W = static_cast<double*>(scratch);
+  double* part = W + elems;
+  double* sum = part + ntiles;
+  F64Gemm g;
+  cudaError_t e = cudaSuccess;
+  if (probes == 0) {
+    g = F64Gemm{n, n, n, A, static_cast<int>(lda), G, static_cast<int>(ldg), -1.0, 0.0, 1.0,
+                nullptr, 0, W, n, part};
+    e = launch_gemm_f64(g, st);
+  } else {
+    double* Z = W;
+    double* Y = W + static_cast<size_t>(n) * probes;
+    double* R = Y + static_cast<size_t>(n) * probes;
+    e = launch_rademacher(Z, n, probes, seed, st);
+    if (e == cudaSuccess) {
+      g = F64Gemm{n, probes, n, G, static_cast<int>(ldg), Z, probes, 1.0, 0.0, 0.0, nullptr, 0, Y, probes, nullptr};
+      e = launch_gemm_f64(g, st);  // Y = G Z
+    }
+    if (e == cudaSuccess) {
+      g = F64Gemm{n, probes, n, A, static_cast<int>(lda), Y, probes, -1.0, 1.0, 0.0, Z, probes, R, probes, part};
+      e = launch_gemm_f64(g, st);  // R = Z - A Y
+    }
+    ctx->launches += 2;
+  }
+  ctx->launches += 2;
+  double h = 0.0;
+  if (e == cudaSuccess) e = launch_reduce_sum(part, ntiles, 1, sum, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sum, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+  *out = std::sqrt(h / (probes > 0 ? probes : 1));
+  return NS_OK;
+}
+
+// The option final_check after a call: ||I - A G||_F of the call's final G into st.
+ns_status final_check(ns_ctx* ctx, const double* A, int64_t lda, bool fp64, int cur, ns_stats* st) {
+  if (ctx->opt.final_check == 0 || st == nullptr) return NS_OK;
+  const int n = static_cast<int>(ctx->n);
+  const int probes = ctx->opt.final_check > 0 ? ctx->opt.final_check : 0;
+  if (fp64) return inverse_check(ctx, A, lda, ctx->G64[cur], ctx->ld, probes, 0ull, &st->final_frob);
+  // the mixed path's G is its f32 master: widen it once for the FP64 check
+  double* G = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&G), sizeof(double) * n * static_cast<size_t>(n), ctx->stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, NS_ERR_OOM, "inverse check workspace");
+  }
+  cudaError_t e = launch_f32_to_f64(ctx->G[cur].m32, ctx->ld, n, n, G, n, ctx->stream);
+  ctx->launches++;
+  ns_status r = e == cudaSuccess ? inverse_check(ctx, A, lda, G, n, probes, 0ull, &st->final_frob)
+                                 : fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+  cudaFreeAsync(G, ctx->stream);
+  return r;
 }
 
 ns_status end_call(ns_ctx* ctx, ns_status r, std::chrono::steady_clock::time_point t0) {
@@ -1222,6 +1298,7 @@ void ns_default_options(ns_options* o) {
   o->timeout_s = 2.0;
   o->aux_ahead = 0;
   o->gemm_cluster = 0;
+  o->final_check = 0;
   o->couple_frob = 0.0;
   o->accel_richardson = 0;
   o->g0_order = 0;
@@ -1255,6 +1332,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
+  if (o.final_check < -1 || o.final_check > 4096) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state
@@ -1344,6 +1422,10 @@ ns_status ns_invert(ns_ctx* ctx, const double* A, const double* G0, int iters, d
   S.lda = (A == ctx->Astage) ? ctx->ld : n;
   S.fp64 = fp64;
   r = run(ctx, S, G0d, iters, 0.0, false, st);
+  if (r >= 0) {
+    const ns_status c = final_check(ctx, S.A, S.lda, fp64, S.cur, st);
+    if (c != NS_OK) r = c;
+  }
   if (r >= 0 && G_out) {
     const bool dev = is_device_ptr(G_out);
     cudaError_t e = cudaSuccess;
@@ -1413,6 +1495,10 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   S.fp64 = fp64;
   S.theta0_given = Theta0 != nullptr;
   r = run(ctx, S, nullptr, iters, tol, true, st);
+  if (r >= 0) {
+    const ns_status c = final_check(ctx, S.A, S.lda, fp64, S.cur, st);
+    if (c != NS_OK) r = c;
+  }
   if (r >= 0 && !out_dev) {
     e = cudaMemcpyAsync(Theta_out, Th, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) r = fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
@@ -1463,6 +1549,41 @@ ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const d
       rel_res_out[c] = b > 0 ? std::sqrt(q / b) : std::sqrt(q);
     }
   }
+  return end_call(ctx, r, t0);
+}
+
+ns_status ns_inverse_residual(ns_ctx* ctx, const double* A, const double* G, int probes, unsigned long long seed,
+                              double* frob_out) {
+  auto t0 = std::chrono::steady_clock::now();
+  NS_TRY(begin_call(ctx, nullptr));
+  if (!A || !G || !frob_out || probes < 0 || probes > 4096)
+    return end_call(ctx, fail(ctx, NS_ERR_ARG, "null pointer or probes outside 0..4096"), t0);
+  const int n = static_cast<int>(ctx->n);
+  ns_status r = ensure_common(ctx, 1);
+  if (r != NS_OK) return end_call(ctx, r, t0);
+  cudaError_t e = cudaSuccess;
+  int64_t lda = n;
+  if (!is_device_ptr(A)) {
+    if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
+    if (r != NS_OK) return end_call(ctx, r, t0);
+    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyDefault, ctx->stream);
+    A = ctx->Astage;
+    lda = ctx->ld;
+  }
+  double* Gtmp = nullptr;
+  if (e == cudaSuccess && !is_device_ptr(G)) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&Gtmp), sizeof(double) * n * static_cast<size_t>(n), ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Gtmp, G, sizeof(double) * n * static_cast<size_t>(n), cudaMemcpyDefault, ctx->stream);
+    G = Gtmp;
+  }
+  if (e != cudaSuccess) {
+    if (Gtmp) cudaFreeAsync(Gtmp, ctx->stream);
+    return end_call(ctx, fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e)), t0);
+  }
+  r = inverse_check(ctx, A, lda, G, n, probes, seed, frob_out);
+  if (Gtmp) cudaFreeAsync(Gtmp, ctx->stream);
   return end_call(ctx, r, t0);
 }
 

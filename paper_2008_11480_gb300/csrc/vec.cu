@@ -386,6 +386,24 @@ __global__ void k_f32_to_f64(const float* __restrict__ X, int64_t ldx, int rows,
   }
 }
 
+// Rademacher probe matrix Z (rows x probes, row-major, ld = probes): entry
+// (i, j) is -1 when the top bit of SplitMix64 output number k = j rows + i
+// after state `seed` is set, else +1.  SplitMix64 (Steele, Lea and Flood,
+// "Fast splittable pseudorandom number generators", 2014): output k is
+// mix(seed + (k + 1) * 0x9E3779B97F4A7C15) with the finalizer below.
+__global__ void k_rademacher(double* __restrict__ Z, int rows, int probes, unsigned long long seed) {
+  const int64_t total = static_cast<int64_t>(rows) * probes;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    unsigned long long z = seed + static_cast<unsigned long long>(k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const int64_t i = k % rows, j = k / rows;
+    Z[i * probes + j] = (z >> 63) ? -1.0 : 1.0;
+  }
+}
+
 __global__ void k_copy_f64(const double* __restrict__ X, int64_t ldx, int rows, int cols, double* __restrict__ Y,
                            int64_t ldy) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
@@ -552,6 +570,13 @@ cudaError_t launch_f32_to_f64(const float* X, int64_t ldx, int rows, int cols, d
   const int64_t total = static_cast<int64_t>(rows) * cols;
   if (total <= 0) return cudaSuccess;
   k_f32_to_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, Y, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rademacher(double* Z, int rows, int probes, unsigned long long seed, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(rows) * probes;
+  if (total <= 0) return cudaSuccess;
+  k_rademacher<<<ew_grid(total), 256, 0, s>>>(Z, rows, probes, seed);
   return cudaGetLastError();
 }
 

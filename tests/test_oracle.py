@@ -510,3 +510,64 @@ def test_gemm_epilogue_forms():
     C = rng.standard_normal((5, 5))
     assert np.allclose(O.gemm_epilogue(P, -1.0, gamma=1.0), np.eye(5) - P)
     assert np.allclose(O.gemm_epilogue(P, 1.0, C, 1.0), C + P)
+
+
+# ---------------------------------------------------------------- final inverse check
+SM64 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64_vectors.json")))
+
+
+def test_splitmix64_published_outputs():
+    for seed, outs in SM64["outputs"].items():
+        for k, v in enumerate(outs):
+            assert O.splitmix64(int(seed), k) == int(v, 0)
+
+
+def test_rademacher_probes_balanced_and_uncorrelated():
+    Z = O.rademacher_probes(64, 64, seed=99)
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    assert abs(float(np.mean(Z))) < 5 / math.sqrt(Z.size)           # P(-1) = 1/2
+    C = Z.T @ Z / 64.0
+    off = C[~np.eye(64, dtype=bool)]
+    assert np.all(np.abs(off) < 5 / math.sqrt(64))                    # E z_j^T z_k = 0
+    assert not np.array_equal(O.rademacher_probes(64, 4, 1), O.rademacher_probes(64, 4, 2))
+
+
+def test_inverse_residual_closed_forms():
+    p = spd(n=30, kappa=50.0, seed=21)
+    c = 1.0 / p.lam.max()
+    # G = c I: I - c A = Q diag(1 - c lambda) Q^T
+    want = math.sqrt(float(np.sum((1.0 - c * p.lam) ** 2)))
+    assert O.inverse_residual(p.A, c * np.eye(30)) == pytest.approx(want, rel=1e-12)
+    Ainv = (p.Q / p.lam) @ p.Q.T
+    assert O.inverse_residual(p.A, Ainv) < 1e-12
+
+
+def test_hutchinson_exact_cases():
+    rng = np.random.default_rng(5)
+    n = 40
+    # G = 0: every probe gives ||z||^2 = n
+    assert O.inverse_residual_hutchinson(np.diag(rng.uniform(1, 2, n)), np.zeros((n, n)), 3, 7) == math.sqrt(n)
+    # diagonal I - A G: z_i^2 = 1 makes every probe exact
+    A = np.diag(rng.uniform(1, 10, n))
+    G = np.diag(rng.uniform(0.05, 0.2, n))
+    assert O.inverse_residual_hutchinson(A, G, 2, 11) == pytest.approx(O.inverse_residual(A, G), rel=1e-13)
+    # likewise whenever each row of I - A G has one nonzero: G = A^{-1} (I - N), N a
+    # scaled cyclic shift, so I - A G = N with ||N||_F^2 = sum of its entries squared
+    w = rng.uniform(0.1, 3.0, n)
+    N_ = np.roll(np.diag(w), 1, axis=1)
+    G = np.linalg.solve(A, np.eye(n) - N_)
+    assert O.inverse_residual_hutchinson(A, G, 3, 13) == pytest.approx(math.sqrt(float(np.sum(w * w))), rel=1e-12)
+
+
+def test_hutchinson_unbiased_within_its_variance():
+    """E z^T M z = tr M and Var = 2 sum_{i != j} M_ij^2 for Rademacher z and
+    symmetric M = R^T R, R = I - A G: the s-probe mean of ||R z||^2 must lie
+    within 5 standard errors of ||R||_F^2."""
+    p = spd(n=24, kappa=20.0, seed=8)
+    G = O.alpha_frobenius(p.A) * np.eye(24) + 0.01 * np.random.default_rng(2).standard_normal((24, 24))
+    R = np.eye(24) - p.A @ G
+    M = R.T @ R
+    var = 2.0 * float(np.sum(M * M) - np.sum(np.diag(M) ** 2))
+    s = 1500
+    est2 = O.inverse_residual_hutchinson(p.A, G, s, 3) ** 2
+    assert abs(est2 - float(np.trace(M))) <= 5.0 * math.sqrt(var / s)

@@ -134,3 +134,36 @@ def test_bf16_truncation_instead_of_rounding(monkeypatch):
 def test_split_dropping_cross_term(monkeypatch):
     monkeypatch.setitem(N.SPLIT_PASSES, "bf16x3", (("hi", "hi"), ("hi", "lo")))
     assert _fails(T.test_split_product_terms)
+
+
+def test_splitmix64_wrong_shift(monkeypatch):
+    def bad(seed, k):
+        z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & N._U64
+        z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9) & N._U64   # 31 where the finalizer shifts by 30
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & N._U64
+        return z ^ (z >> 31)
+    _patch(monkeypatch, "splitmix64", bad)
+    assert _fails(T.test_splitmix64_published_outputs)
+
+
+def test_hutchinson_missing_probe_mean(monkeypatch):
+    def bad(A, G, s, seed):
+        Z = N.rademacher_probes(A.shape[0], s, seed)
+        R = Z - A @ (G @ Z)
+        return float(np.sqrt(np.sum(R * R)))   # sum over probes, not the mean
+    _patch(monkeypatch, "inverse_residual_hutchinson", bad)
+    assert _fails(T.test_hutchinson_exact_cases)
+
+
+def test_hutchinson_transposed_product(monkeypatch):
+    def bad(A, G, s, seed):
+        Z = N.rademacher_probes(A.shape[0], s, seed)
+        R = Z - G @ (A @ Z)   # I - G A instead of I - A G
+        return float(np.sqrt(np.sum(R * R) / s))
+    _patch(monkeypatch, "inverse_residual_hutchinson", bad)
+    assert _fails(T.test_hutchinson_exact_cases)
+
+
+def test_inverse_residual_sign(monkeypatch):
+    _patch(monkeypatch, "inverse_residual", lambda A, G: float(np.linalg.norm(np.eye(A.shape[0]) + A @ G)))
+    assert _fails(T.test_inverse_residual_closed_forms)
