@@ -57,7 +57,11 @@ typedef enum ns_precision {
   NS_FP64 = 0,   /* every product in FP64 on the CUDA cores (plain path) */
   NS_BF16 = 2,   /* products hi*hi of bf16 operands, f32 accumulation (tcgen05) */
   NS_BF16X3 = 3, /* split bf16: hi*hi + hi*lo + lo*hi into one f32 accumulator */
-  NS_AUTO = 5    /* bf16 while ||F_k||_F keeps falling, then bf16x3 (one-step rollback) */
+  NS_BF16X6 = 4, /* three-part split hi, lo = bf16(x - hi), lo2 = bf16(x - hi - lo):
+                    hi*hi + hi*lo + lo*hi + hi*lo2 + lo*lo + lo2*hi into one f32
+                    accumulator (tcgen05 CTA pairs); not with composite rates or form 3 */
+  NS_AUTO = 5    /* bf16 while ||F_k||_F keeps falling, then bf16x3 (one-step rollback);
+                    bf16x6 where bf16x3 stalls at a floor Richardson cannot finish from */
 } ns_precision;
 
 typedef struct ns_options {
@@ -356,6 +360,26 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
                          int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream);
+
+/* Three-part bf16 split for bf16x6 products: x32 = binary32 rounding of X (FP64, x_dtype 0)
+ * or X itself (f32, x_dtype 1), hi = bf16(x32), lo = bf16(x32 - hi), lo2 = bf16(x32 - hi -
+ * lo), each rounded to nearest even; every difference is exact in binary32, so x32 = hi +
+ * lo + lo2.  Layouts and errors as ns_k_split (lo2 must not be NULL). */
+ns_status ns_k_split3(const void* X, int x_dtype, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo,
+                      void* lo2, int64_t ld, void* stream);
+
+/* Split-bf16 x6 product on tcgen05 CTA pairs (256 x 256 tiles), same epilogue as
+ * ns_k_gemm_bf16:
+ *   D = s * P + beta * C + gamma * I,
+ *   P = Lhi Rhi + Lhi Rlo + Llo Rhi + Lhi Rlo2 + Llo Rlo + Llo2 Rhi   (f32 accumulation)
+ * L[3] and R[3] are host arrays of the device parts {hi, lo, lo2} from ns_k_split3 (M x K,
+ * ldl; K x N, ldr; multiples of 8 elements, 16-byte aligned).  D is NULL or a host array
+ * {Dhi, Dlo, Dlo2} of optional outputs (ldd16): the three-part split of D (a part may be
+ * NULL only when the later ones are).  Any M (an odd number of 128-row tiles is allowed).
+ * Synchronises `stream`.  Errors: NS_ERR_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_TIMEOUT. */
+ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl, const void* const* R,
+                           int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma, float* D32,
+                           int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, void* stream);
 
 /* FP64 product with the same epilogue: D = s L R + beta C + gamma I (C may be NULL). */
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,

@@ -642,18 +642,40 @@ def split_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return hi, lo
 
 
+def split3_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Three-term bfloat16 split of binary32 values: hi and lo as in
+    ``split_bf16``, lo2 = RNbf16(x32 - hi - lo).  Each difference is exact in
+    binary32 and the last remainder fits a bfloat16, so hi + lo + lo2 = x32."""
+    x32 = round_f32(x)
+    hi = round_bf16(x32)
+    r1 = round_f32(x32 - hi)
+    lo = round_bf16(r1)
+    lo2 = round_bf16(round_f32(r1 - lo))
+    return hi, lo, lo2
+
+
+# Split terms of each precision, as (L part, R part).  bf16x6 keeps every term
+# whose parts' orders add to at most 2 (hi = 0, lo = 1, lo2 = 2): relative size
+# down to 2^-16, dropping lo*lo2, lo2*lo, lo2*lo2 (2^-24 and below).
 SPLIT_PASSES = {"bf16": (("hi", "hi"),),
-                "bf16x3": (("hi", "hi"), ("hi", "lo"), ("lo", "hi"))}
+                "bf16x3": (("hi", "hi"), ("hi", "lo"), ("lo", "hi")),
+                "bf16x6": (("hi", "hi"), ("hi", "lo"), ("lo", "hi"), ("hi", "lo2"), ("lo", "lo"), ("lo2", "hi"))}
+
+
+def _split_parts(L: np.ndarray, R: np.ndarray, f=lambda v: v) -> dict:
+    Lh, Ll, L2 = split3_bf16(L)
+    Rh, Rl, R2 = split3_bf16(R)
+    return {"hi": (f(Lh), f(Rh)), "lo": (f(Ll), f(Rl)), "lo2": (f(L2), f(R2))}
 
 
 def split_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
     """Exact (float64) value of the split product the tensor cores form:
     bf16:   Lhi Rhi
-    bf16x3: Lhi Rhi + Lhi Rlo + Llo Rhi   (the lo*lo term is dropped).
-    L and R are first rounded to binary32 and split with ``split_bf16``."""
-    Lh, Ll = split_bf16(L)
-    Rh, Rl = split_bf16(R)
-    parts = {"hi": (Lh, Rh), "lo": (Ll, Rl)}
+    bf16x3: Lhi Rhi + Lhi Rlo + Llo Rhi   (the lo*lo term is dropped)
+    bf16x6: those and Lhi Rlo2 + Llo Rlo + Llo2 Rhi.
+    L and R are first rounded to binary32 and split with ``split3_bf16``
+    (whose hi and lo are those of ``split_bf16``)."""
+    parts = _split_parts(L, R)
     out = np.zeros((L.shape[0], R.shape[1]))
     for a, b in SPLIT_PASSES[precision]:
         out += parts[a][0] @ parts[b][1]
@@ -662,9 +684,7 @@ def split_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
 
 def split_abs_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
     """sum_k |L_ik| |R_kj| over the same split terms (for error bounds)."""
-    Lh, Ll = split_bf16(L)
-    Rh, Rl = split_bf16(R)
-    parts = {"hi": (np.abs(Lh), np.abs(Rh)), "lo": (np.abs(Ll), np.abs(Rl))}
+    parts = _split_parts(L, R, np.abs)
     out = np.zeros((L.shape[0], R.shape[1]))
     for a, b in SPLIT_PASSES[precision]:
         out += parts[a][0] @ parts[b][1]

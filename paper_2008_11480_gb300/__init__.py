@@ -27,6 +27,7 @@ __all__ = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_inverse_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
+    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
     "ns_batch_stats", "Batch",
 ]
@@ -34,7 +35,7 @@ __all__ = [
 NS_OK, NS_NOT_CONVERGED = 0, 1
 NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_DIVERGED = -1, -2, -3, -4
 NS_ERR_TIMEOUT, NS_ERR_NONFINITE, NS_ERR_UNSUPPORTED = -5, -6, -7
-NS_FP64, NS_BF16, NS_BF16X3, NS_AUTO = 0, 2, 3, 5
+NS_FP64, NS_BF16, NS_BF16X3, NS_BF16X6, NS_AUTO = 0, 2, 3, 4, 5
 NS_MAX_HIST = 256
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -188,6 +189,10 @@ def lib() -> ctypes.CDLL:
         "ns_last_error": (ctypes.c_char_p, [_vp]),
         "ns_status_string": (ctypes.c_char_p, [_int]),
         "ns_k_split": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
+        "ns_k_split3": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
+        "ns_k_gemm_bf16x6": (_int, [_i64, _i64, _i64, ctypes.POINTER(_vp), _i64, ctypes.POINTER(_vp), _i64,
+                                     ctypes.c_float, _vp, _i64, ctypes.c_float, ctypes.c_float, _vp, _i64,
+                                     ctypes.POINTER(_vp), _i64, _vp, _vp]),
         "ns_k_gemm_bf16": (_int, [_int, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, _vp, _i64,
                                   ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, _int, _int, _vp]),
         "ns_k_gemm_f64": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
@@ -354,6 +359,28 @@ def ns_k_split(X: torch.Tensor, hi: torch.Tensor, lo: torch.Tensor, rows: int, c
     dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
     _raise(lib().ns_k_split(X.data_ptr(), dt, rows, cols, ldx, _ptr(hi, torch.bfloat16), _ptr(lo, torch.bfloat16),
                             ld, _stream_ptr(stream)), "ns_k_split")
+
+
+def ns_k_split3(X: torch.Tensor, hi: torch.Tensor, lo: torch.Tensor, lo2: torch.Tensor, rows: int, cols: int,
+                ldx: int, ld: int, stream=None) -> None:
+    dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
+    bf = torch.bfloat16
+    _raise(lib().ns_k_split3(X.data_ptr(), dt, rows, cols, ldx, _ptr(hi, bf), _ptr(lo, bf), _ptr(lo2, bf), ld,
+                             _stream_ptr(stream)), "ns_k_split3")
+
+
+def ns_k_gemm_bf16x6(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float = 1.0, C=None, ldc: int = 0,
+                     beta: float = 0.0, gamma: float = 0.0, D32=None, ldd32: int = 0, D=None, ldd16: int = 0,
+                     frob_out=None, stream=None) -> None:
+    """L, R: sequences of the three bf16 parts (hi, lo, lo2); D: None or three
+    optional bf16 outputs."""
+    bf = torch.bfloat16
+    Lp = (_vp * 3)(*[_ptr(x, bf) for x in L])
+    Rp = (_vp * 3)(*[_ptr(x, bf) for x in R])
+    Dp = None if D is None else (_vp * 3)(*[_ptr(x, bf) for x in D])
+    r = lib().ns_k_gemm_bf16x6(M, N, K, Lp, ldl, Rp, ldr, s, _ptr(C, torch.float32), ldc, beta, gamma,
+                               _ptr(D32, torch.float32), ldd32, Dp, ldd16, _ptr(frob_out), _stream_ptr(stream))
+    _raise(r, "ns_k_gemm_bf16x6")
 
 
 def ns_k_gemm_bf16(precision: int, M: int, N: int, K: int, Lhi, Llo, ldl: int, Rhi, Rlo, ldr: int, s: float = 1.0,

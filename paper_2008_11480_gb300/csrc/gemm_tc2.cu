@@ -31,8 +31,12 @@
 //
 // Shared-memory layouts per CTA are those of the one-CTA kernel with 128 R
 // columns: one pass -- L 128 x 64 (128-byte swizzle), R 64 x 128 as two 8 KiB
-// chunks of 64 columns; split products -- L_hi, L_lo 128 x 32 (64-byte
-// swizzle), R_hi, R_lo 32 x 128 as two 4 KiB chunks each.  Both are 32 KiB.
+// chunks of 64 columns (32 KiB per stage, 6 stages); split products with NP
+// parts per operand (NP = 2: hi, lo -- the bf16x3 terms; NP = 3: hi, lo, lo2
+// -- the bf16x6 terms hi.hi, hi.lo, lo.hi, hi.lo2, lo.lo, lo2.hi) -- per
+// 32-deep K slice, part p of L (128 x 32, 64-byte swizzle) and of R (32 x 128
+// as two 4 KiB chunks) at p x 8 KiB: 32 KiB per stage and 6 stages for NP = 2,
+// 48 KiB and 4 stages for NP = 3.
 #include <cstdio>
 
 #include "internal.h"
@@ -46,19 +50,30 @@ namespace {
 constexpr int kRows = 128;     // output rows per CTA (256 per pair)
 constexpr int kCols = 256;     // output columns per pair tile
 constexpr int kHalf = kCols / 2;  // R columns staged by each CTA
-constexpr int kBK = 64;
 constexpr int kThreads = 192;
-constexpr int kABytes = kRows * kBK * 2;  // 16 KiB
-constexpr int kBBytes = kHalf * kBK * 2;  // 16 KiB
-constexpr int kStageBytes = kABytes + kBBytes;
-constexpr int kStages = 6;
 constexpr uint32_t kTmemCols = 2 * kCols;  // two accumulators of 128 lanes x 256 columns
 constexpr int kBarBytes = 256;
 constexpr int kEpiStride = 36;
 constexpr int kEpiBytes = 4 * 32 * kEpiStride * 4;
-constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
-static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
+constexpr int kPartBytes = 8192;  // one split part of a 32-deep K slice (L or R)
+
+// Split term t as (L part, R part), in issue order: hi.hi, hi.lo, lo.hi,
+// hi.lo2, lo.lo, lo2.hi; bf16x3 uses the first three.
+__host__ __device__ constexpr int term_l(int t) { return (t == 2 || t == 4) ? 1 : (t == 5 ? 2 : 0); }
+__host__ __device__ constexpr int term_r(int t) { return (t == 1 || t == 4) ? 1 : (t == 3 ? 2 : 0); }
+
+template <int NP>
+struct PairCfg {
+  static constexpr int kBK = NP == 1 ? 64 : 32;          // K per stage
+  static constexpr int kABytes = NP == 1 ? 16384 : NP * kPartBytes;
+  static constexpr int kBBytes = kABytes;                 // 128 of the tile's R columns
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = (196 * 1024) / kStageBytes > 6 ? 6 : (196 * 1024) / kStageBytes;
+  static constexpr int kTerms = NP == 1 ? 1 : (NP == 2 ? 3 : 6);
+  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+  static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
+};
 
 // Work item w: problem, tile row (128-row units, this CTA's half of the pair
 // tile), tile column, and which half of the tile's columns (-1: all 256).
@@ -79,11 +94,13 @@ __device__ __forceinline__ void spin_ns(uint64_t ns) {
     if (globaltimer_ns() - t0 > ns) break;
 }
 
-template <bool X3>
+template <int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant__ TcParams p) {
+  using Cfg = PairCfg<NP>;
+  constexpr int kStages = Cfg::kStages, kABytes = Cfg::kABytes, kBBytes = Cfg::kBBytes, kBK = Cfg::kBK;
   // host-side guarantees, checked once more before any barrier: list mode and
   // multi-pass one-split products are not supported by the pair kernel
-  if (p.gprob != nullptr || (!X3 && p.npass != 1)) {
+  if (p.gprob != nullptr || (NP == 1 && p.npass != 1)) {
     if (threadIdx.x == 0) atomicExch(p.err, DEV_TIMEOUT);
     return;
   }
@@ -139,14 +156,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producers (both CTAs)
-    for (int i = 0; i < p.nprob; ++i) {
-      tma_prefetch_desc(&p.prob[i].L[0]);
-      tma_prefetch_desc(&p.prob[i].R[0]);
-      if (X3) {
-        tma_prefetch_desc(&p.prob[i].L[1]);
-        tma_prefetch_desc(&p.prob[i].R[1]);
+    for (int i = 0; i < p.nprob; ++i)
+      for (int q = 0; q < NP; ++q) {
+        tma_prefetch_desc(&p.prob[i].L[q]);
+        tma_prefetch_desc(&p.prob[i].R[q]);
       }
-    }
     int armed[kStages];
     for (int s = 0; s < kStages; ++s) armed[s] = -1;
     int stage = 0;
@@ -160,9 +174,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
       const int m0 = mt * kRows;                       // this CTA's L rows
       const int cw = half < 0 ? kHalf : kHalf / 2;     // R columns this CTA stages
       const int nb = nt * kCols + (half > 0 ? kHalf : 0) + rank * cw;
-      const uint32_t tx = 2u * static_cast<uint32_t>(kABytes + cw * kBK * 2);  // both CTAs' bytes
-      const int kstep = X3 ? kBK / 2 : kBK;
-      const int nkb = (P.K + kstep - 1) / kstep;
+      const uint32_t tx = 2u * static_cast<uint32_t>(kABytes + (half < 0 ? kBBytes : kBBytes / 2));  // both CTAs
+      const int nkb = (P.K + kBK - 1) / kBK;
       for (int kb = 0; kb < nkb; ++kb) {
         if (!mbar_wait(&empty[stage], phase ^ 1u, tlim, abort_flag)) {
           ok = false;
@@ -176,16 +189,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
           const uint32_t bar = full0 + static_cast<uint32_t>(stage * 8);
           uint8_t* a = sA + stage * kABytes;
           uint8_t* b = sB + stage * kBBytes;
-          if (X3) {
-            const int x = kb * (kBK / 2);
-            tma_load_2d_pair(a, &P.L[0], bar, x, m0);
-            tma_load_2d_pair(a + 4096, &P.L[0], bar, x, m0 + 64);
-            tma_load_2d_pair(a + 8192, &P.L[1], bar, x, m0);
-            tma_load_2d_pair(a + 12288, &P.L[1], bar, x, m0 + 64);
+          if (NP > 1) {
+            const int x = kb * kBK;
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-              tma_load_2d_pair(b + part * (kHalf * 64), &P.R[part], bar, nb, x);
-              if (half < 0) tma_load_2d_pair(b + part * (kHalf * 64) + 4096, &P.R[part], bar, nb + 64, x);
+            for (int part = 0; part < NP; ++part) {
+              tma_load_2d_pair(a + part * kPartBytes, &P.L[part], bar, x, m0);
+              tma_load_2d_pair(a + part * kPartBytes + 4096, &P.L[part], bar, x, m0 + 64);
+            }
+#pragma unroll
+            for (int part = 0; part < NP; ++part) {
+              tma_load_2d_pair(b + part * kPartBytes, &P.R[part], bar, nb, x);
+              if (half < 0) tma_load_2d_pair(b + part * kPartBytes + 4096, &P.R[part], bar, nb + 64, x);
             }
           } else {
             const int x = kb * kBK;
@@ -230,8 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
       int pi, mt, nt, half;
       pair_item(p, w, 0, pi, mt, nt, half);
       const TcProblem& P = p.prob[pi];
-      const int kstep = X3 ? kBK / 2 : kBK;
-      const int nkb = (P.K + kstep - 1) / kstep;
+      const int nkb = (P.K + kBK - 1) / kBK;
       const uint32_t idesc = half < 0 ? idesc_full : idesc_half;
       if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, tlim, abort_flag)) {
         ok = false;
@@ -248,17 +261,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA + stage * kABytes);
         const uint32_t b_base = smem_u32(sB + stage * kBBytes);
-        if (X3) {
+        if (NP > 1) {
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            const uint64_t ah = make_sdesc(a_base + 32u * k, 16u, 512u, kSwz64);
-            const uint64_t al = make_sdesc(a_base + 8192u + 32u * k, 16u, 512u, kSwz64);
-            const uint64_t bh = make_sdesc(b_base + 2048u * k, 4096u, 1024u);
-            const uint64_t bl = make_sdesc(b_base + static_cast<uint32_t>(kHalf * 64) + 2048u * k, 4096u, 1024u);
-            tc_mma_bf16_pair(d_tmem, ah, bh, idesc, accumulate);
-            accumulate = 1;
-            tc_mma_bf16_pair(d_tmem, ah, bl, idesc, 1u);
-            tc_mma_bf16_pair(d_tmem, al, bh, idesc, 1u);
+#pragma unroll
+            for (int t = 0; t < Cfg::kTerms; ++t) {
+              const uint64_t ad =
+                  make_sdesc(a_base + static_cast<uint32_t>(term_l(t) * kPartBytes) + 32u * k, 16u, 512u, kSwz64);
+              const uint64_t bd =
+                  make_sdesc(b_base + static_cast<uint32_t>(term_r(t) * kPartBytes) + 2048u * k, 4096u, 1024u);
+              tc_mma_bf16_pair(d_tmem, ad, bd, idesc, accumulate);
+              accumulate = 1;
+            }
           }
         } else {
 #pragma unroll
@@ -315,8 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
       // whole and half-width tiles as separate constant-width instances
       const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kCols);
       float* wb = ebuf + q * 32 * kEpiStride;
-      const float frob = half < 0 ? tc::epilogue_tile<kCols, kEpiStride>(P, m0, n0, q, lane, wb, tq)
-                                  : tc::epilogue_tile<kHalf, kEpiStride>(P, m0, n0, q, lane, wb, tq);
+      const float frob = half < 0 ? tc::epilogue_tile<kCols, kEpiStride, NP == 3>(P, m0, n0, q, lane, wb, tq)
+                                  : tc::epilogue_tile<kHalf, kEpiStride, NP == 3>(P, m0, n0, q, lane, wb, tq);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty0 + static_cast<uint32_t>(acc * 8));
@@ -349,8 +363,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
   cluster_sync_all();
 }
 
-template <bool X3>
+template <int NP>
 cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
+  constexpr int kSmem = PairCfg<NP>::kSmem;
   static int max_clusters = -1;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -364,11 +379,11 @@ cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (max_clusters < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc2<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc2<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(2 * (num_sms / 2));
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc2<X3>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc2<NP>, &cfg);
     if (e != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = num_sms / 2;
@@ -386,14 +401,19 @@ cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
   const int items = q.total_tiles + q.pair_tail;
   const int clusters = items < max_clusters ? items : max_clusters;
   cfg.gridDim = dim3(2 * clusters);
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<X3>, q);
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<NP>, q);
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_tc_pair(const TcParams& p, bool x3, int num_sms, cudaStream_t s) {
-  if (p.gprob != nullptr || (!x3 && p.npass != 1)) return cudaErrorInvalidValue;
-  return x3 ? launch_pair<true>(p, num_sms, s) : launch_pair<false>(p, num_sms, s);
+cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaStream_t s) {
+  if (p.gprob != nullptr || (parts == 1 && p.npass != 1)) return cudaErrorInvalidValue;
+  switch (parts) {
+    case 1: return launch_pair<1>(p, num_sms, s);
+    case 2: return launch_pair<2>(p, num_sms, s);
+    case 3: return launch_pair<3>(p, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace nsgb

@@ -22,8 +22,8 @@ constexpr int kTcMaxProblems = 4;
 // split, index 1 the lo part.  Outputs (each optional): the f32 master D32,
 // the bf16 split Dhi/Dlo, and per-(tile, epilogue warp) partial sums of D^2.
 struct TcProblem {
-  CUtensorMap L[2];
-  CUtensorMap R[2];
+  CUtensorMap L[3];  // split parts hi, lo, lo2 (lo2: split-bf16 x6 products only)
+  CUtensorMap R[3];
   int M, N, K;
   int tiles_m;     // ceil(M / 128)
   int tiles_n;     // ceil(N / BN)
@@ -37,6 +37,7 @@ struct TcProblem {
   float* D32;
   bf16* Dhi;
   bf16* Dlo;
+  bf16* Dlo2;  // third split part of D (x6 products), may be null
   double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4); the CTA-pair
                           // kernel writes 8 (two half-width slots of 4)
 };
@@ -55,7 +56,8 @@ struct TcParams {
   // work item w is items[w]; prob[] and nprob are unused and CM must be 1.
   const TcProblem* gprob;
   const TcItem* items;
-  int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3)
+  int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3); 6: those and
+              // hi*lo2 + lo*lo + lo2*hi (bf16x6), one pass per term
   int debug_stall_iter;  // -1 for none; else the producer withholds that load
   int pair_tail;  // CTA-pair kernel: the last pair_tail tiles each run as two
                   // half-width (256 x 128) items (set by its launcher)
@@ -71,10 +73,11 @@ cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_s
 // CTA-pair variant (cta_group::2): 256 x 256 output tiles, clusters of two
 // CTAs along M, tile bookkeeping of BN = 256, CM = 2 (tc_items(M, N, 256, 2)
 // tiles, 8 partial sums per tc_tiles(M, N, 256) tile).  Single-problem-table
-// mode only (p.gprob == nullptr); x3 selects split products, otherwise
-// p.npass == 1.  Tiles of a last, partial wave run as two half-width items
-// each when that shortens the wave.
-cudaError_t launch_gemm_tc_pair(const TcParams& p, bool x3, int num_sms, cudaStream_t s);
+// mode only (p.gprob == nullptr).  parts: 1 one bf16 pass (p.npass == 1);
+// 2 the bf16x3 terms of L[0..1], R[0..1] (role 1 / 2 maps); 3 the bf16x6 terms
+// of L[0..2], R[0..2], D written with its third part (Dlo2).  Tiles of a last,
+// partial wave run as two half-width items each when that shortens the wave.
+cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
 int tc_items(int M, int N, int BN, int CM);
 
@@ -117,10 +120,11 @@ cudaError_t launch_reduce_sum(const double* partials, int nblocks, int ncols, do
 cudaError_t launch_reduce_max(const double* partials, int nblocks, double* out, cudaStream_t s);
 // Split an FP64 or FP32 rows x cols matrix into bf16 hi/lo (ld elements) and,
 // optionally, its f32 rounding.
+// (lo2, when given: the third part bf16(v - hi - lo) of bf16x6 operands)
 cudaError_t launch_split_f64(const double* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, float* x32,
-                             int64_t ld, cudaStream_t s);
+                             int64_t ld, cudaStream_t s, bf16* lo2 = nullptr);
 cudaError_t launch_split_f32(const float* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, int64_t ld,
-                             cudaStream_t s);
+                             cudaStream_t s, bf16* lo2 = nullptr);
 // G = alpha I where alpha is read on the device: mode 0 -> 1/sqrt(scal[0])
 // (Frobenius), mode 1 -> 1/(scal[1]/2 + 1e-8 scal[1]) (infinity norm).
 cudaError_t launch_init_g0_mp(const double* scal, int mode, int n, int64_t ld, float* G32, bf16* hi, bf16* lo,

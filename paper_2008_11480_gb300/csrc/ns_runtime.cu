@@ -36,9 +36,11 @@ struct MpMat {
   float* m32 = nullptr;
   bf16* hi = nullptr;
   bf16* lo = nullptr;
+  bf16* lo2 = nullptr;            // third split part (contexts that may run bf16x6)
   CUtensorMap map_hi, map_lo;    // one-pass products (either operand)
   CUtensorMap l3_hi, l3_lo;      // split products, as the L operand
   CUtensorMap r3_hi, r3_lo;      // split products, as the R operand
+  CUtensorMap l3_lo2, r3_lo2;    // third part, as the L / R operand of bf16x6 products
 };
 
 struct GemmSpec {
@@ -94,6 +96,7 @@ struct ns_ctx {
 
   // mixed precision
   bool mp_ready = false;
+  bool x6 = false;  // bf16x6 products possible: MpMat third parts allocated
   MpMat A, G[2], X[2], F, P[2];
   float *A1 = nullptr, *A2 = nullptr;  // f32 limbs of A for the residual
   // composite
@@ -161,6 +164,11 @@ ns_status alloc_mp(ns_ctx* ctx, MpMat& m, bool with32) {
       !encode_bf16_map(&m.l3_hi, m.hi, ld, ld, ld, 1) || !encode_bf16_map(&m.l3_lo, m.lo, ld, ld, ld, 1) ||
       !encode_bf16_map(&m.r3_hi, m.hi, ld, ld, ld, 2) || !encode_bf16_map(&m.r3_lo, m.lo, ld, ld, ld, 2))
     return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  if (ctx->x6) {
+    NS_TRY(alloc(ctx, &m.lo2, cnt));
+    if (!encode_bf16_map(&m.l3_lo2, m.lo2, ld, ld, ld, 1) || !encode_bf16_map(&m.r3_lo2, m.lo2, ld, ld, ld, 2))
+      return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  }
   return NS_OK;
 }
 
@@ -342,11 +350,16 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   const int n = static_cast<int>(ctx->n);
   int bn = 256, cm = 1;
   pick_tile(ctx, nspec, &bn, &cm);
+  const bool x6 = prec == NS_BF16X6;
+  if (x6) {  // the three-part terms run on CTA pairs only
+    bn = 256;
+    cm = -2;
+  }
   const bool x3 = prec == NS_BF16X3 && bn != 192;
   TcParams p;
   memset(&p, 0, sizeof(p));
   p.nprob = nspec;
-  p.npass = prec == NS_BF16X3 ? 3 : 1;
+  p.npass = x6 ? 6 : (prec == NS_BF16X3 ? 3 : 1);
   p.debug_stall_iter = -1;
   p.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
   p.err = ctx->derr;
@@ -356,11 +369,16 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   for (int i = 0; i < nspec; ++i) {
     const GemmSpec& g = specs[i];
     TcProblem& P = p.prob[i];
-    if (x3) {
+    if (x3 || x6) {
       P.L[0] = g.L->l3_hi;
       P.L[1] = g.L->l3_lo;
       P.R[0] = g.R->r3_hi;
       P.R[1] = g.R->r3_lo;
+      if (x6) {
+        P.L[2] = g.L->l3_lo2;
+        P.R[2] = g.R->r3_lo2;
+        P.Dlo2 = g.D->lo2;
+      }
     } else {
       P.L[0] = g.L->map_hi;
       P.L[1] = g.L->map_lo;
@@ -403,7 +421,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   p.total_tiles = tile;
   EventPair* e = ev_begin(ctx, true);
   if (cm == -2)
-    NS_CK(launch_gemm_tc_pair(p, x3, ctx->num_sms, ctx->stream));
+    NS_CK(launch_gemm_tc_pair(p, x6 ? 3 : (x3 ? 2 : 1), ctx->num_sms, ctx->stream));
   else
     NS_CK(launch_gemm_tc(p, bn, cm, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
@@ -714,7 +732,8 @@ int products_per_step(const ns_ctx* ctx) {
 }
 double step_cost(const ns_ctx* ctx, bool fp64, int prec) {
   const double n = static_cast<double>(ctx->n);
-  const double flops = products_per_step(ctx) * 2.0 * n * n * n * (prec == NS_BF16X3 ? 3.0 : 1.0);
+  const double passes = prec == NS_BF16X6 ? 6.0 : (prec == NS_BF16X3 ? 3.0 : 1.0);
+  const double flops = products_per_step(ctx) * 2.0 * n * n * n * passes;
   return flops / (fp64 ? 1.1e12 : 1.0e15) + 3e-6 * products_per_step(ctx);
 }
 double sweep_cost(const ns_ctx* ctx, bool fp64, int nrhs) {
@@ -790,6 +809,22 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
   }
   S.cur = 0;
+
+  // bf16x6 operands: the third split parts of A (from its first f32 limb, the
+  // source of its hi/lo) and of G_k (from its f32 master) before the first
+  // bf16x6 product; every bf16x6 product writes its output's third part
+  bool a_lo2 = false;
+  auto x6_prepare = [&](int cur) -> ns_status {
+    if (!a_lo2) {
+      NS_CK(launch_split_f32(ctx->A1, ld, n, n, ctx->A.hi, ctx->A.lo, ld, s, ctx->A.lo2));
+      ctx->launches++;
+      a_lo2 = true;
+    }
+    NS_CK(launch_split_f32(ctx->G[cur].m32, ld, n, n, ctx->G[cur].hi, ctx->G[cur].lo, ld, s, ctx->G[cur].lo2));
+    ctx->launches++;
+    return NS_OK;
+  };
+  if (!fp64 && ctx->opt.precision == NS_BF16X6) NS_TRY(x6_prepare(0));
 
   // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
   // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
@@ -1081,22 +1116,48 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           const double t_step = step_cost(ctx, fp64, prec);
           if (need <= sweeps_left && need * t_sweep <= t_step + 2.0 * t_sweep) stop = true;
         }
+        // AUTO past a bf16x3 floor: bf16x6 products (a lower floor) where the
+        // floor is too high for Richardson to finish cheaply
+        const bool can_x6 = autop && ctx->x6 && prec == NS_BF16X3;
+        bool floor_hit = false, esc = false;
         if (!stop && prev_frob < 1.0 && frob >= 0.5 * prev_frob) {
-          stop = true;  // quadratic contraction has stalled at the precision floor
+          floor_hit = true;  // quadratic contraction has stalled at the precision floor
+          if (can_x6) {
+            const double f = std::min(frob, prev_frob);
+            if (!rich || tol <= 0) {
+              esc = f > 1e-3;
+            } else {
+              const double need = std::ceil(std::log(tol / last_rr) / std::log(f));
+              esc = need > sweeps_left ||
+                    need * sweep_cost(ctx, fp64, S.nrhs) > 2.0 * step_cost(ctx, fp64, NS_BF16X6);
+            }
+          }
+        }
+        if (!stop && !floor_hit && done >= 2 && frob > 1.0 && std::isfinite(prev_ratio) && ratio > 0.9 &&
+            ratio > prev_ratio + 0.02) {
+          // the contraction got worse again: the floor of this precision lies
+          // above ||F||_F = 1, more steps only repeat it (Richardson takes
+          // over if rho(I - A G) < 1, unless bf16x6 can still go lower)
+          floor_hit = true;
+          esc = can_x6;
+        }
+        if (floor_hit) {
           if (frob > prev_frob) {
             S.cur ^= 1;  // keep the better previous estimate
             if (comp) S.ccur ^= 1;
+            if (esc) {
+              done--;
+              if (st) st->rollbacks++;
+            }
           }
-        }
-        if (!stop && done >= 2 && frob > 1.0 && std::isfinite(prev_ratio) && ratio > 0.9 && ratio > prev_ratio + 0.02) {
-          // at the highest precision the contraction got worse again: the
-          // floor of this precision lies above ||F||_F = 1, more steps only
-          // repeat it (Richardson takes over if rho(I - A G) < 1)
+          if (esc) {
+            prec = NS_BF16X6;
+            NS_TRY(x6_prepare(S.cur));
+            prev_frob = INFINITY;
+            prev_ratio = INFINITY;
+            goto recompute_F;
+          }
           stop = true;
-          if (frob > prev_frob) {
-            S.cur ^= 1;
-            if (comp) S.ccur ^= 1;
-          }
         }
         if (stop) ns_active = false;
       }
@@ -1327,8 +1388,12 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   else
     ns_default_options(&o);
   if (!order_ok(order, o.form)) return NS_ERR_ARG;
-  if (o.precision != NS_FP64 && o.precision != NS_BF16 && o.precision != NS_BF16X3 && o.precision != NS_AUTO)
+  if (o.precision != NS_FP64 && o.precision != NS_BF16 && o.precision != NS_BF16X3 && o.precision != NS_BF16X6 &&
+      o.precision != NS_AUTO)
     return NS_ERR_ARG;
+  // bf16x6 operands carry a third split part that the composite loops and the
+  // elementwise sum of the nested order-45 chain do not produce
+  if (o.precision == NS_BF16X6 && (n_rates > 0 || o.form == 3)) return NS_ERR_UNSUPPORTED;
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
@@ -1343,6 +1408,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   c->order = order;
   c->rates.assign(rates, rates + n_rates);
   c->opt = o;
+  c->x6 = (o.precision == NS_BF16X6 || o.precision == NS_AUTO) && n_rates == 0 && o.form != 3;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -1604,32 +1670,41 @@ ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int
   return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 
-ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
-                         int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
-                         int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
-                         int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream) {
-  if (precision != NS_BF16 && precision != NS_BF16X3) return NS_ERR_ARG;
+namespace {
+// The single-product entry points: parts = 1 (bf16), 2 (bf16x3) or 3 (bf16x6)
+// split parts per operand in L[], R[]; D[] = hi, lo, lo2 outputs.
+ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl,
+                      const void* const* R, int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma,
+                      float* D32, int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, int bn,
+                      int cluster_m, void* stream) {
   if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
-  if (!Lhi || !Rhi || (precision == NS_BF16X3 && (!Llo || !Rlo))) return NS_ERR_ARG;
-  if (ldl < K || ldr < N || ldl % 8 || ldr % 8 || !al16(Lhi) || !al16(Rhi)) return NS_ERR_ARG;
-  if (precision == NS_BF16X3 && (!al16(Llo) || !al16(Rlo))) return NS_ERR_ARG;
+  for (int q = 0; q < parts; ++q)
+    if (!L[q] || !R[q] || !al16(L[q]) || !al16(R[q])) return NS_ERR_ARG;
+  if (ldl < K || ldr < N || ldl % 8 || ldr % 8) return NS_ERR_ARG;
   if (C && (ldc < N || ldc % 4 || !al16(C))) return NS_ERR_ARG;
   if (D32 && (ldd32 < N || ldd32 % 4 || !al16(D32))) return NS_ERR_ARG;
-  if ((Dhi || Dlo) && (ldd16 < N || ldd16 % 8)) return NS_ERR_ARG;
-  if ((Dhi && !al16(Dhi)) || (Dlo && !al16(Dlo)) || (Dlo && !Dhi)) return NS_ERR_ARG;
+  if ((D[0] || D[1] || D[2]) && (ldd16 < N || ldd16 % 8)) return NS_ERR_ARG;
+  for (int q = 0; q < 3; ++q)
+    if (D[q] && !al16(D[q])) return NS_ERR_ARG;
+  if ((D[1] && !D[0]) || (D[2] && !D[1])) return NS_ERR_ARG;
+  if (parts == 3 && cluster_m == 0) cluster_m = -2;  // bf16x6 runs on CTA pairs only
+  if (parts == 3 && cluster_m != -2) return NS_ERR_ARG;
   if (cluster_m == -2 && bn == 0) bn = 256;
   if (bn == 0) bn = N >= 2048 ? 256 : (N > 64 ? 128 : 64);
   if (bn != 64 && bn != 128 && bn != 192 && bn != 256) return NS_ERR_ARG;
   const int tiles_m = static_cast<int>((M + 127) / 128);
   bool pair = cluster_m == -2;
-  if (pair && (bn != 256 || tiles_m % 2 != 0)) return NS_ERR_ARG;
+  // CTA pairs need 256-column tiles; one-pass and bf16x3 pairs also an even
+  // row-tile count (bf16x6 pairs accept an odd one: the last pair's second
+  // CTA then covers rows past M, loaded as zeros and not written)
+  if (pair && (bn != 256 || (parts < 3 && tiles_m % 2 != 0))) return NS_ERR_ARG;
   if (pair) cluster_m = 2;  // same item and partial-sum bookkeeping as two-CTA clusters
   if (cluster_m == 0 && !pair && bn == 256 && tiles_m % 2 == 0) {
     pair = true;  // automatic: CTA pairs where they apply
     cluster_m = 2;
   }
   if (cluster_m == 0) cluster_m = bn < 192 ? 1 : (tiles_m % 2 == 0 ? 2 : 1);
-  if (precision == NS_BF16X3 && bn == 192 && cluster_m > 1) cluster_m = 1;
+  if (parts == 2 && bn == 192 && cluster_m > 1) cluster_m = 1;
   if (cluster_m != 1 && cluster_m != 2 && cluster_m != 4) return NS_ERR_ARG;
   if (cluster_m > 1 && bn < 192) return NS_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1639,7 +1714,7 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   TcParams p;
   memset(&p, 0, sizeof(p));
   p.nprob = 1;
-  p.npass = precision == NS_BF16X3 ? 3 : 1;
+  p.npass = parts == 3 ? 6 : (parts == 2 ? 3 : 1);
   p.debug_stall_iter = -1;
   p.timeout_ns = 2000000000ull;
   // host-side fault injection for the failure-detection tests: the producer
@@ -1652,14 +1727,14 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
     if (ms > 0 && ms <= 10000) p.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
   }
   TcProblem& P = p.prob[0];
-  const bool x3 = p.npass == 3 && bn != 192;
-  const int lr = x3 ? 1 : 0, rr = x3 ? 2 : 0;
-  if (!encode_bf16_map(&P.L[0], Lhi, M, K, ldl, lr) || !encode_bf16_map(&P.R[0], Rhi, K, N, ldr, rr))
-    return NS_ERR_ARG;
-  if (p.npass == 3 &&
-      (!encode_bf16_map(&P.L[1], Llo, M, K, ldl, lr) || !encode_bf16_map(&P.R[1], Rlo, K, N, ldr, rr)))
-    return NS_ERR_ARG;
-  if (p.npass == 1) {
+  // split-operand kernels (role 1 / 2 maps) for bf16x3 except with 192-column
+  // tiles (three one-pass products instead) and always for bf16x6
+  const bool split = parts == 3 || (parts == 2 && bn != 192);
+  const int lr = split ? 1 : 0, rr = split ? 2 : 0;
+  for (int q = 0; q < parts; ++q)
+    if (!encode_bf16_map(&P.L[q], L[q], M, K, ldl, lr) || !encode_bf16_map(&P.R[q], R[q], K, N, ldr, rr))
+      return NS_ERR_ARG;
+  if (parts == 1) {
     P.L[1] = P.L[0];
     P.R[1] = P.R[0];
   }
@@ -1678,8 +1753,9 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   P.ldc = static_cast<int>(ldc);
   P.D32 = D32;
   P.ldd32 = static_cast<int>(ldd32);
-  P.Dhi = static_cast<bf16*>(Dhi);
-  P.Dlo = static_cast<bf16*>(Dlo);
+  P.Dhi = static_cast<bf16*>(D[0]);
+  P.Dlo = static_cast<bf16*>(D[1]);
+  P.Dlo2 = static_cast<bf16*>(D[2]);
   P.ldd16 = static_cast<int>(ldd16);
   p.total_tiles = P.tile_count;
   void* scratch = nullptr;
@@ -1692,7 +1768,8 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   cudaMemsetAsync(scratch, 0, sizeof(int) * 4, st);
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
-  cudaError_t e = pair ? launch_gemm_tc_pair(p, x3, sms, st) : launch_gemm_tc(p, bn, cluster_m, x3, sms, st);
+  cudaError_t e = pair ? launch_gemm_tc_pair(p, parts == 3 ? 3 : (split ? 2 : 1), sms, st)
+                       : launch_gemm_tc(p, bn, cluster_m, split, sms, st);
   if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * per_tile, 1, frob_out, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1700,6 +1777,41 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return NS_ERR_CUDA;
   return herr == DEV_OK ? NS_OK : NS_ERR_TIMEOUT;
+}
+}  // namespace
+
+ns_status ns_k_split3(const void* X, int x_dtype, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo,
+                      void* lo2, int64_t ld, void* stream) {
+  if (!X || !hi || !lo || !lo2 || rows < 0 || cols < 0 || ldx < cols || ld < cols || (x_dtype != 0 && x_dtype != 1))
+    return NS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int r = static_cast<int>(rows), c = static_cast<int>(cols);
+  bf16 *h = static_cast<bf16*>(hi), *l = static_cast<bf16*>(lo), *l2 = static_cast<bf16*>(lo2);
+  cudaError_t e = x_dtype == 0 ? launch_split_f64(static_cast<const double*>(X), ldx, r, c, h, l, nullptr, ld, s, l2)
+                               : launch_split_f32(static_cast<const float*>(X), ldx, r, c, h, l, ld, s, l2);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
+                         int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
+                         int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
+                         int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream) {
+  if (precision != NS_BF16 && precision != NS_BF16X3) return NS_ERR_ARG;
+  const void* L[3] = {Lhi, Llo, nullptr};
+  const void* R[3] = {Rhi, Rlo, nullptr};
+  void* D[3] = {Dhi, Dlo, nullptr};
+  if (!Lhi || !Rhi || (precision == NS_BF16X3 && (!Llo || !Rlo))) return NS_ERR_ARG;
+  return k_gemm_impl(precision == NS_BF16X3 ? 2 : 1, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D,
+                     ldd16, frob_out, bn, cluster_m, stream);
+}
+
+ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl, const void* const* R,
+                           int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma, float* D32,
+                           int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, void* stream) {
+  if (!L || !R) return NS_ERR_ARG;
+  void* none[3] = {nullptr, nullptr, nullptr};
+  return k_gemm_impl(3, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D ? D : none, ldd16, frob_out,
+                     256, -2, stream);
 }
 
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,

@@ -37,7 +37,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 //
 //   D = s * acc + beta * C + gamma * I
 //
-// written as f32 (D32) and as its bf16 hi / lo split (Dhi, Dlo).  `tmem` is
+// written as f32 (D32) and as its bf16 split: hi = bf16(D), lo = bf16(D - hi)
+// (Dhi, Dlo) and, with kLo2 (operands of split-bf16 x6 products),
+// lo2 = bf16(D - hi - lo) (Dlo2).  `tmem` is
 // the TMEM address of the quarter's first lane at the tile's first column;
 // `wb` is this warp's 32 x kStride float transpose buffer.  Each 32-column
 // chunk: tcgen05.ld gives lane l row (32q + l); the warp transposes it through
@@ -45,7 +47,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // segments (8 lanes x 16 B per row, 4 rows per instruction) instead of one
 // 16-byte piece of 32 different rows.  Returns this lane's sum of D^2 over its
 // in-range elements.
-template <int BN, int kStride>
+template <int BN, int kStride, bool kLo2 = false>
 __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n0, int q, int lane, float* wb,
                                                uint32_t tmem) {
   const int sub_r = lane >> 3;       // row within a group of 4
@@ -60,6 +62,7 @@ __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n
   float* __restrict__ e_D32 = P.D32;
   bf16* __restrict__ e_Dhi = P.Dhi;
   bf16* __restrict__ e_Dlo = P.Dlo;
+  bf16* __restrict__ e_Dlo2 = kLo2 && P.Dlo != nullptr ? P.Dlo2 : nullptr;
   float frob = 0.f;
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -131,6 +134,16 @@ __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n
             *reinterpret_cast<uint2*>(e_Dlo + o16) =
                 make_uint2(pack_bf16x2(v[0] - __bfloat162float(h0), v[1] - __bfloat162float(h1)),
                            pack_bf16x2(v[2] - __bfloat162float(h2), v[3] - __bfloat162float(h3)));
+          if (kLo2 && e_Dlo2 != nullptr) {
+            const __nv_bfloat16 hh[4] = {h0, h1, h2, h3};
+            float t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float r = v[u] - __bfloat162float(hh[u]);
+              t[u] = r - __bfloat162float(__float2bfloat16_rn(r));
+            }
+            *reinterpret_cast<uint2*>(e_Dlo2 + o16) = make_uint2(pack_bf16x2(t[0], t[1]), pack_bf16x2(t[2], t[3]));
+          }
         }
       } else {
 #pragma unroll
@@ -143,6 +156,10 @@ __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n
             const __nv_bfloat16 h = __float2bfloat16_rn(v[t]);
             e_Dhi[o16] = h;
             if (e_Dlo != nullptr) e_Dlo[o16] = __float2bfloat16_rn(v[t] - __bfloat162float(h));
+            if (kLo2 && e_Dlo2 != nullptr) {
+              const float r = v[t] - __bfloat162float(h);
+              e_Dlo2[o16] = __float2bfloat16_rn(r - __bfloat162float(__float2bfloat16_rn(r)));
+            }
           }
         }
       }

@@ -293,30 +293,36 @@ __global__ void k_reduce_max(const double* __restrict__ part, int nblocks, doubl
 
 // ---------------------------------------------------------------- splits
 // hi = RN_bf16(RN_f32(x)), lo = RN_bf16(RN_f32(x) - hi) (difference exact in f32).
+// bf16 split of binary32 values: hi = bf16(v), lo = bf16(v - hi) and, when
+// lo2 is given, lo2 = bf16(v - hi - lo); every difference is exact in binary32.
+__device__ __forceinline__ void split_store(float v, bf16* hi, bf16* lo, bf16* lo2, int64_t o) {
+  const bf16 h = __float2bfloat16_rn(v);
+  const float r = v - __bfloat162float(h);
+  const bf16 l = __float2bfloat16_rn(r);
+  hi[o] = h;
+  lo[o] = l;
+  if (lo2 != nullptr) lo2[o] = __float2bfloat16_rn(r - __bfloat162float(l));
+}
+
 __global__ void k_split_f64(const double* __restrict__ X, int64_t ldx, int rows, int cols, bf16* __restrict__ hi,
-                            bf16* __restrict__ lo, float* __restrict__ x32, int64_t ld) {
+                            bf16* __restrict__ lo, bf16* __restrict__ lo2, float* __restrict__ x32, int64_t ld) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = e / cols, c = e % cols;
     const float v = static_cast<float>(X[r * ldx + c]);
-    const bf16 h = __float2bfloat16_rn(v);
-    hi[r * ld + c] = h;
-    lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    split_store(v, hi, lo, lo2, r * ld + c);
     if (x32 != nullptr) x32[r * ld + c] = v;
   }
 }
 
 __global__ void k_split_f32(const float* __restrict__ X, int64_t ldx, int rows, int cols, bf16* __restrict__ hi,
-                            bf16* __restrict__ lo, int64_t ld) {
+                            bf16* __restrict__ lo, bf16* __restrict__ lo2, int64_t ld) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = e / cols, c = e % cols;
-    const float v = X[r * ldx + c];
-    const bf16 h = __float2bfloat16_rn(v);
-    hi[r * ld + c] = h;
-    lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    split_store(X[r * ldx + c], hi, lo, lo2, r * ld + c);
   }
 }
 
@@ -527,18 +533,18 @@ cudaError_t launch_reduce_max(const double* part, int nblocks, double* out, cuda
 }
 
 cudaError_t launch_split_f64(const double* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, float* x32,
-                             int64_t ld, cudaStream_t s) {
+                             int64_t ld, cudaStream_t s, bf16* lo2) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
   if (total <= 0) return cudaSuccess;
-  k_split_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, x32, ld);
+  k_split_f64<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, lo2, x32, ld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_f32(const float* X, int64_t ldx, int rows, int cols, bf16* hi, bf16* lo, int64_t ld,
-                             cudaStream_t s) {
+                             cudaStream_t s, bf16* lo2) {
   const int64_t total = static_cast<int64_t>(rows) * cols;
   if (total <= 0) return cudaSuccess;
-  k_split_f32<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, ld);
+  k_split_f32<<<ew_grid(total), 256, 0, s>>>(X, ldx, rows, cols, hi, lo, lo2, ld);
   return cudaGetLastError();
 }
 

@@ -98,3 +98,24 @@ def test_solve_after_injected_timeout(inject):
         r = ctx.solve(torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev), iters=60, tol=1e-10)
     assert r.status == nsgb.NS_OK
     assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10
+
+
+def test_x6_pair_withheld_load_times_out(inject):
+    on, off = inject
+    M, N, K = 256, 256, 256
+    rng = np.random.default_rng(80)
+    parts = []
+    for shape in ((M, K), (K, N)):
+        X = torch.from_numpy(rng.standard_normal(shape) * 0.05).to(dev)
+        p3 = [torch.zeros(shape, dtype=torch.bfloat16, device=dev) for _ in range(3)]
+        nsgb.ns_k_split3(X, *p3, shape[0], shape[1], shape[1], shape[1])
+        parts.append(p3)
+    D32 = torch.zeros((M, N), dtype=torch.float32, device=dev)
+    on(2)
+    with pytest.raises(nsgb.NSError) as ei:
+        nsgb.ns_k_gemm_bf16x6(M, N, K, parts[0], K, parts[1], N, -1.0, None, 0, 0.0, 1.0, D32, N)
+    assert ei.value.status == nsgb.NS_ERR_TIMEOUT
+    off()
+    nsgb.ns_k_gemm_bf16x6(M, N, K, parts[0], K, parts[1], N, -1.0, None, 0, 0.0, 1.0, D32, N)
+    torch.cuda.synchronize()
+    assert torch.isfinite(D32).all()

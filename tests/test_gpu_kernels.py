@@ -322,3 +322,111 @@ def test_resid_x2(n, nrhs):
     assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
     assert np.median(err / absp) <= 2.0 ** -44
     assert np.allclose(rsq.cpu().numpy(), np.sum(ref * ref, axis=0), rtol=1e-6)
+
+
+# ---------------------------------------------------------------- split-bf16 x6
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("rows,cols", [(1, 1), (130, 70), (513, 257)])
+def test_split3_bit_exact(dtype, rows, cols):
+    X = rnd((rows, cols), 90 + rows, scale=3.0)
+    ld = rup(cols)
+    Xd = torch.from_numpy(X).to(dev).to(dtype)
+    parts = [torch.zeros((rows, ld), dtype=torch.bfloat16, device=dev) for _ in range(3)]
+    nsgb.ns_k_split3(Xd, *parts, rows, cols, cols, ld)
+    torch.cuda.synchronize()
+    want = O.split3_bf16(Xd.double().cpu().numpy())
+    for got, w in zip(parts, want):
+        assert np.array_equal(got[:, :cols].double().cpu().numpy(), w)
+
+
+def gpu_split3(X, ld):
+    Xd = to_dev_padded(X, ld)
+    parts = [torch.zeros((X.shape[0], ld), dtype=torch.bfloat16, device=dev) for _ in range(3)]
+    nsgb.ns_k_split3(Xd, *parts, X.shape[0], X.shape[1], ld, ld)
+    return parts
+
+
+def run_gemm_x6(M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, scale=1.0, frob=True):
+    L = rnd((M, K), seed, scale)
+    R = rnd((K, N), seed + 1, scale)
+    C = rnd((M, N), seed + 2) if with_c else None
+    ldl, ldr, ldd = rup(K), rup(N), rup(N)
+    Lp, Rp = gpu_split3(L, ldl), gpu_split3(R, ldr)
+    Cd = to_dev_padded(O.round_f32(C), ldd, torch.float32) if with_c else None
+    D32 = torch.full((M, ldd), 7.0, dtype=torch.float32, device=dev)
+    Dp = [torch.zeros((M, ldd), dtype=torch.bfloat16, device=dev) for _ in range(3)]
+    fro = torch.zeros(1, dtype=torch.float64, device=dev) if frob else None
+    nsgb.ns_k_gemm_bf16x6(M, N, K, Lp, ldl, Rp, ldr, s, Cd, ldd if with_c else 0, beta, gamma, D32, ldd, Dp, ldd,
+                          fro)
+    torch.cuda.synchronize()
+    prod = O.split_product(L, R, "bf16x6")
+    absprod = O.split_abs_product(L, R, "bf16x6")
+    ref = O.gemm_epilogue(prod, s, O.round_f32(C) if with_c else None, beta, gamma)
+    out = D32.cpu().numpy()[:, :N].astype(np.float64)
+    assert np.all(D32.cpu().numpy()[:, N:] == 7.0), "wrote past N"
+    cabs = np.abs(beta * O.round_f32(C)) if with_c else 0.0
+    tol = K * 2.0 ** -23 * absprod * abs(s) + 2.0 ** -22 * (np.abs(ref) + cabs + abs(gamma)) + 1e-30
+    err = np.abs(out - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    # the three outputs are the exact split of the f32 result
+    parts = [d.double().cpu().numpy()[:, :N] for d in Dp]
+    assert np.array_equal(parts[0] + parts[1] + parts[2], out)
+    want = O.split3_bf16(out)
+    for got, w in zip(parts, want):
+        assert np.array_equal(got, w)
+    if frob:
+        assert float(fro.item()) == pytest.approx(float(np.sum(out * out)), rel=1e-6)
+    return err, tol
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (250, 300, 129), (200, 130, 33), (384, 520, 200),
+                                   (1, 1, 1), (640, 512, 1024)])
+def test_gemm_x6_pairs(M, N, K):
+    """Split-bf16 x6 on CTA pairs: six terms per 32-deep K slice; ragged tails
+    and odd row-tile counts (M = 384, 640: the last pair's second CTA lies past
+    M); the F = I - A G epilogue."""
+    run_gemm_x6(M, N, K, seed=M + 3 * N + K, s=-1.0, gamma=1.0, scale=0.05)
+
+
+def test_gemm_x6_accumulate_epilogue():
+    run_gemm_x6(500, 333, 333, seed=17, beta=1.0, with_c=True)
+
+
+def test_gemm_x6_more_accurate_than_x3():
+    """Against the exact product of the binary32 operands, bf16x6 (f32
+    accumulation) is far closer than bf16x3."""
+    M = N = K = 512
+    L = rnd((M, K), 3, 0.05)
+    R = rnd((K, N), 4, 0.05)
+    full = O.round_f32(L) @ O.round_f32(R)
+    Lp, Rp = gpu_split3(L, K), gpu_split3(R, N)
+    D6 = torch.zeros((M, N), dtype=torch.float32, device=dev)
+    nsgb.ns_k_gemm_bf16x6(M, N, K, Lp, K, Rp, N, 1.0, None, 0, 0.0, 0.0, D6, N)
+    D3 = torch.zeros((M, N), dtype=torch.float32, device=dev)
+    nsgb.ns_k_gemm_bf16(nsgb.NS_BF16X3, M, N, K, Lp[0], Lp[1], K, Rp[0], Rp[1], N, 1.0, None, 0, 0.0, 0.0, D3, N)
+    torch.cuda.synchronize()
+    e6 = np.max(np.abs(D6.cpu().numpy() - full))
+    e3 = np.max(np.abs(D3.cpu().numpy() - full))
+    assert e6 * 10 < e3
+
+
+def test_gemm_x6_full_size_sampled():
+    """4096^3 bf16x6 (the launch the solve uses past the bf16x3 floor): sampled
+    outputs recomputed one by one by the oracle."""
+    n = 4096
+    rng = np.random.default_rng(41)
+    L = rng.standard_normal((n, n)) * 0.02
+    R = rng.standard_normal((n, n)) * 0.02
+    Lp, Rp = gpu_split3(L, n), gpu_split3(R, n)
+    D32 = torch.zeros((n, n), dtype=torch.float32, device=dev)
+    nsgb.ns_k_gemm_bf16x6(n, n, n, Lp, n, Rp, n, -1.0, None, 0, 0.0, 1.0, D32, n)
+    torch.cuda.synchronize()
+    idx = rng.integers(0, n, (64, 2))
+    idx[:8, 1] = idx[:8, 0]
+    out = D32.cpu().numpy()
+    for i, j in idx:
+        p = O.split_product(L[i:i + 1], R[:, j:j + 1], "bf16x6")[0, 0]
+        a = O.split_abs_product(L[i:i + 1], R[:, j:j + 1], "bf16x6")[0, 0]
+        ref = -p + (1.0 if i == j else 0.0)
+        tol = n * 2.0 ** -23 * a + 2.0 ** -22 * (abs(ref) + 1.0)
+        assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)

@@ -329,6 +329,45 @@ def test_mixed_solve_through_cta_pairs(n, kappa):
     assert rel(out[-2], out[2]) <= 10 * kappa * 1e-10
 
 
+@pytest.mark.parametrize("n,kappa", [(300, 1e4), (640, 1e4)])
+def test_bf16x6_solve_reaches_tolerance(n, kappa):
+    """Every product in split-bf16 x6 (CTA pairs; n = 300 and 640 give odd
+    row-tile counts): the solve reaches the tolerance and its final G is at
+    least as good as bf16x3's."""
+    p = make_spd(n, kappa, nrhs=2, seed=18)
+    res = {}
+    for prec in (nsgb.NS_BF16X3, nsgb.NS_BF16X6):
+        with nsgb.Context(n, order=4, precision=prec, final_check=-1) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+        assert r.status == nsgb.NS_OK, (prec, r.stats.res_history())
+        assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10
+        assert set(r.stats.prec_history()) == {prec}
+        res[prec] = r.stats.final_frob
+    assert res[nsgb.NS_BF16X6] <= 1.5 * res[nsgb.NS_BF16X3]
+
+
+def test_bf16x6_invert_floor_below_bf16x3():
+    """The precision floor of ||I - A G||_F (FP64 check) after many steps is
+    lower with bf16x6 products than with bf16x3."""
+    n = 512
+    p = make_spd(n, 1e4, seed=19)
+    fl = {}
+    for prec in (nsgb.NS_BF16X3, nsgb.NS_BF16X6):
+        with nsgb.Context(n, order=4, precision=prec, final_check=-1, ns_stop=0) as ctx:
+            _, st = ctx.invert(tens(p.A), iters=14)
+        fl[prec] = st.final_frob
+    assert fl[nsgb.NS_BF16X6] * 4 < fl[nsgb.NS_BF16X3]
+
+
+def test_bf16x6_rejected_where_not_built():
+    with pytest.raises(nsgb.NSError) as ei:
+        nsgb.Context(64, order=2, rates=(2,), precision=nsgb.NS_BF16X6)
+    assert ei.value.status == nsgb.NS_ERR_UNSUPPORTED
+    with pytest.raises(nsgb.NSError) as ei:
+        nsgb.Context(64, order=45, form=3, precision=nsgb.NS_BF16X6)
+    assert ei.value.status == nsgb.NS_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("prec", [nsgb.NS_BF16, nsgb.NS_BF16X3])
 def test_fixed_precision_solve(prec):
     p = make_spd(128, 50.0, nrhs=2, seed=13)

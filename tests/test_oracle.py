@@ -504,6 +504,49 @@ def test_split_product_terms():
     assert np.all(np.abs(O.split_product(L, R, "bf16x3") - full) <= bound)
 
 
+def test_split3_exact_and_matches_torch():
+    """hi + lo + lo2 reproduces binary32 exactly, each part is a bfloat16, and
+    the parts equal torch's own bfloat16 rounding of the successive binary32
+    remainders."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        [0.0, 1.0, -1.0, 3.0e38, 1.0e-30]])
+    x32 = O.round_f32(x)
+    hi, lo, lo2 = O.split3_bf16(x)
+    assert np.array_equal(hi + lo + lo2, x32)
+    for part in (hi, lo, lo2):
+        assert np.array_equal(O.round_bf16(part), part)
+    t = torch.from_numpy(x32.astype(np.float32))
+    th = t.to(torch.bfloat16).float()
+    tl = (t - th).to(torch.bfloat16).float()
+    t2 = (t - th - tl).to(torch.bfloat16).float()
+    assert np.array_equal(th.double().numpy(), hi)
+    assert np.array_equal(tl.double().numpy(), lo)
+    assert np.array_equal(t2.double().numpy(), lo2)
+    h2, l2 = O.split_bf16(x)
+    assert np.array_equal(h2, hi) and np.array_equal(l2, lo)
+
+
+def test_split_product_x6_terms():
+    """bf16x6 = the six terms of order <= 2; against the binary32 product its
+    error is the three dropped terms only (each <= 2^-24 relative, as x32 =
+    hi + lo + lo2 exactly), far below bf16x3's."""
+    rng = np.random.default_rng(12)
+    L = rng.standard_normal((9, 33))
+    R = rng.standard_normal((33, 7))
+    Lh, Ll, L2 = O.split3_bf16(L)
+    Rh, Rl, R2 = O.split3_bf16(R)
+    want = Lh @ Rh + Lh @ Rl + Ll @ Rh + Lh @ R2 + Ll @ Rl + L2 @ Rh
+    assert np.max(np.abs(O.split_product(L, R, "bf16x6") - want)) <= 1e-13
+    full = O.round_f32(L) @ O.round_f32(R)
+    ab = np.abs(L) @ np.abs(R)
+    err6 = np.abs(O.split_product(L, R, "bf16x6") - full)
+    assert np.all(err6 <= 3 * 2.0 ** -24 * ab + 1e-13)
+    err3 = np.abs(O.split_product(L, R, "bf16x3") - full)
+    assert np.max(err3 / ab) > 100 * np.max(err6 / ab)
+
+
 def test_gemm_epilogue_forms():
     rng = np.random.default_rng(3)
     P = rng.standard_normal((5, 5))

@@ -167,3 +167,19 @@ def test_hutchinson_transposed_product(monkeypatch):
 def test_inverse_residual_sign(monkeypatch):
     _patch(monkeypatch, "inverse_residual", lambda A, G: float(np.linalg.norm(np.eye(A.shape[0]) + A @ G)))
     assert _fails(T.test_inverse_residual_closed_forms)
+
+
+def test_x6_dropping_a_second_order_term(monkeypatch):
+    monkeypatch.setitem(N.SPLIT_PASSES, "bf16x6",
+                        (("hi", "hi"), ("hi", "lo"), ("lo", "hi"), ("hi", "lo2"), ("lo2", "hi")))
+    assert _fails(T.test_split_product_x6_terms)
+
+
+def test_split3_truncated_third_part(monkeypatch):
+    orig = N.split3_bf16
+
+    def bad(x):
+        hi, lo, lo2 = orig(x)
+        return hi, lo, np.trunc(lo2 * 2.0 ** 30) / 2.0 ** 30
+    _patch(monkeypatch, "split3_bf16", bad)
+    assert _fails(T.test_split3_exact_and_matches_torch)
