@@ -392,22 +392,24 @@ def test_gemm_x6_accumulate_epilogue():
     run_gemm_x6(500, 333, 333, seed=17, beta=1.0, with_c=True)
 
 
-def test_gemm_x6_more_accurate_than_x3():
-    """Against the exact product of the binary32 operands, bf16x6 (f32
-    accumulation) is far closer than bf16x3."""
-    M = N = K = 512
-    L = rnd((M, K), 3, 0.05)
-    R = rnd((K, N), 4, 0.05)
-    full = O.round_f32(L) @ O.round_f32(R)
+def test_gemm_x6_reproduces_binary32_operand():
+    """L I with R = I adds nothing but zeros, so the product is exact in any
+    accumulator: bf16x6 must give L's binary32 values bit for bit (hi + lo +
+    lo2 = x32), while bf16x3 gives hi + lo and loses the third part."""
+    M = K = N = 256
+    L = rnd((M, K), 5, 1.0)
+    R = np.eye(K, N)
+    L32 = O.round_f32(L)
     Lp, Rp = gpu_split3(L, K), gpu_split3(R, N)
     D6 = torch.zeros((M, N), dtype=torch.float32, device=dev)
     nsgb.ns_k_gemm_bf16x6(M, N, K, Lp, K, Rp, N, 1.0, None, 0, 0.0, 0.0, D6, N)
     D3 = torch.zeros((M, N), dtype=torch.float32, device=dev)
     nsgb.ns_k_gemm_bf16(nsgb.NS_BF16X3, M, N, K, Lp[0], Lp[1], K, Rp[0], Rp[1], N, 1.0, None, 0, 0.0, 0.0, D3, N)
     torch.cuda.synchronize()
-    e6 = np.max(np.abs(D6.cpu().numpy() - full))
-    e3 = np.max(np.abs(D3.cpu().numpy() - full))
-    assert e6 * 10 < e3
+    assert np.array_equal(D6.cpu().numpy().astype(np.float64), L32)
+    hi, lo, lo2 = O.split3_bf16(L)
+    assert np.array_equal(D3.cpu().numpy().astype(np.float64), hi + lo)
+    assert np.count_nonzero(lo2) > M * K // 2
 
 
 def test_gemm_x6_full_size_sampled():
