@@ -8,6 +8,8 @@
   oracle in FP64 and must be <= 1e-10; theta then lies within
   kappa * 1e-10 (times a safety factor 10) of the exact solution.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -348,7 +350,9 @@ def test_bf16x6_solve_reaches_tolerance(n, kappa):
 
 def test_bf16x6_invert_floor_below_bf16x3():
     """The precision floor of ||I - A G||_F (FP64 check) after many steps is
-    lower with bf16x6 products than with bf16x3."""
+    lower with bf16x6 products than with bf16x3 -- by a factor ~2.6 here, not
+    2^8: past the split error, the binary32 master of G (kappa 2^-24 sqrt(n)
+    ~ 0.013) sets the floor."""
     n = 512
     p = make_spd(n, 1e4, seed=19)
     fl = {}
@@ -356,7 +360,8 @@ def test_bf16x6_invert_floor_below_bf16x3():
         with nsgb.Context(n, order=4, precision=prec, final_check=-1, ns_stop=0) as ctx:
             _, st = ctx.invert(tens(p.A), iters=14)
         fl[prec] = st.final_frob
-    assert fl[nsgb.NS_BF16X6] * 4 < fl[nsgb.NS_BF16X3]
+    assert fl[nsgb.NS_BF16X6] * 1.8 < fl[nsgb.NS_BF16X3]
+    assert fl[nsgb.NS_BF16X6] < 3.0 * 1e4 * 2.0 ** -24 * math.sqrt(n)
 
 
 def test_bf16x6_rejected_where_not_built():
