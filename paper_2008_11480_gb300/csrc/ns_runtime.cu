@@ -1116,8 +1116,10 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           const double t_step = step_cost(ctx, fp64, prec);
           if (need <= sweeps_left && need * t_sweep <= t_step + 2.0 * t_sweep) stop = true;
         }
-        // AUTO past a bf16x3 floor: bf16x6 products (a lower floor) where the
-        // floor is too high for Richardson to finish cheaply
+        // AUTO past a bf16x3 floor below one: bf16x6 products (a lower floor)
+        // where Richardson would need too many sweeps from it.  A floor above
+        // one is left to Richardson (rho(I - A G) < 1 often holds there); if
+        // its sweeps then stall far above tol, Newton-Schulz resumes in bf16x6
         const bool can_x6 = autop && ctx->x6 && prec == NS_BF16X3;
         bool floor_hit = false, esc = false;
         if (!stop && prev_frob < 1.0 && frob >= 0.5 * prev_frob) {
@@ -1137,9 +1139,8 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
             ratio > prev_ratio + 0.02) {
           // the contraction got worse again: the floor of this precision lies
           // above ||F||_F = 1, more steps only repeat it (Richardson takes
-          // over if rho(I - A G) < 1, unless bf16x6 can still go lower)
+          // over if rho(I - A G) < 1)
           floor_hit = true;
-          esc = can_x6;
         }
         if (floor_hit) {
           if (frob > prev_frob) {
@@ -1210,6 +1211,20 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       if (tol > 0 && rho < 1.0 && last_rr > tol &&
           std::log(tol / last_rr) / std::log(rho) > static_cast<double>(sweeps_left))
         give_up = true;
+    }
+    if (give_up && autop && ctx->x6 && prec != NS_BF16X6 && done < iters && best_rr > 1e-6 && tol > 0) {
+      // the sweeps stall far above tol: G itself does not contract enough at
+      // this precision -- resume Newton-Schulz from G_k in bf16x6
+      prec = NS_BF16X6;
+      NS_TRY(x6_prepare(S.cur));
+      ns_active = true;
+      prev_frob = INFINITY;
+      prev_ratio = INFINITY;
+      stall = 0;
+      best_rr = INFINITY;
+      prev_sweep_rr = INFINITY;
+      prev_sweep_ratio = INFINITY;
+      continue;
     }
     if (give_up) {
       if (fp64 || resid64 || !(tol > 0)) break;

@@ -364,6 +364,20 @@ def test_bf16x6_invert_floor_below_bf16x3():
     assert fl[nsgb.NS_BF16X6] < 3.0 * 1e4 * 2.0 ** -24 * math.sqrt(n)
 
 
+def test_auto_resumes_in_bf16x6_when_richardson_stalls():
+    """n = 2048, kappa = 5e6: bf16x3 Newton-Schulz stalls with ||F||_F ~ 16 and the
+    Richardson sweeps from that G do not contract; AUTO then resumes Newton-Schulz
+    in bf16x6 from G_k and reaches the tolerance."""
+    from workloads import make_spd_device
+    A, B = make_spd_device(2048, 5e6, nrhs=1, seed=3, device=dev)
+    with nsgb.Context(2048, order=8) as ctx:
+        r = ctx.solve(A, B, iters=80, tol=1e-10)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert nsgb.NS_BF16X6 in r.stats.prec_history()
+    rr = O.rel_residual(A.cpu().numpy(), r.theta.cpu().numpy(), B.cpu().numpy())
+    assert float(np.max(rr)) <= 1e-10
+
+
 def test_bf16x6_rejected_where_not_built():
     with pytest.raises(nsgb.NSError) as ei:
         nsgb.Context(64, order=2, rates=(2,), precision=nsgb.NS_BF16X6)
