@@ -1103,8 +1103,21 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         if (st) st->rollbacks++;
         goto recompute_F;
       }
-      if (frob > 2.0 * sqrt_n + 1.0 && frob > 2.0 * prev_frob)
+      if (frob > 2.0 * sqrt_n + 1.0 && frob > 2.0 * prev_frob) {
+        if (autop && ctx->x6 && prec == NS_BF16X3 && done > 0) {
+          // bf16x3 rounding threw the step out of the contraction region:
+          // go back to G_{k-1} and continue with bf16x6 products
+          S.cur ^= 1;
+          done--;
+          if (st) st->rollbacks++;
+          prec = NS_BF16X6;
+          NS_TRY(x6_prepare(S.cur));
+          prev_frob = INFINITY;
+          prev_ratio = INFINITY;
+          goto recompute_F;
+        }
         return fail(ctx, NS_ERR_DIVERGED, "Newton-Schulz diverged (||F||_F grew past sqrt(n))");
+      }
       if (ctx->opt.ns_stop && (!autop || prec != NS_BF16)) {
         bool stop = frob <= ctx->opt.ns_stop_frob;
         if (!stop && rich && frob < 1.0 && tol > 0 && last_rr > tol) {
