@@ -386,9 +386,16 @@ def run_kernel_gemm(a):
     Lh, Ll = mk(), mk()
     nsgb.ns_k_split(L, Lh, Ll, n, n, n, n)
     D32, Dh, Dl = mk(torch.float32), mk(), mk()
-    prec = nsgb.NS_BF16X3 if a.precision == "bf16x3" else nsgb.NS_BF16
+    prec = {"bf16": nsgb.NS_BF16, "bf16x3": nsgb.NS_BF16X3, "bf16x6": nsgb.NS_BF16X6}[a.precision]
+    if prec == nsgb.NS_BF16X6:
+        L3, D2 = mk(), mk()
+        nsgb.ns_k_split3(L, Lh, Ll, L3, n, n, n, n)
 
     def call():
+        if prec == nsgb.NS_BF16X6:
+            nsgb.ns_k_gemm_bf16x6(n, n, n, (Lh, Ll, L3), n, (Lh, Ll, L3), n, -1.0, None, 0, 0.0, 1.0, D32, n,
+                                  (Dh, Dl, D2), n)
+            return
         nsgb.ns_k_gemm_bf16(prec, n, n, n, Lh, Ll, n, Lh, Ll, n, -1.0, None, 0, 0.0, 1.0, D32, n, Dh, Dl, n,
                             None, a.bn, a.cm)
     for _ in range(a.warmup):
@@ -401,7 +408,7 @@ def run_kernel_gemm(a):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
-    passes = 3 if prec == nsgb.NS_BF16X3 else 1
+    passes = {nsgb.NS_BF16: 1, nsgb.NS_BF16X3: 3, nsgb.NS_BF16X6: 6}[prec]
     print(json.dumps({"kernel": "k_gemm_tc", "n": n, "precision": a.precision, "bn": a.bn, "cm": a.cm,
                       "ms_per_call": ms, "tflops_incl_call_overhead": passes * 2 * n ** 3 / (ms * 1e-3) / 1e12}))
 
@@ -759,7 +766,7 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=9)
     ap.add_argument("--kernel", default="", choices=["", "gemm"],
                     help="microbenchmark one kernel instead of the solve")
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
     ap.add_argument("--gemm-cluster", type=int, default=0,
