@@ -691,6 +691,65 @@ def split_abs_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarra
     return out
 
 
+# --------------------------------------------------------------------------
+# FP64-accurate products from exact integer slices (an Ozaki-style error-free
+# splitting: T. Ozaki, T. Ogita, S. M. Rump, S. Oishi, "Error-free
+# transformations of matrix multiplication by using fast routines of matrix
+# multiplication and its applications", Numer. Algorithms 59, 2012).  Each row
+# i of L is written as mu_i sum_t 2^{-8t} A_t[i, :] and each column j of R as
+# nu_j sum_u 2^{-8u} B_u[:, j] with integer slices |A_t|, |B_u| <= 255 and
+# powers of two mu_i >= max_k |L_ik|, nu_j >= max_k |R_kj|; every slice
+# product A_t B_u is then an exact integer matrix.
+# --------------------------------------------------------------------------
+
+
+def ozaki_scales(X: np.ndarray, axis: int) -> np.ndarray:
+    """Power-of-two scale per row (axis = 1: max over each row) or per column
+    (axis = 0): 2^e with max |x| = m 2^e, m in [0.5, 1), so |x| / scale < 1;
+    1 for an all-zero line."""
+    mx = np.max(np.abs(X), axis=axis)
+    _, e = np.frexp(mx)
+    return np.where(mx > 0, np.ldexp(1.0, e), 1.0)
+
+
+def ozaki_slices(X: np.ndarray, scale: np.ndarray, axis: int, s: int) -> list:
+    """Integer slices S_1..S_s of X / scale (scale broadcast along rows for
+    axis = 1, along columns for axis = 0): x <- 256 x, S_t = trunc(x),
+    x <- x - S_t, each step exact in binary64, |S_t| <= 255."""
+    x = X / (scale[:, None] if axis == 1 else scale[None, :])
+    out = []
+    for _ in range(s):
+        x = x * 256.0
+        a = np.trunc(x)
+        x = x - a
+        out.append(a)
+    return out
+
+
+def ozaki_pairs(s: int) -> list:
+    """Slice pairs (t, u), 1 <= t, u <= s, kept by the product: t + u <= s + 1
+    (the others weigh at most 2^{-8(s+2)} relative), ordered by d = t + u."""
+    return [(t, d - t) for d in range(2, s + 2) for t in range(1, d) if 1 <= d - t <= s]
+
+
+def ozaki_product(L: np.ndarray, R: np.ndarray, s: int = 7) -> np.ndarray:
+    """sum over kept pairs of mu_i nu_j 2^{-8(t+u)} (A_t B_u)_ij, with every
+    A_t B_u formed exactly in integer arithmetic (int64) and the per-level sums
+    S_d = sum_{t+u=d} A_t B_u combined in binary64."""
+    mu = ozaki_scales(L, 1)
+    nu = ozaki_scales(R, 0)
+    A = [a.astype(np.int64) for a in ozaki_slices(L, mu, 1, s)]
+    B = [b.astype(np.int64) for b in ozaki_slices(R, nu, 0, s)]
+    out = np.zeros((L.shape[0], R.shape[1]))
+    for d in range(2, s + 2):
+        S = np.zeros_like(out, dtype=np.int64)
+        for t, u in ozaki_pairs(s):
+            if t + u == d:
+                S += A[t - 1] @ B[u - 1]
+        out += np.ldexp(S.astype(np.float64), -8 * d)
+    return out * mu[:, None] * nu[None, :]
+
+
 def gemm_epilogue(prod: np.ndarray, s: float = 1.0, C: np.ndarray | None = None,
                   beta: float = 0.0, gamma: float = 0.0) -> np.ndarray:
     """D = s * prod + beta * C + gamma * I: the affine forms every step of the

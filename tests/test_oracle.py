@@ -614,3 +614,53 @@ def test_hutchinson_unbiased_within_its_variance():
     s = 1500
     est2 = O.inverse_residual_hutchinson(p.A, G, s, 3) ** 2
     assert abs(est2 - float(np.trace(M))) <= 5.0 * math.sqrt(var / s)
+
+
+# ---------------------------------------------------------------- FP64-accurate products (integer slices)
+def test_ozaki_slices_exact_integers_and_reconstruction():
+    from fractions import Fraction
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((17, 29)) * 10.0 ** rng.integers(-8, 8, (17, 1))
+    X[3] = 0.0
+    for axis in (0, 1):
+        sc = O.ozaki_scales(X, axis)
+        assert np.all(np.log2(sc) == np.round(np.log2(sc)))           # powers of two
+        lim = np.max(np.abs(X), axis=axis)
+        assert np.all((lim < sc) & ((lim >= sc / 2) | (lim == 0)))
+        sl7 = O.ozaki_slices(X, sc, axis, 7)
+        sl9 = O.ozaki_slices(X, sc, axis, 9)
+        for a in sl9:
+            assert np.array_equal(a, np.trunc(a)) and np.max(np.abs(a)) <= 255
+        for i, j in zip(rng.integers(0, 17, 120), rng.integers(0, 29, 120)):
+            scale = Fraction(float(sc[i] if axis == 1 else sc[j]))
+            x = Fraction(float(X[i, j]))
+            r7 = scale * sum(Fraction(int(a[i, j])) / 256 ** (t + 1) for t, a in enumerate(sl7))
+            assert abs(x - r7) < scale / 2 ** 56      # truncation after 7 slices
+            if abs(x) >= scale / 2 ** 19:             # 53 bits within 72: 9 slices are exact
+                r9 = scale * sum(Fraction(int(a[i, j])) / 256 ** (t + 1) for t, a in enumerate(sl9))
+                assert r9 == x
+
+
+def test_ozaki_pairs_count():
+    assert O.ozaki_pairs(7) == sorted(O.ozaki_pairs(7), key=lambda p: p[0] + p[1])
+    assert len(O.ozaki_pairs(7)) == 28 and len(O.ozaki_pairs(2)) == 3
+    assert all(t + u <= 8 for t, u in O.ozaki_pairs(7))
+
+
+def test_ozaki_product_against_exact_arithmetic():
+    """Against the exact product (Python fractions on a small case) the error is
+    far below an FP64 GEMM's bound K u |L||R|, and small integer matrices
+    multiply exactly."""
+    from fractions import Fraction
+    rng = np.random.default_rng(14)
+    L = rng.standard_normal((6, 40)) * 10.0 ** rng.integers(-3, 3, (6, 1))
+    R = rng.standard_normal((40, 5))
+    P = O.ozaki_product(L, R, 7)
+    ab = np.abs(L) @ np.abs(R)
+    for i in range(6):
+        for j in range(5):
+            exact = sum(Fraction(float(L[i, k])) * Fraction(float(R[k, j])) for k in range(40))
+            assert abs(float(Fraction(float(P[i, j])) - exact)) <= 2.0 ** -50 * ab[i, j]
+    Li = rng.integers(-1000, 1000, (9, 13)).astype(float)
+    Ri = rng.integers(-1000, 1000, (13, 7)).astype(float)
+    assert np.array_equal(O.ozaki_product(Li, Ri, 7), Li @ Ri)

@@ -183,3 +183,30 @@ def test_split3_truncated_third_part(monkeypatch):
         return hi, lo, np.trunc(lo2 * 2.0 ** 30) / 2.0 ** 30
     _patch(monkeypatch, "split3_bf16", bad)
     assert _fails(T.test_split3_exact_and_matches_torch)
+
+
+def test_ozaki_rounding_instead_of_truncation(monkeypatch):
+    def bad(X, scale, axis, s):
+        x = X / (scale[:, None] if axis == 1 else scale[None, :])
+        out = []
+        for _ in range(s):
+            x = x * 256.0
+            a = np.round(x)
+            x = x - a
+            out.append(a)
+        return out
+    _patch(monkeypatch, "ozaki_slices", bad)
+    assert _fails(T.test_ozaki_slices_exact_integers_and_reconstruction)
+
+
+def test_ozaki_level_weight_off_by_one(monkeypatch):
+    def bad(L, R, s=7):
+        mu, nu = N.ozaki_scales(L, 1), N.ozaki_scales(R, 0)
+        A = [a.astype(np.int64) for a in N.ozaki_slices(L, mu, 1, s)]
+        B = [b.astype(np.int64) for b in N.ozaki_slices(R, nu, 0, s)]
+        out = np.zeros((L.shape[0], R.shape[1]))
+        for t, u in N.ozaki_pairs(s):
+            out += np.ldexp((A[t - 1] @ B[u - 1]).astype(np.float64), -8 * (t + u - 1))
+        return out * mu[:, None] * nu[None, :]
+    _patch(monkeypatch, "ozaki_product", bad)
+    assert _fails(T.test_ozaki_product_against_exact_arithmetic)
