@@ -631,6 +631,7 @@ def test_ozaki_slices_exact_integers_and_reconstruction():
         sl9 = O.ozaki_slices(X, sc, axis, 9)
         for a in sl9:
             assert np.array_equal(a, np.trunc(a)) and np.max(np.abs(a)) <= 255
+            assert np.all(a * X >= 0)  # truncation: every slice has the element's sign (or is 0)
         for i, j in zip(rng.integers(0, 17, 120), rng.integers(0, 29, 120)):
             scale = Fraction(float(sc[i] if axis == 1 else sc[j]))
             x = Fraction(float(X[i, j]))
