@@ -111,6 +111,9 @@ typedef struct ns_options {
                           the final G by one FP64 product; s = 1..4096 Hutchinson's estimate with s
                           Rademacher probes and seed 0 (see ns_inverse_residual); into
                           ns_stats.final_frob.  On the mixed path G is the f32 master, widened. */
+  int fp64_slices;      /* precision NS_FP64 only: 0 (default) products on the FP64 CUDA cores;
+                          s = 2..8: FP64-accurate products on the bf16 tensor cores from s integer
+                          slices of 8 bits per operand (see ns_k_gemm_oz; 7 covers binary64) */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -380,6 +383,23 @@ ns_status ns_k_split3(const void* X, int x_dtype, int64_t rows, int64_t cols, in
 ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl, const void* const* R,
                            int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma, float* D32,
                            int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, void* stream);
+
+/* FP64-accurate product on the bf16 tensor cores by an Ozaki-style error-free splitting
+ * (Ozaki, Ogita, Rump, Oishi, Numer. Algorithms 59, 2012):
+ *   D = s L R + beta C + gamma I   (L M x K, R K x N, C and D M x N: FP64, row-major)
+ * Each row i of L is scaled by the power of two mu_i >= max_k |L_ik| and cut into `slices`
+ * integer slices of 8 bits (x <- 256 x, S = trunc(x), x <- x - S; |S| <= 255, exact in
+ * bf16); each column of R likewise.  Slice products A_t B_u with t + u <= slices + 1 run on
+ * tcgen05 CTA pairs over K chunks of 256, where their f32 accumulation is exact (256 * 255^2
+ * < 2^24); chunk results are summed exactly in int32 and added into D in FP64 per level
+ * t + u.  slices = 7 carries 56 bits per line (binary64: 53).  Workspace (2 slices (M K + K N)
+ * bytes and three vectors) is taken from the stream-ordered allocator; `stream` is
+ * synchronised.  frob_out (device double, may be NULL) receives sum(D^2).  D may alias C.
+ * Errors: NS_ERR_ARG (sizes, leading dimensions, null pointers, slices outside 2..8),
+ * NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_TIMEOUT. */
+ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R, int64_t ldr,
+                       double s, const double* C, int64_t ldc, double beta, double gamma, double* D, int64_t ldd,
+                       int slices, double* frob_out, void* stream);
 
 /* FP64 product with the same epilogue: D = s L R + beta C + gamma I (C may be NULL). */
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,

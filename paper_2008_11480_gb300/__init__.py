@@ -27,7 +27,7 @@ __all__ = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_inverse_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
-    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6",
+    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6", "ns_k_gemm_oz",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
     "ns_batch_stats", "Batch",
 ]
@@ -68,6 +68,7 @@ class ns_options(ctypes.Structure):
         ("accel_richardson", ctypes.c_int),
         ("g0_order", ctypes.c_int),
         ("final_check", ctypes.c_int),
+        ("fp64_slices", ctypes.c_int),
     ]
 
 
@@ -190,6 +191,8 @@ def lib() -> ctypes.CDLL:
         "ns_status_string": (ctypes.c_char_p, [_int]),
         "ns_k_split": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
         "ns_k_split3": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
+        "ns_k_gemm_oz": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
+                                 ctypes.c_double, _vp, _i64, _int, _vp, _vp]),
         "ns_k_gemm_bf16x6": (_int, [_i64, _i64, _i64, ctypes.POINTER(_vp), _i64, ctypes.POINTER(_vp), _i64,
                                      ctypes.c_float, _vp, _i64, ctypes.c_float, ctypes.c_float, _vp, _i64,
                                      ctypes.POINTER(_vp), _i64, _vp, _vp]),
@@ -381,6 +384,15 @@ def ns_k_gemm_bf16x6(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float 
     r = lib().ns_k_gemm_bf16x6(M, N, K, Lp, ldl, Rp, ldr, s, _ptr(C, torch.float32), ldc, beta, gamma,
                                _ptr(D32, torch.float32), ldd32, Dp, ldd16, _ptr(frob_out), _stream_ptr(stream))
     _raise(r, "ns_k_gemm_bf16x6")
+
+
+def ns_k_gemm_oz(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float = 1.0, C=None, ldc: int = 0,
+                 beta: float = 0.0, gamma: float = 0.0, D=None, ldd: int = 0, slices: int = 7, frob_out=None,
+                 stream=None) -> None:
+    """FP64-accurate product from integer bf16 slices on the tensor cores (FP64 tensors)."""
+    r = lib().ns_k_gemm_oz(M, N, K, _ptr(L), ldl, _ptr(R), ldr, s, _ptr(C), ldc, beta, gamma, _ptr(D), ldd, slices,
+                           _ptr(frob_out), _stream_ptr(stream))
+    _raise(r, "ns_k_gemm_oz")
 
 
 def ns_k_gemm_bf16(precision: int, M: int, N: int, K: int, Lhi, Llo, ldl: int, Rhi, Rlo, ldr: int, s: float = 1.0,

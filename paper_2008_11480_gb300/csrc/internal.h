@@ -79,6 +79,34 @@ cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_s
 // partial wave run as two half-width items each when that shortens the wave.
 cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
+
+// ---- FP64-accurate products from integer bf16 slices (gemm_oz.cu)
+constexpr int kOzMaxSlices = 8;
+constexpr int kOzMaxPairs = 36;  // slice pairs with t + u <= s + 1, s = 8
+struct OzParams {
+  CUtensorMap L[kOzMaxSlices];  // slices of L: M x K bf16 (role 0 maps, 64 x 64 boxes)
+  CUtensorMap R[kOzMaxSlices];  // slices of R: K x N bf16
+  int M, N, K;
+  int slices, npairs;
+  int tiles_n;      // 128-column tiles along N
+  int total_tiles;  // ceil(M / 256) * tiles_n pair tiles
+  int pair_t[kOzMaxPairs], pair_u[kOzMaxPairs];  // kept pairs, ordered by t + u
+  const double* mu;  // M power-of-two row scales of L
+  const double* nu;  // N power-of-two column scales of R
+  double s;          // D += s * L R
+  double* D;         // FP64 output, holding beta C + gamma I on entry
+  int64_t ldd;
+  int debug_stall_iter;
+  unsigned long long timeout_ns;
+  int* err;
+};
+// Scales (per row of X if by_row, else per column) and s integer slices of an
+// FP64 matrix X (rows x cols, ld): slice t at out + (t - 1) slice_stride (ldo).
+cudaError_t launch_oz_prepare(const double* X, int64_t ld, int rows, int cols, bool by_row, int s, double* scale,
+                              bf16* out, int64_t ldo, int64_t slice_stride, cudaStream_t st);
+cudaError_t launch_oz_init(double* D, int64_t ldd, const double* C, int64_t ldc, double beta, double gamma, int rows,
+                           int cols, cudaStream_t st);
+cudaError_t launch_gemm_oz(const OzParams& p, int num_sms, cudaStream_t s);
 int tc_items(int M, int N, int BN, int CM);
 
 // Encode a 2-D bf16 tensor map (rows x cols, leading dimension ld elements).

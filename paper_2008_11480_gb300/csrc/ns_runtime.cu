@@ -105,6 +105,13 @@ struct ns_ctx {
   MpMat Gam, Tc[2], Pre[2], Xs[2];
   // fp64
   bool f64_ready = false;
+  // FP64-accurate tensor-core products (option fp64_slices): integer bf16
+  // slices of both operands, their scales and column sums of squares
+  bf16* oz_L = nullptr;
+  bf16* oz_R = nullptr;
+  double* oz_mu = nullptr;
+  double* oz_nu = nullptr;
+  double* oz_sq = nullptr;
   double *G64[2] = {nullptr, nullptr}, *X64[2] = {nullptr, nullptr}, *F64 = nullptr, *P64[2] = {nullptr, nullptr};
   std::vector<double*> T64[2];
   double *Gam64 = nullptr, *Tc64[2] = {nullptr, nullptr}, *Pre64[2] = {nullptr, nullptr}, *Xs64[2] = {nullptr, nullptr};
@@ -439,8 +446,70 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   return NS_OK;
 }
 
+// One FP64-accurate product D = s L R + beta C + gamma I from integer bf16
+// slices on the tensor cores (n x n, leading dimension ld).  L and R are
+// sliced before D is first written, so D may alias any operand.
+ns_status oz_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const double* C, double beta, double gamma,
+                  double* D, double* frob_dst) {
+  const int n = static_cast<int>(ctx->n);
+  const int64_t ld = ctx->ld;
+  const int ns = ctx->opt.fp64_slices;
+  cudaStream_t st = ctx->stream;
+  const size_t per = static_cast<size_t>(n) * ld;
+  if (ctx->oz_L == nullptr) {
+    NS_TRY(alloc(ctx, &ctx->oz_L, per * kOzMaxSlices));
+    NS_TRY(alloc(ctx, &ctx->oz_R, per * kOzMaxSlices));
+    NS_TRY(alloc(ctx, &ctx->oz_mu, static_cast<size_t>(n)));
+    NS_TRY(alloc(ctx, &ctx->oz_nu, static_cast<size_t>(n)));
+    NS_TRY(alloc(ctx, &ctx->oz_sq, static_cast<size_t>(n)));
+  }
+  EventPair* e = ev_begin(ctx, false);
+  NS_CK(launch_oz_prepare(L, ld, n, n, true, ns, ctx->oz_mu, ctx->oz_L, ld, static_cast<int64_t>(per), st));
+  NS_CK(launch_oz_prepare(R, ld, n, n, false, ns, ctx->oz_nu, ctx->oz_R, ld, static_cast<int64_t>(per), st));
+  NS_CK(launch_oz_init(D, ld, C, ld, beta, gamma, n, n, st));
+  OzParams p;
+  memset(&p, 0, sizeof(p));
+  for (int t = 0; t < ns; ++t)
+    if (!encode_bf16_map(&p.L[t], ctx->oz_L + t * per, n, n, ld, 0) ||
+        !encode_bf16_map(&p.R[t], ctx->oz_R + t * per, n, n, ld, 0))
+      return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  p.M = p.N = p.K = n;
+  p.slices = ns;
+  for (int d = 2; d <= ns + 1; ++d)
+    for (int t = 1; t < d; ++t)
+      if (d - t >= 1 && d - t <= ns) {
+        p.pair_t[p.npairs] = t;
+        p.pair_u[p.npairs] = d - t;
+        p.npairs++;
+      }
+  p.tiles_n = (n + 127) / 128;
+  p.total_tiles = ((n + 255) / 256) * p.tiles_n;
+  p.mu = ctx->oz_mu;
+  p.nu = ctx->oz_nu;
+  p.s = s;
+  p.D = D;
+  p.ldd = ld;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
+  p.err = ctx->derr;
+  NS_CK(launch_gemm_oz(p, ctx->num_sms, st));
+  ev_end(ctx, e);
+  ctx->launches += 6;
+  if (ctx->st) {
+    ctx->st->gemm_launches++;
+    ctx->st->gemm_flops += 2.0 * n * static_cast<double>(n) * n;
+  }
+  if (frob_dst) {
+    NS_CK(launch_colsumsq(D, ld, n, n, ctx->oz_sq, nullptr, st));
+    NS_CK(launch_reduce_sum(ctx->oz_sq, n, 1, frob_dst, st));
+    ctx->launches += 2;
+  }
+  return NS_OK;
+}
+
 ns_status f64_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const double* C, double beta,
                    double gamma, double* D, double* frob_dst) {
+  if (ctx->opt.fp64_slices > 0) return oz_gemm(ctx, L, R, s, C, beta, gamma, D, frob_dst);
   const int n = static_cast<int>(ctx->n);
   F64Gemm g;
   g.M = g.N = g.K = n;
@@ -1388,6 +1457,7 @@ void ns_default_options(ns_options* o) {
   o->aux_ahead = 0;
   o->gemm_cluster = 0;
   o->final_check = 0;
+  o->fp64_slices = 0;
   o->couple_frob = 0.0;
   o->accel_richardson = 0;
   o->g0_order = 0;
@@ -1426,6 +1496,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   if (o.final_check < -1 || o.final_check > 4096) return NS_ERR_ARG;
+  if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state
@@ -1840,6 +1911,87 @@ ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L
   void* none[3] = {nullptr, nullptr, nullptr};
   return k_gemm_impl(3, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D ? D : none, ldd16, frob_out,
                      256, -2, stream);
+}
+
+ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R, int64_t ldr,
+                       double s, const double* C, int64_t ldc, double beta, double gamma, double* D, int64_t ldd,
+                       int slices, double* frob_out, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
+  if (!L || !R || !D || ldl < K || ldr < N || ldd < N || (C && ldc < N)) return NS_ERR_ARG;
+  if (slices < 2 || slices > kOzMaxSlices) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ldk = (K + 7) / 8 * 8, ldn = (N + 7) / 8 * 8;  // 16-byte rows for the tensor maps
+  const size_t lbytes = sizeof(bf16) * static_cast<size_t>(M) * ldk * slices;
+  const size_t rbytes = sizeof(bf16) * static_cast<size_t>(K) * ldn * slices;
+  const size_t vbytes = sizeof(double) * static_cast<size_t>(M + N + N + 1);
+  char* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), lbytes + rbytes + vbytes + sizeof(int) * 4 + 512, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  bf16* Ls = reinterpret_cast<bf16*>(ws);
+  bf16* Rs = reinterpret_cast<bf16*>(ws + lbytes);
+  double* mu = reinterpret_cast<double*>(ws + ((lbytes + rbytes + 255) / 256) * 256);
+  double* nu = mu + M;
+  double* sq = nu + N;
+  int* err = reinterpret_cast<int*>(sq + N + 1);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = launch_oz_prepare(L, ldl, static_cast<int>(M), static_cast<int>(K), true, slices, mu, Ls, ldk, M * ldk, st);
+  if (e == cudaSuccess)
+    e = launch_oz_prepare(R, ldr, static_cast<int>(K), static_cast<int>(N), false, slices, nu, Rs, ldn, K * ldn, st);
+  if (e == cudaSuccess) e = launch_oz_init(D, ldd, C, ldc, beta, gamma, static_cast<int>(M), static_cast<int>(N), st);
+  OzParams p;
+  memset(&p, 0, sizeof(p));
+  bool maps = true;
+  for (int t = 0; t < slices && maps; ++t)
+    maps = encode_bf16_map(&p.L[t], Ls + t * M * ldk, M, K, ldk, 0) &&
+           encode_bf16_map(&p.R[t], Rs + t * K * ldn, K, N, ldn, 0);
+  if (!maps) {
+    cudaFreeAsync(ws, st);
+    return NS_ERR_ARG;
+  }
+  p.M = static_cast<int>(M);
+  p.N = static_cast<int>(N);
+  p.K = static_cast<int>(K);
+  p.slices = slices;
+  for (int d = 2; d <= slices + 1; ++d)
+    for (int t = 1; t < d; ++t)
+      if (d - t >= 1 && d - t <= slices) {
+        p.pair_t[p.npairs] = t;
+        p.pair_u[p.npairs] = d - t;
+        p.npairs++;
+      }
+  p.tiles_n = static_cast<int>((N + 127) / 128);
+  p.total_tiles = static_cast<int>((M + 255) / 256) * p.tiles_n;
+  p.mu = mu;
+  p.nu = nu;
+  p.s = s;
+  p.D = D;
+  p.ldd = ldd;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = 2000000000ull;
+  if (const char* v = std::getenv("NSGB_INJECT_WITHHOLD_LOAD")) p.debug_stall_iter = std::atoi(v);
+  if (const char* v = std::getenv("NSGB_WAIT_LIMIT_MS")) {
+    const long ms = std::atol(v);
+    if (ms > 0 && ms <= 10000) p.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
+  }
+  p.err = err;
+  if (e == cudaSuccess) e = launch_gemm_oz(p, sms, st);
+  if (e == cudaSuccess && frob_out) {
+    e = launch_colsumsq(D, ldd, static_cast<int>(M), static_cast<int>(N), sq, nullptr, st);
+    if (e == cudaSuccess) e = launch_reduce_sum(sq, static_cast<int>(N), 1, frob_out, st);
+  }
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NS_ERR_CUDA;
+  return herr == DEV_OK ? NS_OK : NS_ERR_TIMEOUT;
 }
 
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,

@@ -119,3 +119,21 @@ def test_x6_pair_withheld_load_times_out(inject):
     nsgb.ns_k_gemm_bf16x6(M, N, K, parts[0], K, parts[1], N, -1.0, None, 0, 0.0, 1.0, D32, N)
     torch.cuda.synchronize()
     assert torch.isfinite(D32).all()
+
+
+def test_slice_product_withheld_load_times_out(inject):
+    on, off = inject
+    n = 256
+    rng = np.random.default_rng(81)
+    L = torch.from_numpy(rng.standard_normal((n, n))).to(dev)
+    R = torch.from_numpy(rng.standard_normal((n, n))).to(dev)
+    D = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    on(3)
+    with pytest.raises(nsgb.NSError) as ei:
+        nsgb.ns_k_gemm_oz(n, n, n, L, n, R, n, D=D, ldd=n)
+    assert ei.value.status == nsgb.NS_ERR_TIMEOUT
+    off()
+    nsgb.ns_k_gemm_oz(n, n, n, L, n, R, n, D=D, ldd=n)
+    torch.cuda.synchronize()
+    ref = L.cpu().numpy() @ R.cpu().numpy()
+    assert np.allclose(D.cpu().numpy(), ref, rtol=1e-13, atol=1e-12)

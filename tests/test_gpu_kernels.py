@@ -432,3 +432,80 @@ def test_gemm_x6_full_size_sampled():
         ref = -p + (1.0 if i == j else 0.0)
         tol = n * 2.0 ** -23 * a + 2.0 ** -22 * (abs(ref) + 1.0)
         assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)
+
+
+# ---------------------------------------------------------------- FP64-accurate products from integer slices
+def run_gemm_oz(M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, slices=7, spread=True):
+    rng = np.random.default_rng(seed)
+    L = rng.standard_normal((M, K))
+    R = rng.standard_normal((K, N))
+    if spread:  # rows and columns of very different magnitudes: the scales must follow them
+        L *= 10.0 ** rng.integers(-6, 6, (M, 1))
+        R *= 10.0 ** rng.integers(-6, 6, (1, N))
+    C = rng.standard_normal((M, N)) if with_c else None
+    Ld, Rd = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
+    Cd = torch.from_numpy(C).to(dev) if with_c else None
+    D = torch.full((M, N), 7.0, dtype=torch.float64, device=dev)
+    fro = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_oz(M, N, K, Ld, K, Rd, N, s, Cd, N if with_c else 0, beta, gamma, D, N, slices, fro)
+    torch.cuda.synchronize()
+    prod = O.ozaki_product(L, R, slices)
+    ref = O.gemm_epilogue(prod, s, C, beta, gamma)
+    out = D.cpu().numpy()
+    ab = np.abs(L) @ np.abs(R)
+    # same slices and integer sums; only the binary64 combination of the levels
+    # (one rounding per level and per flush) differs from the oracle's order
+    tol = 16 * 2.0 ** -53 * (abs(s) * ab + np.abs(ref)) + 1e-300
+    err = np.abs(out - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    assert float(fro.item()) == pytest.approx(float(np.sum(out * out)), rel=1e-12)
+    return L, R, out
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 128, 256), (300, 200, 130), (513, 257, 1000), (128, 64, 4096), (1, 1, 1),
+                                   (640, 384, 33)])
+def test_gemm_oz_matches_oracle(M, N, K):
+    run_gemm_oz(M, N, K, seed=M + 7 * N + K)
+
+
+def test_gemm_oz_epilogues_and_slices():
+    run_gemm_oz(300, 300, 300, seed=3, s=-1.0, gamma=1.0, spread=False)
+    run_gemm_oz(257, 129, 200, seed=4, beta=1.0, with_c=True)
+    run_gemm_oz(200, 160, 300, seed=5, slices=3)
+
+
+def test_gemm_oz_fp64_accuracy():
+    """Against the product in (quad on the GPU machine's host, else extended)
+    precision the slice product is as accurate as binary64 allows: far inside
+    an FP64 GEMM's K u |L||R| bound, and exact for small integer matrices."""
+    L, R, out = run_gemm_oz(200, 150, 2048, seed=6)
+    exact = (L.astype(np.longdouble) @ R.astype(np.longdouble)).astype(np.float64)
+    ab = np.abs(L) @ np.abs(R)
+    assert np.all(np.abs(out - exact) <= 8 * 2.0 ** -53 * ab + 4 * 2.0 ** -53 * np.abs(exact))
+    rng = np.random.default_rng(7)
+    Li = rng.integers(-1000, 1000, (130, 300)).astype(float)
+    Ri = rng.integers(-1000, 1000, (300, 70)).astype(float)
+    D = torch.zeros((130, 70), dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_oz(130, 70, 300, torch.from_numpy(Li).to(dev), 300, torch.from_numpy(Ri).to(dev), 70, D=D, ldd=70)
+    torch.cuda.synchronize()
+    assert np.array_equal(D.cpu().numpy(), Li @ Ri)
+
+
+def test_gemm_oz_full_size_sampled():
+    """n = 4096 (seven slices, 28 slice pairs, 16 chunks): sampled entries
+    against the exact dot product."""
+    n = 4096
+    rng = np.random.default_rng(42)
+    L = rng.standard_normal((n, n))
+    R = rng.standard_normal((n, n))
+    D = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_oz(n, n, n, torch.from_numpy(L).to(dev), n, torch.from_numpy(R).to(dev), n, -1.0, None, 0, 0.0,
+                      1.0, D, n, 7)
+    torch.cuda.synchronize()
+    out = D.cpu().numpy()
+    idx = rng.integers(0, n, (64, 2))
+    idx[:8, 1] = idx[:8, 0]
+    for i, j in idx:
+        ex = float(-(L[i].astype(np.longdouble) @ R[:, j].astype(np.longdouble)) + (1.0 if i == j else 0.0))
+        ab = float(np.abs(L[i]) @ np.abs(R[:, j]))
+        assert abs(out[i, j] - ex) <= 16 * 2.0 ** -53 * (ab + abs(ex)), (i, j)

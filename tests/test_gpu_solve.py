@@ -383,6 +383,41 @@ def test_auto_resumes_in_bf16x6_when_richardson_stalls():
     assert rr <= 1e-10 + 0.5 * 2.0 ** -53 * 5e6, rr
 
 
+def test_fp64_path_with_slice_products_matches_cuda_cores():
+    """NS_FP64 with fp64_slices = 7 (FP64-accurate tensor-core products) follows
+    the CUDA-core FP64 path step for step: the same ||F_k||_F history to FP64
+    rounding, the same stopping, theta to the residual bar."""
+    n = 400
+    p = make_spd(n, 1e6, nrhs=2, seed=20)
+    runs = {}
+    for sl in (0, 7):
+        with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, fp64_slices=sl) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+        assert r.status == nsgb.NS_OK
+        assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1e-10 + 0.5 * 2.0 ** -53 * 1e6
+        runs[sl] = r
+    f0, f7 = runs[0].stats.frob_history(), runs[7].stats.frob_history()
+    assert len(f0) == len(f7)
+    for a, b in zip(f0, f7):
+        assert b == pytest.approx(a, rel=1e-9, abs=1e-11)
+
+
+def test_slice_products_solve_where_mixed_precision_cannot():
+    """kappa = 1e9 at n = 512: beyond what binary32 masters can carry (the mixed
+    path does not converge), the FP64 path with slice products reaches the
+    tolerance."""
+    n = 512
+    p = make_spd(n, 1e9, nrhs=1, seed=21)
+    with nsgb.Context(n, order=4) as ctx:
+        rm = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    assert rm.status != nsgb.NS_OK
+    with nsgb.Context(n, order=4, precision=nsgb.NS_FP64, fp64_slices=7) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(r.theta.cpu().numpy(), tstar) <= 10 * 1e9 * 1e-10 * 2
+
+
 def test_bf16x6_rejected_where_not_built():
     with pytest.raises(nsgb.NSError) as ei:
         nsgb.Context(64, order=2, rates=(2,), precision=nsgb.NS_BF16X6)
