@@ -205,7 +205,8 @@ ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const d
 ns_status ns_inverse_residual(ns_ctx* ctx, const double* A, const double* G, int probes,
                               unsigned long long seed, double* frob_out);
 
-/* Message for the last failing call on ctx ("" if none; static text for NULL). */
+/* Message for the last failing call on ctx ("" if none).  NULL: the last failure of a
+ * single-kernel entry point (ns_k_gemm_oz) on the calling host thread. */
 const char* ns_last_error(const ns_ctx* ctx);
 const char* ns_status_string(ns_status s);
 

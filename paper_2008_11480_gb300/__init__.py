@@ -392,7 +392,7 @@ def ns_k_gemm_oz(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float = 1.
     """FP64-accurate product from integer bf16 slices on the tensor cores (FP64 tensors)."""
     r = lib().ns_k_gemm_oz(M, N, K, _ptr(L), ldl, _ptr(R), ldr, s, _ptr(C), ldc, beta, gamma, _ptr(D), ldd, slices,
                            _ptr(frob_out), _stream_ptr(stream))
-    _raise(r, "ns_k_gemm_oz")
+    _raise(r, "ns_k_gemm_oz: " + lib().ns_last_error(None).decode())
 
 
 def ns_k_gemm_bf16(precision: int, M: int, N: int, K: int, Lhi, Llo, ldl: int, Rhi, Rlo, ldr: int, s: float = 1.0,

@@ -17,10 +17,12 @@
 //
 // Kernel layout: CTA pairs (tcgen05 cta_group::2), 256 x 128 output tiles
 // (CTA r: rows m0 + 128 r.., and R columns n0 + 64 r.. staged; its TMEM holds
-// its 128 rows x 128 columns), 320 threads: warp 0 TMA producer, warp 1 TMEM
-// allocation and (CTA 0) the MMA issuer, warps 2..9 epilogue (TMEM lane
-// quarter warp % 4, column half (warp - 2) / 4, one row of 64 columns per
-// thread).  A tile runs npairs * ceil(K / 256) rounds; each round is four
+// its 128 rows x 128 columns), 576 threads: warp 0 TMA producer, warp 1 TMEM
+// allocation and (CTA 0) the MMA issuer, warps 2..17 epilogue (TMEM lane
+// quarter warp % 4, column quarter (warp - 2) / 4: one row of 32 columns per
+// thread, whose int32 sums live in registers; eighteen warps leave 96
+// registers a thread, the register file being split over the SM's four
+// sub-partitions).  A tile runs npairs * ceil(K / 256) rounds; each round is four
 // 64-deep stages (L slice 128 x 64, R slice 64 x 64, 24 KiB per CTA) into one
 // of two TMEM accumulators, so the epilogue of a round overlaps the MMAs of the
 // next.  Synchronisation and bounded waits as in the pair kernel (gemm_tc2.cu).
@@ -31,10 +33,12 @@ namespace nsgb {
 
 namespace {
 
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kRows = 128;
 constexpr int kCols = 128;
-constexpr int kHalfCols = 64;
+constexpr int kHalfCols = 64;   // R columns staged by each CTA of the pair
+constexpr int kColsPer = 32;    // output columns per epilogue thread
 constexpr int kBK = 64;
 constexpr int kChunk = 256;
 constexpr int kABytes = kRows * kBK * 2;      // 16 KiB
@@ -54,7 +58,7 @@ __device__ __forceinline__ void spin_ns(uint64_t ns) {
     if (globaltimer_ns() - t0 > ns) break;
 }
 
-__global__ void __maxnreg__(200) k_gemm_oz(const __grid_constant__ OzParams p) {
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__ OzParams p) {
   const int rank = static_cast<int>(cluster_ctarank());
   const int first = blockIdx.x / 2;
   const int stride = gridDim.x / 2;
@@ -83,7 +87,7 @@ __global__ void __maxnreg__(200) k_gemm_oz(const __grid_constant__ OzParams p) {
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 16);  // one arrival per epilogue warp of either CTA
+      mbar_init(&tempty[a], 2 * kEpiWarps);  // one arrival per epilogue warp of either CTA
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -219,17 +223,17 @@ __global__ void __maxnreg__(200) k_gemm_oz(const __grid_constant__ OzParams p) {
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue (both CTAs)
     const int q = warp & 3;              // TMEM lane quarter
-    const int h = (warp - 2) >> 2;       // column half of the tile
+    const int h = (warp - 2) >> 2;       // column quarter of the tile
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int w = first; w < p.total_tiles && ok; w += stride) {
       const int row = ((w / p.tiles_n) * 2 + rank) * kRows + q * 32 + lane;
-      const int col0 = (w % p.tiles_n) * kCols + h * kHalfCols;
+      const int col0 = (w % p.tiles_n) * kCols + h * kColsPer;
       const double mu = row < p.M ? p.mu[row] : 0.0;
-      int s32[kHalfCols];
+      int s32[kColsPer];
 #pragma unroll
-      for (int j = 0; j < kHalfCols; ++j) s32[j] = 0;
+      for (int j = 0; j < kColsPer; ++j) s32[j] = 0;
       int since = 0;
       for (int r = 0; r < rounds; ++r) {
         bool got = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
@@ -242,14 +246,14 @@ __global__ void __maxnreg__(200) k_gemm_oz(const __grid_constant__ OzParams p) {
         }
         tc_fence_after();
         const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
-                            static_cast<uint32_t>(acc * kCols + h * kHalfCols);
+                            static_cast<uint32_t>(acc * kCols + h * kColsPer);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t v[32];
-          tmem_ld_32x32b_x32(tq + 32u * half, v);
+        for (int part = 0; part < kColsPer / 16; ++part) {
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tq + 16u * part, v);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) s32[32 * half + j] += __float2int_rn(__uint_as_float(v[j]));
+          for (int j = 0; j < 16; ++j) s32[16 * part + j] += __float2int_rn(__uint_as_float(v[j]));
         }
         tc_fence_before();
         __syncwarp();
@@ -268,13 +272,13 @@ __global__ void __maxnreg__(200) k_gemm_oz(const __grid_constant__ OzParams p) {
             const double sc = p.s * mu * ldexp(1.0, -8 * d);
             double* drow = p.D + static_cast<int64_t>(row) * p.ldd;
 #pragma unroll
-            for (int j = 0; j < kHalfCols; ++j) {
+            for (int j = 0; j < kColsPer; ++j) {
               const int col = col0 + j;
               if (col < p.N) drow[col] += sc * p.nu[col] * static_cast<double>(s32[j]);
             }
           }
 #pragma unroll
-          for (int j = 0; j < kHalfCols; ++j) s32[j] = 0;
+          for (int j = 0; j < kColsPer; ++j) s32[j] = 0;
           since = 0;
         }
       }

@@ -1543,8 +1543,15 @@ ns_status ns_set_stream(ns_ctx* ctx, void* stream) {
   return NS_OK;
 }
 
+// Last failure of a single-kernel entry point (ns_k_*) on this host thread.
+static thread_local std::string g_kernel_err;
+static ns_status kernel_fail(ns_status s, const char* what, cudaError_t e) {
+  g_kernel_err = std::string(what) + ": " + (e == cudaSuccess ? "" : cudaGetErrorString(e));
+  return s;
+}
+
 const char* ns_last_error(const ns_ctx* ctx) {
-  if (!ctx) return "null context";
+  if (!ctx) return g_kernel_err.c_str();
   return ctx->err.c_str();
 }
 
@@ -1981,17 +1988,25 @@ ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t
     if (ms > 0 && ms <= 10000) p.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
   }
   p.err = err;
-  if (e == cudaSuccess) e = launch_gemm_oz(p, sms, st);
+  const char* stage = "slicing";
+  if (e == cudaSuccess) {
+    stage = "product launch";
+    e = launch_gemm_oz(p, sms, st);
+  }
   if (e == cudaSuccess && frob_out) {
+    stage = "sum of squares";
     e = launch_colsumsq(D, ldd, static_cast<int>(M), static_cast<int>(N), sq, nullptr, st);
     if (e == cudaSuccess) e = launch_reduce_sum(sq, static_cast<int>(N), 1, frob_out, st);
   }
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(ws, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return NS_ERR_CUDA;
-  return herr == DEV_OK ? NS_OK : NS_ERR_TIMEOUT;
+  if (e == cudaSuccess) {
+    stage = "execution";
+    e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return kernel_fail(NS_ERR_CUDA, stage, e);
+  return herr == DEV_OK ? NS_OK : kernel_fail(NS_ERR_TIMEOUT, "bounded device wait ran out", cudaSuccess);
 }
 
 ns_status ns_k_gemm_f64(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R,
