@@ -111,9 +111,12 @@ typedef struct ns_options {
                           the final G by one FP64 product; s = 1..4096 Hutchinson's estimate with s
                           Rademacher probes and seed 0 (see ns_inverse_residual); into
                           ns_stats.final_frob.  On the mixed path G is the f32 master, widened. */
-  int fp64_slices;      /* precision NS_FP64 only: 0 (default) products on the FP64 CUDA cores;
-                          s = 2..8: FP64-accurate products on the bf16 tensor cores from s integer
-                          slices of 8 bits per operand (see ns_k_gemm_oz; 7 covers binary64) */
+  int fp64_slices;      /* 0 (default): FP64 products on the CUDA cores.  s = 2..8: FP64-accurate
+                          products on the bf16 tensor cores from s integer slices of 8 bits per
+                          operand (see ns_k_gemm_oz; 7 covers binary64) -- for precision NS_FP64,
+                          and with NS_AUTO (no composite rates) for a solve the binary32 masters
+                          cannot finish: after NS_NOT_CONVERGED or divergence the FP64 path with
+                          these products continues from the mixed solve's theta (NS from G0) */
 } ns_options;
 
 #define NS_MAX_HIST 256

@@ -1667,8 +1667,21 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   S.fp64 = fp64;
   S.theta0_given = Theta0 != nullptr;
   r = run(ctx, S, nullptr, iters, tol, true, st);
+  if (!fp64 && ctx->opt.precision == NS_AUTO && ctx->opt.fp64_slices > 0 && ctx->rates.empty() && tol > 0 &&
+      (r == NS_NOT_CONVERGED || r == NS_ERR_DIVERGED)) {
+    // the binary32 masters cannot carry this system: the FP64 path with
+    // slice products takes over, Newton-Schulz from G0, theta from where the
+    // mixed solve left it
+    r = ensure_f64(ctx);
+    if (r == NS_OK) {
+      ctx->err.clear();
+      S.fp64 = true;
+      S.theta0_given = true;
+      r = run(ctx, S, nullptr, iters, tol, true, st);
+    }
+  }
   if (r >= 0) {
-    const ns_status c = final_check(ctx, S.A, S.lda, fp64, S.cur, st);
+    const ns_status c = final_check(ctx, S.A, S.lda, S.fp64, S.cur, st);
     if (c != NS_OK) r = c;
   }
   if (r >= 0 && !out_dev) {

@@ -420,6 +420,19 @@ def test_slice_products_solve_where_mixed_precision_cannot():
     assert rel(r.theta.cpu().numpy(), tstar) <= 10 * kappa * tol
 
 
+def test_auto_hands_over_to_slice_products():
+    """AUTO with fp64_slices: the mixed solve of kappa = 1e8 cannot reach the
+    tolerance, the FP64 path with slice products takes over from its theta and
+    finishes (FP64 steps appear in the precision history)."""
+    n, kappa, tol = 1024, 1e8, 1e-7
+    p = make_spd(n, kappa, nrhs=1, seed=21)
+    with nsgb.Context(n, order=4, fp64_slices=7) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=tol)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert nsgb.NS_FP64 in r.stats.prec_history() and nsgb.NS_BF16 in r.stats.prec_history()
+    assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1.1 * tol
+
+
 def test_bf16x6_rejected_where_not_built():
     with pytest.raises(nsgb.NSError) as ei:
         nsgb.Context(64, order=2, rates=(2,), precision=nsgb.NS_BF16X6)
