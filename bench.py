@@ -386,12 +386,17 @@ def run_kernel_gemm(a):
     Lh, Ll = mk(), mk()
     nsgb.ns_k_split(L, Lh, Ll, n, n, n, n)
     D32, Dh, Dl = mk(torch.float32), mk(), mk()
-    prec = {"bf16": nsgb.NS_BF16, "bf16x3": nsgb.NS_BF16X3, "bf16x6": nsgb.NS_BF16X6}[a.precision]
+    prec = {"bf16": nsgb.NS_BF16, "bf16x3": nsgb.NS_BF16X3, "bf16x6": nsgb.NS_BF16X6,
+            "fp64slices": nsgb.NS_FP64}[a.precision]
+    D64 = torch.empty((n, n), dtype=torch.float64, device=dev) if prec == nsgb.NS_FP64 else None
     if prec == nsgb.NS_BF16X6:
         L3, D2 = mk(), mk()
         nsgb.ns_k_split3(L, Lh, Ll, L3, n, n, n, n)
 
     def call():
+        if prec == nsgb.NS_FP64:
+            nsgb.ns_k_gemm_oz(n, n, n, L, n, L, n, -1.0, None, 0, 0.0, 1.0, D64, n, 7)
+            return
         if prec == nsgb.NS_BF16X6:
             nsgb.ns_k_gemm_bf16x6(n, n, n, (Lh, Ll, L3), n, (Lh, Ll, L3), n, -1.0, None, 0, 0.0, 1.0, D32, n,
                                   (Dh, Dl, D2), n)
@@ -408,7 +413,7 @@ def run_kernel_gemm(a):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
-    passes = {nsgb.NS_BF16: 1, nsgb.NS_BF16X3: 3, nsgb.NS_BF16X6: 6}[prec]
+    passes = {nsgb.NS_BF16: 1, nsgb.NS_BF16X3: 3, nsgb.NS_BF16X6: 6, nsgb.NS_FP64: 28}[prec]
     print(json.dumps({"kernel": "k_gemm_tc", "n": n, "precision": a.precision, "bn": a.bn, "cm": a.cm,
                       "ms_per_call": ms, "tflops_incl_call_overhead": passes * 2 * n ** 3 / (ms * 1e-3) / 1e12}))
 
@@ -749,6 +754,69 @@ def run_small(a):
         "single_solve_latency": lat}), flush=True)
 
 
+def run_ill(a):
+    """Configuration 5 size: one ill-conditioned SPD system n = 16384, kappa =
+    1e6 (A = V diag(sigma^2) V^T with sigma log-uniform in [1e-3, 1], the Gram
+    matrix X^T X of X = U diag(sigma) V^T; built as Q diag(lambda) Q^T with
+    lambda log-uniform in [1e-6, 1] scaled), one RHS, order 8, tol 1e-10.  The
+    mixed path cannot carry G at this kappa and n (binary32 masters); AUTO with
+    fp64_slices = 7 hands the solve to the FP64 path with FP64-accurate
+    slice products on the tensor cores.  The plain FP64 path (products on the
+    CUDA cores) is estimated from one timed FP64 product times the products of
+    the slice-product run (a full run takes minutes)."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_spd_device
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n, kappa = a.n if "--n" in sys.argv else 16384, a.kappa if "--kappa" in sys.argv else 1e6
+    A, B = make_spd_device(n, kappa, nrhs=1, seed=a.seed, device=dev)
+    out = torch.empty_like(B)
+    runs = {}
+    for name, kw in [("auto + fp64 slice products", {"fp64_slices": 7}),
+                     ("fp64 path, slice products", {"precision": nsgb.NS_FP64, "fp64_slices": 7})]:
+        with nsgb.Context(n, order=8, stream=stream, couple_frob=a.couple, **kw) as ctx:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            rr = max(ctx.residual(A, out, B))
+        runs[name] = {"s": e0.elapsed_time(e1) / 1e3, "status": int(r.status), "rel_res": rr,
+                      "ns_iters": r.stats.ns_iters, "sweeps": r.stats.sweeps,
+                      "products": int(r.stats.gemm_launches), "prec_history": r.stats.prec_history()}
+    with nsgb.Context(n, order=8, stream=stream) as ctx:
+        r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
+        runs["mixed alone"] = {"status": int(r.status), "rel_res": max(ctx.residual(A, out, B))}
+    L = A
+    D = torch.empty_like(A)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nsgb.ns_k_gemm_f64(n, n, n, L, n, L, n, 1.0, None, 0, 0.0, 0.0, D, n, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    f64_product_s = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    nsgb.ns_k_gemm_oz(n, n, n, L, n, L, n, D=D, ldd=n, slices=7, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    oz_product_s = e0.elapsed_time(e1) / 1e3
+    best = runs["fp64 path, slice products"]
+    est_plain = f64_product_s * best["products"]
+    print(json.dumps({
+        "metric": METRIC + " (ill-conditioned n = 16384 system)", "value": 1.0 / runs["auto + fp64 slice products"]["s"],
+        "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (bf16 integer slices, exact accumulation)", "data": "synthetic",
+        "config": {"workload": f"dense SPD n={n} kappa={kappa:g} (Gram matrix of X = U diag(sigma) V^T, sigma "
+                               "log-uniform [1e-3, 1]), 1 RHS, order 8, tol 1e-10", "seed": a.seed},
+        "runs": runs, "fp64_product_s": f64_product_s, "slice_product_s": oz_product_s,
+        "plain_fp64_path_estimate": {"s": est_plain, "solves_per_s": 1.0 / est_plain,
+                                     "how": "one timed CUDA-core FP64 product x the products of the slice run"}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -766,12 +834,13 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=9)
     ap.add_argument("--kernel", default="", choices=["", "gemm"],
                     help="microbenchmark one kernel instead of the solve")
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6", "fp64slices"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
     ap.add_argument("--gemm-cluster", type=int, default=0,
                     help="single workload: product-kernel clustering (0 automatic, 1, 2, 4; -2 CTA pairs)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "orders", "small"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "serving", "orders", "small", "ill"],
                     help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems; "
                          "serving: continuous batching of a Poisson request trace")
     ap.add_argument("--count", type=int, default=2048)
@@ -795,6 +864,9 @@ def main():
         if "--steps" not in sys.argv:
             a.steps = 20
         run_small(a)
+        return
+    if a.workload == "ill" and a.impl == "ours":
+        run_ill(a)
         return
     if a.workload == "serving" and a.impl == "ours":
         if a.order == 8 and "--order" not in sys.argv:
