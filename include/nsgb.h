@@ -115,8 +115,8 @@ typedef struct ns_options {
                           products on the bf16 tensor cores from s integer slices of 8 bits per
                           operand (see ns_k_gemm_oz; 7 covers binary64) -- for precision NS_FP64,
                           and with NS_AUTO (no composite rates) for a solve the binary32 masters
-                          cannot finish: after NS_NOT_CONVERGED or divergence the FP64 path with
-                          these products continues from the mixed solve's theta (NS from G0) */
+                          cannot finish: after NS_NOT_CONVERGED or divergence the solve starts
+                          over on the FP64 path with these products (from G0 and theta0) */
 } ns_options;
 
 #define NS_MAX_HIST 256

@@ -1670,13 +1670,19 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   if (!fp64 && ctx->opt.precision == NS_AUTO && ctx->opt.fp64_slices > 0 && ctx->rates.empty() && tol > 0 &&
       (r == NS_NOT_CONVERGED || r == NS_ERR_DIVERGED)) {
     // the binary32 masters cannot carry this system: the FP64 path with
-    // slice products takes over, Newton-Schulz from G0, theta from where the
-    // mixed solve left it
+    // slice products starts over (Newton-Schulz from G0, theta from the
+    // caller's theta0 -- a mixed attempt that did not contract may have left
+    // theta worse than it found it)
     r = ensure_f64(ctx);
+    if (r == NS_OK) {
+      e = Theta0 ? (Theta0 == Th ? cudaSuccess
+                                 : cudaMemcpyAsync(Th, Theta0, nb * sizeof(double), cudaMemcpyDefault, ctx->stream))
+                 : cudaMemsetAsync(Th, 0, nb * sizeof(double), ctx->stream);
+      r = e == cudaSuccess ? NS_OK : fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+    }
     if (r == NS_OK) {
       ctx->err.clear();
       S.fp64 = true;
-      S.theta0_given = true;
       r = run(ctx, S, nullptr, iters, tol, true, st);
     }
   }
