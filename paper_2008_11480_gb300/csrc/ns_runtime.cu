@@ -112,6 +112,7 @@ struct ns_ctx {
   double* oz_mu = nullptr;
   double* oz_nu = nullptr;
   double* oz_sq = nullptr;
+  int oz_now = 0;  // slices of the current product (fewer while ||F_k||_F >= 1)
   double *G64[2] = {nullptr, nullptr}, *X64[2] = {nullptr, nullptr}, *F64 = nullptr, *P64[2] = {nullptr, nullptr};
   std::vector<double*> T64[2];
   double *Gam64 = nullptr, *Tc64[2] = {nullptr, nullptr}, *Pre64[2] = {nullptr, nullptr}, *Xs64[2] = {nullptr, nullptr};
@@ -453,7 +454,7 @@ ns_status oz_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const
                   double* D, double* frob_dst) {
   const int n = static_cast<int>(ctx->n);
   const int64_t ld = ctx->ld;
-  const int ns = ctx->opt.fp64_slices;
+  const int ns = ctx->oz_now > 0 ? ctx->oz_now : ctx->opt.fp64_slices;
   cudaStream_t st = ctx->stream;
   const size_t per = static_cast<size_t>(n) * ld;
   if (ctx->oz_L == nullptr) {
@@ -894,6 +895,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     return NS_OK;
   };
   if (!fp64 && ctx->opt.precision == NS_BF16X6) NS_TRY(x6_prepare(0));
+  // FP64 slice products: while ||F_k||_F >= 1 the step's own error is corrected
+  // by the steps after it, so four slices (10 pairs, a 2^-32 split) do; the
+  // full count takes over below one or at that precision's floor
+  constexpr int kOzEarly = 4;
+  const int oz_full = fp64 ? ctx->opt.fp64_slices : 0;
+  ctx->oz_now = oz_full > kOzEarly ? kOzEarly : oz_full;
 
   // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
   // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
@@ -1153,6 +1160,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       frob = std::sqrt(ctx->hscal[2]);
       push_frob(frob, prec);
       if (!std::isfinite(frob)) return fail(ctx, NS_ERR_NONFINITE, "||F||_F is not finite");
+      if (ctx->oz_now < oz_full && frob < 1.0) ctx->oz_now = oz_full;
       const double ratio = frob / prev_frob;
       if (autop && prec == NS_BF16 && done >= 2 && frob < prev_frob && ratio > prev_ratio + 0.02) {
         // the contraction of ||F||_F got worse: bf16 rounding noise is becoming
@@ -1223,6 +1231,17 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           // above ||F||_F = 1, more steps only repeat it (Richardson takes
           // over if rho(I - A G) < 1)
           floor_hit = true;
+        }
+        if (floor_hit && ctx->oz_now < oz_full) {
+          // the floor of the reduced slice count: full slices from G_k on
+          if (frob > prev_frob) {
+            S.cur ^= 1;
+            done--;
+          }
+          ctx->oz_now = oz_full;
+          prev_frob = INFINITY;
+          prev_ratio = INFINITY;
+          goto recompute_F;
         }
         if (floor_hit) {
           if (frob > prev_frob) {
