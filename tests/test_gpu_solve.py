@@ -399,8 +399,9 @@ def test_fp64_path_with_slice_products_matches_cuda_cores():
         runs[sl] = r
     f0, f7 = runs[0].stats.frob_history(), runs[7].stats.frob_history()
     assert len(f0) == len(f7)
+    # the early four-slice products differ from FP64 by ~kappa 2^-32 = 2.3e-4 relative
     for a, b in zip(f0, f7):
-        assert b == pytest.approx(a, rel=1e-4, abs=1e-6)
+        assert b == pytest.approx(a, rel=10 * 1e6 * 2.0 ** -32, abs=1e-6)
 
 
 def test_slice_products_solve_where_mixed_precision_cannot():
