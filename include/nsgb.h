@@ -117,6 +117,9 @@ typedef struct ns_options {
                           and with NS_AUTO (no composite rates) for a solve the binary32 masters
                           cannot finish: after NS_NOT_CONVERGED or divergence the solve starts
                           over on the FP64 path with these products (from G0 and theta0) */
+  int fp64_slices_early; /* slices of the products while ||F_k||_F >= 1 (their error is corrected
+                          by the later steps); the full fp64_slices take over below one or at
+                          the reduced count's floor.  Default 4; 0: always fp64_slices */
 } ns_options;
 
 #define NS_MAX_HIST 256

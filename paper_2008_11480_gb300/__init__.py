@@ -69,6 +69,7 @@ class ns_options(ctypes.Structure):
         ("g0_order", ctypes.c_int),
         ("final_check", ctypes.c_int),
         ("fp64_slices", ctypes.c_int),
+        ("fp64_slices_early", ctypes.c_int),
     ]
 
 

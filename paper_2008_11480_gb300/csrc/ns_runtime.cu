@@ -896,11 +896,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   };
   if (!fp64 && ctx->opt.precision == NS_BF16X6) NS_TRY(x6_prepare(0));
   // FP64 slice products: while ||F_k||_F >= 1 the step's own error is corrected
-  // by the steps after it, so four slices (10 pairs, a 2^-32 split) do; the
-  // full count takes over below one or at that precision's floor
-  constexpr int kOzEarly = 4;
+  // by the steps after it, so fewer slices do (option fp64_slices_early; four:
+  // 10 pairs, a 2^-32 split); the full count takes over below one or at the
+  // reduced count's floor
   const int oz_full = fp64 ? ctx->opt.fp64_slices : 0;
-  ctx->oz_now = oz_full > kOzEarly ? kOzEarly : oz_full;
+  const int oz_early = ctx->opt.fp64_slices_early > 0 ? ctx->opt.fp64_slices_early : oz_full;
+  ctx->oz_now = oz_full > oz_early ? oz_early : oz_full;
 
   // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
   // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
@@ -1477,6 +1478,7 @@ void ns_default_options(ns_options* o) {
   o->gemm_cluster = 0;
   o->final_check = 0;
   o->fp64_slices = 0;
+  o->fp64_slices_early = 4;
   o->couple_frob = 0.0;
   o->accel_richardson = 0;
   o->g0_order = 0;
@@ -1516,6 +1518,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   if (o.final_check < -1 || o.final_check > 4096) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
+  if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state
