@@ -52,6 +52,22 @@ constexpr int kFlushRounds = 128;
 static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
 
+// Named barrier 2 over the epilogue warps with an AND over their votes: every
+// epilogue thread learns whether all of them may go on (the waits before it
+// are bounded, so every thread reaches it and the warps stop together).
+__device__ __forceinline__ bool epi_all(bool ok) {
+  uint32_t all;
+  asm volatile(
+      "{\n\t.reg .pred q, r;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred r, 2, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, r;\n\t}"
+      : "=r"(all)
+      : "r"(ok ? 1u : 0u), "r"(kEpiWarps * 32)
+      : "memory");
+  return all != 0;
+}
+
 __device__ __forceinline__ void spin_ns(uint64_t ns) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 0; it < 0x10000000u; ++it)
@@ -87,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 2 * kEpiWarps);  // one arrival per epilogue warp of either CTA
+      mbar_init(&tempty[a], 2);  // one arrival per CTA once its epilogue warps have read the accumulator
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -236,11 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
       for (int j = 0; j < kColsPer; ++j) s32[j] = 0;
       int since = 0;
       for (int r = 0; r < rounds; ++r) {
-        bool got = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
-        got = __all_sync(0xffffffffu, got);
-        if (!got) {
+        const bool got = mbar_wait(&tfull[acc], acc_phase, tlim, abort_flag);
+        if (!epi_all(got)) {  // all epilogue warps stop at the same round
           *abort_flag = 1;
-          if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+          if (!got) atomicExch(p.err, DEV_TIMEOUT);
           ok = false;
           break;
         }
@@ -255,9 +270,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
 #pragma unroll
           for (int j = 0; j < 16; ++j) s32[16 * part + j] += __float2int_rn(__uint_as_float(v[j]));
         }
+        // all sixteen epilogue warps are done with this accumulator: one
+        // arrival per CTA (a cluster-scope release per warp and round stalled
+        // the warps on memory barriers).  No thread can leave between the
+        // vote above and this barrier.
         tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(tempty0 + static_cast<uint32_t>(acc * 8));
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+        if (threadIdx.x == 64) {
+          if (rank == 0)
+            mbar_arrive(&tempty[acc]);
+          else
+            mbar_arrive_cluster(tempty0 + static_cast<uint32_t>(acc * 8));
+        }
         if (++acc == 2) {
           acc = 0;
           acc_phase ^= 1u;
