@@ -24,8 +24,8 @@
 // registers a thread, the register file being split over the SM's four
 // sub-partitions).  A tile runs npairs * ceil(K / 256) rounds; each round is four
 // 64-deep stages (L slice 128 x 64, R slice 64 x 64, 24 KiB per CTA) into one
-// of two TMEM accumulators, so the epilogue of a round overlaps the MMAs of the
-// next.  Synchronisation and bounded waits as in the pair kernel (gemm_tc2.cu).
+// of four TMEM accumulators (all 512 columns), so the MMAs run up to three
+// rounds ahead of the epilogue.  Synchronisation and bounded waits as in the pair kernel (gemm_tc2.cu).
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -45,12 +45,13 @@ constexpr int kABytes = kRows * kBK * 2;      // 16 KiB
 constexpr int kBBytes = kHalfCols * kBK * 2;  // 8 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kStages = 8;
-constexpr uint32_t kTmemCols = 2 * kCols;
+constexpr int kAcc = 4;  // TMEM accumulators: the MMAs run up to three rounds ahead of the epilogue
+constexpr uint32_t kTmemCols = kAcc * kCols;  // all 512 columns
 constexpr int kBarBytes = 256;
 constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
 constexpr int kFlushRounds = 128;
 static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
+static_assert((2 * kStages + 2 * kAcc + 1) * 8 + 8 <= kBarBytes, "barrier area");
 
 // Named barrier 2 over the epilogue warps with an AND over their votes: every
 // epilogue thread learns whether all of them may go on (the waits before it
@@ -88,8 +89,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* tfull = bars + 2 * kStages;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;
+  uint64_t* tempty = tfull + kAcc;
+  uint64_t* drain = tempty + kAcc;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < kAcc; ++a) {
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 2);  // one arrival per CTA once its epilogue warps have read the accumulator
     }
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
         }
         if (!ok) break;
         tc_commit_pair_mc(&tfull[acc], 0x3);
-        if (++acc == 2) {
+        if (++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const __grid_constant__
           else
             mbar_arrive_cluster(tempty0 + static_cast<uint32_t>(acc * 8));
         }
-        if (++acc == 2) {
+        if (++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
