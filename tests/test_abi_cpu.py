@@ -114,6 +114,42 @@ def test_create_rejects_bad_precision(L):
     assert L.ns_create(16, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG
 
 
+def test_create_validates_precision_options(L):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * 1)(2)
+    for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
+               {"fp64_slices_early": 9}, {"final_check": -2}, {"final_check": 4097}):
+        opt = nsgb.default_options(**kw)
+        assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG, kw
+    # bf16x6 needs the third split part, which composite loops and form 3 do not carry
+    opt = nsgb.default_options(precision=nsgb.NS_BF16X6)
+    assert L.ns_create(64, 4, arr, 1, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
+    opt = nsgb.default_options(precision=nsgb.NS_BF16X6, form=3)
+    assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
+    d = nsgb.default_options()
+    assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0
+
+
+def test_new_kernel_entry_points_validate_before_launch(L):
+    vp = ctypes.c_void_p
+    three = (vp * 3)(16, 16, 16)
+    none3 = (vp * 3)(16, None, 16)
+    # x6 products: null parts, K = 0, unaligned leading dimensions
+    assert L.ns_k_gemm_bf16x6(64, 64, 64, none3, 64, three, 64, 1.0, None, 0, 0.0, 0.0, None, 0, None, 0, None,
+                              None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_bf16x6(64, 64, 0, three, 64, three, 64, 1.0, None, 0, 0.0, 0.0, None, 0, None, 0, None,
+                              None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_bf16x6(64, 64, 64, three, 60, three, 64, 1.0, None, 0, 0.0, 0.0, None, 0, None, 0, None,
+                              None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_split3(16, 0, 4, 4, 4, 16, 16, None, 4, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_split3(16, 2, 4, 4, 4, 16, 16, 16, 4, None) == nsgb.NS_ERR_ARG
+    # slice products: slice count outside 2..8, null output, short leading dimension
+    for sl in (1, 9):
+        assert L.ns_k_gemm_oz(8, 8, 8, 16, 8, 16, 8, 1.0, None, 0, 0.0, 0.0, 16, 8, sl, None, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_oz(8, 8, 8, 16, 8, 16, 8, 1.0, None, 0, 0.0, 0.0, None, 8, 7, None, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_oz(8, 8, 8, 16, 4, 16, 8, 1.0, None, 0, 0.0, 0.0, 16, 8, 7, None, None) == nsgb.NS_ERR_ARG
+
+
 def test_horner_form_accepts_any_order(L):
     opt = nsgb.default_options(form=1)
     h = ctypes.c_void_p()
