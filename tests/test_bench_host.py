@@ -1,0 +1,39 @@
+"""Host-side logic of the benchmark that needs no GPU: the per-launch DRAM
+traffic recorded with an ncu capture is reported only while the kernel
+sources hash to the values recorded with it."""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _record(tmp_path, files, nbytes, digest):
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    (tmp_path / "profiles" / "t.md").write_text(
+        "# capture\n\ntraffic_bytes_per_launch: %d\nkernel_sources: %s\nkernel_sources_sha256: %s\n"
+        % (nbytes, " ".join(files), digest))
+
+
+def test_recorded_traffic_follows_the_sources(tmp_path, monkeypatch):
+    (tmp_path / "k1.cu").write_text("kernel one\n")
+    (tmp_path / "k2.cuh").write_text("kernel two\n")
+    h = hashlib.sha256()
+    for f in ("k1.cu", "k2.cuh"):
+        h.update((tmp_path / f).read_bytes())
+    _record(tmp_path, ["k1.cu", "k2.cuh"], 123456789, h.hexdigest())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("t.md") == 123456789.0
+    (tmp_path / "k2.cuh").write_text("kernel two, changed\n")
+    assert bench.recorded_traffic("t.md") is None            # kernel changed since the capture
+    assert bench.recorded_traffic("missing.md") is None      # no capture
+
+
+def test_repository_record_is_well_formed():
+    txt = open(os.path.join(ROOT, "profiles", "traffic_k_gemm_tc2_bench_n4096.md")).read()
+    assert "traffic_bytes_per_launch:" in txt and "kernel_sources_sha256:" in txt
+    for f in txt.split("kernel_sources:")[1].splitlines()[0].split():
+        assert os.path.exists(os.path.join(ROOT, f)), f
