@@ -109,7 +109,8 @@ typedef struct ns_options {
                           order h from S^{-1} (bf16x3 products on the mixed path) */
   int final_check;      /* after ns_invert / ns_richardson_solve: 0 (default) none; -1 ||I - A G||_F of
                           the final G by one FP64 product; s = 1..4096 Hutchinson's estimate with s
-                          Rademacher probes and seed 0 (see ns_inverse_residual); into
+                          Rademacher probes and seed 0 (see ns_inverse_residual); -2 the FP64
+                          product for n <= 4096 and 8 probes above; into
                           ns_stats.final_frob.  On the mixed path G is the f32 master, widened. */
   int fp64_slices;      /* 0 (default): FP64 products on the CUDA cores.  s = 2..8: FP64-accurate
                           products on the bf16 tensor cores from s integer slices of 8 bits per

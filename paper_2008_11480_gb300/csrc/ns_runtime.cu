@@ -1425,7 +1425,9 @@ ns_status inverse_check(ns_ctx* ctx, const double* A, int64_t lda, const double*
 ns_status final_check(ns_ctx* ctx, const double* A, int64_t lda, bool fp64, int cur, ns_stats* st) {
   if (ctx->opt.final_check == 0 || st == nullptr) return NS_OK;
   const int n = static_cast<int>(ctx->n);
-  const int probes = ctx->opt.final_check > 0 ? ctx->opt.final_check : 0;
+  // -2: the exact form up to n = 4096 (one FP64 product), 8 probes above
+  const int probes = ctx->opt.final_check > 0 ? ctx->opt.final_check
+                                              : (ctx->opt.final_check == -2 && n > 4096 ? 8 : 0);
   if (fp64) return inverse_check(ctx, A, lda, ctx->G64[cur], ctx->ld, probes, 0ull, &st->final_frob);
   // the mixed path's G is its f32 master: widen it once for the FP64 check
   double* G = nullptr;
@@ -1516,7 +1518,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.timeout_s <= 0) o.timeout_s = 2.0;
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
-  if (o.final_check < -1 || o.final_check > 4096) return NS_ERR_ARG;
+  if (o.final_check < -2 || o.final_check > 4096) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)

@@ -10,7 +10,7 @@ import torch
 
 import oracle as O
 import paper_2008_11480_gb300 as nsgb
-from workloads import make_spd
+from workloads import make_spd, make_spd_device
 
 pytestmark = pytest.mark.gpu
 dev = torch.device("cuda:0")
@@ -72,13 +72,14 @@ def test_host_buffers_and_argument_errors():
 
 
 @pytest.mark.parametrize("precision", [nsgb.NS_AUTO, nsgb.NS_FP64])
-@pytest.mark.parametrize("check", [-1, 16])
+@pytest.mark.parametrize("check", [-1, -2, 16])
 def test_final_check_option(precision, check):
     n = 200
     p = make_spd(n, 1e3, nrhs=2, seed=52)
     with nsgb.Context(n, order=4, precision=precision, final_check=check) as ctx:
         G, st = ctx.invert(tens(p.A), iters=5)
         Gn = G.cpu().numpy()
+        # -2 takes the exact form at this size
         want = O.inverse_residual(p.A, Gn) if check < 0 else O.inverse_residual_hutchinson(p.A, Gn, check, 0)
         assert st.final_frob == pytest.approx(want, rel=1e-10, abs=1e-13)
         r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
@@ -89,3 +90,15 @@ def test_final_check_option(precision, check):
     with nsgb.Context(n, order=4, precision=precision) as ctx:
         _, st = ctx.invert(tens(p.A), iters=2)
         assert st.final_frob == -1.0
+
+
+@pytest.mark.parametrize("precision", [nsgb.NS_AUTO, nsgb.NS_FP64])
+def test_final_check_auto_uses_probes_above_4096(precision):
+    """final_check = -2 above n = 4096: Hutchinson's estimate with 8 probes and
+    seed 0, the same number the oracle's estimator gives for the same G."""
+    n = 4100
+    A, _ = make_spd_device(n, 1e2, nrhs=1, seed=53, device=torch.device("cuda:0"))
+    with nsgb.Context(n, order=4, precision=precision, final_check=-2) as ctx:
+        G, st = ctx.invert(A, iters=3)
+        want = O.inverse_residual_hutchinson(A.cpu().numpy(), G.cpu().numpy(), 8, 0)
+        assert st.final_frob == pytest.approx(want, rel=1e-9, abs=1e-12)
