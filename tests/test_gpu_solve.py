@@ -520,6 +520,32 @@ def test_errors_leave_context_usable():
         assert r.status == nsgb.NS_OK
 
 
+def test_config5_size_solve_with_slice_products():
+    """The ill-conditioned n = 16384 system (kappa = 1e6: eigenvalues
+    log-uniform over six decades, as A = X^T X with sigma log-uniform in
+    [1e-3, 1]) in the launch configuration the benchmark times: AUTO with
+    fp64_slices = 7, order 8, one RHS, tol 1e-10.  The mixed attempt cannot
+    finish (binary32 masters) and hands over to the FP64 path with slice
+    products.  Checked at full size by properties: the FP64 residual through
+    the library and in torch, and theta against the closed form
+    Q diag(1/lam) Q^T b from the generator's factors."""
+    from workloads import make_spd_device
+    n, kappa = 16384, 1e6
+    A, B, Q, lam = make_spd_device(n, kappa, nrhs=1, seed=5, device=dev, return_factors=True)
+    tstar = Q @ ((Q.T @ B) / lam[:, None])
+    del Q
+    torch.cuda.empty_cache()
+    with nsgb.Context(n, order=8, fp64_slices=7, couple_frob=1.0) as ctx:
+        r = ctx.solve(A, B, iters=80, tol=1e-10)
+        assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history()[-5:])
+        assert max(ctx.residual(A, r.theta, B)) <= 1e-10
+    # an FP64 evaluation of b - A theta itself carries about u kappa of ||b||
+    res = torch.linalg.vector_norm(B - A @ r.theta) / torch.linalg.vector_norm(B)
+    assert float(res) <= 1e-10 + 8 * 2.0 ** -53 * kappa
+    err = torch.linalg.vector_norm(r.theta - tstar) / torch.linalg.vector_norm(tstar)
+    assert float(err) <= 10 * kappa * 1e-10
+
+
 def test_bench_size_solve():
     """The benchmark workload: n = 4096, kappa = 1e4, 4 RHS, order 8, mixed
     precision; the residual is recomputed in FP64 by the oracle and theta is

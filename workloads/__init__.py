@@ -163,13 +163,15 @@ def make_serving_trace(rate_per_s: float, duration_s: float, seed: int = 0,
     return out
 
 
-def make_spd_device(n: int, kappa: float, nrhs: int = 1, seed: int = 0, device="cuda", qr_on_host: bool = False):
+def make_spd_device(n: int, kappa: float, nrhs: int = 1, seed: int = 0, device="cuda", qr_on_host: bool = False,
+                    return_factors: bool = False):
     """The system ``make_spd(n, kappa, nrhs, seed)`` describes, built on a torch
     device: the same Gaussian draws, spectrum and B from the same seed, with
     the QR and Q diag(lam) Q^T done in FP64 by torch on ``device`` (so large
     pools of systems can be drawn quickly; A agrees with make_spd's to
     rounding).  ``qr_on_host`` does the QR with torch on the CPU instead.
-    Returns (A, B) as device tensors."""
+    Returns (A, B) as device tensors, or (A, B, Q, lam) with
+    ``return_factors`` (the closed-form solution is Q diag(1/lam) Q^T B)."""
     import torch
 
     rng = np.random.default_rng(seed)
@@ -184,4 +186,6 @@ def make_spd_device(n: int, kappa: float, nrhs: int = 1, seed: int = 0, device="
     Q = Q * torch.sign(torch.diagonal(R))[None, :]
     A = (Q * lam[None, :]) @ Q.T
     A = 0.5 * (A + A.T)
+    if return_factors:
+        return A.contiguous(), B.contiguous(), Q, lam
     return A.contiguous(), B.contiguous()
