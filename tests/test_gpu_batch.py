@@ -68,6 +68,10 @@ def test_batch_harmonic_instances():
         if r["status"] == nsgb.NS_OK:
             nconv += 1
             assert rr <= 1e-10
+            # b = A theta* by construction: the exact answer within cond(A) x the residual
+            kap = float(np.linalg.cond(p.A))
+            err = np.linalg.norm(th.cpu().numpy().ravel() - p.theta_star.ravel()) / np.linalg.norm(p.theta_star)
+            assert err <= 10 * kap * 1e-10 + 1e-12, (p.n, kap, err)
         else:
             assert r["status"] in (nsgb.NS_NOT_CONVERGED, nsgb.NS_ERR_DIVERGED, nsgb.NS_ERR_NONFINITE)
     assert nconv == st.converged

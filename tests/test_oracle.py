@@ -665,3 +665,24 @@ def test_ozaki_product_against_exact_arithmetic():
     Li = rng.integers(-1000, 1000, (9, 13)).astype(float)
     Ri = rng.integers(-1000, 1000, (13, 7)).astype(float)
     assert np.array_equal(O.ozaki_product(Li, Ri, 7), Li @ Ri)
+
+
+def test_solve_reaches_harmonic_exact_answer():
+    """Harmonic-regressor Gram systems are built as b = A theta* (theta* drawn
+    by the generator), so the oracle's solve must land on theta* within
+    cond(A) times its residual: an independent pin of the whole solve
+    (Newton-Schulz, Richardson, stopping) on the batched workload's systems."""
+    from workloads import make_harmonic
+    rng = np.random.default_rng(21)
+    checked = 0
+    for m in (4, 6, 9, 12, 16):
+        p = make_harmonic(m, rng=rng)
+        kap = float(np.linalg.cond(p.A))
+        if kap > 1e7:
+            continue
+        r = O.ns_richardson_solve(p.A, p.B, order=4, ns_iters=40, tol=1e-12, max_sweeps=400)
+        assert r.converged, (m, kap, r.rel_res[-3:])
+        err = np.linalg.norm(r.theta - p.theta_star) / np.linalg.norm(p.theta_star)
+        assert err <= 10 * kap * (1e-12 + p.n * 2.0 ** -53), (m, kap, err)
+        checked += 1
+    assert checked >= 3
