@@ -686,3 +686,27 @@ def test_solve_reaches_harmonic_exact_answer():
         assert err <= 10 * kap * (1e-12 + p.n * 2.0 ** -53), (m, kap, err)
         checked += 1
     assert checked >= 3
+
+
+def test_solve_reaches_gram_closed_form():
+    """The Gram system of the large ill-conditioned workload, at a small size:
+    X = U diag(sigma) V^T (2n x n, U and V Haar), A = X^T X, b = X^T y.  Its
+    exact answer is theta* = V diag(1/sigma) U^T y (the least-squares solution
+    of X theta = y), known from the factors without any solve; the oracle's
+    order-8 solve reaches it within cond(A) times its residual."""
+    n = 48
+    rng = np.random.default_rng(22)
+    U, _ = np.linalg.qr(rng.standard_normal((2 * n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sigma = np.exp(rng.uniform(np.log(1e-2), 0.0, n))
+    X = (U * sigma) @ V.T
+    y = rng.standard_normal((2 * n, 1))
+    A = X.T @ X
+    A = 0.5 * (A + A.T)
+    b = X.T @ y
+    tstar = V @ ((U.T @ y) / sigma[:, None])
+    kap = float((sigma.max() / sigma.min()) ** 2)
+    r = O.ns_richardson_solve(A, b, order=8, ns_iters=30, tol=1e-12, max_sweeps=400)
+    assert r.converged, r.rel_res[-3:]
+    err = np.linalg.norm(r.theta - tstar) / np.linalg.norm(tstar)
+    assert err <= 10 * kap * (1e-12 + n * 2.0 ** -53), (kap, err)
