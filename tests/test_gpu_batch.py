@@ -8,7 +8,7 @@ import torch
 
 import oracle as O
 import paper_2008_11480_gb300 as nsgb
-from workloads import make_harmonic, make_spd
+from workloads import make_harmonic, make_harmonic_batch, make_spd
 
 pytestmark = pytest.mark.gpu
 dev = torch.device("cuda:0")
@@ -76,6 +76,28 @@ def test_batch_harmonic_instances():
             assert r["status"] in (nsgb.NS_NOT_CONVERGED, nsgb.NS_ERR_DIVERGED, nsgb.NS_ERR_NONFINITE)
     assert nconv == st.converged
     assert nconv >= len(probs) // 3
+
+
+def test_batch_full_harmonic_workload():
+    """The batched benchmark's workload in its launch configuration: 2048
+    harmonic-regressor systems (m ~ U{8..128}, n = 2m, seed 3), one RHS, order
+    4, couple_frob 1, one batched solve.  Every instance reported converged has
+    an FP64 residual <= 1e-10 recomputed by the oracle, every other one carries
+    a non-converged status, the count matches the batch statistics, and most
+    converge (the rest have cond(A) beyond what binary32 masters carry)."""
+    probs = make_harmonic_batch(2048, seed=3)
+    with nsgb.Batch([p.n for p in probs], [1] * len(probs), order=4, couple_frob=1.0) as bt:
+        outs, status, st = bt.solve([tens(p.A) for p in probs], [tens(p.B) for p in probs], iters=60, tol=1e-10)
+        res = [bt.result(i) for i in range(len(probs))]
+    nconv = 0
+    for p, th, r in zip(probs, outs, res):
+        if r["status"] == nsgb.NS_OK:
+            nconv += 1
+            assert float(np.max(O.rel_residual(p.A, th.cpu().numpy(), p.B))) <= 1e-10, p.n
+        else:
+            assert r["status"] in (nsgb.NS_NOT_CONVERGED, nsgb.NS_ERR_DIVERGED, nsgb.NS_ERR_NONFINITE)
+    assert nconv == st.converged
+    assert nconv >= 1700
 
 
 def test_batch_delayed_coupling():
