@@ -407,6 +407,16 @@ def test_delayed_coupling_error_model(order):
     assert np.array_equal(r0.theta, r1.theta)
 
 
+def test_rel_residual_closed_forms():
+    """theta = (1 - t_c) A^{-1} b_c leaves r_c = t_c b_c, so the per-column
+    relative residual is t_c exactly (to rounding); theta = 0 gives 1."""
+    pr = spd(12, 10.0, nrhs=3, seed=23)
+    t = np.array([1.0, 0.5, 1e-3])
+    theta = np.linalg.solve(pr.A, pr.B) * (1.0 - t)[None, :]
+    assert np.allclose(O.rel_residual(pr.A, theta, pr.B), t, rtol=1e-9, atol=1e-13)
+    assert np.array_equal(O.rel_residual(pr.A, np.zeros_like(pr.B), pr.B), np.ones(3))
+
+
 def test_richardson_converges_to_cholesky():
     pr = spd(32, 100.0, nrhs=3, seed=20)
     r = O.ns_richardson_solve(pr.A, pr.B, order=4, ns_iters=8, tol=1e-12, max_sweeps=50)

@@ -210,3 +210,91 @@ def test_ozaki_level_weight_off_by_one(monkeypatch):
         return out * mu[:, None] * nu[None, :]
     _patch(monkeypatch, "ozaki_product", bad)
     assert _fails(T.test_ozaki_product_against_exact_arithmetic)
+
+
+def test_alpha_inf_missing_half(monkeypatch):
+    """alpha_s = ||A||_inf + eps instead of ||A||_inf / 2 + eps (Section 2)."""
+    _patch(monkeypatch, "alpha_inf", lambda A, eps=None: 1.0 / (1.0 + 1e-8) / np.linalg.norm(A, np.inf))
+    assert _fails(T.test_alpha_inf_matches_definition_and_contracts)
+
+
+def test_jacobi_returns_diagonal_not_inverse(monkeypatch):
+    _patch(monkeypatch, "jacobi_preconditioner", lambda A: np.diag(np.diag(A)))
+    assert _fails(T.test_jacobi_splitting_contracts_for_sdd)
+
+
+def test_initial_series_one_term_short(monkeypatch):
+    """G0 = sum_{j < h-1} (S^{-1}D)^j S^{-1}: one term of eq. g01 dropped."""
+    orig = N.initial_series
+
+    def bad(A, S_inv, p, w, cnt=None):
+        G0, F0 = orig(A, S_inv, p, w, cnt)
+        SD = N.splitting_residual(A, S_inv)
+        return G0 - np.linalg.matrix_power(SD, w * (p + 1) - 1) @ S_inv, F0
+    _patch(monkeypatch, "initial_series", bad)
+    assert _fails(T.test_initial_series_g01_g03, 1, 2)
+
+
+def test_toolkit_p_and_w_swapped(monkeypatch):
+    """Reading a table row's (p, w) the wrong way round: h = 5 (eq. ztab2 with
+    p = 1, w = 2) becomes order w (p + 1) + 1 = 4 with the pair swapped."""
+    def bad(X, A, h, cnt=None):
+        kind, p, w = N.TOOLKIT_TABLE[h]
+        if kind == "z":
+            return N.unified_factorization(X, A, w, p, cnt)
+        return N.schroder_traub(X, A, w, p, cnt)
+    _patch(monkeypatch, "toolkit", bad)
+    assert _fails(T.test_toolkit_rows_equal_series, 5)
+
+
+def test_order3_dropped_linear_term(monkeypatch):
+    """W = F F instead of F + F F: G (I + F^2) is not the order-3 step."""
+    def bad(A, G, cnt=None):
+        F = N.residual_right(A, G, cnt)
+        return G + N.mm(G, N.mm(F, F, cnt), cnt), F
+    _patch(monkeypatch, "ns_step_order3", bad)
+    assert _fails(T.test_exponent_law_plain_ns, 3, "factorized")
+
+
+def test_nested45_missing_square_in_outer_factor(monkeypatch):
+    """Outer factor (I + Y18)(Y9) instead of (I + Y18)(Y9 + Y18) (eq. ex3)."""
+    def bad(X, A, cnt=None):
+        I = N._eye_like(A)
+        XA = N.mm(X, A, cnt)
+        W3 = N.mm(3.0 * I + N.mm(XA, -3.0 * I + XA, cnt), X, cnt)
+        Y3 = I - N.mm(W3, A, cnt)
+        W9 = N.mm(Y3, N.mm(Y3, W3, cnt) + W3, cnt) + W3
+        Y9 = I - N.mm(W9, A, cnt)
+        Y18 = N.mm(Y9, Y9, cnt)
+        Q = N.mm(I + Y18, Y9, cnt)
+        return W9 + N.mm(Q, W9, cnt)
+    _patch(monkeypatch, "nested_order45", bad)
+    assert _fails(T.test_nested_order45_ten_mmm)
+
+
+def test_gemm_epilogue_identity_sign(monkeypatch):
+    def bad(prod, s=1.0, C=None, beta=0.0, gamma=0.0):
+        D = s * prod
+        if C is not None and beta != 0.0:
+            D = D + beta * C
+        return D - gamma * np.eye(D.shape[0])
+    _patch(monkeypatch, "gemm_epilogue", bad)
+    assert _fails(T.test_gemm_epilogue_forms)
+
+
+def test_ozaki_scale_not_a_power_of_two(monkeypatch):
+    """Scaling by the line's exact maximum: slicing x / max is no longer exact."""
+    _patch(monkeypatch, "ozaki_scales",
+           lambda X, axis: np.where(np.max(np.abs(X), axis=axis) > 0, np.max(np.abs(X), axis=axis) * 1.5, 1.0))
+    assert _fails(T.test_ozaki_slices_exact_integers_and_reconstruction)
+
+
+def test_relative_residual_not_normalised(monkeypatch):
+    _patch(monkeypatch, "rel_residual", lambda A, theta, B: np.sqrt(np.sum((B - A @ theta) ** 2, axis=0)))
+    assert _fails(T.test_rel_residual_closed_forms)
+
+
+def test_accelerated_richardson_plain_G(monkeypatch):
+    """theta - G_k (A theta - b): the omega_k of eq. ttk1 replaced by G_k."""
+    _patch(monkeypatch, "accelerated_richardson_step", lambda A, b, theta, st, q: theta - st.G @ (A @ theta - b))
+    assert _fails(T.test_accelerated_richardson_gamma, 2)
