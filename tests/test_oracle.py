@@ -575,6 +575,15 @@ def test_splitmix64_published_outputs():
             assert O.splitmix64(int(seed), k) == int(v, 0)
 
 
+def test_rademacher_probes_follow_published_outputs():
+    """Probe entries are -1 exactly where the published SplitMix64 output has
+    its top bit set (a column of three probes per seed, and a row)."""
+    for seed, outs in SM64["outputs"].items():
+        want = np.array([-1.0 if int(v, 0) >> 63 else 1.0 for v in outs])
+        assert np.array_equal(O.rademacher_probes(len(outs), 1, int(seed))[:, 0], want)
+        assert np.array_equal(O.rademacher_probes(1, len(outs), int(seed))[0], want)
+
+
 def test_rademacher_probes_balanced_and_uncorrelated():
     Z = O.rademacher_probes(64, 64, seed=99)
     assert set(np.unique(Z)) == {-1.0, 1.0}

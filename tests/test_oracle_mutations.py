@@ -298,3 +298,35 @@ def test_accelerated_richardson_plain_G(monkeypatch):
     """theta - G_k (A theta - b): the omega_k of eq. ttk1 replaced by G_k."""
     _patch(monkeypatch, "accelerated_richardson_step", lambda A, b, theta, st, q: theta - st.G @ (A @ theta - b))
     assert _fails(T.test_accelerated_richardson_gamma, 2)
+
+
+def test_rademacher_low_bit(monkeypatch):
+    """Sign from the lowest bit instead of the top bit of each output."""
+    def bad(n, s, seed):
+        Z = np.empty((n, s))
+        for j in range(s):
+            for i in range(n):
+                Z[i, j] = -1.0 if N.splitmix64(seed, j * n + i) & 1 else 1.0
+        return Z
+    _patch(monkeypatch, "rademacher_probes", bad)
+    assert _fails(T.test_rademacher_probes_follow_published_outputs)
+
+
+def test_horner_right_one_product_short(monkeypatch):
+    """X = G + X F repeated n - 2 times: order n - 1 instead of n."""
+    def bad(A, G, n, cnt=None):
+        F = N.residual_right(A, G, cnt)
+        X = G.copy()
+        for _ in range(n - 2):
+            X = G + N.mm(X, F, cnt)
+        return X, F
+    _patch(monkeypatch, "ns_step_horner_right", bad)
+    assert _fails(T.test_exponent_law_plain_ns, 4, "horner")
+
+
+def test_left_residual_transposed_product(monkeypatch):
+    """I - A G where the left form I - G A is meant: equal while G commutes
+    with A, caught by the non-commuting push-through pin."""
+    _patch(monkeypatch, "residual_left", lambda G, A, cnt=None: np.eye(A.shape[0]) - N.mm(A, G, cnt))
+    T.test_exponent_law_plain_ns(2, "factorized")
+    assert _fails(T.test_push_through_right_equals_left_noncommuting)
