@@ -52,6 +52,7 @@ def workload_config(a):
         "tol": 1e-10, "l2": "flushed between timed steps (512 MiB write)", "seed": 1,
         "couple_frob": a.couple,
         **({"gemm_cluster": a.gemm_cluster} if getattr(a, "gemm_cluster", 0) else {}),
+        **({"pow_bf16": a.pow_bf16} if getattr(a, "pow_bf16", 0) else {}),
     }
 
 
@@ -248,7 +249,7 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
 
     ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1, couple_frob=a.couple,
-                       gemm_cluster=a.gemm_cluster)
+                       gemm_cluster=a.gemm_cluster, pow_bf16=a.pow_bf16)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
     assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
@@ -290,7 +291,8 @@ def run_ours(a):
     Ah = torch.from_numpy(p.A).pin_memory()
     Bh = torch.from_numpy(p.B).pin_memory()
     Th = torch.empty_like(Bh).pin_memory()
-    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple, gemm_cluster=a.gemm_cluster)
+    ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple, gemm_cluster=a.gemm_cluster,
+                         pow_bf16=a.pow_bf16)
     ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
     e2e_steps = max(1, min(a.steps, 5))
     barrier()
@@ -332,7 +334,7 @@ def run_ours(a):
     pk, pk_kind = peaks()
     achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     # the capture's workload: the default single system (n = 4096, order 8, 4 RHS)
-    default_cfg = (a.n, a.kappa, a.nrhs, a.order, a.couple, a.gemm_cluster) == (4096, 1e4, 4, 8, 1.0, 0)
+    default_cfg = (a.n, a.kappa, a.nrhs, a.order, a.couple, a.gemm_cluster, a.pow_bf16) == (4096, 1e4, 4, 8, 1.0, 0, 0)
     traffic = recorded_traffic("traffic_k_gemm_tc2_bench_n4096.md") if default_cfg else None
     roof = {"bound": "tensor",
             "kernel": "k_gemm_tc2 / k_gemm_tc (tcgen05 bf16 / bf16x3 products with fused NS epilogue; "
@@ -842,6 +844,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6", "fp64slices"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
+    ap.add_argument("--pow-bf16", type=int, default=0, choices=(0, 1),
+                    help="powers F^(2^j) of bf16x3 steps in one bf16 pass (library option pow_bf16)")
     ap.add_argument("--gemm-cluster", type=int, default=0,
                     help="single workload: product-kernel clustering (0 automatic, 1, 2, 4; -2 CTA pairs)")
     ap.add_argument("--workload", default="single",

@@ -121,6 +121,10 @@ typedef struct ns_options {
   int fp64_slices_early; /* slices of the products while ||F_k||_F >= 1 (their error is corrected
                           by the later steps); the full fp64_slices take over below one or at
                           the reduced count's floor.  Default 4; 0: always fp64_slices */
+  int pow_bf16;         /* 0 (default): the powers F^{2^{j+1}} = F^{2^j} F^{2^j} of a factorized step
+                          run in the step's precision.  1: in bf16x3 steps they run as one bf16
+                          pass, in their own launch (their error reaches G_{k+1} only through
+                          X P, quadratic in F_k); pow_mode 0 only */
 } ns_options;
 
 #define NS_MAX_HIST 256

@@ -70,6 +70,7 @@ class ns_options(ctypes.Structure):
         ("final_check", ctypes.c_int),
         ("fp64_slices", ctypes.c_int),
         ("fp64_slices_early", ctypes.c_int),
+        ("pow_bf16", ctypes.c_int),
     ]
 
 

@@ -682,6 +682,13 @@ ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int pr
     GemmSpec gx{Xc, Pc, 1.f, Xc->m32, 1.f, 0.f, xo, true, nullptr};
     if (last) {
       NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+    } else if (ctx->opt.pow_mode == 0 && ctx->opt.pow_bf16 && prec == NS_BF16X3) {
+      // option pow_bf16: the power P_{j+1} = P_j P_j in one bf16 pass.  Its
+      // error enters G_{k+1} only through X P, as ~2^-9 |P_j|^2, quadratic in
+      // F_k, so it stays below the bf16x3 floor once F_k is small
+      NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+      GemmSpec gp{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr};
+      NS_TRY(mp_gemm(ctx, &gp, 1, NS_BF16));
     } else if (ctx->opt.pow_mode == 0) {
       GemmSpec two[2] = {gx, GemmSpec{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr}};
       NS_TRY(mp_gemm(ctx, two, 2, prec));
@@ -1519,6 +1526,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   if (o.final_check < -2 || o.final_check > 4096) return NS_ERR_ARG;
+  if (o.pow_bf16 != 0 && o.pow_bf16 != 1) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)

@@ -118,7 +118,7 @@ def test_create_validates_precision_options(L):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 1)(2)
     for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
-               {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}):
+               {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 2}):
         opt = nsgb.default_options(**kw)
         assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG, kw
     # bf16x6 needs the third split part, which composite loops and form 3 do not carry
@@ -127,7 +127,7 @@ def test_create_validates_precision_options(L):
     opt = nsgb.default_options(precision=nsgb.NS_BF16X6, form=3)
     assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
     d = nsgb.default_options()
-    assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0
+    assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0 and d.pow_bf16 == 0
 
 
 def test_new_kernel_entry_points_validate_before_launch(L):

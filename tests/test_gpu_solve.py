@@ -546,6 +546,26 @@ def test_config5_size_solve_with_slice_products():
     assert float(err) <= 10 * kappa * 1e-10
 
 
+@pytest.mark.parametrize("kappa,nrhs", [(1e4, 4), (1e5, 4)])
+def test_bf16_powers_in_split_steps(kappa, nrhs):
+    """Option pow_bf16: in bf16x3 steps the powers F^{2^{j+1}} run as one bf16
+    pass.  On the n = 4096 systems the solve reaches the tolerance with the same
+    Newton-Schulz steps and sweeps as with split powers, and theta matches the
+    closed form."""
+    p = make_spd(4096, kappa, nrhs=nrhs, seed=1)
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    steps = {}
+    for pb in (0, 1):
+        with nsgb.Context(4096, order=8, couple_frob=1.0, pow_bf16=pb) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=80, tol=1e-10)
+        th = r.theta.cpu().numpy()
+        assert r.status == nsgb.NS_OK, (pb, r.stats.res_history())
+        assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+        assert rel(th, tstar) <= 10 * kappa * 1e-10
+        steps[pb] = (r.stats.ns_iters, r.stats.sweeps)
+    assert steps[1] == steps[0]
+
+
 def test_bench_size_solve():
     """The benchmark workload: n = 4096, kappa = 1e4, 4 RHS, order 8, mixed
     precision; the residual is recomputed in FP64 by the oracle and theta is
