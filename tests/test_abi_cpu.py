@@ -82,8 +82,8 @@ def test_status_strings(L):
         assert nsgb.ns_status_string(getattr(nsgb, name)) == name
 
 
-@pytest.mark.parametrize("n,order,rates", [(0, 4, ()), (-3, 2, ()), (16, 1, ()), (16, 5, ()), (16, 6, ()),
-                                           (16, 4, (0,)), (16, 4, (5,))])
+@pytest.mark.parametrize("n,order,rates", [(0, 4, ()), (-3, 2, ()), ((1 << 20) + 1, 4, ()), (16, 1, ()), (16, 5, ()),
+                                           (16, 6, ()), (16, 4, (0,)), (16, 4, (5,))])
 def test_create_rejects_bad_arguments(L, n, order, rates):
     opt = nsgb.default_options()
     arr = (ctypes.c_int * max(1, len(rates)))(*rates) if rates else None
