@@ -161,8 +161,10 @@ void ns_default_options(ns_options* opt);
  *   rates   composite mixed-rate orders m_i of eqs. gkgen1-ga1 (Section 5): n_rates
  *           auxiliary expansions T_i with x_i = m_i^k; n_rates = 0 for plain NS.
  *   opt     NULL for defaults.
- * Errors: NS_ERR_ARG (n <= 0, order < 2, order not factorizable with form = 0,
- * n_rates < 0 or a rate < 1), NS_ERR_CUDA (no device), NS_ERR_OOM.  On success *out
+ * Errors: NS_ERR_ARG (n <= 0 or n > 2^20, order < 2, order not factorizable with form = 0,
+ * n_rates < 0 or a rate < 1, an option outside its documented range),
+ * NS_ERR_UNSUPPORTED (NS_BF16X6 with composite rates or form 3), NS_ERR_CUDA (no
+ * device), NS_ERR_OOM.  On success *out
  * owns the workspace (about 14 n^2 bytes for NS_FP64 plus 32 n^2 for mixed precision,
  * allocated on first use). */
 ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const ns_options* opt, ns_ctx** out);
