@@ -538,6 +538,26 @@ def test_split3_exact_and_matches_torch():
     assert np.array_equal(h2, hi) and np.array_equal(l2, lo)
 
 
+def test_split_abs_product_bounds():
+    """sum_k |L_ik||R_kj| over the split terms: for operands that bf16 holds
+    exactly (lo = lo2 = 0) it is |L| |R| in every precision; in general it
+    bounds the split product's magnitude and grows with the terms kept."""
+    rng = np.random.default_rng(14)
+    Lb = O.round_bf16(O.round_f32(rng.standard_normal((6, 20))))
+    Rb = O.round_bf16(O.round_f32(rng.standard_normal((20, 4))))
+    for prec in ("bf16", "bf16x3", "bf16x6"):
+        assert np.array_equal(O.split_abs_product(Lb, Rb, prec), np.abs(Lb) @ np.abs(Rb))
+    L = rng.standard_normal((6, 20))
+    R = rng.standard_normal((20, 4))
+    prev = None
+    for prec in ("bf16", "bf16x3", "bf16x6"):
+        ab = O.split_abs_product(L, R, prec)
+        assert np.all(np.abs(O.split_product(L, R, prec)) <= ab)
+        if prev is not None:
+            assert np.all(ab >= prev)
+        prev = ab
+
+
 def test_split_product_x6_terms():
     """bf16x6 = the six terms of order <= 2; against the binary32 product its
     error is the three dropped terms only (each <= 2^-24 relative, as x32 =

@@ -330,3 +330,11 @@ def test_left_residual_transposed_product(monkeypatch):
     _patch(monkeypatch, "residual_left", lambda G, A, cnt=None: np.eye(A.shape[0]) - N.mm(A, G, cnt))
     T.test_exponent_law_plain_ns(2, "factorized")
     assert _fails(T.test_push_through_right_equals_left_noncommuting)
+
+
+def test_abs_product_taken_after_the_sum(monkeypatch):
+    """|sum of the split terms| instead of the sum of |terms|: no longer an
+    error scale (it vanishes where the terms cancel)."""
+    orig = N.split_product
+    _patch(monkeypatch, "split_abs_product", lambda L, R, precision: np.abs(orig(L, R, precision)))
+    assert _fails(T.test_split_abs_product_bounds)
