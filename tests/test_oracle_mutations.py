@@ -338,3 +338,11 @@ def test_abs_product_taken_after_the_sum(monkeypatch):
     orig = N.split_product
     _patch(monkeypatch, "split_abs_product", lambda L, R, precision: np.abs(orig(L, R, precision)))
     assert _fails(T.test_split_abs_product_bounds)
+
+
+def test_ozaki_last_level_dropped(monkeypatch):
+    """Pairs of level t + u <= s only: the s pairs of the last level missing."""
+    _patch(monkeypatch, "ozaki_pairs",
+           lambda s: [(t, d - t) for d in range(2, s + 1) for t in range(1, d) if 1 <= d - t <= s])
+    assert _fails(T.test_ozaki_pairs_count)
+    assert _fails(T.test_ozaki_product_against_exact_arithmetic)
