@@ -346,3 +346,24 @@ def test_ozaki_last_level_dropped(monkeypatch):
            lambda s: [(t, d - t) for d in range(2, s + 1) for t in range(1, d) if 1 <= d - t <= s])
     assert _fails(T.test_ozaki_pairs_count)
     assert _fails(T.test_ozaki_product_against_exact_arithmetic)
+
+
+def test_composite_aux_loops_at_the_main_order(monkeypatch):
+    """Every auxiliary loop advanced with the main order n instead of its own
+    rate m_i (eq. ti with x_i = m_i^k)."""
+    def bad(A, st, n, rates, cnt=None):
+        T_new = [N.ns_classical_step(Ti, A, n, cnt) for Ti in st.T]
+        return N.CompositeState(G=N.composite_step(A, st.G, T_new, n, cnt), T=T_new, k=st.k + 1)
+    _patch(monkeypatch, "composite_iterate", bad)
+    assert _fails(T.test_composite_exponent_law, 2, [3])
+
+
+def test_composite_exponent_recursion_without_rates(monkeypatch):
+    """e_k = n e_{k-1}: the auxiliary loops' contribution sum_i m_i^k dropped."""
+    def bad(n, rates, h, K):
+        e = [h]
+        for _ in range(K):
+            e.append(n * e[-1])
+        return e
+    _patch(monkeypatch, "composite_exponents", bad)
+    assert _fails(T.test_composite_exponent_values)
