@@ -367,3 +367,19 @@ def test_composite_exponent_recursion_without_rates(monkeypatch):
         return e
     _patch(monkeypatch, "composite_exponents", bad)
     assert _fails(T.test_composite_exponent_values)
+
+
+def test_double_ns_exponent_power_off_by_one(monkeypatch):
+    """h (k n^k + n^k) instead of h (k n^{k+1} + n^k) (eq. ermoex1)."""
+    _patch(monkeypatch, "double_ns_exponent", lambda n, h, k: h * (k * n ** k + n ** k))
+    assert _fails(T.test_double_ns_exponent_values)
+    assert _fails(T.test_double_ns_exponent, 2)
+
+
+def test_accelerated_exponent_missing_factor(monkeypatch):
+    """gamma_k of eq. riem6 without its leading factor n."""
+    def bad(n, h, k):
+        num = k * n ** (k + 2) - (k - 1) * n ** (k + 1) - 2 * n ** k - n + 2
+        return h * n * num / (n - 1) ** 2
+    _patch(monkeypatch, "accelerated_richardson_exponent", bad)
+    assert _fails(T.test_gamma_closed_form_equals_sum)
