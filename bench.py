@@ -285,6 +285,38 @@ def run_ours(a):
         total_s = float(t.item())
     value = world * a.steps / total_s
 
+    # the option that runs the powers of bf16x3 steps in one bf16 pass,
+    # measured beside the headline configuration on the same box (not the
+    # headline: the library's default keeps them split)
+    variants = {}
+    if world == 1 and a.pow_bf16 == 0 and not a.no_variants:
+        try:
+            out_v = torch.empty_like(B)
+            cv = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple, gemm_cluster=a.gemm_cluster,
+                              pow_bf16=1)
+            for _ in range(3):
+                cv.solve(A, B, iters=a.iters, tol=1e-10, out=out_v)
+            vms, vit, vsw = [], [], []
+            for _ in range(max(1, min(a.steps, 20))):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = cv.solve(A, B, iters=a.iters, tol=1e-10, out=out_v)
+                e1.record(stream)
+                e1.synchronize()
+                assert r.status == nsgb.NS_OK
+                vms.append(e0.elapsed_time(e1))
+                vit.append(r.stats.ns_iters)
+                vsw.append(r.stats.sweeps)
+            variants["pow_bf16"] = {"value": 1e3 / statistics.mean(vms), "unit": UNIT,
+                                    "ms_per_step": statistics.mean(vms), "steps": len(vms),
+                                    "verified_rel_res": max(cv.residual(A, out_v, B)),
+                                    "ns_iters": int(statistics.median(vit)), "sweeps": int(statistics.median(vsw))}
+            cv.close()
+        except Exception as ex:  # reported, never fatal to the headline line
+            variants["pow_bf16"] = {"error": str(ex)[:200]}
+
     # end to end through the same C-ABI call with host (pinned) buffers: the
     # host->device copy of A and B and the device->host copy of theta are
     # inside the timed region
@@ -364,6 +396,7 @@ def run_ours(a):
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
             "fp64_path": fp64, "verified_rel_res": rel, "ns_iters": ns_med, "sweeps": int(statistics.median(sw)),
             "gemm_ms_per_step": tc_ms / a.steps,
+            **({"variants": variants} if variants else {}),
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -844,6 +877,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6", "fp64slices"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the pow_bf16 variant measured beside the default single-system line")
     ap.add_argument("--pow-bf16", type=int, default=0, choices=(0, 1),
                     help="powers F^(2^j) of bf16x3 steps in one bf16 pass (library option pow_bf16)")
     ap.add_argument("--gemm-cluster", type=int, default=0,
