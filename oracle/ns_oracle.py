@@ -750,6 +750,41 @@ def ozaki_product(L: np.ndarray, R: np.ndarray, s: int = 7) -> np.ndarray:
     return out * mu[:, None] * nu[None, :]
 
 
+def ozaki_slices_signed(X: np.ndarray, scale: np.ndarray, axis: int, s: int) -> list:
+    """Signed-digit slices of X / (2 scale), a second slicing rule for the same
+    splitting: x starts in (-1/2, 1/2); x <- 256 x, S_t = RN(x) (nearest, ties
+    to even), x <- x - S_t.  Every step is exact in binary64 (x - RN(x) is),
+    |x| <= 1/2 after each step, so |S_t| <= 128 and
+    X = 2 scale (sum_t S_t 256^{-t} + r) with |r| <= 256^{-s} / 2.  With digits
+    of at most 2^7 a pair's products sum exactly in binary32 over 1024 of K
+    (1024 * 2^14 = 2^24), four times the truncated slices' 256."""
+    x = X / (2.0 * (scale[:, None] if axis == 1 else scale[None, :]))
+    out = []
+    for _ in range(s):
+        x = x * 256.0
+        a = np.rint(x)
+        x = x - a
+        out.append(a)
+    return out
+
+
+def ozaki_product_signed(L: np.ndarray, R: np.ndarray, s: int = 7) -> np.ndarray:
+    """ozaki_product with the signed-digit slices: sum over the kept pairs of
+    (2 mu_i)(2 nu_j) 2^{-8(t+u)} (A_t B_u)_ij, each A_t B_u exact in int64."""
+    mu = ozaki_scales(L, 1)
+    nu = ozaki_scales(R, 0)
+    A = [a.astype(np.int64) for a in ozaki_slices_signed(L, mu, 1, s)]
+    B = [b.astype(np.int64) for b in ozaki_slices_signed(R, nu, 0, s)]
+    out = np.zeros((L.shape[0], R.shape[1]))
+    for d in range(2, s + 2):
+        S = np.zeros_like(out, dtype=np.int64)
+        for t, u in ozaki_pairs(s):
+            if t + u == d:
+                S += A[t - 1] @ B[u - 1]
+        out += np.ldexp(S.astype(np.float64), -8 * d)
+    return out * (2.0 * mu)[:, None] * (2.0 * nu)[None, :]
+
+
 def gemm_epilogue(prod: np.ndarray, s: float = 1.0, C: np.ndarray | None = None,
                   beta: float = 0.0, gamma: float = 0.0) -> np.ndarray:
     """D = s * prod + beta * C + gamma * I: the affine forms every step of the

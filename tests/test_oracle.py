@@ -749,3 +749,70 @@ def test_solve_reaches_gram_closed_form():
     assert r.converged, r.rel_res[-3:]
     err = np.linalg.norm(r.theta - tstar) / np.linalg.norm(tstar)
     assert err <= 10 * kap * (1e-12 + n * 2.0 ** -53), (kap, err)
+
+
+
+def test_ozaki_signed_digits_exact_and_bounded():
+    """Signed-digit slices: integers of at most 128 in magnitude, and the
+    rational reconstruction 2 scale sum_t S_t 256^{-t} is within
+    scale 256^{-s} of x (exactly x once the digits cover its 53 bits)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(15)
+    X = rng.standard_normal((13, 21)) * 10.0 ** rng.integers(-6, 6, (13, 1))
+    X[2] = 0.0
+    X[4, 3] = np.max(np.abs(X[4])) * 1.0     # the line maximum itself
+    for axis in (0, 1):
+        sc = O.ozaki_scales(X, axis)
+        sl7 = O.ozaki_slices_signed(X, sc, axis, 7)
+        sl9 = O.ozaki_slices_signed(X, sc, axis, 9)
+        for a in sl9:
+            assert np.array_equal(a, np.rint(a)) and np.max(np.abs(a)) <= 128
+        for i, j in zip(rng.integers(0, 13, 100), rng.integers(0, 21, 100)):
+            scale = Fraction(float(sc[i] if axis == 1 else sc[j]))
+            x = Fraction(float(X[i, j]))
+            r7 = 2 * scale * sum(Fraction(int(a[i, j])) / 256 ** (t + 1) for t, a in enumerate(sl7))
+            assert abs(x - r7) <= scale / 256 ** 7
+            if abs(x) >= scale / 2 ** 18:
+                r9 = 2 * scale * sum(Fraction(int(a[i, j])) / 256 ** (t + 1) for t, a in enumerate(sl9))
+                assert r9 == x
+
+
+def test_ozaki_signed_chunk_sums_exact_in_binary32():
+    """Any 1024-term dot product of signed digits stays within 2^24, so its
+    binary32 sum in any order is exact: checked against int64 on digits drawn
+    to the extremes (sums of exactly 2^24 included)."""
+    rng = np.random.default_rng(16)
+    # magnitudes just below the unit scale: first digits RN(128 (1 - delta)) = 128
+    X = rng.choice([-1.0, 1.0], (64, 1024)) * (1.0 - rng.uniform(0, 1e-3, (64, 1024)))
+    Y = rng.choice([-1.0, 1.0], (1024, 48)) * (1.0 - rng.uniform(0, 1e-3, (1024, 48)))
+    X[:8] = np.abs(X[:8])          # first digits all +128: those sums reach 2^24 itself
+    Y[:, :8] = np.abs(Y[:, :8])
+    A = O.ozaki_slices_signed(X, np.full(64, 1.0), 1, 2)
+    B = O.ozaki_slices_signed(Y, np.full(48, 1.0), 0, 2)
+    for a in A:
+        for b in B:
+            exact = a.astype(np.int64) @ b.astype(np.int64)
+            assert np.max(np.abs(exact)) <= 2 ** 24
+            if a is A[0] and b is B[0]:
+                assert np.max(np.abs(exact)) == 2 ** 24
+            f32 = np.zeros(exact.shape, dtype=np.float32)
+            for k in range(1024):
+                f32 += np.outer(a[:, k], b[k, :]).astype(np.float32)
+            assert np.array_equal(f32.astype(np.int64), exact)
+
+
+def test_ozaki_signed_product_matches_truncated_and_exact():
+    """Both slicing rules give the product to binary64 accuracy: against the
+    exact rational product on a small case, and against each other."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    L = rng.standard_normal((5, 9)) * 10.0 ** rng.integers(-3, 3, (5, 1))
+    R = rng.standard_normal((9, 4)) * 10.0 ** rng.integers(-3, 3, (1, 4))
+    got = O.ozaki_product_signed(L, R, 7)
+    for i in range(5):
+        for j in range(4):
+            ex = sum(Fraction(float(L[i, k])) * Fraction(float(R[k, j])) for k in range(9))
+            ab = sum(abs(float(L[i, k]) * float(R[k, j])) for k in range(9))
+            assert abs(Fraction(float(got[i, j])) - ex) <= Fraction(2.0 ** -50 * ab)
+    tr = O.ozaki_product(L, R, 7)
+    assert np.all(np.abs(got - tr) <= 2.0 ** -49 * (np.abs(L) @ np.abs(R)))

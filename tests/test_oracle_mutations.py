@@ -383,3 +383,26 @@ def test_accelerated_exponent_missing_factor(monkeypatch):
         return h * n * num / (n - 1) ** 2
     _patch(monkeypatch, "accelerated_richardson_exponent", bad)
     assert _fails(T.test_gamma_closed_form_equals_sum)
+
+
+def test_signed_digits_truncated(monkeypatch):
+    """trunc in place of round-to-nearest: digits reach 255 and the 1024-term
+    sums leave binary32's exact range."""
+    def bad(X, scale, axis, s):
+        x = X / (2.0 * (scale[:, None] if axis == 1 else scale[None, :]))
+        out = []
+        for _ in range(s):
+            x = x * 256.0
+            a = np.trunc(x)
+            x = x - a
+            out.append(a)
+        return out
+    _patch(monkeypatch, "ozaki_slices_signed", bad)
+    assert _fails(T.test_ozaki_signed_digits_exact_and_bounded)
+
+
+def test_signed_product_missing_factor_two(monkeypatch):
+    """The scales mu, nu of the truncated rule reused without the signed rule's 2."""
+    orig = N.ozaki_product_signed
+    _patch(monkeypatch, "ozaki_product_signed", lambda L, R, s=7: 0.25 * orig(L, R, s))
+    assert _fails(T.test_ozaki_signed_product_matches_truncated_and_exact)
