@@ -84,11 +84,11 @@ typedef struct ns_options {
   int aux_ahead;       /* composite only: 1 starts the auxiliary loops one step ahead,
                           T_i = NS_{m_i}(G0), so rates = {n} gives the double Newton-Schulz
                           method of Section 5.1 (eqs. gamk11-fks1); 0: T_i start at G0 */
-  int gemm_cluster;    /* CTAs per cluster sharing each R tile by TMA multicast: 0 automatic,
-                          1 none, 2 or 4 (with 192- or 256-column tiles); -2: CTA pairs
-                          sharing each MMA (tcgen05 cta_group::2, 256 x 256 tiles) where
-                          ceil(n / 128) is even, else automatic.  Automatic picks CTA
-                          pairs wherever 256-column tiles are chosen and apply */
+  int gemm_cluster;    /* product-kernel grouping: 0 automatic (CTA pairs wherever 256-column
+                          tiles are chosen and ceil(n / 128) is even, else one CTA per tile);
+                          1 one CTA per tile; -2 CTA pairs sharing each MMA (tcgen05
+                          cta_group::2, 256 x 256 tiles) where they apply, else automatic.
+                          Other values: NS_ERR_ARG */
   double couple_frob;  /* 0 (default): the Richardson branch (residual, test, update) runs on
                           every NS step, as in Section 6.  > 0: it starts with the first
                           G_k whose ||I - A G_k||_F <= couple_frob and stays on.  Earlier G_k
@@ -121,10 +121,11 @@ typedef struct ns_options {
   int fp64_slices_early; /* slices of the products while ||F_k||_F >= 1 (their error is corrected
                           by the later steps); the full fp64_slices take over below one or at
                           the reduced count's floor.  Default 4; 0: always fp64_slices */
-  int pow_bf16;         /* 0 (default): the powers F^{2^{j+1}} = F^{2^j} F^{2^j} of a factorized step
-                          run in the step's precision.  1: in bf16x3 steps they run as one bf16
+  int pow_bf16;         /* 0: the powers F^{2^{j+1}} = F^{2^j} F^{2^j} of a factorized step run
+                          in the step's precision.  1: in bf16x3 steps they run as one bf16
                           pass, in their own launch (their error reaches G_{k+1} only through
-                          X P, quadratic in F_k); pow_mode 0 only */
+                          X P, quadratic in F_k); pow_mode 0 only.  2 (default of
+                          ns_default_options): 1 where n >= 4096, else 0 */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -368,11 +369,10 @@ ns_status ns_k_split(const void* X, int x_dtype, int64_t rows, int64_t cols, int
  * (ldd16), frob_out a device double receiving sum(D^2).  Leading dimensions of bf16
  * arrays must be multiples of 8 and of f32 arrays multiples of 4; base pointers
  * 16-byte aligned.  bn = 0 picks the tile width (64, 128, 192 or 256 columns);
- * cluster_m: 1, 2 or 4 CTAs (2 and 4 need bn >= 192) share each R tile through TMA
- * multicast; -2 runs CTA pairs that share each MMA (tcgen05 cta_group::2, 256 x 256
- * tiles: bn must be 0 or 256 and ceil(M / 128) even); 0 picks CTA pairs where they
- * apply (bn = 256, ceil(M / 128) even), else 2 with bn >= 192, else 1.  Returns
- * NS_ERR_ARG on violations. */
+ * cluster_m: 1 runs one CTA per tile; -2 runs CTA pairs that share each MMA (tcgen05
+ * cta_group::2, 256 x 256 tiles: bn must be 0 or 256 and ceil(M / 128) even); 0 picks
+ * CTA pairs where they apply (bn = 256, ceil(M / 128) even), else one CTA per tile.
+ * Other values, and violations of the rules above, return NS_ERR_ARG. */
 ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const void* Lhi, const void* Llo,
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,

@@ -426,7 +426,7 @@ ns_status launch_products(ns_batch* b, const std::vector<int>& ids, const std::v
         cudaEventCreate(&e1);
         cudaEventRecord(e0, b->pstream);
       }
-      B_CK(launch_gemm_tc(p, bnv, 1, x3 == 1, b->num_sms, b->pstream));
+      B_CK(launch_gemm_tc(p, bnv, x3 == 1, b->num_sms, b->pstream));
       if (b->stats) {
         b->stats->gemm_launches++;
         b->stats->kernel_launches++;

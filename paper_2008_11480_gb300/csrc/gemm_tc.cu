@@ -17,12 +17,8 @@
 // The accumulator is double-buffered in TMEM (2 x BN columns), so the
 // epilogue of tile i overlaps the MMAs of tile i+1.
 //
-// Clusters (CM = 2 or 4 CTAs along M): the CM CTAs of a cluster compute the
-// tiles (m, n) ... (m + CM - 1, n), which share their R tile.  Each CTA loads
-// its own L tile and 1/CM of the R tile, multicast into every CTA of the
-// cluster, so each SM pulls 16 + 32/CM KiB per stage from L2 instead of 48.
-// A stage may be refilled only when all CM CTAs have consumed it: every MMA
-// commit arrives on the `empty` barrier of all CTAs (count CM).
+// One CTA per tile: every CTA loads its own L and R tiles (no cluster, no
+// shared loads); the CTA-pair kernel (gemm_tc2.cu) is the wide-tile form.
 //
 // Shared-memory layouts (both 128-byte swizzled, atoms of 8 rows x 128 B):
 //   L tile 128 x 64 (K-major):  row r at r*128 B; MMA K-slice k at +32k B.
@@ -69,13 +65,13 @@ struct TcCfg {
 
 using tc::decode_item;
 
-template <int BN, int CM, bool X3>
+template <int BN, bool X3>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
   using Cfg = TcCfg<BN>;
-  const int rank = CM > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-  const int first = blockIdx.x / CM;   // this cluster's first work item
-  const int stride = gridDim.x / CM;   // clusters in the grid
-  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CM) - 1u);
+  constexpr int CM = 1;
+  constexpr int rank = 0;
+  const int first = blockIdx.x;   // this CTA's first work item
+  const int stride = gridDim.x;   // CTAs in the grid
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -96,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CM);
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -113,8 +109,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   }
   tc_fence_before();
   __syncthreads();
-  // no CTA of the cluster may multicast into a peer before its barriers exist
-  if (CM > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const uint64_t tlim = p.timeout_ns;
@@ -174,10 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             for (int j = 0; j < 2 * (BN / 64); ++j) {
               const int part = j / (BN / 64), c = j % (BN / 64);
               uint8_t* dst = b + part * (BN * 64) + c * 4096;
-              if (CM == 1)
-                tma_load_2d(dst, &P.R[part], &full[stage], n0 + 64 * c, x);
-              else if (j % CM == rank)
-                tma_load_2d_mc(dst, &P.R[part], &full[stage], n0 + 64 * c, x, kMask);
+              tma_load_2d(dst, &P.R[part], &full[stage], n0 + 64 * c, x);
             }
           } else if (!X3 && it != p.debug_stall_iter) {
             const CUtensorMap* ml = &P.L[ps == 2 ? 1 : 0];
@@ -189,12 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             tma_load_2d(a, ml, &full[stage], kb * kBK, m0);
             tma_load_2d(a + 8192, ml, &full[stage], kb * kBK, m0 + 64);
 #pragma unroll
-            for (int j = 0; j < BN / 64; ++j) {
-              if (CM == 1)
-                tma_load_2d(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK);
-              else if (j % CM == rank)
-                tma_load_2d_mc(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK, kMask);
-            }
+            for (int j = 0; j < BN / 64; ++j) tma_load_2d(b + j * 8192, mr, &full[stage], n0 + 64 * j, kb * kBK);
           }
           ++it;
           if (++stage == Cfg::kStages) {
@@ -266,10 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             }
           }
           issued = true;
-          if (CM == 1)
-            tc_commit(&empty[stage]);
-          else
-            tc_commit_mc(&empty[stage], kMask);
+          tc_commit(&empty[stage]);
           if (++stage == Cfg::kStages) {
             stage = 0;
             phase ^= 1u;
@@ -335,58 +318,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
-  // peers may still arrive on this CTA's barriers until they are done too
-  if (CM > 1) cluster_sync_all();
 }
 
-template <int BN, int CM, bool X3>
+template <int BN, bool X3>
 cudaError_t launch_bn(const TcParams& p, int num_sms, cudaStream_t s) {
   using Cfg = TcCfg<BN>;
-  static int max_clusters = -1;
-  if (max_clusters < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, CM, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    max_clusters = num_sms;
-    if (CM > 1) {
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = CM;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(CM * (num_sms / CM));
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = Cfg::kSmem;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN, CM, X3>, &cfg);
-      if (e != cudaSuccess || n <= 0) {
-        cudaGetLastError();
-        n = num_sms / CM;
-      }
-      max_clusters = n;
-    }
+    attr_set = true;
   }
-  const int clusters = p.total_tiles < max_clusters ? p.total_tiles : max_clusters;
-  if (clusters <= 0) return cudaSuccess;
-  if (CM == 1) {
-    k_gemm_tc<BN, 1, X3><<<clusters, kThreads, Cfg::kSmem, s>>>(p);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CM;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(clusters * CM);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg::kSmem;
-  cfg.stream = s;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN, CM, X3>, p);
+  const int ctas = p.total_tiles < num_sms ? p.total_tiles : num_sms;
+  if (ctas <= 0) return cudaSuccess;
+  k_gemm_tc<BN, X3><<<ctas, kThreads, Cfg::kSmem, s>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -399,27 +345,20 @@ int tc_items(int M, int N, int BN, int CM) {
   return ((tiles_m + CM - 1) / CM) * ((N + BN - 1) / BN);
 }
 
-cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s) {
-  const int key = BN * 10 + CM;
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, bool x3, int num_sms, cudaStream_t s) {
   if (x3) {
-    switch (key) {
-      case 641: return launch_bn<64, 1, true>(p, num_sms, s);
-      case 1281: return launch_bn<128, 1, true>(p, num_sms, s);
-      case 2561: return launch_bn<256, 1, true>(p, num_sms, s);
-      case 2562: return launch_bn<256, 2, true>(p, num_sms, s);
-      case 2564: return launch_bn<256, 4, true>(p, num_sms, s);
+    switch (BN) {
+      case 64: return launch_bn<64, true>(p, num_sms, s);
+      case 128: return launch_bn<128, true>(p, num_sms, s);
+      case 256: return launch_bn<256, true>(p, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }
-  switch (key) {
-    case 641: return launch_bn<64, 1, false>(p, num_sms, s);
-    case 1281: return launch_bn<128, 1, false>(p, num_sms, s);
-    case 1921: return launch_bn<192, 1, false>(p, num_sms, s);
-    case 1922: return launch_bn<192, 2, false>(p, num_sms, s);
-    case 1924: return launch_bn<192, 4, false>(p, num_sms, s);
-    case 2561: return launch_bn<256, 1, false>(p, num_sms, s);
-    case 2562: return launch_bn<256, 2, false>(p, num_sms, s);
-    case 2564: return launch_bn<256, 4, false>(p, num_sms, s);
+  switch (BN) {
+    case 64: return launch_bn<64, false>(p, num_sms, s);
+    case 128: return launch_bn<128, false>(p, num_sms, s);
+    case 192: return launch_bn<192, false>(p, num_sms, s);
+    case 256: return launch_bn<256, false>(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

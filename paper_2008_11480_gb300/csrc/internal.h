@@ -28,7 +28,7 @@ struct TcProblem {
   int tiles_m;     // ceil(M / 128)
   int tiles_n;     // ceil(N / BN)
   int tile_begin;  // first global work item of this problem (a work item is
-                   // CM vertically adjacent tiles, one per CTA of a cluster)
+                   // one tile, or for CTA pairs two vertically adjacent tiles)
   int tile_count;  // work items of this problem
   
   float s, beta, gamma;
@@ -53,7 +53,7 @@ struct TcParams {
   int total_tiles;  // work items over all problems
   // List-driven mode (batched / served solves): when gprob is non-null, the
   // problems live in device memory (64-byte aligned, tensor maps included) and
-  // work item w is items[w]; prob[] and nprob are unused and CM must be 1.
+  // work item w is items[w]; prob[] and nprob are unused (one-CTA kernel only).
   const TcProblem* gprob;
   const TcItem* items;
   int npass;  // 1: hi*hi (bf16); 3: hi*hi + hi*lo + lo*hi (bf16x3); 6: those and
@@ -65,11 +65,11 @@ struct TcParams {
   int* err;
 };
 
-// Launch a grouped tcgen05 GEMM: BN in {64, 128, 192, 256} output columns per
-// tile, CM in {1, 2, 4} CTAs per cluster along M (2 and 4 only with BN 192/256).
-// x3 selects the split-product kernel (L/R maps of roles 1/2 below; BN 64, 128
-// or 256; p.npass ignored); otherwise p.npass passes over role-0 maps.
-cudaError_t launch_gemm_tc(const TcParams& p, int BN, int CM, bool x3, int num_sms, cudaStream_t s);
+// Launch a grouped tcgen05 GEMM, one CTA per 128 x BN tile: BN in {64, 128,
+// 192, 256} output columns per tile.  x3 selects the split-product kernel (L/R
+// maps of roles 1/2 below; BN 64, 128 or 256; p.npass ignored); otherwise
+// p.npass passes over role-0 maps.
+cudaError_t launch_gemm_tc(const TcParams& p, int BN, bool x3, int num_sms, cudaStream_t s);
 // CTA-pair variant (cta_group::2): 256 x 256 output tiles, clusters of two
 // CTAs along M, tile bookkeeping of BN = 256, CM = 2 (tc_items(M, N, 256, 2)
 // tiles, 8 partial sums per tc_tiles(M, N, 256) tile).  Single-problem-table

@@ -310,23 +310,17 @@ void ev_collect(ns_ctx* ctx) {
   cudaGetLastError();
 }
 
-// Tile width and cluster size for n x n products, nprob of them in one launch:
+// Tile width and CTA grouping for n x n products, nprob of them in one launch:
 // maximise (filled fraction of the last wave) x (useful columns) x (relative
 // efficiency of the tile shape, which falls with the L2 bytes per flop).
+// Grouping: -2 is a CTA pair sharing each MMA (cta_group::2, 256 x 256 tiles;
+// needs an even row-tile count), 1 one CTA per tile.
 void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
   const int n = static_cast<int>(ctx->n);
   const int tiles_m = (n + 127) / 128;
   auto cm_for = [&](int bn) {
-    const int gc = ctx->opt.gemm_cluster;
-    if (gc == 1 || bn < 192) return 1;
-    if (gc == 2 || gc == 4) return tiles_m % gc == 0 ? gc : 1;
-    // automatic and -2: CTA pairs sharing each MMA (cta_group::2) where the
-    // tile width and the row-tile count allow (in-solve product rate at
-    // n = 4096: 1609 vs 1441 TFLOP/s for two-CTA multicast clusters); else two
-    // CTAs per cluster (four-CTA clusters leave SMs idle: fewer co-resident)
-    if (bn == 256 && tiles_m % 2 == 0) return -2;
-    if (tiles_m % 2 == 0) return 2;
-    return 1;
+    if (ctx->opt.gemm_cluster == 1) return 1;
+    return (bn == 256 && tiles_m % 2 == 0) ? -2 : 1;
   };
   const int fixed = ctx->opt.gemm_bn;
   const int bns[4] = {256, 192, 128, 64};
@@ -342,7 +336,7 @@ void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
     const int waves = (items + slots - 1) / slots;
     const double fill = static_cast<double>(items) / (static_cast<double>(waves) * slots);
     const double cols = static_cast<double>(n) / (static_cast<double>((n + bn - 1) / bn) * bn);
-    const double e = fill * cols * shape_eff[i] * (cm == 1 ? 0.93 : (cm == -2 ? 1.1 : 1.0));
+    const double e = fill * cols * shape_eff[i] * (cm == -2 ? 1.1 : 0.93);
     if (e > best + 1e-9) {
       best = e;
       best_bn = bn;
@@ -431,7 +425,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   if (cm == -2)
     NS_CK(launch_gemm_tc_pair(p, x6 ? 3 : (x3 ? 2 : 1), ctx->num_sms, ctx->stream));
   else
-    NS_CK(launch_gemm_tc(p, bn, cm, x3, ctx->num_sms, ctx->stream));
+    NS_CK(launch_gemm_tc(p, bn, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
   ctx->launches++;
   if (ctx->st) {
@@ -652,6 +646,12 @@ ns_status mp_chain_nested45(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int prec
   return mp_gemm(ctx, &s9, 1, prec);
 }
 
+// Option pow_bf16: 1 always, 2 (default) where n >= 4096.  Below that size a
+// single product fills less than one wave of CTA pairs, and splitting the two
+// products of a level into two launches was measured 2-4 % slower (n = 1024,
+// 2048); at n = 4096 it was measured 6-7 % faster per solve.
+bool pow_bf16_on(const ns_ctx* ctx) { return ctx->opt.pow_bf16 == 1 || (ctx->opt.pow_bf16 == 2 && ctx->n >= 4096); }
+
 ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int prec) {
   if (ctx->opt.form == 2) return mp_chain_toolkit(ctx, Gin, Gout, order, prec);
   if (ctx->opt.form == 3) return mp_chain_nested45(ctx, Gin, Gout, prec);
@@ -682,7 +682,7 @@ ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int pr
     GemmSpec gx{Xc, Pc, 1.f, Xc->m32, 1.f, 0.f, xo, true, nullptr};
     if (last) {
       NS_TRY(mp_gemm(ctx, &gx, 1, prec));
-    } else if (ctx->opt.pow_mode == 0 && ctx->opt.pow_bf16 && prec == NS_BF16X3) {
+    } else if (ctx->opt.pow_mode == 0 && pow_bf16_on(ctx) && prec == NS_BF16X3) {
       // option pow_bf16: the power P_{j+1} = P_j P_j in one bf16 pass.  Its
       // error enters G_{k+1} only through X P, as ~2^-9 |P_j|^2, quadratic in
       // F_k, so it stays below the bf16x3 floor once F_k is small
@@ -1491,6 +1491,7 @@ void ns_default_options(ns_options* o) {
   o->couple_frob = 0.0;
   o->accel_richardson = 0;
   o->g0_order = 0;
+  o->pow_bf16 = 2;
 }
 
 const char* ns_status_string(ns_status s) {
@@ -1526,7 +1527,8 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.g0_mode < 0 || o.g0_mode > 2) return NS_ERR_ARG;
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   if (o.final_check < -2 || o.final_check > 4096) return NS_ERR_ARG;
-  if (o.pow_bf16 != 0 && o.pow_bf16 != 1) return NS_ERR_ARG;
+  if (o.pow_bf16 < 0 || o.pow_bf16 > 2) return NS_ERR_ARG;
+  if (o.gemm_cluster != 0 && o.gemm_cluster != 1 && o.gemm_cluster != -2) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
@@ -1855,15 +1857,9 @@ ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* co
   // row-tile count (bf16x6 pairs accept an odd one: the last pair's second
   // CTA then covers rows past M, loaded as zeros and not written)
   if (pair && (bn != 256 || (parts < 3 && tiles_m % 2 != 0))) return NS_ERR_ARG;
-  if (pair) cluster_m = 2;  // same item and partial-sum bookkeeping as two-CTA clusters
-  if (cluster_m == 0 && !pair && bn == 256 && tiles_m % 2 == 0) {
-    pair = true;  // automatic: CTA pairs where they apply
-    cluster_m = 2;
-  }
-  if (cluster_m == 0) cluster_m = bn < 192 ? 1 : (tiles_m % 2 == 0 ? 2 : 1);
-  if (parts == 2 && bn == 192 && cluster_m > 1) cluster_m = 1;
-  if (cluster_m != 1 && cluster_m != 2 && cluster_m != 4) return NS_ERR_ARG;
-  if (cluster_m > 1 && bn < 192) return NS_ERR_ARG;
+  if (cluster_m == 0 && !pair && bn == 256 && tiles_m % 2 == 0) pair = true;  // automatic: CTA pairs where they apply
+  if (!pair && cluster_m != 0 && cluster_m != 1) return NS_ERR_ARG;
+  cluster_m = pair ? 2 : 1;  // pairs: same item and partial-sum bookkeeping as two-CTA groups
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1926,7 +1922,7 @@ ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* co
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
   cudaError_t e = pair ? launch_gemm_tc_pair(p, parts == 3 ? 3 : (split ? 2 : 1), sms, st)
-                       : launch_gemm_tc(p, bn, cluster_m, split, sms, st);
+                       : launch_gemm_tc(p, bn, split, sms, st);
   if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * per_tile, 1, frob_out, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);

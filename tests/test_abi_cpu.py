@@ -118,7 +118,8 @@ def test_create_validates_precision_options(L):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 1)(2)
     for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
-               {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 2}):
+               {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 3}, {"pow_bf16": -1},
+               {"gemm_cluster": 2}, {"gemm_cluster": 4}):
         opt = nsgb.default_options(**kw)
         assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG, kw
     # bf16x6 needs the third split part, which composite loops and form 3 do not carry
@@ -127,7 +128,7 @@ def test_create_validates_precision_options(L):
     opt = nsgb.default_options(precision=nsgb.NS_BF16X6, form=3)
     assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
     d = nsgb.default_options()
-    assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0 and d.pow_bf16 == 0
+    assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0 and d.pow_bf16 == 2
 
 
 def test_new_kernel_entry_points_validate_before_launch(L):
@@ -169,11 +170,11 @@ def test_kernel_entry_points_validate_before_launch(L):
                             None, None, 0, None, 0, 0, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 60, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
                             None, None, 0, None, 0, 0, None) == nsgb.NS_ERR_ARG
-    # cluster sizes other than 1, 2, 4, and clusters with narrow tiles, are rejected
-    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
-                            None, None, 0, None, 256, 3, None) == nsgb.NS_ERR_ARG
-    assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 64, 64, 64, 16, 16, 64, 16, 16, 64, 1.0, None, 0, 0.0, 0.0, None, 0,
-                            None, None, 0, None, 128, 2, None) == nsgb.NS_ERR_ARG
+    # groupings other than 0 (automatic), 1 (one CTA per tile) and -2 (CTA pairs) are
+    # rejected: there are no multi-CTA clusters sharing loads
+    for cm in (2, 3, 4):
+        assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 256, 256, 64, 16, 16, 64, 16, 16, 256, 1.0, None, 0, 0.0, 0.0, None,
+                                0, None, None, 0, None, 256, cm, None) == nsgb.NS_ERR_ARG
     # CTA pairs (cluster_m = -2) need 256-column tiles and an even number of 128-row tiles
     assert L.ns_k_gemm_bf16(nsgb.NS_BF16, 256, 256, 64, 16, 16, 64, 16, 16, 256, 1.0, None, 0, 0.0, 0.0, None,
                             0, None, None, 0, None, 128, -2, None) == nsgb.NS_ERR_ARG
