@@ -151,6 +151,8 @@ typedef struct ns_stats {
   double wall_ms;                    /* host wall time of the call */
   double final_frob;                 /* ||I - A G||_F of the final G in FP64 (option final_check);
                                         -1 when not computed */
+  double tc_gemm_alg_flops;          /* algorithmic work of the tcgen05 launches: 2 M N K per
+                                        product, whatever its passes (bf16x3 counts once) */
 } ns_stats;
 
 /* Fill *opt with the defaults documented in ns_options. */

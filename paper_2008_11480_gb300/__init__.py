@@ -95,6 +95,7 @@ class ns_stats(ctypes.Structure):
         ("tc_gemm_flops", ctypes.c_double),
         ("wall_ms", ctypes.c_double),
         ("final_frob", ctypes.c_double),
+        ("tc_gemm_alg_flops", ctypes.c_double),
     ]
 
     def frob_history(self) -> list[float]:

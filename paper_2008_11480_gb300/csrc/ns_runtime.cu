@@ -418,6 +418,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
       const double f = 2.0 * n * static_cast<double>(n) * n * p.npass;
       ctx->st->gemm_flops += f;
       ctx->st->tc_gemm_flops += f;
+      ctx->st->tc_gemm_alg_flops += 2.0 * n * static_cast<double>(n) * n;
     }
   }
   p.total_tiles = tile;

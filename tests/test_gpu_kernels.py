@@ -183,7 +183,11 @@ def test_gemm_tc_full_size_sampled(prec, bn, cm):
         assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)
 
 
-@pytest.mark.parametrize("M,N,K", [(64, 64, 64), (130, 70, 33), (1, 1, 1), (200, 300, 150)])
+@pytest.mark.parametrize("M,N,K", [(64, 64, 64), (130, 70, 33), (1, 1, 1), (200, 300, 150),
+                                   # 76 or more 64 x 64 output tiles: the large-tile kernel
+                                   # k_gemm_f64 (the plain FP64 path's product from n = 576 on),
+                                   # with ragged row, column and K tails
+                                   (640, 576, 200), (1000, 1030, 333), (1024, 1024, 1024)])
 def test_gemm_f64(M, N, K):
     L, R, C = rnd((M, K), 1), rnd((K, N), 2), rnd((M, N), 3)
     Ld, Rd, Cd = (torch.from_numpy(x).to(dev) for x in (L, R, C))

@@ -578,3 +578,134 @@ def test_bench_size_solve():
     assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
     tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
     assert rel(th, tstar) <= 10 * 1e4 * 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Parity at sizes where the plain FP64 path runs its large-tile product kernel
+# (k_gemm_f64, from 76 output tiles of 64 x 64 on, i.e. n >= 576)
+# ---------------------------------------------------------------------------
+def test_fp64_solve_n1024_matches_oracle():
+    """n = 1024, kappa = 1e4, 2 RHS, order 8 factorized, 9 coupled NS steps
+    (F_0^{8^9} is far below rounding here) + 3 sweeps, Richardson from the
+    first step.  The FP64 attainable accuracy of G is ~kappa u sqrt(n), above
+    1e-12, so G and theta are held to max(1e-12, 2 x the oracle's own error
+    against the closed forms A^-1 = Q diag(1/lambda) Q^T and theta* = A^-1 B)."""
+    n, K, S = 1024, 9, 3
+    p = make_spd(n, 1e4, nrhs=2, seed=31)
+    ref = O.ns_richardson_solve(p.A, p.B, order=8, ns_iters=K, max_sweeps=S)
+    Ainv = (p.Q / p.lam) @ p.Q.T
+    tstar = Ainv @ p.B
+    with nsgb.Context(n, order=8, precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=S) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=K, tol=0.0)
+        G, st = ctx.invert(tens(p.A), iters=K)
+    th = r.theta.cpu().numpy()
+    Gg = G.cpu().numpy()
+    tol_G = max(1e-12, 2 * rel(ref.G, Ainv))
+    tol_t = max(1e-12, 2 * rel(ref.theta, tstar))
+    assert rel(Gg, ref.G) <= tol_G, (rel(Gg, ref.G), tol_G)
+    assert rel(th, ref.theta) <= tol_t, (rel(th, ref.theta), tol_t)
+    # the GPU iterate is as close to the closed form as the oracle's
+    assert rel(Gg, Ainv) <= tol_G
+    assert r.stats.sweeps == ref.sweeps
+    assert np.allclose(st.frob_history(), ref.frob_E, rtol=1e-8, atol=1e-10)
+    assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Reduced precision: a stated bound on G itself against the FP64 oracle
+# ---------------------------------------------------------------------------
+# Error model (the paper fixes no precision; this is the library's own bound).
+# One tensor-core product in precision p carries a relative error of at most
+# about eps_p = eps_operand(p) + 2^-24 sqrt(K) per entry: the operand split
+# (bf16: RN to 8 bits, 2^-8 counting both operands; bf16x3: the dropped
+# lo*lo term and the 16-bit lo part, 2^-16; bf16x6: a binary32 operand is
+# exact, the dropped third-order terms 2^-23) plus the f32 accumulation of K
+# terms (random-walk size).  Two consequences for the Newton-Schulz iterate:
+#  * while it is far from A^-1, every product adds ~eps_p to the relative error
+#    of G (the slow eigen-directions of G grow by the order each step, as their
+#    errors do), so after P products ||G_p - G||_2 / ||G||_2 <= 4 eps_p P;
+#  * at the precision floor, the computed F = I - A G is off by
+#    E ~ eps_p |A||G|, ||E||_2 <~ eps_p kappa_2, and the next step inherits
+#    -E, so ||I - A G_p||_2 <= 4 eps_p kappa_2 and ||G_p - A^-1||_2 <=
+#    ||A^-1||_2 ||I - A G_p||_2.
+# The factor 4 is the safety margin over the model's typical size.
+EPS_OPERAND = {nsgb.NS_BF16: 2.0 ** -8, nsgb.NS_BF16X3: 2.0 ** -16, nsgb.NS_BF16X6: 2.0 ** -23}
+
+
+def eps_p(prec, K):
+    return EPS_OPERAND[prec] + 2.0 ** -24 * math.sqrt(K)
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b, 2) / np.linalg.norm(b, 2))
+
+
+@pytest.mark.parametrize("prec,kappa,k_floor", [(nsgb.NS_BF16, 10.0, 8), (nsgb.NS_BF16X3, 1e3, 10),
+                                                (nsgb.NS_BF16X6, 1e4, 12)])
+def test_mixed_G_within_per_precision_bound(prec, kappa, k_floor):
+    """G after k fixed-precision order-4 steps against oracle.ns_invert (FP64)
+    on the same system (n = 300: a ragged last tile): early (k = 2, 8 products)
+    within 4 eps_p P, and at the floor within 4 eps_p (P + kappa) with
+    ||I - A G_p||_2, formed here in FP64, within 4 eps_p kappa."""
+    n = 300
+    p = make_spd(n, kappa, seed=32)
+    Ainv = (p.Q / p.lam) @ p.Q.T
+    e = eps_p(prec, n)
+    for k in (2, k_floor):
+        with nsgb.Context(n, order=4, precision=prec, ns_stop=0) as ctx:
+            G, _ = ctx.invert(tens(p.A), iters=k)
+        Gp = G.cpu().numpy()
+        Go, _ = O.ns_invert(p.A, order=4, iters=k)
+        P = 4 * k
+        if k == 2:
+            assert rel2(Gp, Go) <= 4 * e * P, (k, rel2(Gp, Go), 4 * e * P)
+        else:
+            F2 = float(np.linalg.norm(np.eye(n) - p.A @ Gp, 2))
+            assert F2 <= 4 * e * kappa, (F2, 4 * e * kappa)
+            assert rel2(Gp, Go) <= 4 * e * (P + kappa), (rel2(Gp, Go), 4 * e * (P + kappa))
+            assert np.linalg.norm(Gp - Ainv, 2) <= np.linalg.norm(Ainv, 2) * F2 * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("n_order,rates", [(2, [2]), (2, [2, 3])])
+@pytest.mark.parametrize("prec", [nsgb.NS_BF16X3, nsgb.NS_BF16])
+def test_mixed_composite_matches_oracle(prec, n_order, rates):
+    """The composite mixed-rate method (Section 5, eqs. gkgen1-ga1) on the
+    tensor cores (T_i loops, Gamma_i = I - T_i A, T_c, prefix products,
+    G = T_c + Gamma_c X) against the oracle's composite_iterate: after K = 3
+    steps G is within 4 eps_p P of the FP64 iterate (P = the oracle's product
+    count); the GPU's F_K follows the exponent law of eq. gem1 as closely."""
+    n = 256
+    p = make_spd(n, 100.0, seed=33)
+    K = 3
+    with nsgb.Context(n, order=n_order, rates=rates, precision=prec, ns_stop=0) as ctx:
+        G, _ = ctx.invert(tens(p.A), iters=K)
+    Gp = G.cpu().numpy()
+    cnt = O.MMCount()
+    st = O.composite_init(O.alpha_frobenius(p.A) * np.eye(n), len(rates))
+    for _ in range(K):
+        st = O.composite_iterate(p.A, st, n_order, rates, cnt)
+    bound = 4 * eps_p(prec, n) * cnt.n
+    assert rel2(Gp, st.G) <= bound, (rel2(Gp, st.G), bound)
+    ek = O.composite_exponents(n_order, rates, 1, K)[K]
+    a = O.alpha_frobenius(p.A)
+    Fk = (p.Q * (1 - a * p.lam) ** ek) @ p.Q.T
+    Fo = np.eye(n) - st.G @ p.A
+    Fg = np.eye(n) - Gp @ p.A
+    assert np.linalg.norm(Fo - Fk) <= 1e-11 * n
+    assert np.linalg.norm(Fg - Fk, 2) <= bound * np.linalg.norm(p.A, 2) * np.linalg.norm(st.G, 2)
+
+
+@pytest.mark.parametrize("rates", [[2], [2, 3]])
+def test_mixed_composite_solve_reaches_tolerance(rates):
+    """Composite order 2 with rates {2} and {2, 3} through AUTO precision and
+    FP64 Richardson: the relative residual (recomputed in FP64) reaches 1e-10
+    and theta lies within 10 kappa 1e-10 of the closed-form solution."""
+    n, kappa = 520, 1e3
+    p = make_spd(n, kappa, nrhs=2, seed=34)
+    with nsgb.Context(n, order=2, rates=rates) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    th = r.theta.cpu().numpy()
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(th, tstar) <= 10 * kappa * 1e-10
