@@ -441,7 +441,7 @@ def run_kernel_gemm(a):
 
     def call():
         if prec == nsgb.NS_FP64:
-            nsgb.ns_k_gemm_oz(n, n, n, L, n, L, n, -1.0, None, 0, 0.0, 1.0, D64, n, 7)
+            nsgb.ns_k_gemm_oz(n, n, n, L, n, L, n, -1.0, None, 0, 0.0, 1.0, D64, n, a.slices)
             return
         if prec == nsgb.NS_BF16X6:
             nsgb.ns_k_gemm_bf16x6(n, n, n, (Lh, Ll, L3), n, (Lh, Ll, L3), n, -1.0, None, 0, 0.0, 1.0, D32, n,
@@ -459,7 +459,8 @@ def run_kernel_gemm(a):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
-    passes = {nsgb.NS_BF16: 1, nsgb.NS_BF16X3: 3, nsgb.NS_BF16X6: 6, nsgb.NS_FP64: 28}[prec]
+    passes = {nsgb.NS_BF16: 1, nsgb.NS_BF16X3: 3, nsgb.NS_BF16X6: 6,
+              nsgb.NS_FP64: a.slices * (a.slices + 1) // 2}[prec]
     print(json.dumps({"kernel": "k_gemm_tc", "n": n, "precision": a.precision, "bn": a.bn, "cm": a.cm,
                       "ms_per_call": ms, "tflops_incl_call_overhead": passes * 2 * n ** 3 / (ms * 1e-3) / 1e12}))
 
@@ -888,6 +889,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "bf16x6", "fp64slices"])
     ap.add_argument("--bn", type=int, default=256)
     ap.add_argument("--cm", type=int, default=0)
+    ap.add_argument("--slices", type=int, default=7, help="--kernel gemm --precision fp64slices: digits per operand")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the pow_bf16 variant measured beside the default single-system line")
     ap.add_argument("--pow-bf16", type=int, default=2, choices=(0, 1, 2),

@@ -112,8 +112,8 @@ typedef struct ns_options {
                           Rademacher probes and seed 0 (see ns_inverse_residual); -2 the FP64
                           product for n <= 4096 and 8 probes above; into
                           ns_stats.final_frob.  On the mixed path G is the f32 master, widened. */
-  int fp64_slices;      /* 0 (default): FP64 products on the CUDA cores.  s = 2..8: FP64-accurate
-                          products on the bf16 tensor cores from s integer slices of 8 bits per
+  int fp64_slices;      /* 0 (default): FP64 products on the CUDA cores.  s = 2..7: FP64-accurate
+                          products on the bf16 tensor cores from s signed digits of 8 bits per
                           operand (see ns_k_gemm_oz; 7 covers binary64) -- for precision NS_FP64,
                           and with NS_AUTO (no composite rates) for a solve the binary32 masters
                           cannot finish: after NS_NOT_CONVERGED or divergence the solve starts
@@ -401,18 +401,21 @@ ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L
                            int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, void* stream);
 
 /* FP64-accurate product on the bf16 tensor cores by an Ozaki-style error-free splitting
- * (Ozaki, Ogita, Rump, Oishi, Numer. Algorithms 59, 2012):
+ * (Ozaki, Ogita, Rump, Oishi, Numer. Algorithms 59, 2012), with signed digits:
  *   D = s L R + beta C + gamma I   (L M x K, R K x N, C and D M x N: FP64, row-major)
- * Each row i of L is scaled by the power of two mu_i >= max_k |L_ik| and cut into `slices`
- * integer slices of 8 bits (x <- 256 x, S = trunc(x), x <- x - S; |S| <= 255, exact in
- * bf16); each column of R likewise.  Slice products A_t B_u with t + u <= slices + 1 run on
- * tcgen05 CTA pairs over K chunks of 256, where their f32 accumulation is exact (256 * 255^2
- * < 2^24); chunk results are summed exactly in int32 and added into D in FP64 per level
- * t + u.  slices = 7 carries 56 bits per line (binary64: 53).  Workspace (2 slices (M K + K N)
- * bytes and three vectors) is taken from the stream-ordered allocator; `stream` is
- * synchronised.  frob_out (device double, may be NULL) receives sum(D^2).  D may alias C.
- * Errors: NS_ERR_ARG (sizes, leading dimensions, null pointers, slices outside 2..8),
- * NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_TIMEOUT. */
+ * Each row i of L is scaled by the power of two mu_i > max_k |L_ik| and L_ik / (2 mu_i),
+ * in (-1/2, 1/2), is cut into `slices` digits a_t = RN(256 x), x <- 256 x - a_t (|a_t| <= 128,
+ * exact in bf16); each column of R likewise (lines whose largest magnitude is below 2^-1000
+ * are taken as zero).  The digit products of level d = t + u <= slices + 1 run on tcgen05
+ * CTA pairs, summed exactly in f32 over chunks of 1024 / (d - 1) of K and in int32 over
+ * K; D = s (2 mu)(2 nu) sum_d 256^-d S_d + beta C + gamma I is then formed once per element
+ * (levels 2..5 and 6..s+1 exactly in int64, then binary64).  slices = 7 carries 56 bits per
+ * line (binary64: 53).  K is taken in blocks of at most 16384.  Workspace (slices x (2 M +
+ * 2 N) x min(K, 16384) + 4 M N slices bytes and a few vectors) is taken from the
+ * stream-ordered allocator; `stream` is synchronised.  frob_out (device double, may be NULL)
+ * receives sum(D^2).  D may alias C, and L or R when K <= 16384.
+ * Errors: NS_ERR_ARG (sizes, leading dimensions, null pointers, slices outside 2..7, D
+ * aliasing L or R with K > 16384), NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_TIMEOUT. */
 ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R, int64_t ldr,
                        double s, const double* C, int64_t ldc, double beta, double gamma, double* D, int64_t ldd,
                        int slices, double* frob_out, void* stream);

@@ -80,33 +80,51 @@ cudaError_t launch_gemm_tc(const TcParams& p, int BN, bool x3, int num_sms, cuda
 cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaStream_t s);
 int tc_tiles(int M, int N, int BN);
 
-// ---- FP64-accurate products from integer bf16 slices (gemm_oz.cu)
-constexpr int kOzMaxSlices = 8;
-constexpr int kOzMaxPairs = 36;  // slice pairs with t + u <= s + 1, s = 8
+// ---- FP64-accurate products from signed-digit bf16 slices (gemm_oz.cu)
+constexpr int kOzMaxSlices = 7;      // 7 digits of 8 bits cover binary64
+constexpr int64_t kOzMaxK = 16384;   // K per level-kernel launch: |S_d| < 2^31
+// The level kernel's launch: every level d of every 256 x 256 pair tile of
+// D = L R (M x N, K <= kOzMaxK) as one work item; writes the level sums S_d
+// (int32) to planes + (d - 2) plane_stride (leading dimension ldp).
 struct OzParams {
   CUtensorMap L[kOzMaxSlices];  // slices of L: M x K bf16 (role 0 maps, 64 x 64 boxes)
   CUtensorMap R[kOzMaxSlices];  // slices of R: K x N bf16
   int M, N, K;
-  int slices, npairs;
-  int tiles_n;      // 128-column tiles along N
-  int total_tiles;  // ceil(M / 256) * tiles_n pair tiles
-  int pair_t[kOzMaxPairs], pair_u[kOzMaxPairs];  // kept pairs, ordered by t + u
-  const double* mu;  // M power-of-two row scales of L
-  const double* nu;  // N power-of-two column scales of R
-  double s;          // D += s * L R
-  double* D;         // FP64 output, holding beta C + gamma I on entry
-  int64_t ldd;
+  int slices;
+  int tiles_m2;     // ceil(M / 256)
+  int tiles_n;      // ceil(N / 256)
+  int nlev;         // levels in this launch, in work-item order
+  int lev_d[kOzMaxSlices];    // level d = t + u
+  int lev_kcb[kOzMaxSlices];  // 64-deep K blocks per exactly summed chunk of that level
+  int total_items;  // nlev * tiles_m2 * tiles_n
+  int32_t* planes;
+  int64_t ldp, plane_stride;
   int debug_stall_iter;
   unsigned long long timeout_ns;
   int* err;
 };
-// Scales (per row of X if by_row, else per column) and s integer slices of an
-// FP64 matrix X (rows x cols, ld): slice t at out + (t - 1) slice_stride (ldo).
-cudaError_t launch_oz_prepare(const double* X, int64_t ld, int rows, int cols, bool by_row, int s, double* scale,
-                              bf16* out, int64_t ldo, int64_t slice_stride, cudaStream_t st);
-cudaError_t launch_oz_init(double* D, int64_t ldd, const double* C, int64_t ldc, double beta, double gamma, int rows,
-                           int cols, cudaStream_t st);
-cudaError_t launch_gemm_oz(const OzParams& p, int num_sms, cudaStream_t s);
+// One slice product D = s L R + beta C + gamma I (FP64 row-major, device),
+// with its workspace (oz_workspace_bytes) at `work`.
+struct OzArgs {
+  const double* L;
+  int64_t ldl;
+  const double* R;
+  int64_t ldr;
+  int M, N, K, slices;
+  double s;
+  const double* C;
+  int64_t ldc;
+  double beta, gamma;
+  double* D;
+  int64_t ldd;
+  double* frob_out;  // device double receiving sum(D^2), or null
+  void* work;
+  int debug_stall_iter;
+  unsigned long long timeout_ns;
+  int* err;
+};
+size_t oz_workspace_bytes(int64_t M, int64_t N, int64_t K, int slices);
+cudaError_t launch_oz_product(const OzArgs& g, int num_sms, cudaStream_t st);
 int tc_items(int M, int N, int BN, int CM);
 
 // Encode a 2-D bf16 tensor map (rows x cols, leading dimension ld elements).

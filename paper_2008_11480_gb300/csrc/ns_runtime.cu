@@ -107,11 +107,7 @@ struct ns_ctx {
   bool f64_ready = false;
   // FP64-accurate tensor-core products (option fp64_slices): integer bf16
   // slices of both operands, their scales and column sums of squares
-  bf16* oz_L = nullptr;
-  bf16* oz_R = nullptr;
-  double* oz_mu = nullptr;
-  double* oz_nu = nullptr;
-  double* oz_sq = nullptr;
+  void* oz_work = nullptr;  // slices, scales and level planes of one product (oz_workspace_bytes)
   int oz_now = 0;  // slices of the current product (fewer while ||F_k||_F >= 1)
   double *G64[2] = {nullptr, nullptr}, *X64[2] = {nullptr, nullptr}, *F64 = nullptr, *P64[2] = {nullptr, nullptr};
   std::vector<double*> T64[2];
@@ -442,63 +438,47 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   return NS_OK;
 }
 
-// One FP64-accurate product D = s L R + beta C + gamma I from integer bf16
-// slices on the tensor cores (n x n, leading dimension ld).  L and R are
-// sliced before D is first written, so D may alias any operand.
+// One FP64-accurate product D = s L R + beta C + gamma I from signed-digit
+// bf16 slices on the tensor cores (n x n, leading dimension ld).  L and R are
+// sliced before D is first written, so D may alias any operand (n <= 16384:
+// one K block).
 ns_status oz_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const double* C, double beta, double gamma,
                   double* D, double* frob_dst) {
   const int n = static_cast<int>(ctx->n);
   const int64_t ld = ctx->ld;
   const int ns = ctx->oz_now > 0 ? ctx->oz_now : ctx->opt.fp64_slices;
-  cudaStream_t st = ctx->stream;
-  const size_t per = static_cast<size_t>(n) * ld;
-  if (ctx->oz_L == nullptr) {
-    NS_TRY(alloc(ctx, &ctx->oz_L, per * kOzMaxSlices));
-    NS_TRY(alloc(ctx, &ctx->oz_R, per * kOzMaxSlices));
-    NS_TRY(alloc(ctx, &ctx->oz_mu, static_cast<size_t>(n)));
-    NS_TRY(alloc(ctx, &ctx->oz_nu, static_cast<size_t>(n)));
-    NS_TRY(alloc(ctx, &ctx->oz_sq, static_cast<size_t>(n)));
+  if (ctx->oz_work == nullptr) {
+    char* w = nullptr;
+    NS_TRY(alloc(ctx, &w, oz_workspace_bytes(n, n, n, kOzMaxSlices)));
+    ctx->oz_work = w;
   }
   EventPair* e = ev_begin(ctx, false);
-  NS_CK(launch_oz_prepare(L, ld, n, n, true, ns, ctx->oz_mu, ctx->oz_L, ld, static_cast<int64_t>(per), st));
-  NS_CK(launch_oz_prepare(R, ld, n, n, false, ns, ctx->oz_nu, ctx->oz_R, ld, static_cast<int64_t>(per), st));
-  NS_CK(launch_oz_init(D, ld, C, ld, beta, gamma, n, n, st));
-  OzParams p;
-  memset(&p, 0, sizeof(p));
-  for (int t = 0; t < ns; ++t)
-    if (!encode_bf16_map(&p.L[t], ctx->oz_L + t * per, n, n, ld, 0) ||
-        !encode_bf16_map(&p.R[t], ctx->oz_R + t * per, n, n, ld, 0))
-      return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-  p.M = p.N = p.K = n;
-  p.slices = ns;
-  for (int d = 2; d <= ns + 1; ++d)
-    for (int t = 1; t < d; ++t)
-      if (d - t >= 1 && d - t <= ns) {
-        p.pair_t[p.npairs] = t;
-        p.pair_u[p.npairs] = d - t;
-        p.npairs++;
-      }
-  p.tiles_n = (n + 127) / 128;
-  p.total_tiles = ((n + 255) / 256) * p.tiles_n;
-  p.mu = ctx->oz_mu;
-  p.nu = ctx->oz_nu;
-  p.s = s;
-  p.D = D;
-  p.ldd = ld;
-  p.debug_stall_iter = -1;
-  p.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
-  p.err = ctx->derr;
-  NS_CK(launch_gemm_oz(p, ctx->num_sms, st));
+  OzArgs g;
+  memset(&g, 0, sizeof(g));
+  g.L = L;
+  g.ldl = ld;
+  g.R = R;
+  g.ldr = ld;
+  g.M = g.N = g.K = n;
+  g.slices = ns;
+  g.s = s;
+  g.C = C;
+  g.ldc = ld;
+  g.beta = beta;
+  g.gamma = gamma;
+  g.D = D;
+  g.ldd = ld;
+  g.frob_out = frob_dst;
+  g.work = ctx->oz_work;
+  g.debug_stall_iter = -1;
+  g.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
+  g.err = ctx->derr;
+  NS_CK(launch_oz_product(g, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
-  ctx->launches += 6;
+  ctx->launches += 6 + (frob_dst ? 1 : 0);
   if (ctx->st) {
     ctx->st->gemm_launches++;
     ctx->st->gemm_flops += 2.0 * n * static_cast<double>(n) * n;
-  }
-  if (frob_dst) {
-    NS_CK(launch_colsumsq(D, ld, n, n, ctx->oz_sq, nullptr, st));
-    NS_CK(launch_reduce_sum(ctx->oz_sq, n, 1, frob_dst, st));
-    ctx->launches += 2;
   }
   return NS_OK;
 }
@@ -1974,78 +1954,49 @@ ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t
   if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
   if (!L || !R || !D || ldl < K || ldr < N || ldd < N || (C && ldc < N)) return NS_ERR_ARG;
   if (slices < 2 || slices > kOzMaxSlices) return NS_ERR_ARG;
+  // with K in several blocks, later blocks are sliced after D was written
+  if (K > kOzMaxK && (D == L || D == R)) return NS_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t ldk = (K + 7) / 8 * 8, ldn = (N + 7) / 8 * 8;  // 16-byte rows for the tensor maps
-  const size_t lbytes = sizeof(bf16) * static_cast<size_t>(M) * ldk * slices;
-  const size_t rbytes = sizeof(bf16) * static_cast<size_t>(K) * ldn * slices;
-  const size_t vbytes = sizeof(double) * static_cast<size_t>(M + N + N + 1);
+  const size_t wbytes = oz_workspace_bytes(M, N, K, slices);
   char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), lbytes + rbytes + vbytes + sizeof(int) * 4 + 512, st) !=
-      cudaSuccess) {
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), wbytes + 256, st) != cudaSuccess) {
     cudaGetLastError();
     return NS_ERR_OOM;
   }
-  bf16* Ls = reinterpret_cast<bf16*>(ws);
-  bf16* Rs = reinterpret_cast<bf16*>(ws + lbytes);
-  double* mu = reinterpret_cast<double*>(ws + ((lbytes + rbytes + 255) / 256) * 256);
-  double* nu = mu + M;
-  double* sq = nu + N;
-  int* err = reinterpret_cast<int*>(sq + N + 1);
+  int* err = reinterpret_cast<int*>(ws + wbytes);
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
-  if (e == cudaSuccess)
-    e = launch_oz_prepare(L, ldl, static_cast<int>(M), static_cast<int>(K), true, slices, mu, Ls, ldk, M * ldk, st);
-  if (e == cudaSuccess)
-    e = launch_oz_prepare(R, ldr, static_cast<int>(K), static_cast<int>(N), false, slices, nu, Rs, ldn, K * ldn, st);
-  if (e == cudaSuccess) e = launch_oz_init(D, ldd, C, ldc, beta, gamma, static_cast<int>(M), static_cast<int>(N), st);
-  OzParams p;
-  memset(&p, 0, sizeof(p));
-  bool maps = true;
-  for (int t = 0; t < slices && maps; ++t)
-    maps = encode_bf16_map(&p.L[t], Ls + t * M * ldk, M, K, ldk, 0) &&
-           encode_bf16_map(&p.R[t], Rs + t * K * ldn, K, N, ldn, 0);
-  if (!maps) {
-    cudaFreeAsync(ws, st);
-    return NS_ERR_ARG;
-  }
-  p.M = static_cast<int>(M);
-  p.N = static_cast<int>(N);
-  p.K = static_cast<int>(K);
-  p.slices = slices;
-  for (int d = 2; d <= slices + 1; ++d)
-    for (int t = 1; t < d; ++t)
-      if (d - t >= 1 && d - t <= slices) {
-        p.pair_t[p.npairs] = t;
-        p.pair_u[p.npairs] = d - t;
-        p.npairs++;
-      }
-  p.tiles_n = static_cast<int>((N + 127) / 128);
-  p.total_tiles = static_cast<int>((M + 255) / 256) * p.tiles_n;
-  p.mu = mu;
-  p.nu = nu;
-  p.s = s;
-  p.D = D;
-  p.ldd = ldd;
-  p.debug_stall_iter = -1;
-  p.timeout_ns = 2000000000ull;
-  if (const char* v = std::getenv("NSGB_INJECT_WITHHOLD_LOAD")) p.debug_stall_iter = std::atoi(v);
+  OzArgs g;
+  memset(&g, 0, sizeof(g));
+  g.L = L;
+  g.ldl = ldl;
+  g.R = R;
+  g.ldr = ldr;
+  g.M = static_cast<int>(M);
+  g.N = static_cast<int>(N);
+  g.K = static_cast<int>(K);
+  g.slices = slices;
+  g.s = s;
+  g.C = C;
+  g.ldc = ldc;
+  g.beta = beta;
+  g.gamma = gamma;
+  g.D = D;
+  g.ldd = ldd;
+  g.frob_out = frob_out;
+  g.work = ws;
+  g.debug_stall_iter = -1;
+  g.timeout_ns = 2000000000ull;
+  if (const char* v = std::getenv("NSGB_INJECT_WITHHOLD_LOAD")) g.debug_stall_iter = std::atoi(v);
   if (const char* v = std::getenv("NSGB_WAIT_LIMIT_MS")) {
     const long ms = std::atol(v);
-    if (ms > 0 && ms <= 10000) p.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
+    if (ms > 0 && ms <= 10000) g.timeout_ns = static_cast<unsigned long long>(ms) * 1000000ull;
   }
-  p.err = err;
-  const char* stage = "slicing";
-  if (e == cudaSuccess) {
-    stage = "product launch";
-    e = launch_gemm_oz(p, sms, st);
-  }
-  if (e == cudaSuccess && frob_out) {
-    stage = "sum of squares";
-    e = launch_colsumsq(D, ldd, static_cast<int>(M), static_cast<int>(N), sq, nullptr, st);
-    if (e == cudaSuccess) e = launch_reduce_sum(sq, static_cast<int>(N), 1, frob_out, st);
-  }
+  g.err = err;
+  const char* stage = "slice product launch";
+  if (e == cudaSuccess) e = launch_oz_product(g, sms, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(ws, st);
@@ -2053,6 +2004,7 @@ ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t
     stage = "execution";
     e = cudaStreamSynchronize(st);
   }
+  if (e == cudaErrorInvalidValue && stage[0] == 's') return NS_ERR_ARG;
   if (e != cudaSuccess) return kernel_fail(NS_ERR_CUDA, stage, e);
   return herr == DEV_OK ? NS_OK : kernel_fail(NS_ERR_TIMEOUT, "bounded device wait ran out", cudaSuccess);
 }

@@ -117,8 +117,8 @@ def test_create_rejects_bad_precision(L):
 def test_create_validates_precision_options(L):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 1)(2)
-    for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
-               {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 3}, {"pow_bf16": -1},
+    for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 8}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
+               {"fp64_slices_early": 8}, {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 3}, {"pow_bf16": -1},
                {"gemm_cluster": 2}, {"gemm_cluster": 4}):
         opt = nsgb.default_options(**kw)
         assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG, kw
@@ -144,11 +144,14 @@ def test_new_kernel_entry_points_validate_before_launch(L):
                               None) == nsgb.NS_ERR_ARG
     assert L.ns_k_split3(16, 0, 4, 4, 4, 16, 16, None, 4, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_split3(16, 2, 4, 4, 4, 16, 16, 16, 4, None) == nsgb.NS_ERR_ARG
-    # slice products: slice count outside 2..8, null output, short leading dimension
-    for sl in (1, 9):
+    # slice products: slice count outside 2..7, null output, short leading dimension,
+    # an output aliasing an operand when K is taken in several blocks
+    for sl in (1, 8, 9):
         assert L.ns_k_gemm_oz(8, 8, 8, 16, 8, 16, 8, 1.0, None, 0, 0.0, 0.0, 16, 8, sl, None, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_oz(8, 8, 8, 16, 8, 16, 8, 1.0, None, 0, 0.0, 0.0, None, 8, 7, None, None) == nsgb.NS_ERR_ARG
     assert L.ns_k_gemm_oz(8, 8, 8, 16, 4, 16, 8, 1.0, None, 0, 0.0, 0.0, 16, 8, 7, None, None) == nsgb.NS_ERR_ARG
+    assert L.ns_k_gemm_oz(8, 8, 20000, 16, 20000, 32, 8, 1.0, None, 0, 0.0, 0.0, 16, 8, 7, None,
+                          None) == nsgb.NS_ERR_ARG
 
 
 def test_horner_form_accepts_any_order(L):

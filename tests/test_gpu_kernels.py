@@ -439,7 +439,7 @@ def test_gemm_x6_full_size_sampled():
         assert abs(out[i, j] - ref) <= tol, (i, j, out[i, j], ref)
 
 
-# ---------------------------------------------------------------- FP64-accurate products from integer slices
+# ---------------------------------------------------------------- FP64-accurate products from signed-digit slices
 def run_gemm_oz(M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, slices=7, spread=True):
     rng = np.random.default_rng(seed)
     L = rng.standard_normal((M, K))
@@ -454,12 +454,13 @@ def run_gemm_oz(M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, slices=
     fro = torch.zeros(1, dtype=torch.float64, device=dev)
     nsgb.ns_k_gemm_oz(M, N, K, Ld, K, Rd, N, s, Cd, N if with_c else 0, beta, gamma, D, N, slices, fro)
     torch.cuda.synchronize()
-    prod = O.ozaki_product(L, R, slices)
+    prod = O.ozaki_product_signed(L, R, slices)
     ref = O.gemm_epilogue(prod, s, C, beta, gamma)
     out = D.cpu().numpy()
     ab = np.abs(L) @ np.abs(R)
-    # same slices and integer sums; only the binary64 combination of the levels
-    # (one rounding per level and per flush) differs from the oracle's order
+    # same digits and exact integer level sums; only the binary64 combination
+    # of the levels (the kernel: two int64 groups, three roundings; the
+    # oracle: one rounding per level) differs
     tol = 16 * 2.0 ** -53 * (abs(s) * ab + np.abs(ref)) + 1e-300
     err = np.abs(out - ref)
     assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
@@ -477,6 +478,33 @@ def test_gemm_oz_epilogues_and_slices():
     run_gemm_oz(300, 300, 300, seed=3, s=-1.0, gamma=1.0, spread=False)
     run_gemm_oz(257, 129, 200, seed=4, beta=1.0, with_c=True)
     run_gemm_oz(200, 160, 300, seed=5, slices=3)
+
+
+@pytest.mark.parametrize("slices", [2, 3, 4, 5, 6])
+def test_gemm_oz_slice_counts(slices):
+    """Every digit count: levels d = 2 .. s + 1, each with its own exactly
+    summed chunk length (1024 / (d - 1) of K) and int64 grouping (levels
+    2..5 and 6..s+1), against the oracle's signed-digit product; K spans
+    several chunks of every level and a ragged last one."""
+    run_gemm_oz(520, 300, 1100, seed=50 + slices, slices=slices, s=-1.0, gamma=1.0)
+
+
+def test_gemm_oz_K_in_blocks():
+    """K beyond one level-kernel launch (16384): the blocks are sliced with
+    their own scales and added into D; against the exact product."""
+    M, N, K = 130, 70, 20000
+    rng = np.random.default_rng(60)
+    L, R, C = rng.standard_normal((M, K)), rng.standard_normal((K, N)), rng.standard_normal((M, N))
+    D = torch.zeros((M, N), dtype=torch.float64, device=dev)
+    fro = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_oz(M, N, K, torch.from_numpy(L).to(dev), K, torch.from_numpy(R).to(dev), N, 0.5,
+                      torch.from_numpy(C).to(dev), N, 2.0, 1.0, D, N, 7, fro)
+    torch.cuda.synchronize()
+    out = D.cpu().numpy()
+    exact = (0.5 * (L.astype(np.longdouble) @ R.astype(np.longdouble)) + 2.0 * C + np.eye(M, N)).astype(np.float64)
+    ab = np.abs(L) @ np.abs(R)
+    assert np.all(np.abs(out - exact) <= 16 * 2.0 ** -53 * (ab + np.abs(exact)))
+    assert float(fro.item()) == pytest.approx(float(np.sum(out * out)), rel=1e-12)
 
 
 def test_gemm_oz_fp64_accuracy():
