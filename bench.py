@@ -1,15 +1,22 @@
-"""Benchmark: SPD solves/s at relative residual <= 1e-10 on one dense system
-n = 4096, kappa = 1e4, 4 right-hand sides (A = Q diag(lambda) Q^T, lambda
-log-uniform in [1, 1e4]), by factorized Newton-Schulz (mixed bf16/bf16x3
-products on the tensor cores) coupled to FP64 Richardson iteration.
+"""Benchmark: SPD solves/s at relative residual <= 1e-10, mixed precision
+against the plain FP64 method, on one GB300.
+
+Default workload (the metric's largest single-GPU configuration): the
+least-squares Gram system n = 16384, A = X^T X with cond(A) = 1e6 (X = U
+diag(sigma) V^T, sigma log-uniform in [1e-3, 1]), b = X^T y, order-8
+factorized Newton-Schulz coupled to FP64 Richardson.  Products run in bf16,
+then bf16x3, and where binary32 masters stop contracting, FP64-accurate
+4-digit slice products on the bf16 tensor cores continue from the last
+contracting G.  The dense n = 4096 system (kappa = 1e4, 4 RHS) is measured
+beside it (variants.dense_n4096; --workload dense makes it the line).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one complete solve from the system alone (norms, splits, G0, every
 NS step and Richardson sweep until the residual test passes), inputs resident
-in HBM.  L2 is flushed (512 MiB write) between timed steps, outside the timed
-events.  Under torchrun each rank solves its own system (independent replicas;
-the problem does not shard without an exchange per product).  Rank 0 prints one
+in HBM.  512 MiB is written between timed steps, outside the timed events.
+Under torchrun each rank solves its own system (independent replicas; the
+problem does not shard without an exchange per product).  Rank 0 prints one
 JSON line.
 """
 from __future__ import annotations
@@ -217,6 +224,332 @@ def run_reference(a):
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sample_wall_s": wall}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ the Gram system (default workload)
+# Least-squares Gram system of the metric's largest single-GPU configuration:
+# n = 16384, A = X^T X with cond(A) = 1e6, b = X^T y, order 8 factorized.
+GRAM_SIGMA_LO, GRAM_SEED, GRAM_ORDER, GRAM_SLICES = 1e-3, 5, 8, 4
+
+
+def gram_config(a):
+    n = a.gram_n
+    return {
+        "workload": f"least-squares Gram system n={n}: A = X^T X, b = X^T y for a {2 * n} x {n} design "
+                    f"X = U diag(sigma) V^T, sigma log-uniform in [1e-3, 1] (cond(A) = 1e6), y ~ N(0,1); 1 RHS",
+        "n": n, "kappa": 1e6, "nrhs": 1, "order": GRAM_ORDER, "form": "factorized (I+F)(I+F^2)(I+F^4)",
+        "precision": "auto: bf16 products while ||F||_F falls, then bf16x3 (f32 accumulate); where the binary32 "
+                     "masters stop contracting, the FP64 path with 4-digit slice products (bf16 tensor cores, "
+                     "exact integer accumulation) from the last contracting G; FP64 residual and Richardson",
+        "tol": 1e-10, "l2": "inputs larger than L2 (A: 2 GiB FP64); 512 MiB written between timed steps",
+        "seed": GRAM_SEED, "couple_frob": a.couple, "fp64_slices": GRAM_SLICES}
+
+
+def plain_fp64_model(n, seed=GRAM_SEED, order=GRAM_ORDER, stop=0.02, tol=1e-10):
+    """Work of the plain FP64 method on the Gram system, from its exact-arithmetic
+    iterates: with G_0 = I / ||A||_F, F_k = (I - A/||A||_F)^{order^k}, so
+    ||F_k||_F^2 = sum_i (1 - lambda_i / ||A||_F)^{2 order^k} over the generator's
+    spectrum lambda = sigma^2.  Newton-Schulz runs until ||F_k||_F <= stop (the
+    library's ns_stop_frob), 2 m products a step for order 2^m (the residual
+    product included), then Richardson sweeps at the rate ||F_k||_F.
+    Returns (steps, products, sweeps)."""
+    from workloads import gram_spectrum
+    sigma, _, _ = gram_spectrum(n, GRAM_SIGMA_LO, seed)
+    lam = sigma ** 2
+    le = np.log1p(-lam / np.sqrt(np.sum(lam * lam)))  # log(1 - alpha lambda) < 0
+    k, frob = 0, float(np.sqrt(n))
+    while frob > stop and k < 64:
+        k += 1
+        frob = float(np.sqrt(np.sum(np.exp(2.0 * order ** k * le))))
+    m = int(round(np.log2(order)))
+    sweeps = max(1, int(np.ceil(np.log(tol) / np.log(max(frob, 1e-300)))))
+    return k, 2 * m * k, sweeps
+
+
+def oracle_sample_gram(a, L, R, x):
+    """Time the FP64 oracle as it stands on the host cores on a bounded piece of
+    the Gram workload: one oracle product of a rows x n panel by an n x n
+    matrix (the solve's products are n x n x n) and one matrix-vector product
+    (a Richardson sweep is two), extrapolated with plain_fp64_model's counts."""
+    import oracle as O
+    rows, n = L.shape
+    t0 = time.perf_counter()
+    O.mm(L, R)
+    t1 = time.perf_counter()
+    R @ x
+    t2 = time.perf_counter()
+    t_prod = (t1 - t0) * n / rows
+    t_sweep = 2.0 * (t2 - t1)
+    k, prods, sweeps = plain_fp64_model(n)
+    solve_s = prods * t_prod + sweeps * t_sweep
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / solve_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one numpy FP64 oracle product of a {rows} x {n} panel by an {n} x {n} matrix "
+                      f"({t1 - t0:.2f} s, scaled to n rows) and one matrix-vector product, extrapolated to the "
+                      f"plain method's {prods} products ({k} order-{GRAM_ORDER} steps) + {sweeps} sweeps on this system"}
+
+
+def gram_oracle_operands(n, rows):
+    rng = np.random.default_rng(11)
+    return rng.standard_normal((rows, n)), rng.standard_normal((n, n)), rng.standard_normal((n, 1))
+
+
+def run_reference_gram(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L, R, x = gram_oracle_operands(a.gram_n, a.ref_rows)
+    for _ in range(min(a.warmup, 1)):
+        oracle_sample_gram(a, L, R, x)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        vals.append(oracle_sample_gram(a, L, R, x))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": gram_config(a),
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def run_gram(a):
+    """The default line: the n = 16384 Gram system (cond 1e6), one solve per step
+    from the system alone to a verified relative residual <= 1e-10."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_gram_device
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = a.gram_n
+    A, B, V, sg, z = make_gram_device(n, GRAM_SIGMA_LO, seed=GRAM_SEED + rank, device=dev, return_factors=True)
+    tstar = V @ (z / sg[:, None])
+    del V
+    out = torch.empty_like(B)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    opts = dict(order=GRAM_ORDER, stream=stream, couple_frob=a.couple, fp64_slices=GRAM_SLICES, fp64_slices_early=0)
+    ctx = nsgb.Context(n, profile=1, **opts)
+    for _ in range(max(3, a.warmup)):
+        r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
+    assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
+
+    sampler = ClockSampler(local)
+    step_ms, ns_it, sw = [], [], []
+    acc = dict(tc_ms=0.0, tc_flops=0.0, tc_alg=0.0, tc_l=0, gemm_ms=0.0, gemm_l=0, launches=0)
+    barrier()
+    sampler.start()
+    for _ in range(a.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        assert r.status == nsgb.NS_OK
+        step_ms.append(e0.elapsed_time(e1))
+        st = r.stats
+        acc["tc_ms"] += st.tc_gemm_ms
+        acc["tc_flops"] += st.tc_gemm_flops
+        acc["tc_alg"] += st.tc_gemm_alg_flops
+        acc["tc_l"] += st.tc_gemm_launches
+        acc["gemm_ms"] += st.gemm_ms
+        acc["gemm_l"] += st.gemm_launches
+        acc["launches"] += st.kernel_launches
+        ns_it.append(st.ns_iters)
+        sw.append(st.sweeps)
+    barrier()
+    clocks = sampler.stop()
+    rel = max(ctx.residual(A, out, B))
+    th_err = float(torch.linalg.norm(out - tstar) / torch.linalg.norm(tstar))
+    total_s = reduce_over_ranks([sum(step_ms) / 1e3], "max", dev)[0]
+    value = world * a.steps / total_s
+
+    # end to end through the same C-ABI call with host (pinned) buffers: the
+    # host->device copy of A and b and the device->host copy of theta are
+    # inside the timed region
+    Ah = A.cpu().pin_memory()
+    Bh = B.cpu().pin_memory()
+    Th = torch.empty_like(Bh).pin_memory()
+    ctx_h = nsgb.Context(n, **opts)
+    ctx_h.solve(Ah, Bh, iters=80, tol=1e-10, out=Th)
+    e2e_steps = max(1, min(a.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rh = ctx_h.solve(Ah, Bh, iters=80, tol=1e-10, out=Th)
+        assert rh.status == nsgb.NS_OK
+    torch.cuda.synchronize(dev)
+    e2e_s = reduce_over_ranks([time.perf_counter() - t0], "max", dev)[0]
+    ctx_h.close()
+    del Ah
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(n * n * 8 + Bh.numel() * 8), "d2h_bytes_per_step": int(Th.numel() * 8)}
+
+    # the plain FP64 method on the GPU (CUDA-core FP64 products, FP64
+    # Richardson), priced: one timed n^3 product x its product count
+    fp64 = None
+    if not a.no_fp64:
+        D = torch.empty_like(A)
+        nsgb.ns_k_gemm_f64(256, 256, 256, A, n, A, n, 1.0, None, 0, 0.0, 0.0, D, n, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nsgb.ns_k_gemm_f64(n, n, n, A, n, A, n, -1.0, None, 0, 0.0, 1.0, D, n, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_prod = e0.elapsed_time(e1) / 1e3
+        del D
+        k, prods, sweeps = plain_fp64_model(n)
+        est = prods * t_prod
+        fp64 = {"value": 1.0 / est, "unit": UNIT, "ms_per_step": est * 1e3, "fp64_product_s": t_prod,
+                "ns_iters": k, "products": prods, "sweeps": sweeps,
+                "how": "one event-timed CUDA-core FP64 product (k_gemm_f64) x the plain method's products on this "
+                       "system (its exact-arithmetic iterates; sweeps are negligible)",
+                "speedup_of_mixed": value / max(world, 1) * est}
+
+    # roofline of the dominant kernel by event-timed share: the tcgen05 bf16 /
+    # bf16x3 products (k_gemm_tc2) or the slice products (k_gemm_oz with its
+    # slicing and combine kernels).  achieved counts algorithmic work, 2 n^3
+    # per product of the method whatever its passes or digit pairs
+    pk, pk_kind = peaks()
+    sus = pk["bf16_tflops_sustained"]
+    f3 = 2.0 * float(n) ** 3
+    oz_ms = acc["gemm_ms"] - acc["tc_ms"]
+    oz_l = acc["gemm_l"] - acc["tc_l"]
+    pairs = GRAM_SLICES * (GRAM_SLICES + 1) // 2
+    kern = {
+        "k_gemm_tc2": {"ms_per_step": acc["tc_ms"] / a.steps, "launches_per_step": acc["tc_l"] / a.steps,
+                       "achieved_tflops": acc["tc_alg"] / (acc["tc_ms"] / 1e3) / 1e12 if acc["tc_ms"] else None,
+                       "executed_tflops": acc["tc_flops"] / (acc["tc_ms"] / 1e3) / 1e12 if acc["tc_ms"] else None},
+        "k_gemm_oz": {"ms_per_step": oz_ms / a.steps, "products_per_step": oz_l / a.steps, "digit_pairs": pairs,
+                      "achieved_tflops": oz_l * f3 / (oz_ms / 1e3) / 1e12 if oz_ms > 0 else None,
+                      "executed_tflops": oz_l * pairs * f3 / (oz_ms / 1e3) / 1e12 if oz_ms > 0 else None,
+                      "note": "time of the whole slice product: scales, digit slicing, level kernel, combine"}}
+    dom = "k_gemm_oz" if oz_ms > acc["tc_ms"] else "k_gemm_tc2"
+    kd = kern[dom]
+    ach, exe = kd["achieved_tflops"], kd["executed_tflops"]
+    roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": sus, "unit": "TFLOP/s",
+            "frac": ach / sus if ach else None,
+            "peak_kind": f"bf16 dense sustained ({pk_kind}); kernel timed inside back-to-back solves; achieved and "
+                         "frac count algorithmic flops (2 n^3 per product)",
+            "executed": exe, "frac_executed": exe / sus if exe else None,
+            "executed_note": "bf16 tensor work run: bf16x3 = 3 passes, a 4-digit slice product = 10 digit pairs",
+            "traffic": recorded_traffic("traffic_k_gemm_oz_gram16384.md") if dom == "k_gemm_oz" else None,
+            "traffic_unit": "bytes per level-kernel launch (ncu dram read + write)",
+            "avg_launch_ms": (oz_ms / max(oz_l, 1)) if dom == "k_gemm_oz" else acc["tc_ms"] / max(acc["tc_l"], 1),
+            "flops_per_launch": f3 if dom == "k_gemm_oz" else acc["tc_alg"] / max(acc["tc_l"], 1),
+            "kernels": kern}
+    variants = {}
+    if world == 1 and not a.no_variants:
+        try:
+            variants["dense_n4096"] = dense_variant(a, dev, stream, flush)
+        except Exception as ex:  # reported, never fatal to the headline line
+            variants["dense_n4096"] = {"error": str(ex)[:300]}
+    if rank == 0:
+        cpu = None
+        if not a.no_cpu:
+            L, R, x = gram_oracle_operands(n, a.ref_rows)
+            cpu = oracle_sample_gram(a, L, R, x)
+            del L, R, x
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 / bf16x3 / bf16 digit slices (FP64-accurate); FP64 Richardson",
+            "data": "synthetic", "config": gram_config(a),
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                           "min": srt[0], "max": srt[-1]},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(acc["launches"]), "roofline": roof,
+            "cpu_baseline": cpu, "fp64_path": fp64, "verified_rel_res": rel, "theta_rel_err_vs_closed_form": th_err,
+            "ns_iters": int(statistics.median(ns_it)), "sweeps": int(statistics.median(sw)),
+            "prec_history": r.stats.prec_history(), "frob_history": [round(f, 4) for f in r.stats.frob_history()],
+            **({"variants": variants} if variants else {}),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def dense_variant(a, dev, stream, flush):
+    """The dense n = 4096 system (kappa = 1e4, 4 RHS, order 8), measured beside
+    the headline on the same box: solves/s, the product kernels' algorithmic
+    roofline fraction, and the plain FP64 method timed on the GPU."""
+    import torch
+
+    import paper_2008_11480_gb300 as nsgb
+    from workloads import make_spd
+    n, kappa, nrhs = 4096, 1e4, 4
+    p = make_spd(n, kappa, nrhs=nrhs, seed=1)
+    A = torch.from_numpy(p.A).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    out = torch.empty_like(B)
+    ctx = nsgb.Context(n, order=8, stream=stream, profile=1, couple_frob=a.couple)
+    for _ in range(3):
+        ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+    ms, tc_ms, tc_alg, tc_fl, tc_l, it, sw = [], 0.0, 0.0, 0.0, 0, [], []
+    for _ in range(max(1, min(a.steps, 20))):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        assert r.status == nsgb.NS_OK
+        ms.append(e0.elapsed_time(e1))
+        tc_ms += r.stats.tc_gemm_ms
+        tc_alg += r.stats.tc_gemm_alg_flops
+        tc_fl += r.stats.tc_gemm_flops
+        tc_l += r.stats.tc_gemm_launches
+        it.append(r.stats.ns_iters)
+        sw.append(r.stats.sweeps)
+    rel = max(ctx.residual(A, out, B))
+    ctx.close()
+    pk, pk_kind = peaks()
+    sus = pk["bf16_tflops_sustained"]
+    ach = tc_alg / (tc_ms / 1e3) / 1e12
+    exe = tc_fl / (tc_ms / 1e3) / 1e12
+    res = {"workload": "dense SPD n=4096 kappa=1e4 nrhs=4 (A = Q diag(lambda) Q^T, Q Haar, lambda log-uniform), "
+                       "order 8 factorized, auto bf16/bf16x3, FP64 Richardson",
+           "value": 1e3 / statistics.mean(ms), "unit": UNIT, "ms_per_step": statistics.mean(ms), "steps": len(ms),
+           "verified_rel_res": rel, "ns_iters": int(statistics.median(it)), "sweeps": int(statistics.median(sw)),
+           "roofline": {"bound": "tensor", "kernel": "k_gemm_tc2", "achieved": ach, "peak": sus, "unit": "TFLOP/s",
+                        "frac": ach / sus, "executed": exe, "frac_executed": exe / sus,
+                        "peak_kind": f"bf16 dense sustained ({pk_kind}); achieved counts 2 n^3 per product",
+                        "traffic": recorded_traffic("traffic_k_gemm_tc2_bench_n4096.md"),
+                        "traffic_unit": "bytes per launch (ncu dram read + write)",
+                        "avg_launch_ms": tc_ms / max(tc_l, 1)}}
+    if not a.no_fp64:
+        with nsgb.Context(n, order=8, stream=stream, precision=nsgb.NS_FP64, couple_frob=a.couple) as c64:
+            out64 = torch.empty_like(B)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = c64.solve(A, B, iters=a.iters, tol=1e-10, out=out64)
+            e1.record(stream)
+            e1.synchronize()
+            ms64 = e0.elapsed_time(e1)
+        res["fp64_path"] = {"value": 1e3 / ms64, "ms_per_step": ms64, "status": int(r64.status),
+                            "ns_iters": r64.stats.ns_iters, "sweeps": r64.stats.sweeps, "rel_res": r64.stats.rel_res,
+                            "speedup_of_mixed": res["value"] / (1e3 / ms64)}
+    return res
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -872,7 +1205,7 @@ def run_ill(a):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
@@ -897,10 +1230,14 @@ def main():
                          "0 off, 1 on, 2 on from n = 4096)")
     ap.add_argument("--gemm-cluster", type=int, default=0, choices=(0, 1, -2),
                     help="single workload: product-kernel grouping (0 automatic, 1 one CTA per tile, -2 CTA pairs)")
-    ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "serving", "orders", "small", "ill"],
-                    help="single: the n = 4096 system the metric is quoted on; batched: many harmonic systems; "
-                         "serving: continuous batching of a Poisson request trace")
+    ap.add_argument("--workload", default="gram",
+                    choices=["gram", "single", "dense", "batched", "serving", "orders", "small", "ill"],
+                    help="gram (default): the n = 16384 least-squares Gram system, cond 1e6; single / dense: the "
+                         "n = 4096 dense system; batched: many harmonic systems; serving: continuous batching of a "
+                         "Poisson request trace")
+    ap.add_argument("--gram-n", type=int, default=16384, help="gram workload: system size")
+    ap.add_argument("--ref-rows", type=int, default=512,
+                    help="gram workload: rows of the panel the oracle sample multiplies")
     ap.add_argument("--count", type=int, default=2048)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=10.0)
@@ -943,6 +1280,12 @@ def main():
         return
     if a.warmup < 3 and a.impl == "ours":
         a.warmup = 3
+    if a.workload == "gram":
+        if a.impl == "reference":
+            run_reference_gram(a)
+        else:
+            run_gram(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

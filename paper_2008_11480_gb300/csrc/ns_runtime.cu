@@ -812,7 +812,15 @@ struct Solve {
   int prec = NS_BF16X3;
   int cur = 0;  // G buffer holding G_k
   int ccur = 0; // composite buffers holding T_i
+  bool g0_resident = false;  // FP64 path: G64[0] already holds G_0 (hand-over from the mixed path)
+  int handover = -1;         // mixed path: the G buffer handed to the FP64 slice path
+  int done0 = 0;             // Newton-Schulz steps taken before this run (statistics)
 };
+
+// run() on the mixed path with AUTO precision and slice products enabled:
+// binary32 masters cannot carry this system past the current G, which the
+// FP64 path with slice products continues from (S.handover).  Internal only.
+constexpr ns_status kHandover = static_cast<ns_status>(64);
 
 ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bool richardson, ns_stats* st) {
   const int n = static_cast<int>(ctx->n);
@@ -842,7 +850,9 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       NS_CK(launch_copy_f64(S.A, S.lda, n, n, ctx->Astage, ld, s));
       ctx->launches++;
     }
-    if (G0)
+    if (S.g0_resident) {
+      // G64[0] holds the G_k the mixed path handed over
+    } else if (G0)
       NS_CK(launch_copy_f64(G0, n, n, n, ctx->G64[0], ld, s));
     else if (ctx->opt.g0_mode == 2)
       NS_CK(launch_init_g0_jacobi(S.A, S.lda, n, ld, nullptr, nullptr, nullptr, ctx->G64[0], s));
@@ -894,7 +904,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
   // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
   // S^{-1} (F = I - A S^{-1} mirrors S^{-1} D)
-  if (ctx->opt.g0_order >= 2) {
+  if (ctx->opt.g0_order >= 2 && !S.g0_resident) {
     const int saved_form = ctx->opt.form;
     ctx->opt.form = 2;
     ns_status r0;
@@ -929,6 +939,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   }
 
   const bool autop = !fp64 && ctx->opt.precision == NS_AUTO;
+  // AUTO with slice products (option fp64_slices): where the binary32 masters
+  // stop carrying the iteration (bf16x3 leaves the contraction region, or its
+  // floor lies above ||F||_F = 1), the FP64 path with slice products takes
+  // over from the best G so far instead of bf16x6 and sweeps that cannot reach tol
+  const bool slice_handover = autop && ctx->opt.fp64_slices > 0 && !comp && richardson && tol > 0 &&
+                              ctx->opt.accel_richardson == 0;
   int prec = fp64 ? NS_FP64 : (autop ? NS_BF16 : ctx->opt.precision);
   int done = 0;
   int sweeps_left = ctx->opt.max_sweeps;
@@ -1170,6 +1186,28 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         goto recompute_F;
       }
       if (frob > 2.0 * sqrt_n + 1.0 && frob > 2.0 * prev_frob) {
+        if (fp64 && ctx->oz_now < oz_full && done > 0) {
+          // the reduced slice count threw the step out of the contraction
+          // region: back to G_{k-1}, full slices from there
+          S.cur ^= 1;
+          done--;
+          if (st) st->rollbacks++;
+          ctx->oz_now = oz_full;
+          prev_frob = INFINITY;
+          prev_ratio = INFINITY;
+          goto recompute_F;
+        }
+        if (slice_handover && prec != NS_BF16 && done > 0) {
+          S.cur ^= 1;  // G_{k-1}, the last G inside the contraction region
+          done--;
+          if (st) {
+            st->rollbacks++;
+            st->ns_iters = done + S.done0;
+          }
+          S.handover = S.cur;
+          if (richardson) NS_TRY(join_streams(ctx, rs, s));
+          return kHandover;
+        }
         if (autop && ctx->x6 && prec == NS_BF16X3 && done > 0) {
           // bf16x3 rounding threw the step out of the contraction region:
           // go back to G_{k-1} and continue with bf16x6 products
@@ -1220,6 +1258,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           // above ||F||_F = 1, more steps only repeat it (Richardson takes
           // over if rho(I - A G) < 1)
           floor_hit = true;
+          if (slice_handover) {
+            if (frob > prev_frob) {
+              S.cur ^= 1;
+              done--;
+            }
+            if (st) st->ns_iters = done + S.done0;
+            S.handover = S.cur;
+            if (richardson) NS_TRY(join_streams(ctx, rs, s));
+            return kHandover;
+          }
         }
         if (floor_hit && ctx->oz_now < oz_full) {
           // the floor of the reduced slice count: full slices from G_k on
@@ -1280,7 +1328,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       prev_ratio = (done > 0 && std::isfinite(prev_frob)) ? frob / prev_frob : INFINITY;
       prev_frob = frob;
       done++;
-      if (st) st->ns_iters = done;
+      if (st) st->ns_iters = done + S.done0;
       if (done >= iters) ns_active = false;
       continue;
     }
@@ -1682,8 +1730,31 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   S.fp64 = fp64;
   S.theta0_given = Theta0 != nullptr;
   r = run(ctx, S, nullptr, iters, tol, true, st);
-  if (!fp64 && ctx->opt.precision == NS_AUTO && ctx->opt.fp64_slices > 0 && ctx->rates.empty() && tol > 0 &&
-      (r == NS_NOT_CONVERGED || r == NS_ERR_DIVERGED)) {
+  if (r == kHandover) {
+    // the FP64 path with slice products continues Newton-Schulz from the G_k
+    // the mixed path handed over (widened from its binary32 master), with
+    // theta from the caller's theta0 (the mixed attempt coupled Richardson to
+    // G that may not contract)
+    const int done0 = st ? st->ns_iters : 0;
+    r = ensure_f64(ctx);
+    if (r == NS_OK) {
+      e = launch_f32_to_f64(ctx->G[S.handover].m32, ctx->ld, n, n, ctx->G64[0], ctx->ld, ctx->stream);
+      if (e == cudaSuccess)
+        e = Theta0 ? (Theta0 == Th ? cudaSuccess
+                                   : cudaMemcpyAsync(Th, Theta0, nb * sizeof(double), cudaMemcpyDefault, ctx->stream))
+                   : cudaMemsetAsync(Th, 0, nb * sizeof(double), ctx->stream);
+      r = e == cudaSuccess ? NS_OK : fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (r == NS_OK) {
+      ctx->launches++;
+      S.fp64 = true;
+      S.g0_resident = true;
+      S.done0 = done0;
+      r = run(ctx, S, nullptr, iters > done0 ? iters - done0 : 0, tol, true, st);
+    }
+  }
+  if (!fp64 && !S.fp64 && ctx->opt.precision == NS_AUTO && ctx->opt.fp64_slices > 0 && ctx->rates.empty() &&
+      tol > 0 && (r == NS_NOT_CONVERGED || r == NS_ERR_DIVERGED)) {
     // the binary32 masters cannot carry this system: the FP64 path with
     // slice products starts over (Newton-Schulz from G0, theta from the
     // caller's theta0 -- a mixed attempt that did not contract may have left

@@ -39,18 +39,52 @@ def test_repository_record_is_well_formed():
         assert os.path.exists(os.path.join(ROOT, f)), f
 
 
-def test_reference_arm_line_follows_the_contract():
-    """`bench.py --impl reference` (the oracle on the host cores) prints one
-    JSON line with the contract's keys; checked on a small system so that it
-    runs in seconds without a GPU."""
+def _reference_line(args):
     import json
     import subprocess
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "256",
-                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"] + args,
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
-    d = json.loads(lines[0])
+    return json.loads(lines[0])
+
+
+def test_reference_arm_gram_line():
+    """The default (Gram) workload's reference arm, on a small Gram system:
+    the contract's keys, the workload's config, and an oracle sample whose
+    extrapolation uses the plain method's product count on that system."""
+    d = _reference_line(["--gram-n", "512", "--ref-rows", "64", "--steps", "2", "--warmup", "1"])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["config"]["n"] == 512 and d["config"]["kappa"] == 1e6 and "Gram" in d["config"]["workload"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and "products" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_plain_fp64_model_counts():
+    """The plain method's work on the Gram system from its exact iterates: the
+    step count makes ||F_K||_F <= 0.02 and ||F_{K-1}||_F > 0.02 on the
+    generator's spectrum, 2 m products per order-2^m step."""
+    import numpy as np
+
+    from workloads import gram_spectrum
+    n = 2048
+    k, prods, sweeps = bench.plain_fp64_model(n, order=8)
+    lam = gram_spectrum(n, 1e-3, bench.GRAM_SEED)[0] ** 2
+    a = 1.0 / np.sqrt(np.sum(lam * lam))
+    frob = lambda j: np.sqrt(np.sum((1 - a * lam) ** (2 * 8 ** j)))  # noqa: E731
+    assert frob(k) <= 0.02 < frob(k - 1)
+    assert prods == 6 * k and sweeps >= 1
+
+
+def test_reference_arm_line_follows_the_contract():
+    """`bench.py --impl reference --workload dense` (the oracle on the host
+    cores) prints one JSON line with the contract's keys; checked on a small
+    system so that it runs in seconds without a GPU."""
+    d = _reference_line(["--workload", "dense", "--n", "256", "--steps", "2", "--warmup", "1"])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k

@@ -33,3 +33,24 @@ def test_serving_trace_distribution():
     # log-uniform: the median of log n sits mid-way
     assert abs(np.median(np.log(ns)) - 0.5 * (np.log(32) + np.log(2048))) < 0.15
     assert all(1 <= r.nrhs <= 64 for r in tr) and all(1e2 <= r.kappa <= 1e6 for r in tr)
+
+
+def test_make_gram_device_is_the_gram_system():
+    """A = V diag(sigma^2) V^T with cond(A) = sigma_lo^-2 exactly, b = V (sigma z),
+    and theta* = V (z / sigma) solves it; checked against an explicit design
+    X = U diag(sigma) V^T built from the returned factors (A = X^T X, b = X^T y
+    with y = U z for U with orthonormal columns)."""
+    from workloads import make_gram_device
+    n = 48
+    A, b, V, s, z = make_gram_device(n, sigma_lo=1e-2, seed=7, device="cpu", return_factors=True)
+    A, b, V, s, z = (t.numpy() for t in (A, b, V, s, z))
+    assert np.array_equal(A, A.T)
+    ev = np.linalg.eigvalsh(A)
+    assert abs(ev.max() / ev.min() - 1e4) / 1e4 < 1e-8
+    U = np.linalg.qr(np.random.default_rng(1).standard_normal((2 * n, n)))[0]
+    X = (U * s[None, :]) @ V.T
+    y = U @ z
+    assert np.allclose(X.T @ X, A, rtol=0, atol=1e-14)
+    assert np.allclose(X.T @ y, b, rtol=0, atol=1e-13)
+    theta = V @ (z / s[:, None])
+    assert np.linalg.norm(A @ theta - b) <= 1e-11 * np.linalg.norm(b) * 1e4

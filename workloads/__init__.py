@@ -19,6 +19,8 @@ stand in for those:
 * ``make_serving_trace``  -- Poisson arrival times with per-request (n, kappa,
                          nrhs) drawn as described in each docstring.
 * ``make_spd_device``     -- make_spd's system built with torch on a device.
+* ``make_gram_device``    -- the Gram system A = X^T X, b = X^T y of a design
+                         X = U diag(sigma) V^T, sigma log-uniform, on a device.
 
 Draw order inside one generator is fixed (Q, then lambda, then B) so that a
 seed always yields the same system.
@@ -37,6 +39,8 @@ __all__ = [
     "make_harmonic_batch",
     "make_serving_trace",
     "make_spd_device",
+    "make_gram_device",
+    "gram_spectrum",
     "ServingRequest",
 ]
 
@@ -189,3 +193,47 @@ def make_spd_device(n: int, kappa: float, nrhs: int = 1, seed: int = 0, device="
     if return_factors:
         return A.contiguous(), B.contiguous(), Q, lam
     return A.contiguous(), B.contiguous()
+
+
+def gram_spectrum(n: int, sigma_lo: float = 1e-3, seed: int = 0) -> tuple[np.ndarray, np.ndarray, np.random.Generator]:
+    """The host draws of ``make_gram_device`` in its order: sigma (n, log-uniform
+    in [sigma_lo, 1], ends pinned), z = U^T y (n x 1, standard normal); returns
+    (sigma, z, rng) with rng positioned for the Gaussian matrix of V."""
+    rng = np.random.default_rng(seed)
+    sigma = np.exp(rng.uniform(np.log(sigma_lo), 0.0, size=n))
+    if n >= 2:
+        sigma[0] = sigma_lo
+        sigma[1] = 1.0
+    z = rng.standard_normal((n, 1))
+    return sigma, z, rng
+
+
+def make_gram_device(n: int, sigma_lo: float = 1e-3, seed: int = 0, device="cuda", return_factors: bool = False):
+    """The least-squares Gram system of an m x n design X = U diag(sigma) V^T
+    (m >= n, U with orthonormal columns and V Haar), sigma log-uniform in
+    [sigma_lo, 1] with both ends pinned, built on a torch device in FP64:
+
+        A = X^T X = V diag(sigma^2) V^T      (cond(A) = sigma_lo^-2 exactly)
+        b = X^T y = V diag(sigma) (U^T y),   y ~ N(0, 1)^m.
+
+    For U with orthonormal columns drawn independently of y, z = U^T y is
+    N(0, 1)^n, so b = V (sigma * z) is drawn directly (X itself is never
+    formed; its m only fixes that z is standard normal).  The exact solution
+    is theta* = V (z / sigma).  Draw order: sigma, z, the Gaussian matrix of V
+    (``gram_spectrum`` gives the first two without the matrix).
+    Returns (A, b) as device tensors (b: n x 1), or (A, b, V, sigma, z) with
+    ``return_factors``."""
+    import torch
+
+    sigma, z, rng = gram_spectrum(n, sigma_lo, seed)
+    Zg = torch.from_numpy(rng.standard_normal((n, n)))
+    V, R = torch.linalg.qr(Zg.to(device))
+    V = V * torch.sign(torch.diagonal(R))[None, :]
+    s = torch.from_numpy(sigma).to(device)
+    A = (V * (s * s)[None, :]) @ V.T
+    A = 0.5 * (A + A.T)
+    zt = torch.from_numpy(z).to(device)
+    b = V @ (s[:, None] * zt)
+    if return_factors:
+        return A.contiguous(), b.contiguous(), V, s, zt
+    return A.contiguous(), b.contiguous()
