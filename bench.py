@@ -334,7 +334,8 @@ def run_gram(a):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     n = a.gram_n
-    A, B, V, sg, z = make_gram_device(n, GRAM_SIGMA_LO, seed=GRAM_SEED + rank, device=dev, return_factors=True)
+    A, B, V, sg, z = make_gram_device(n, GRAM_SIGMA_LO, seed=GRAM_SEED + rank, device=dev, return_factors=True,
+                                      qr_on_host=a.gram_qr_host)
     tstar = V @ (z / sg[:, None])
     del V
     out = torch.empty_like(B)
@@ -534,7 +535,7 @@ def dense_variant(a, dev, stream, flush):
            "roofline": {"bound": "tensor", "kernel": "k_gemm_tc2", "achieved": ach, "peak": sus, "unit": "TFLOP/s",
                         "frac": ach / sus, "executed": exe, "frac_executed": exe / sus,
                         "peak_kind": f"bf16 dense sustained ({pk_kind}); achieved counts 2 n^3 per product",
-                        "traffic": recorded_traffic("traffic_k_gemm_tc2_bench_n4096.md"),
+                        "traffic": recorded_traffic("traffic_k_gemm_tc2_dense_n4096.md"),
                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                         "avg_launch_ms": tc_ms / max(tc_l, 1)}}
     if not a.no_fp64:
@@ -705,7 +706,7 @@ def run_ours(a):
     executed = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     # the capture's workload: the default single system (n = 4096, order 8, 4 RHS)
     default_cfg = (a.n, a.kappa, a.nrhs, a.order, a.couple, a.gemm_cluster, a.pow_bf16) == (4096, 1e4, 4, 8, 1.0, 0, 2)
-    traffic = recorded_traffic("traffic_k_gemm_tc2_bench_n4096.md") if default_cfg else None
+    traffic = recorded_traffic("traffic_k_gemm_tc2_dense_n4096.md") if default_cfg else None
     sus = pk["bf16_tflops_sustained"]
     roof = {"bound": "tensor",
             "kernel": "k_gemm_tc2 / k_gemm_tc (tcgen05 bf16 / bf16x3 products with fused NS epilogue; "
@@ -824,7 +825,7 @@ def run_batched(a):
     outs = [torch.empty_like(b) for b in Bs]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     bt = nsgb.Batch([p.n for p in probs], [1] * len(probs), order=a.order, stream=stream, profile=1,
-                    couple_frob=a.couple)
+                    couple_frob=a.couple, batch_fused=a.batch_fused)
     for _ in range(max(3, a.warmup)):
         _, status, st = bt.solve(As, Bs, iters=a.iters, tol=1e-10, outs=outs)
     sampler = ClockSampler(local)
@@ -832,7 +833,7 @@ def run_batched(a):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ms, conv, gflops, gms, gbytes = [], [], 0.0, 0.0, 0.0
+    ms, conv, gflops, gms, gbytes, fused_ms, useful = [], [], 0.0, 0.0, 0.0, 0.0, 0.0
     for _ in range(a.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -845,6 +846,8 @@ def run_batched(a):
         gflops += st.gemm_flops
         gms += st.gemm_ms
         gbytes += st.gemm_bytes
+        fused_ms += st.fused_ms
+        useful += st.useful_flops
     clocks = sampler.stop()
     import oracle as O
     worst = 0.0
@@ -864,6 +867,26 @@ def run_batched(a):
     if rank != 0:
         bt.close()
         return
+    if st.fused:
+        # the fused launch solves every system whole: tensor-core products,
+        # row kernels and the controller in one kernel; its time is the bound
+        f_ach = useful / (fused_ms / 1e3) / 1e12 if fused_ms > 0 else None
+        f_exe = gflops / (fused_ms / 1e3) / 1e12 if fused_ms > 0 else None
+        roof = {"bound": "tensor", "kernel": "k_bsolve (fused small-system solve, one CTA per system)",
+                "achieved": f_ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "frac": f_ach / pk["bf16_tflops_sustained"] if f_ach else None,
+                "executed": f_exe, "traffic": None,
+                "note": "achieved: the systems' products x 2 n^3 over the whole fused launch (products, "
+                        "Richardson sweeps, preparation and control of every system); executed counts bf16x3 "
+                        f"as 3 passes; {pk_kind} sustained bf16 peak"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_gbs / pk["hbm_gbs"] if hbm_gbs else None, "traffic": None,
+                "note": "list-driven product launches: algorithmic bytes (operands once, C term, f32 and "
+                        "bf16 outputs) / their event time; tiles of K <= 256 have ~30 flop/B, below the "
+                        f"bf16 ridge, so HBM bounds them ({pk_kind} copy peak)",
+                "tensor_tflops": ach, "tensor_frac_of_sustained": ach / pk["bf16_tflops_sustained"] if ach
+                else None}
     print(json.dumps({
         "metric": METRIC + " (batched harmonic-regressor systems)", "value": value, "unit": UNIT,
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
@@ -875,14 +898,8 @@ def run_batched(a):
         "not_converged_per_step": a.count - conv_all / a.steps,
         "worst_verified_rel_res_of_converged": worst, "passes": st.passes,
         "gemm_launches_per_step": st.gemm_launches, "kernel_launches_per_step": st.kernel_launches,
-        "gpu_launches": int(st.kernel_launches) * a.steps,
-        "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": hbm_gbs / pk["hbm_gbs"] if hbm_gbs else None, "traffic": None,
-                     "note": "list-driven product launches: algorithmic bytes (operands once, C term, f32 and "
-                             "bf16 outputs) / their event time; tiles of K <= 256 have ~30 flop/B, below the "
-                             f"bf16 ridge, so HBM bounds them ({pk_kind} copy peak)",
-                     "tensor_tflops": ach, "tensor_frac_of_sustained": ach / pk["bf16_tflops_sustained"] if ach
-                     else None},
+        "gpu_launches": int(st.kernel_launches) * a.steps, "fused": int(st.fused),
+        "host_syncs_per_step": 1 if st.fused else int(st.passes), "roofline": roof,
         "useful_flops_per_product_level": st.useful_flops_per_product, "clocks": clocks}), flush=True)
     bt.close()
 
@@ -1236,9 +1253,13 @@ def main():
                          "n = 4096 dense system; batched: many harmonic systems; serving: continuous batching of a "
                          "Poisson request trace")
     ap.add_argument("--gram-n", type=int, default=16384, help="gram workload: system size")
+    ap.add_argument("--gram-qr-host", action="store_true",
+                    help="gram workload: draw the orthogonal factor with a host QR (e.g. under a profiler)")
     ap.add_argument("--ref-rows", type=int, default=512,
                     help="gram workload: rows of the panel the oracle sample multiplies")
     ap.add_argument("--count", type=int, default=2048)
+    ap.add_argument("--batch-fused", type=int, default=1, choices=(0, 1),
+                    help="batched workload: 1 one fused launch (systems of n <= 256), 0 pass by pass")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--pool", type=int, default=256)

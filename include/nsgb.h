@@ -126,6 +126,11 @@ typedef struct ns_options {
                           pass, in their own launch (their error reaches G_{k+1} only through
                           X P, quadratic in F_k); pow_mode 0 only.  2 (default of
                           ns_default_options): 1 where n >= 4096, else 0 */
+  int batch_fused;      /* batched solves (ns_batch_solve): 1 (default of ns_default_options) runs
+                          a batch whose systems all have n <= 256 as one persistent launch, one
+                          CTA per system solving it whole (same arithmetic and controller as the
+                          pass-by-pass path, so the same results); 0 always runs pass by pass
+                          (one launch per product level and one host decision per pass) */
 } ns_options;
 
 #define NS_MAX_HIST 256
@@ -250,6 +255,10 @@ typedef struct ns_batch_stats {
   double wall_ms;
   double gemm_bytes;                /* algorithmic HBM bytes of the products: operands once
                                        (hi, or hi and lo), C term, outputs */
+  int fused;                        /* 1: the batch ran as one fused launch (opt.batch_fused) */
+  int fused_pad;
+  double fused_ms;                  /* duration of that launch (opt.profile = 1), else 0 */
+  double useful_flops;              /* fused launch: sum over systems of their products x 2 n^3 */
 } ns_batch_stats;
 
 /* Create a batch of `count` systems; n[i] in [1, 16384], nrhs[i] in [1, 1024].

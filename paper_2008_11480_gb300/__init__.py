@@ -71,6 +71,7 @@ class ns_options(ctypes.Structure):
         ("fp64_slices", ctypes.c_int),
         ("fp64_slices_early", ctypes.c_int),
         ("pow_bf16", ctypes.c_int),
+        ("batch_fused", ctypes.c_int),
     ]
 
 
@@ -120,6 +121,10 @@ class ns_batch_stats(ctypes.Structure):
         ("useful_flops_per_product", ctypes.c_double),
         ("wall_ms", ctypes.c_double),
         ("gemm_bytes", ctypes.c_double),
+        ("fused", ctypes.c_int),
+        ("fused_pad", ctypes.c_int),
+        ("fused_ms", ctypes.c_double),
+        ("useful_flops", ctypes.c_double),
     ]
 
 

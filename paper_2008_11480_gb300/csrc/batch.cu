@@ -17,6 +17,8 @@
 // its reductions run in a fixed order inside its own blocks, so its result is
 // bitwise the same whether it is solved alone or together with any others.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -154,6 +156,8 @@ struct ns_batch {
   std::vector<InstState> st;
   ns_batch_stats* stats = nullptr;
   double wait_ms = 0.0;  // host time blocked in the per-pass stream synchronisation
+  FusedOut* dfout = nullptr;  // fused launch: per-slot outcome
+  int* dnext = nullptr;       // fused launch: work counter
   int fixed_count = 0;  // systems of a fixed batch (slots 0 .. fixed_count - 1)
   int max_pre = 0;      // extra Richardson-only sweeps per pass (fixed batches: fewer syncs;
                         // the server keeps ticks short for latency)
@@ -793,6 +797,104 @@ ns_status pass(ns_batch* b, const std::vector<int>& act) {
   return NS_OK;
 }
 
+// A fixed batch whose systems all fit one CTA: one persistent launch solves
+// every system whole (batch_fused.cu), largest first; one synchronisation.
+ns_status fused_solve(ns_batch* b, int count, int iters, double tol, ns_batch_stats* stats) {
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+  const int* dl = static_cast<const int*>(stage(b, order.data(), order.size() * sizeof(int), b->stream));
+  if (!dl) return bfail(b, NS_ERR_OOM, "staging area exhausted");
+  B_CK(cudaMemsetAsync(b->dnext, 0, sizeof(int), b->stream));
+  FusedParams p;
+  memset(&p, 0, sizeof(p));
+  p.prob = b->dprob;
+  p.inst = b->dinst;
+  p.list = dl;
+  p.count = count;
+  p.next = b->dnext;
+  p.out = b->dfout;
+  p.ntypes = b->ntypes;
+  p.levels = b->levels;
+  p.precision = b->opt.precision;
+  p.g0_mode = b->opt.g0_mode;
+  p.ns_stop = b->opt.ns_stop;
+  p.max_sweeps = b->opt.max_sweeps;
+  p.max_pre = b->max_pre;
+  p.iters = iters;
+  p.ns_stop_frob = b->opt.ns_stop_frob;
+  p.couple_frob = b->opt.couple_frob;
+  p.tol = tol;
+  p.timeout_ns = static_cast<unsigned long long>(b->opt.timeout_s * 1e9);
+  p.err = b->derr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (b->opt.profile) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->stream);
+  }
+  B_CK(launch_fused_solve(p, b->num_sms, b->stream));
+  if (b->opt.profile) cudaEventRecord(e1, b->stream);
+  const size_t off = rup(b->stage_used, 256);
+  const size_t bytes = sizeof(FusedOut) * static_cast<size_t>(count);
+  if (off + bytes + 64 > b->stage_cap) return bfail(b, NS_ERR_OOM, "staging area exhausted");
+  FusedOut* hout = reinterpret_cast<FusedOut*>(b->hstage + off);
+  int* herr = reinterpret_cast<int*>(b->hstage + off + bytes);
+  B_CK(cudaMemcpyAsync(hout, b->dfout, bytes, cudaMemcpyDeviceToHost, b->stream));
+  B_CK(cudaMemcpyAsync(herr, b->derr, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  B_CK(cudaStreamSynchronize(b->stream));
+  b->stage_used = 0;
+  float ms = 0.f;
+  if (b->opt.profile) {
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (*herr != DEV_OK) {
+    cudaMemsetAsync(b->derr, 0, sizeof(int), b->stream);
+    cudaStreamSynchronize(b->stream);
+    return bfail(b, NS_ERR_TIMEOUT, "a bounded device-side wait ran out (fused small-system solve)");
+  }
+  int passes = 0;
+  double useful = 0.0, executed = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const FusedOut& o = hout[i];
+    InstState& st = b->st[i];
+    st = InstState();
+    st.finished = true;
+    st.status = o.status;
+    st.converged = o.converged != 0;
+    st.done = o.done;
+    st.sweeps = o.sweeps;
+    st.rollbacks = o.rollbacks;
+    st.rel_res = o.rel_res;
+    passes = std::max(passes, o.passes);
+    const double f = 2.0 * b->n[i] * static_cast<double>(b->n[i]) * b->n[i];
+    useful += f * (o.prods1 + o.prods3);
+    executed += f * (o.prods1 + 3.0 * o.prods3);
+  }
+  if (const char* path = std::getenv("NSGB_FUSED_TRACE")) {
+    // per-system record of the fused launch, for profiling: n, outcome, steps,
+    // sweeps, passes, SM cycles and SM
+    if (FILE* f = std::fopen(path, "w")) {
+      std::fprintf(f, "slot,n,status,ns_iters,sweeps,passes,cycles,sm\n");
+      for (int i = 0; i < count; ++i)
+        std::fprintf(f, "%d,%d,%d,%d,%d,%d,%lld,%d\n", i, b->n[i], hout[i].status, hout[i].done, hout[i].sweeps,
+                     hout[i].passes, hout[i].cycles, hout[i].sm);
+      std::fclose(f);
+    }
+  }
+  if (stats) {
+    stats->passes = passes;
+    stats->kernel_launches = 1;
+    stats->gemm_flops = executed;
+    stats->useful_flops = useful;
+    stats->fused = 1;
+    stats->fused_ms = ms;
+  }
+  return NS_OK;
+}
+
 // Options the batched path supports, checked for both the batch and the server.
 ns_status check_opts(ns_options* o, const ns_options* opt, int order) {
   if (opt)
@@ -822,6 +924,7 @@ ns_status alloc_batch(ns_batch* b, int cap, int max_nrhs, size_t arena_bytes) {
   const size_t o_inst = take(sizeof(BInst) * static_cast<size_t>(cap));
   const size_t o_scal = take(sizeof(double) * static_cast<size_t>(cap) * b->scal_stride);
   const size_t o_err = take(64);
+  const size_t o_fout = take(sizeof(FusedOut) * static_cast<size_t>(cap) + 64);
   const size_t o_stage = take(b->stage_cap);
   const size_t o_arena = take(arena_bytes);
   if (cudaMalloc(&b->dmem, total) != cudaSuccess) {
@@ -839,6 +942,8 @@ ns_status alloc_batch(ns_batch* b, int cap, int max_nrhs, size_t arena_bytes) {
   b->dinst = reinterpret_cast<BInst*>(base + o_inst);
   b->dscal = reinterpret_cast<double*>(base + o_scal);
   b->derr = reinterpret_cast<int*>(base + o_err);
+  b->dnext = b->derr + 4;
+  b->dfout = reinterpret_cast<FusedOut*>(base + o_fout);
   b->dstage = base + o_stage;
   b->abase = base + o_arena;
   b->asize = arena_bytes;
@@ -1006,9 +1111,16 @@ ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* cons
     b->hinst[i].Th = Theta[i];
   }
   B_CK(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, b->stream));
-  B_TRY(prep_slots(b, all, std::vector<int>(count, iters), std::vector<double>(count, tol)));
+  bool fuse = b->opt.batch_fused != 0;
+  for (int i = 0; i < count && fuse; ++i) fuse = b->n[i] <= kFusedMaxN;
   int passes = 0;
-  for (;;) {
+  if (fuse) {
+    B_TRY(fused_solve(b, count, iters, tol, stats));
+    passes = stats ? stats->passes : 0;
+  } else {
+    B_TRY(prep_slots(b, all, std::vector<int>(count, iters), std::vector<double>(count, tol)));
+  }
+  for (; !fuse;) {
     std::vector<int> act;
     for (int i = 0; i < count; ++i)
       if (!b->st[i].finished) act.push_back(i);

@@ -49,4 +49,35 @@ cudaError_t launch_brsq(const BInst* insts, const int* list, int ninst, cudaStre
 cudaError_t launch_bupdate(const BInst* insts, const BItem* items, int nitems, cudaStream_t s);
 cudaError_t launch_bfrob(const BInst* insts, const int* list, int ninst, cudaStream_t s);
 
+// ---- fused small-system solve (batch_fused.cu): one CTA runs the whole solve
+// of one system of n <= kFusedMaxN (preparation, G0, every Newton-Schulz step
+// on the tensor cores, Richardson sweeps, the precision controller) and then
+// takes the next system of `list` (an atomic counter, largest systems first).
+constexpr int kFusedMaxN = 256;
+
+// Outcome of one system (the fields of the host controller's record).
+struct FusedOut {
+  int status, done, sweeps, rollbacks, converged, passes;
+  int prods1, prods3;  // products run in bf16 (one pass) and in bf16x3
+  double rel_res;
+  long long cycles;    // SM clock cycles the CTA spent on this system
+  int sm, pad;         // the SM that solved it
+};
+
+struct FusedParams {
+  const TcProblem* prob;  // problem table (ntypes x 2 G buffers x 2 precisions per slot)
+  const BInst* inst;
+  const int* list;        // slots to solve, in the order they are taken
+  int count;
+  int* next;              // work counter (zero on entry)
+  FusedOut* out;          // per slot
+  int ntypes, levels;
+  int precision;          // NS_AUTO, NS_BF16 or NS_BF16X3
+  int g0_mode, ns_stop, max_sweeps, max_pre, iters;
+  double ns_stop_frob, couple_frob, tol;
+  unsigned long long timeout_ns;
+  int* err;
+};
+cudaError_t launch_fused_solve(const FusedParams& p, int num_sms, cudaStream_t s);
+
 }  // namespace nsgb

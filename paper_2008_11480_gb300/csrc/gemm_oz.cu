@@ -79,13 +79,20 @@ __device__ __forceinline__ void spin_ns(uint64_t ns) {
 }
 
 // Work item w: level index (into p.lev_d), pair-tile row (256-row units) and
-// tile column (256-column units).
+// tile column (256-column units).  Within a level the tiles run in bands of
+// kBand tile rows, column by column inside a band, so that the items in
+// flight at once (one per CTA pair) share both their L row panels and their
+// R column panels in L2 (row-major order would share only the L panels).
+constexpr int kBand = 8;
 __device__ __forceinline__ void oz_item(const OzParams& p, int w, int& lev, int& mt2, int& nt) {
   const int per = p.tiles_m2 * p.tiles_n;
   lev = w / per;
   const int t = w - lev * per;
-  mt2 = t / p.tiles_n;
-  nt = t - mt2 * p.tiles_n;
+  const int band = t / (kBand * p.tiles_n);
+  const int rows = min(kBand, p.tiles_m2 - band * kBand);
+  const int idx = t - band * kBand * p.tiles_n;
+  mt2 = band * kBand + idx % rows;
+  nt = idx / rows;
 }
 
 // Slice pairs of level d: t = t_lo .. t_hi, u = d - t (1 <= t, u <= s).

@@ -1521,6 +1521,7 @@ void ns_default_options(ns_options* o) {
   o->accel_richardson = 0;
   o->g0_order = 0;
   o->pow_bf16 = 2;
+  o->batch_fused = 1;
 }
 
 const char* ns_status_string(ns_status s) {

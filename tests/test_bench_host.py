@@ -33,7 +33,7 @@ def test_recorded_traffic_follows_the_sources(tmp_path, monkeypatch):
 
 
 def test_repository_record_is_well_formed():
-    txt = open(os.path.join(ROOT, "profiles", "traffic_k_gemm_tc2_bench_n4096.md")).read()
+    txt = open(os.path.join(ROOT, "profiles", "traffic_k_gemm_tc2_dense_n4096.md")).read()
     assert "traffic_bytes_per_launch:" in txt and "kernel_sources_sha256:" in txt
     for f in txt.split("kernel_sources:")[1].splitlines()[0].split():
         assert os.path.exists(os.path.join(ROOT, f)), f

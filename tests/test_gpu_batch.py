@@ -120,3 +120,38 @@ def test_batch_delayed_coupling():
         with nsgb.Batch([p.n], [p.nrhs], order=4, couple_frob=1.0) as one:
             alone, _, _ = one.solve([tens(p.A)], [tens(p.B)], iters=60, tol=1e-10)
         assert torch.equal(alone[0], outs[k])
+
+
+def _solve_batch(probs, order, **opt):
+    with nsgb.Batch([p.n for p in probs], [p.nrhs for p in probs], order=order, profile=1, **opt) as bt:
+        outs, status, st = bt.solve([tens(p.A) for p in probs], [tens(p.B) for p in probs], iters=60, tol=1e-10)
+        res = [bt.result(i) for i in range(len(probs))]
+    return outs, status, st, res
+
+
+@pytest.mark.parametrize("order", [4, 8, 3])
+def test_fused_matches_pass_by_pass_bitwise(order):
+    """The fused small-system solve (one persistent launch, one CTA per system,
+    device-side controller) against the pass-by-pass path (a launch per product
+    level, host decisions): the same theta bit for bit, the same outcome,
+    Newton-Schulz steps and sweeps, for systems that switch precision, roll
+    back, take more than one chunk of right-hand sides (nrhs > 8), escalate
+    to the FP64 residual (kappa 1e6) or fail (ill-conditioned harmonic Gram
+    systems)."""
+    rng = np.random.default_rng(70 + order)
+    probs = [make_spd(n, k, nrhs=r, seed=200 + i) for i, (n, k, r) in
+             enumerate([(16, 30.0, 1), (64, 1e3, 3), (100, 1e4, 12), (129, 1e5, 2), (200, 1e6, 1), (256, 1e4, 9),
+                        (33, 1e2, 17)])]
+    probs += [make_harmonic(int(m), rng=rng) for m in rng.integers(8, 129, size=10)]
+    fo, fs, fst, fres = _solve_batch(probs, order)
+    lo, ls, lst, lres = _solve_batch(probs, order, batch_fused=0)
+    assert fst.fused == 1 and lst.fused == 0
+    assert fst.kernel_launches == 1 and lst.kernel_launches > 10
+    assert fs == ls
+    for k, (a, b, ra, rb) in enumerate(zip(fo, lo, fres, lres)):
+        assert ra == rb, (k, ra, rb)
+        assert torch.equal(a, b), f"system {k} (n = {probs[k].n}) differs between the fused and pass-by-pass paths"
+    for p, th, r in zip(probs, fo, fres):
+        if r["status"] == nsgb.NS_OK:
+            assert float(np.max(O.rel_residual(p.A, th.cpu().numpy(), p.B))) <= 1e-10
+    assert fst.converged >= 7

@@ -208,7 +208,8 @@ def gram_spectrum(n: int, sigma_lo: float = 1e-3, seed: int = 0) -> tuple[np.nda
     return sigma, z, rng
 
 
-def make_gram_device(n: int, sigma_lo: float = 1e-3, seed: int = 0, device="cuda", return_factors: bool = False):
+def make_gram_device(n: int, sigma_lo: float = 1e-3, seed: int = 0, device="cuda", return_factors: bool = False,
+                     qr_on_host: bool = False):
     """The least-squares Gram system of an m x n design X = U diag(sigma) V^T
     (m >= n, U with orthonormal columns and V Haar), sigma log-uniform in
     [sigma_lo, 1] with both ends pinned, built on a torch device in FP64:
@@ -222,12 +223,16 @@ def make_gram_device(n: int, sigma_lo: float = 1e-3, seed: int = 0, device="cuda
     is theta* = V (z / sigma).  Draw order: sigma, z, the Gaussian matrix of V
     (``gram_spectrum`` gives the first two without the matrix).
     Returns (A, b) as device tensors (b: n x 1), or (A, b, V, sigma, z) with
-    ``return_factors``."""
+    ``return_factors``.  ``qr_on_host`` does the QR with torch on the CPU."""
     import torch
 
     sigma, z, rng = gram_spectrum(n, sigma_lo, seed)
     Zg = torch.from_numpy(rng.standard_normal((n, n)))
-    V, R = torch.linalg.qr(Zg.to(device))
+    if qr_on_host:
+        V, R = torch.linalg.qr(Zg)
+        V, R = V.to(device), R.to(device)
+    else:
+        V, R = torch.linalg.qr(Zg.to(device))
     V = V * torch.sign(torch.diagonal(R))[None, :]
     s = torch.from_numpy(sigma).to(device)
     A = (V * (s * s)[None, :]) @ V.T
