@@ -55,6 +55,9 @@ typedef enum ns_status {
 
 typedef enum ns_precision {
   NS_FP64 = 0,   /* every product in FP64 on the CUDA cores (plain path) */
+  NS_TF32 = 1,   /* one pass of TF32 operands (binary32 rounded to nearest, ties away, to
+                    10 stored significand bits), f32 accumulation (tcgen05 kind::tf32, CTA
+                    pairs); between bf16 (8 bits) and bf16x3 (16) at 2x the bf16 cost */
   NS_BF16 = 2,   /* products hi*hi of bf16 operands, f32 accumulation (tcgen05) */
   NS_BF16X3 = 3, /* split bf16: hi*hi + hi*lo + lo*hi into one f32 accumulator */
   NS_BF16X6 = 4, /* three-part split hi, lo = bf16(x - hi), lo2 = bf16(x - hi - lo):
@@ -126,6 +129,9 @@ typedef struct ns_options {
                           pass, in their own launch (their error reaches G_{k+1} only through
                           X P, quadratic in F_k); pow_mode 0 only.  2 (default of
                           ns_default_options): 1 where n >= 4096, else 0 */
+  int tf32_rung;        /* NS_AUTO: 1 puts TF32 products between bf16 and bf16x3 (bf16 until its
+                          contraction worsens, then TF32 until TF32's does, then bf16x3); 0
+                          (default) goes from bf16 straight to bf16x3 */
   int batch_fused;      /* batched solves (ns_batch_solve): 1 (default of ns_default_options) runs
                           a batch whose systems all have n <= 256 as one persistent launch, one
                           CTA per system solving it whole (same arithmetic and controller as the
@@ -408,6 +414,19 @@ ns_status ns_k_split3(const void* X, int x_dtype, int64_t rows, int64_t cols, in
 ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl, const void* const* R,
                            int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma, float* D32,
                            int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, void* stream);
+
+/* TF32 tensor-core product (tcgen05 kind::tf32 on CTA pairs) with the Newton-Schulz
+ * epilogue: D = s * RN_tf32(L) RN_tf32(R) + beta C + gamma I, L (M x K, ldl) and R
+ * (K x N, ldr) f32 on the device, rounded to TF32 (nearest, ties away from zero) into
+ * scratch taken from the stream-ordered allocator (L row-major, R transposed: both
+ * operands K-major), f32 accumulation.  Outputs (each may be NULL): D32 (ldd32), the
+ * TF32 forms of D row-major (Dt) and transposed (DtT, column j at DtT + j ldt; ldt >=
+ * max(M, N)), frob_out a device double receiving sum(D^2).  Pointers 16-byte aligned,
+ * f32 leading dimensions multiples of 4; `stream` is synchronised.  Errors:
+ * NS_ERR_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_TIMEOUT. */
+ns_status ns_k_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* L, int64_t ldl, const float* R, int64_t ldr,
+                         float s, const float* C, int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32,
+                         float* Dt, float* DtT, int64_t ldt, double* frob_out, void* stream);
 
 /* FP64-accurate product on the bf16 tensor cores by an Ozaki-style error-free splitting
  * (Ozaki, Ogita, Rump, Oishi, Numer. Algorithms 59, 2012), with signed digits:

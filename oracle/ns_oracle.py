@@ -632,6 +632,25 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
+def round_tf32(x: np.ndarray) -> np.ndarray:
+    """Round binary32 values to TF32 (binary32 with 10 stored significand bits,
+    the low 13 bits zero): round to nearest, ties away from zero, written out
+    on the sign-magnitude bit pattern -- add half of the dropped range
+    (0x1000) to the magnitude and clear the low 13 bits.  A magnitude that
+    carries past the largest finite value becomes infinity.  NaN stays NaN.
+    Input is first rounded to binary32; the result is returned as float64."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    sign = u & np.uint64(0x80000000)
+    mag = u & np.uint64(0x7FFFFFFF)
+    r = ((mag + np.uint64(0x1000)) & np.uint64(0xFFFFE000)) | sign
+    out = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(f)
+    if np.any(nan):
+        out = np.where(nan, np.nan, out)
+    return out
+
+
 def split_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """Two-term bfloat16 split of binary32 values: x32 = RN32(x),
     hi = RNbf16(x32), lo = RNbf16(x32 - hi) (the difference is exact in
@@ -670,11 +689,14 @@ def _split_parts(L: np.ndarray, R: np.ndarray, f=lambda v: v) -> dict:
 
 def split_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
     """Exact (float64) value of the split product the tensor cores form:
+    tf32:   RNtf32(L) RNtf32(R)   (one pass; operands rounded by round_tf32)
     bf16:   Lhi Rhi
     bf16x3: Lhi Rhi + Lhi Rlo + Llo Rhi   (the lo*lo term is dropped)
     bf16x6: those and Lhi Rlo2 + Llo Rlo + Llo2 Rhi.
     L and R are first rounded to binary32 and split with ``split3_bf16``
     (whose hi and lo are those of ``split_bf16``)."""
+    if precision == "tf32":
+        return round_tf32(round_f32(L)) @ round_tf32(round_f32(R))
     parts = _split_parts(L, R)
     out = np.zeros((L.shape[0], R.shape[1]))
     for a, b in SPLIT_PASSES[precision]:
@@ -684,6 +706,8 @@ def split_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
 
 def split_abs_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
     """sum_k |L_ik| |R_kj| over the same split terms (for error bounds)."""
+    if precision == "tf32":
+        return np.abs(round_tf32(round_f32(L))) @ np.abs(round_tf32(round_f32(R)))
     parts = _split_parts(L, R, np.abs)
     out = np.zeros((L.shape[0], R.shape[1]))
     for a, b in SPLIT_PASSES[precision]:

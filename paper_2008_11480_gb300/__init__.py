@@ -27,7 +27,7 @@ __all__ = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_inverse_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
-    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6", "ns_k_gemm_oz",
+    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6", "ns_k_gemm_oz", "ns_k_gemm_tf32", "NS_TF32",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
     "ns_batch_stats", "Batch",
 ]
@@ -35,7 +35,7 @@ __all__ = [
 NS_OK, NS_NOT_CONVERGED = 0, 1
 NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_DIVERGED = -1, -2, -3, -4
 NS_ERR_TIMEOUT, NS_ERR_NONFINITE, NS_ERR_UNSUPPORTED = -5, -6, -7
-NS_FP64, NS_BF16, NS_BF16X3, NS_BF16X6, NS_AUTO = 0, 2, 3, 4, 5
+NS_FP64, NS_TF32, NS_BF16, NS_BF16X3, NS_BF16X6, NS_AUTO = 0, 1, 2, 3, 4, 5
 NS_MAX_HIST = 256
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -71,6 +71,7 @@ class ns_options(ctypes.Structure):
         ("fp64_slices", ctypes.c_int),
         ("fp64_slices_early", ctypes.c_int),
         ("pow_bf16", ctypes.c_int),
+        ("tf32_rung", ctypes.c_int),
         ("batch_fused", ctypes.c_int),
     ]
 
@@ -201,6 +202,8 @@ def lib() -> ctypes.CDLL:
         "ns_k_split3": (_int, [_vp, _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
         "ns_k_gemm_oz": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
                                  ctypes.c_double, _vp, _i64, _int, _vp, _vp]),
+        "ns_k_gemm_tf32": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64, ctypes.c_float,
+                                   ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, _vp]),
         "ns_k_gemm_bf16x6": (_int, [_i64, _i64, _i64, ctypes.POINTER(_vp), _i64, ctypes.POINTER(_vp), _i64,
                                      ctypes.c_float, _vp, _i64, ctypes.c_float, ctypes.c_float, _vp, _i64,
                                      ctypes.POINTER(_vp), _i64, _vp, _vp]),
@@ -392,6 +395,16 @@ def ns_k_gemm_bf16x6(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float 
     r = lib().ns_k_gemm_bf16x6(M, N, K, Lp, ldl, Rp, ldr, s, _ptr(C, torch.float32), ldc, beta, gamma,
                                _ptr(D32, torch.float32), ldd32, Dp, ldd16, _ptr(frob_out), _stream_ptr(stream))
     _raise(r, "ns_k_gemm_bf16x6")
+
+
+def ns_k_gemm_tf32(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float = 1.0, C=None, ldc: int = 0,
+                   beta: float = 0.0, gamma: float = 0.0, D32=None, ldd32: int = 0, Dt=None, DtT=None, ldt: int = 0,
+                   frob_out=None, stream=None) -> None:
+    """TF32 tensor-core product with the Newton-Schulz epilogue (f32 tensors)."""
+    f = torch.float32
+    r = lib().ns_k_gemm_tf32(M, N, K, _ptr(L, f), ldl, _ptr(R, f), ldr, s, _ptr(C, f), ldc, beta, gamma,
+                             _ptr(D32, f), ldd32, _ptr(Dt, f), _ptr(DtT, f), ldt, _ptr(frob_out), _stream_ptr(stream))
+    _raise(r, "ns_k_gemm_tf32: " + lib().ns_last_error(None).decode())
 
 
 def ns_k_gemm_oz(M: int, N: int, K: int, L, ldl: int, R, ldr: int, s: float = 1.0, C=None, ldc: int = 0,

@@ -346,7 +346,7 @@ __device__ void wide_resid_x2(const BInst& I, int c0, uint8_t* scratch) {
 // task is one float4 step (k = 4 lane + 128 half < n & ~3) and a tail of at
 // most three elements: each warp runs kU tasks at once, all loads first, the
 // same operations per row as above.
-constexpr int kU = 4;
+constexpr int kU = 2;
 
 __device__ void wide_resid_x2_1(const BInst& I, uint8_t* scratch) {
   constexpr int NRW = 1;

@@ -62,14 +62,17 @@ constexpr int kPartBytes = 8192;  // one split part of a 32-deep K slice (L or R
 __host__ __device__ constexpr int term_l(int t) { return (t == 2 || t == 4) ? 1 : (t == 5 ? 2 : 0); }
 __host__ __device__ constexpr int term_r(int t) { return (t == 1 || t == 4) ? 1 : (t == 3 ? 2 : 0); }
 
+// NP = 4: one TF32 pass; per CTA a stage holds L 128 rows x 32 K and 128 of
+// the tile's R columns x 32 K, both as f32 words K-major (the transposed TF32
+// form of R), 128-byte swizzle: 16 + 16 KiB.
 template <int NP>
 struct PairCfg {
   static constexpr int kBK = NP == 1 ? 64 : 32;          // K per stage
-  static constexpr int kABytes = NP == 1 ? 16384 : NP * kPartBytes;
+  static constexpr int kABytes = (NP == 1 || NP == 4) ? 16384 : NP * kPartBytes;
   static constexpr int kBBytes = kABytes;                 // 128 of the tile's R columns
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages = (196 * 1024) / kStageBytes > 6 ? 6 : (196 * 1024) / kStageBytes;
-  static constexpr int kTerms = NP == 1 ? 1 : (NP == 2 ? 3 : 6);
+  static constexpr int kTerms = (NP == 1 || NP == 4) ? 1 : (NP == 2 ? 3 : 6);
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
   static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
   constexpr int kStages = Cfg::kStages, kABytes = Cfg::kABytes, kBBytes = Cfg::kBBytes, kBK = Cfg::kBK;
   // host-side guarantees, checked once more before any barrier: list mode and
   // multi-pass one-split products are not supported by the pair kernel
-  if (p.gprob != nullptr || (NP == 1 && p.npass != 1)) {
+  if (p.gprob != nullptr || ((NP == 1 || NP == 4) && p.npass != 1)) {
     if (threadIdx.x == 0) atomicExch(p.err, DEV_TIMEOUT);
     return;
   }
@@ -189,7 +192,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
           const uint32_t bar = full0 + static_cast<uint32_t>(stage * 8);
           uint8_t* a = sA + stage * kABytes;
           uint8_t* b = sB + stage * kBBytes;
-          if (NP > 1) {
+          if (NP == 4) {
+            const int x = kb * kBK;
+            tma_load_2d_pair(a, &P.L[0], bar, x, m0);
+            tma_load_2d_pair(a + 8192, &P.L[0], bar, x, m0 + 64);
+            tma_load_2d_pair(b, &P.R[0], bar, x, nb);
+            if (half < 0) tma_load_2d_pair(b + 8192, &P.R[0], bar, x, nb + 64);
+          } else if (NP > 1) {
             const int x = kb * kBK;
 #pragma unroll
             for (int part = 0; part < NP; ++part) {
@@ -232,8 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ------------------------------------------------------------ MMA issuer (CTA 0)
-    constexpr uint32_t idesc_full = make_idesc_bf16(2 * kRows, kCols, 0, 1);
-    constexpr uint32_t idesc_half = make_idesc_bf16(2 * kRows, kCols / 2, 0, 1);
+    constexpr uint32_t idesc_full =
+        NP == 4 ? make_idesc_tf32(2 * kRows, kCols) : make_idesc_bf16(2 * kRows, kCols, 0, 1);
+    constexpr uint32_t idesc_half =
+        NP == 4 ? make_idesc_tf32(2 * kRows, kCols / 2) : make_idesc_bf16(2 * kRows, kCols / 2, 0, 1);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
@@ -261,7 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA + stage * kABytes);
         const uint32_t b_base = smem_u32(sB + stage * kBBytes);
-        if (NP > 1) {
+        if (NP == 4) {
+#pragma unroll
+          for (int k = 0; k < kBK / 8; ++k) {  // K = 8 per TF32 MMA (32 bytes)
+            const uint64_t ad = make_sdesc(a_base + 32u * k, 16u, 1024u);
+            const uint64_t bd = make_sdesc(b_base + 32u * k, 16u, 1024u);
+            tc_mma_tf32_pair(d_tmem, ad, bd, idesc, accumulate);
+            accumulate = 1;
+          }
+        } else if (NP > 1) {
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
 #pragma unroll
@@ -407,11 +426,12 @@ cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaStream_t s) {
-  if (p.gprob != nullptr || (parts == 1 && p.npass != 1)) return cudaErrorInvalidValue;
+  if (p.gprob != nullptr || ((parts == 1 || parts == 4) && p.npass != 1)) return cudaErrorInvalidValue;
   switch (parts) {
     case 1: return launch_pair<1>(p, num_sms, s);
     case 2: return launch_pair<2>(p, num_sms, s);
     case 3: return launch_pair<3>(p, num_sms, s);
+    case 4: return launch_pair<4>(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

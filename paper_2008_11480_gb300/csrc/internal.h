@@ -38,6 +38,9 @@ struct TcProblem {
   bf16* Dhi;
   bf16* Dlo;
   bf16* Dlo2;  // third split part of D (x6 products), may be null
+  float* Dt;   // TF32 forms of D (RN to 10 stored bits, ties away): row-major
+  float* DtT;  // and transposed (the K-major R operand of a TF32 product); may be null
+  int ldt;
   double* frob_partials;  // 4 values per tile (tiles_m * tiles_n * 4); the CTA-pair
                           // kernel writes 8 (two half-width slots of 4)
 };
@@ -65,12 +68,22 @@ struct TcParams {
   int* err;
 };
 
+// TF32 forms of an f32 matrix (rows x cols, ld): Y = RN_tf32(X) row-major and
+// YT = RN_tf32(X)^T (cols x rows, leading dimension ldt); either may be null.
+cudaError_t launch_tf32_pack(const float* X, int64_t ld, int rows, int cols, float* Y, float* YT, int64_t ldt,
+                             cudaStream_t s);
+// Encode a 2-D f32 tensor map (rows x cols, leading dimension ld elements):
+// 32-column (128-byte) x 64-row box, 128-byte swizzle (TF32 operands, K-major).
+bool encode_f32_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld);
+
 // Launch a grouped tcgen05 GEMM, one CTA per 128 x BN tile: BN in {64, 128,
 // 192, 256} output columns per tile.  x3 selects the split-product kernel (L/R
 // maps of roles 1/2 below; BN 64, 128 or 256; p.npass ignored); otherwise
 // p.npass passes over role-0 maps.
 cudaError_t launch_gemm_tc(const TcParams& p, int BN, bool x3, int num_sms, cudaStream_t s);
 // CTA-pair variant (cta_group::2): 256 x 256 output tiles, clusters of two
+// (parts 4: one TF32 pass, L[0] the row-major TF32 form of L and R[0] the
+// transposed TF32 form of R, both encode_f32_map maps)
 // CTAs along M, tile bookkeeping of BN = 256, CM = 2 (tc_items(M, N, 256, 2)
 // tiles, 8 partial sums per tc_tiles(M, N, 256) tile).  Single-problem-table
 // mode only (p.gprob == nullptr).  parts: 1 one bf16 pass (p.npass == 1);

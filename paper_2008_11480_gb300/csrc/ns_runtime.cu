@@ -41,6 +41,12 @@ struct MpMat {
   CUtensorMap l3_hi, l3_lo;      // split products, as the L operand
   CUtensorMap r3_hi, r3_lo;      // split products, as the R operand
   CUtensorMap l3_lo2, r3_lo2;    // third part, as the L / R operand of bf16x6 products
+  // TF32 forms (NS_TF32 products): row-major and transposed, RN to 10 stored
+  // bits; t_fresh: they hold the matrix's current value
+  float* t32 = nullptr;
+  float* t32T = nullptr;
+  CUtensorMap map_t, map_tT;
+  bool t_fresh = false;
 };
 
 struct GemmSpec {
@@ -343,11 +349,51 @@ void pick_tile(const ns_ctx* ctx, int nprob, int* bn_out, int* cm_out) {
   *cm_out = best_cm;
 }
 
+// TF32 forms of a split matrix, allocated on first use.
+ns_status ensure_tf32(ns_ctx* ctx, MpMat& m) {
+  if (m.t32 != nullptr) return NS_OK;
+  const size_t cnt = static_cast<size_t>(ctx->ld) * ctx->ld;
+  NS_TRY(alloc(ctx, &m.t32, cnt));
+  NS_TRY(alloc(ctx, &m.t32T, cnt));
+  if (!encode_f32_map(&m.map_t, m.t32, ctx->ld, ctx->ld, ctx->ld) ||
+      !encode_f32_map(&m.map_tT, m.t32T, ctx->ld, ctx->ld, ctx->ld))
+    return fail(ctx, NS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  m.t_fresh = false;
+  return NS_OK;
+}
+
+// The TF32 forms of an operand from its binary32 value (A: its first f32
+// limb, RN32(A); others: their f32 master) when a product of another
+// precision wrote it last.
+ns_status tf32_operand(ns_ctx* ctx, const MpMat& cm) {
+  MpMat& m = const_cast<MpMat&>(cm);
+  NS_TRY(ensure_tf32(ctx, m));
+  if (m.t_fresh) return NS_OK;
+  const float* src = &m == &ctx->A ? ctx->A1 : m.m32;
+  if (src == nullptr) return fail(ctx, NS_ERR_ARG, "TF32 operand without a binary32 value");
+  const int n = static_cast<int>(ctx->n);
+  NS_CK(launch_tf32_pack(src, ctx->ld, n, n, m.t32, m.t32T, ctx->ld, ctx->stream));
+  ctx->launches++;
+  m.t_fresh = true;
+  return NS_OK;
+}
+
 // One grouped tcgen05 launch of up to kTcMaxProblems products of n x n matrices.
 ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   const int n = static_cast<int>(ctx->n);
   int bn = 256, cm = 1;
   pick_tile(ctx, nspec, &bn, &cm);
+  const bool tf = prec == NS_TF32;
+  if (tf) {  // TF32 products run on CTA pairs (the last pair may cover rows past n)
+    bn = 256;
+    cm = -2;
+    for (int i = 0; i < nspec; ++i) {
+      NS_TRY(tf32_operand(ctx, *specs[i].L));
+      NS_TRY(tf32_operand(ctx, *specs[i].R));
+      NS_TRY(ensure_tf32(ctx, *specs[i].D));
+    }
+  }
+  for (int i = 0; i < nspec; ++i) specs[i].D->t_fresh = tf;
   const bool x6 = prec == NS_BF16X6;
   if (x6) {  // the three-part terms run on CTA pairs only
     bn = 256;
@@ -367,7 +413,13 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   for (int i = 0; i < nspec; ++i) {
     const GemmSpec& g = specs[i];
     TcProblem& P = p.prob[i];
-    if (x3 || x6) {
+    if (tf) {
+      P.L[0] = P.L[1] = g.L->map_t;
+      P.R[0] = P.R[1] = g.R->map_tT;
+      P.Dt = g.D->t32;
+      P.DtT = g.D->t32T;
+      P.ldt = static_cast<int>(ctx->ld);
+    } else if (x3 || x6) {
       P.L[0] = g.L->l3_hi;
       P.L[1] = g.L->l3_lo;
       P.R[0] = g.R->r3_hi;
@@ -420,7 +472,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   p.total_tiles = tile;
   EventPair* e = ev_begin(ctx, true);
   if (cm == -2)
-    NS_CK(launch_gemm_tc_pair(p, x6 ? 3 : (x3 ? 2 : 1), ctx->num_sms, ctx->stream));
+    NS_CK(launch_gemm_tc_pair(p, tf ? 4 : (x6 ? 3 : (x3 ? 2 : 1)), ctx->num_sms, ctx->stream));
   else
     NS_CK(launch_gemm_tc(p, bn, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
@@ -1167,20 +1219,24 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       if (!std::isfinite(frob)) return fail(ctx, NS_ERR_NONFINITE, "||F||_F is not finite");
       if (ctx->oz_now < oz_full && frob < 1.0) ctx->oz_now = oz_full;
       const double ratio = frob / prev_frob;
-      if (autop && prec == NS_BF16 && done >= 2 && frob < prev_frob && ratio > prev_ratio + 0.02) {
+      // the early, cheap precisions of the AUTO ladder: bf16, then (option
+      // tf32_rung) TF32; each hands over to the next when its contraction worsens
+      const bool early = prec == NS_BF16 || prec == NS_TF32;
+      const int next_prec = (prec == NS_BF16 && ctx->opt.tf32_rung) ? NS_TF32 : NS_BF16X3;
+      if (autop && early && done >= 2 && frob < prev_frob && ratio > prev_ratio + 0.02) {
         // the contraction of ||F||_F got worse: bf16 rounding noise is becoming
         // comparable to the error being removed.  Keep G_k, but F_k itself was
-        // formed in bf16 and carries that noise: form it again in bf16x3.
-        prec = NS_BF16X3;
+        // formed in bf16 and carries that noise: form it again in the next precision.
+        prec = next_prec;
         prev_ratio = INFINITY;
         goto recompute_F;
       }
-      if (autop && prec == NS_BF16 && done > 0 && frob >= prev_frob) {
+      if (autop && early && done > 0 && frob >= prev_frob) {
         // bf16 rounding has stopped the contraction: redo the last step in bf16x3
         S.cur ^= 1;
         if (comp) S.ccur ^= 1;
         done--;
-        prec = NS_BF16X3;
+        prec = next_prec;
         prev_frob = INFINITY;
         if (st) st->rollbacks++;
         goto recompute_F;
@@ -1197,7 +1253,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           prev_ratio = INFINITY;
           goto recompute_F;
         }
-        if (slice_handover && prec != NS_BF16 && done > 0) {
+        if (slice_handover && !early && done > 0) {
           S.cur ^= 1;  // G_{k-1}, the last G inside the contraction region
           done--;
           if (st) {
@@ -1222,7 +1278,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         }
         return fail(ctx, NS_ERR_DIVERGED, "Newton-Schulz diverged (||F||_F grew past sqrt(n))");
       }
-      if (ctx->opt.ns_stop && (!autop || prec != NS_BF16)) {
+      if (ctx->opt.ns_stop && (!autop || !early)) {
         bool stop = frob <= ctx->opt.ns_stop_frob;
         if (!stop && rich && frob < 1.0 && tol > 0 && last_rr > tol) {
           // rho(I - A G_k) <= ||F_k||_F < 1 bounds the Richardson contraction:
@@ -1547,9 +1603,14 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   else
     ns_default_options(&o);
   if (!order_ok(order, o.form)) return NS_ERR_ARG;
-  if (o.precision != NS_FP64 && o.precision != NS_BF16 && o.precision != NS_BF16X3 && o.precision != NS_BF16X6 &&
-      o.precision != NS_AUTO)
+  if (o.precision != NS_FP64 && o.precision != NS_TF32 && o.precision != NS_BF16 && o.precision != NS_BF16X3 &&
+      o.precision != NS_BF16X6 && o.precision != NS_AUTO)
     return NS_ERR_ARG;
+  if (o.tf32_rung != 0 && o.tf32_rung != 1) return NS_ERR_ARG;
+  // TF32 products write the TF32 forms their successors read; the composite
+  // loops and the elementwise sum of the nested order-45 chain are not built for them
+  const bool uses_tf32 = o.precision == NS_TF32 || (o.precision == NS_AUTO && o.tf32_rung);
+  if (uses_tf32 && (n_rates > 0 || o.form == 3)) return NS_ERR_UNSUPPORTED;
   // bf16x6 operands carry a third split part that the composite loops and the
   // elementwise sum of the nested order-45 chain do not produce
   if (o.precision == NS_BF16X6 && (n_rates > 0 || o.form == 3)) return NS_ERR_UNSUPPORTED;
@@ -2018,6 +2079,80 @@ ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L
   void* none[3] = {nullptr, nullptr, nullptr};
   return k_gemm_impl(3, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D ? D : none, ldd16, frob_out,
                      256, -2, stream);
+}
+
+ns_status ns_k_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* L, int64_t ldl, const float* R, int64_t ldr,
+                         float s, const float* C, int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32,
+                         float* Dt, float* DtT, int64_t ldt, double* frob_out, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
+  if (!L || !R || ldl < K || ldr < N || !al16(L) || !al16(R)) return NS_ERR_ARG;
+  if (C && (ldc < N || ldc % 4 || !al16(C))) return NS_ERR_ARG;
+  if (D32 && (ldd32 < N || ldd32 % 4 || !al16(D32))) return NS_ERR_ARG;
+  if ((Dt || DtT) && (ldt < std::max(M, N) || ldt % 4)) return NS_ERR_ARG;
+  if ((Dt && !al16(Dt)) || (DtT && !al16(DtT))) return NS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // scratch: the TF32 row form of L (M x ldk) and transposed form of R (N x ldk)
+  const int64_t ldk = (K + 3) / 4 * 4;
+  const int tiles_m = static_cast<int>((M + 127) / 128), tiles_n = static_cast<int>((N + 255) / 256);
+  const size_t lbytes = sizeof(float) * static_cast<size_t>(M) * ldk;
+  const size_t rbytes = sizeof(float) * static_cast<size_t>(N) * ldk;
+  const size_t pbytes = sizeof(double) * static_cast<size_t>(tiles_m + 1) * tiles_n * 8;
+  char* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), lbytes + rbytes + pbytes + 1024, st) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_ERR_OOM;
+  }
+  float* Lt = reinterpret_cast<float*>(ws);
+  float* RtT = reinterpret_cast<float*>(ws + (lbytes + 255) / 256 * 256);
+  double* parts = reinterpret_cast<double*>(ws + (lbytes + 255) / 256 * 256 + (rbytes + 255) / 256 * 256);
+  int* err = reinterpret_cast<int*>(parts + static_cast<size_t>(tiles_m + 1) * tiles_n * 8);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_tf32_pack(L, ldl, static_cast<int>(M), static_cast<int>(K), Lt, nullptr, ldk, st);
+  if (e == cudaSuccess) e = launch_tf32_pack(R, ldr, static_cast<int>(K), static_cast<int>(N), nullptr, RtT, ldk, st);
+  TcParams p;
+  memset(&p, 0, sizeof(p));
+  TcProblem& P = p.prob[0];
+  if (!encode_f32_map(&P.L[0], Lt, M, K, ldk) || !encode_f32_map(&P.R[0], RtT, N, K, ldk)) {
+    cudaFreeAsync(ws, st);
+    return NS_ERR_ARG;
+  }
+  P.L[1] = P.L[0];
+  P.R[1] = P.R[0];
+  P.M = static_cast<int>(M);
+  P.N = static_cast<int>(N);
+  P.K = static_cast<int>(K);
+  P.tiles_m = tiles_m;
+  P.tiles_n = tiles_n;
+  P.tile_begin = 0;
+  P.tile_count = tc_items(P.M, P.N, 256, 2);
+  P.s = s;
+  P.beta = beta;
+  P.gamma = gamma;
+  P.C = C;
+  P.ldc = static_cast<int>(ldc);
+  P.D32 = D32;
+  P.ldd32 = static_cast<int>(ldd32);
+  P.Dt = Dt;
+  P.DtT = DtT;
+  P.ldt = static_cast<int>(ldt);
+  P.frob_partials = frob_out ? parts : nullptr;
+  p.nprob = 1;
+  p.npass = 1;
+  p.total_tiles = P.tile_count;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = 2000000000ull;
+  p.err = err;
+  if (e == cudaSuccess) e = launch_gemm_tc_pair(p, 4, sms, st);
+  if (e == cudaSuccess && frob_out) e = launch_reduce_sum(parts, tc_tiles(P.M, P.N, 256) * 8, 1, frob_out, st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return kernel_fail(NS_ERR_CUDA, "TF32 product", e);
+  return herr == DEV_OK ? NS_OK : kernel_fail(NS_ERR_TIMEOUT, "bounded device wait ran out", cudaSuccess);
 }
 
 ns_status ns_k_gemm_oz(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* R, int64_t ldr,

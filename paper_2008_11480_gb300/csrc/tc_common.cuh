@@ -63,6 +63,9 @@ __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n
   bf16* __restrict__ e_Dhi = P.Dhi;
   bf16* __restrict__ e_Dlo = P.Dlo;
   bf16* __restrict__ e_Dlo2 = kLo2 && P.Dlo != nullptr ? P.Dlo2 : nullptr;
+  float* __restrict__ e_Dt = P.Dt;
+  float* __restrict__ e_DtT = P.DtT;
+  const int64_t e_ldt = P.ldt;
   float frob = 0.f;
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -112,6 +115,26 @@ __device__ __forceinline__ float epilogue_tile(const TcProblem& P, int m0, int n
       if (e_gamma != 0.f) {
 #pragma unroll
         for (int t = 0; t < 4; ++t) v[t] += (row == col + t) ? e_gamma : 0.f;
+      }
+      if (e_Dt != nullptr || e_DtT != nullptr) {
+        // TF32 forms of D for the next TF32 product (row form: whole 16-byte
+        // pieces of a row; transposed form: 4 consecutive rows of one column)
+        const float t0 = rna_tf32(v[0]), t1 = rna_tf32(v[1]), t2 = rna_tf32(v[2]), t3 = rna_tf32(v[3]);
+        const float tv[4] = {t0, t1, t2, t3};
+        if (e_Dt != nullptr) {
+          if (cols4) {
+            *reinterpret_cast<float4*>(e_Dt + static_cast<int64_t>(row) * e_ldt + col) = make_float4(t0, t1, t2, t3);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (col + t < e_N) e_Dt[static_cast<int64_t>(row) * e_ldt + col + t] = tv[t];
+          }
+        }
+        if (e_DtT != nullptr) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (col + t < e_N) e_DtT[static_cast<int64_t>(col + t) * e_ldt + row] = tv[t];
+        }
       }
       if (cols4) {
 #pragma unroll

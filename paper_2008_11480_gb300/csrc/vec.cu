@@ -2,6 +2,7 @@
 // R = B - A Theta (FP64), the update Theta += G R, matrix/column norms,
 // fixed-order (deterministic) reductions, the bf16 hi/lo splits and G0.
 #include "internal.h"
+#include "ptx.cuh"
 #include "split.cuh"
 
 namespace nsgb {
@@ -427,6 +428,32 @@ int ew_grid(int64_t total) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+
+// TF32 forms of an f32 matrix: Y = RN_tf32(X) (row-major, ldt) and
+// YT = RN_tf32(X)^T (ldt), through a 32 x 33 shared tile so that both the
+// reads and the transposed writes cover whole rows of 32 words.
+__global__ void __launch_bounds__(256) k_tf32_pack(const float* __restrict__ X, int64_t ld, int rows, int cols,
+                                                   float* __restrict__ Y, float* __restrict__ YT, int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int row = by + r, col = bx + tx;
+    float v = 0.f;
+    if (row < rows && col < cols) {
+      v = rna_tf32(X[static_cast<int64_t>(row) * ld + col]);
+      if (Y != nullptr) Y[static_cast<int64_t>(row) * ldt + col] = v;
+    }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  if (YT == nullptr) return;
+  for (int r = ty; r < 32; r += 8) {
+    const int orow = bx + r, ocol = by + tx;  // YT row = X column
+    if (orow < cols && ocol < rows) YT[static_cast<int64_t>(orow) * ldt + ocol] = tile[tx][r];
+  }
+}
 
 }  // namespace
 
@@ -1074,6 +1101,15 @@ cudaError_t launch_update_x2(const float* G, int64_t ldg, const float* R32T, int
       k_update_x2<1><<<nb, 256, 0, s>>>(G, ldg, R32T, ldt, Th, T1, T2, n, nrhs, c0);
     c0 += nr;
   }
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_tf32_pack(const float* X, int64_t ld, int rows, int cols, float* Y, float* YT, int64_t ldt,
+                             cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_tf32_pack<<<grid, 256, 0, s>>>(X, ld, rows, cols, Y, YT, ldt);
   return cudaGetLastError();
 }
 

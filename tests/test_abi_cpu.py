@@ -117,7 +117,7 @@ def test_create_rejects_bad_precision(L):
 def test_create_validates_precision_options(L):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 1)(2)
-    for kw in ({"precision": 1}, {"fp64_slices": 1}, {"fp64_slices": 8}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
+    for kw in ({"precision": 6}, {"precision": -1}, {"tf32_rung": 2}, {"fp64_slices": 1}, {"fp64_slices": 8}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
                {"fp64_slices_early": 8}, {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 3}, {"pow_bf16": -1},
                {"gemm_cluster": 2}, {"gemm_cluster": 4}):
         opt = nsgb.default_options(**kw)
@@ -127,8 +127,15 @@ def test_create_validates_precision_options(L):
     assert L.ns_create(64, 4, arr, 1, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
     opt = nsgb.default_options(precision=nsgb.NS_BF16X6, form=3)
     assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED
+    # TF32 products likewise (fixed, or as AUTO's rung)
+    for kw in ({"precision": nsgb.NS_TF32}, {"tf32_rung": 1}):
+        opt = nsgb.default_options(**kw)
+        assert L.ns_create(64, 4, arr, 1, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED, kw
+        opt = nsgb.default_options(form=3, **kw)
+        assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED, kw
     d = nsgb.default_options()
     assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0 and d.pow_bf16 == 2
+    assert d.tf32_rung == 0 and d.batch_fused == 1
 
 
 def test_new_kernel_entry_points_validate_before_launch(L):

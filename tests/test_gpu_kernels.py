@@ -542,3 +542,75 @@ def test_gemm_oz_full_size_sampled():
         ex = float(-(L[i].astype(np.longdouble) @ R[:, j].astype(np.longdouble)) + (1.0 if i == j else 0.0))
         ab = float(np.abs(L[i]) @ np.abs(R[:, j]))
         assert abs(out[i, j] - ex) <= 16 * 2.0 ** -53 * (ab + abs(ex)), (i, j)
+
+
+# ---------------------------------------------------------------- TF32 products (tcgen05 kind::tf32)
+def run_gemm_tf32(M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False):
+    """D = s RN_tf32(L) RN_tf32(R) + beta C + gamma I against the oracle's
+    split_product("tf32"): the product of the rounded operands is exact in
+    float64 and the kernel adds K of them in f32, so the bound is the bf16
+    one (K 2^-23 sum|terms| + 2^-22 (|D| + |beta C| + |gamma|)).  The TF32
+    forms the epilogue writes for the next product are RN_tf32 of the kernel's
+    own D32, bit for bit, row-major and transposed."""
+    rng = np.random.default_rng(seed)
+    L = O.round_f32(rng.standard_normal((M, K)))
+    R = O.round_f32(rng.standard_normal((K, N)))
+    C = O.round_f32(rng.standard_normal((M, N))) if with_c else None
+    ldl, ldr, ldd = rup(K, 4), rup(N, 4), rup(N, 4)
+    ldt = rup(max(M, N), 4)
+    Ld = to_dev_padded(L, ldl, torch.float32)
+    Rd = to_dev_padded(R, ldr, torch.float32)
+    Cd = to_dev_padded(C, ldd, torch.float32) if with_c else None
+    D32 = torch.full((M, ldd), 7.0, dtype=torch.float32, device=dev)
+    Dt = torch.zeros((M, ldt), dtype=torch.float32, device=dev)
+    DtT = torch.zeros((N, ldt), dtype=torch.float32, device=dev)
+    fro = torch.zeros(1, dtype=torch.float64, device=dev)
+    nsgb.ns_k_gemm_tf32(M, N, K, Ld, ldl, Rd, ldr, s, Cd, ldd if with_c else 0, beta, gamma, D32, ldd, Dt, DtT, ldt,
+                        fro)
+    torch.cuda.synchronize()
+    prod = O.split_product(L, R, "tf32")
+    absprod = O.split_abs_product(L, R, "tf32")
+    ref = O.gemm_epilogue(prod, s, C, beta, gamma)
+    out = D32.cpu().numpy()[:, :N].astype(np.float64)
+    assert np.all(D32.cpu().numpy()[:, N:] == 7.0), "wrote past N"
+    cabs = np.abs(beta * C) if with_c else 0.0
+    tol = K * 2.0 ** -23 * absprod * abs(s) + 2.0 ** -22 * (np.abs(ref) + cabs + abs(gamma)) + 1e-30
+    err = np.abs(out - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    # a bf16 product of the same operands would be off by ~2^-8: TF32 keeps 2^-11
+    assert np.median(err / (absprod * abs(s) + 1e-30)) <= 2.0 ** -20
+    want_t = O.round_tf32(out)
+    assert np.array_equal(Dt.cpu().numpy()[:, :N].astype(np.float64), want_t)
+    assert np.array_equal(DtT.cpu().numpy()[:, :M].astype(np.float64), want_t.T)
+    assert float(fro.item()) == pytest.approx(float(np.sum(out * out)), rel=1e-5)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 130, 257), (512, 520, 200), (1024, 1024, 1024),
+                                   (129, 1000, 31)])
+def test_gemm_tf32(M, N, K):
+    """TF32 CTA-pair products: whole and ragged tiles, an odd number of 128-row
+    tiles (the last pair's second CTA covers rows past M), K not a multiple of
+    the 32-deep stage."""
+    run_gemm_tf32(M, N, K, seed=M + 3 * N + K)
+
+
+def test_gemm_tf32_epilogues():
+    run_gemm_tf32(333, 333, 333, seed=8, s=-1.0, gamma=1.0)
+    run_gemm_tf32(257, 300, 129, seed=9, beta=1.0, with_c=True)
+
+
+def test_gemm_tf32_differs_from_bf16():
+    """The TF32 path really reads 10 stored bits: on operands that bf16 rounds
+    but TF32 keeps exactly (11 significant bits) the TF32 product is exact."""
+    rng = np.random.default_rng(10)
+    M = N = 256
+    K = 16  # products are multiples of 2^-20 below 1, so K = 16 of them sum exactly within 24 bits
+    L = rng.integers(-1023, 1024, (M, K)).astype(np.float64) / 1024.0
+    R = rng.integers(-1023, 1024, (K, N)).astype(np.float64) / 1024.0
+    Ld, Rd = to_dev_padded(L, K, torch.float32), to_dev_padded(R, N, torch.float32)
+    D32 = torch.zeros((M, N), dtype=torch.float32, device=dev)
+    nsgb.ns_k_gemm_tf32(M, N, K, Ld, K, Rd, N, 1.0, None, 0, 0.0, 0.0, D32, N)
+    torch.cuda.synchronize()
+    exact = L @ R
+    assert np.array_equal(D32.cpu().numpy().astype(np.float64), exact)
+    assert not np.array_equal(O.round_bf16(L), L)  # bf16 would have rounded the operands

@@ -709,3 +709,47 @@ def test_mixed_composite_solve_reaches_tolerance(rates):
     assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
     tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
     assert rel(th, tstar) <= 10 * kappa * 1e-10
+
+
+# ---------------------------------------------------------------- TF32 products
+def test_tf32_solve_reaches_tolerance():
+    """NS_TF32: every product a TF32 tcgen05 pass (CTA pairs, odd row-tile count
+    at n = 300); FP64 Richardson wins the accuracy back; G within the stated
+    per-precision bound (eps_tf32 = 2^-10 + 2^-24 sqrt(K), as for bf16 with
+    TF32's 11 significant bits) at the floor."""
+    for n, kappa in ((300, 1e3), (1000, 1e4)):
+        p = make_spd(n, kappa, nrhs=2, seed=40)
+        with nsgb.Context(n, order=8, precision=nsgb.NS_TF32) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+        th = r.theta.cpu().numpy()
+        assert r.status == nsgb.NS_OK, r.stats.res_history()
+        assert set(r.stats.prec_history()) == {nsgb.NS_TF32}
+        assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+        tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+        assert rel(th, tstar) <= 10 * kappa * 1e-10
+    n, kappa = 300, 100.0
+    p = make_spd(n, kappa, seed=41)
+    with nsgb.Context(n, order=4, precision=nsgb.NS_TF32, ns_stop=0) as ctx:
+        G, _ = ctx.invert(tens(p.A), iters=10)
+    Gp = G.cpu().numpy()
+    e = 2.0 ** -10 + 2.0 ** -24 * math.sqrt(n)
+    F2 = float(np.linalg.norm(np.eye(n) - p.A @ Gp, 2))
+    assert F2 <= 4 * e * kappa, (F2, 4 * e * kappa)
+
+
+def test_auto_tf32_rung_reaches_tolerance():
+    """AUTO with tf32_rung: bf16 steps, then TF32 once bf16's contraction
+    worsens, then bf16x3; the residual reaches 1e-10 and the precision
+    history shows the ladder in order."""
+    n, kappa = 1024, 1e5
+    p = make_spd(n, kappa, nrhs=2, seed=42)
+    with nsgb.Context(n, order=8, tf32_rung=1, couple_frob=1.0) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    th = r.theta.cpu().numpy()
+    assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history())
+    assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+    hist = r.stats.prec_history()
+    assert nsgb.NS_TF32 in hist and hist[0] == nsgb.NS_BF16, hist
+    order = {nsgb.NS_BF16: 0, nsgb.NS_TF32: 1, nsgb.NS_BF16X3: 2, nsgb.NS_BF16X6: 3}
+    ranks = [order[h] for h in hist]
+    assert ranks == sorted(ranks), hist

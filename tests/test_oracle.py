@@ -485,6 +485,74 @@ def test_round_bf16_matches_torch():
     assert np.array_equal(got, ref)
 
 
+def _tf32_nearest_brute(x32):
+    """Nearest TF32 value of each binary32 x by explicit comparison of its two
+    TF32 neighbours in magnitude (ties away from zero), in float64."""
+    out = np.empty_like(x32, dtype=np.float64)
+    for i, v in enumerate(x32):
+        if np.isnan(v):
+            out[i] = np.nan
+            continue
+        m = abs(float(v))
+        u = np.array([m], dtype=np.float32).view(np.uint32)[0]
+        lo_bits = np.uint32(u & np.uint32(0xFFFFE000))
+        lo = float(np.array([lo_bits], dtype=np.uint32).view(np.float32)[0])
+        if lo == m:
+            r = m
+        else:
+            hi_bits = np.uint64(lo_bits) + np.uint64(0x2000)
+            hi = float(np.array([hi_bits], dtype=np.uint64).astype(np.uint32).view(np.float32)[0]) \
+                if hi_bits < 0x7F800000 else np.inf
+            dl, dh = m - lo, hi - m
+            if hi_bits >= 0x7F800000:
+                # beyond the largest TF32 value: the half-way point to 2^128
+                r = np.inf if m >= lo + 2.0 ** 116 else lo  # half the TF32 spacing 2^117 at 2^127
+            else:
+                r = hi if dh <= dl else lo
+        out[i] = -r if v < 0 else r
+    return out
+
+
+def test_round_tf32_nearest_ties_away():
+    """TF32 rounding (10 stored significand bits): worked cases -- ties go away
+    from zero, not to even -- and agreement with a brute-force search of the
+    two TF32 neighbours on random and edge values."""
+    one = 1.0
+    cases = {one + 2.0 ** -12: one, one + 2.0 ** -11: one + 2.0 ** -10,       # tie -> away
+             one + 3 * 2.0 ** -11: one + 2.0 ** -9,                             # tie (odd) -> away
+             one + 2.0 ** -11 + 2.0 ** -23: one + 2.0 ** -10,
+             -(one + 2.0 ** -11): -(one + 2.0 ** -10), 0.0: 0.0, 2.0 ** -130: 2.0 ** -130,
+             3.4028234663852886e38: np.inf}
+    for x, want in cases.items():
+        assert O.round_tf32(np.array([x]))[0] == want, (x, O.round_tf32(np.array([x]))[0], want)
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.uniform(-35, 35, 3000),
+                        np.array([1e-45, -3e-39, 65504.0, 1.0 + 2.0 ** -11, -0.0])])
+    x32 = x.astype(np.float32)
+    got = O.round_tf32(x32)
+    ref = _tf32_nearest_brute(x32)
+    assert np.array_equal(got, ref)
+    fin = np.isfinite(got) & (np.abs(x32) > 1e-37)
+    assert np.all(np.abs(got[fin] - x32[fin]) <= 2.0 ** -11 * np.abs(x32[fin].astype(np.float64)))
+    assert np.all((got[np.isfinite(got)].astype(np.float32).view(np.uint32) & 0x1FFF) == 0)
+
+
+def test_tf32_split_product():
+    """The tf32 product is the exact product of the rounded operands: equal to
+    a float64 product of round_tf32 values, off the float64 product by at most
+    ~2 2^-11 |L||R|, and exact for operands with 11 significant bits."""
+    rng = np.random.default_rng(4)
+    L, R = rng.standard_normal((12, 40)), rng.standard_normal((40, 7))
+    P = O.split_product(L, R, "tf32")
+    assert np.array_equal(P, O.round_tf32(L) @ O.round_tf32(R))
+    ab = np.abs(L) @ np.abs(R)
+    assert np.all(np.abs(P - L @ R) <= 2.1 * 2.0 ** -11 * ab)
+    Li = rng.integers(-1024, 1024, (5, 9)).astype(float)
+    Ri = rng.integers(-1024, 1024, (9, 3)).astype(float)
+    assert np.array_equal(O.split_product(Li, Ri, "tf32"), Li @ Ri)
+    assert np.array_equal(O.split_abs_product(Li, Ri, "tf32"), np.abs(Li) @ np.abs(Ri))
+
+
 def test_split_bf16_error_bound():
     rng = np.random.default_rng(1)
     x = rng.standard_normal(10000)

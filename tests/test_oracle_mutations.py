@@ -406,3 +406,26 @@ def test_signed_product_missing_factor_two(monkeypatch):
     orig = N.ozaki_product_signed
     _patch(monkeypatch, "ozaki_product_signed", lambda L, R, s=7: 0.25 * orig(L, R, s))
     assert _fails(T.test_ozaki_signed_product_matches_truncated_and_exact)
+
+
+def test_tf32_ties_to_even(monkeypatch):
+    """TF32 rounding with ties to even instead of away from zero."""
+    def bad(x):
+        f = np.asarray(x, dtype=np.float64).astype(np.float32)
+        u = f.view(np.uint32).astype(np.uint64)
+        lsb = (u >> np.uint64(13)) & np.uint64(1)
+        r = ((u + np.uint64(0xFFF) + lsb) >> np.uint64(13)) << np.uint64(13)
+        return (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    _patch(monkeypatch, "round_tf32", bad)
+    assert _fails(T.test_round_tf32_nearest_ties_away)
+
+
+def test_tf32_truncation(monkeypatch):
+    """TF32 by truncation (the low 13 bits dropped, as an input conversion
+    that ignores them would do)."""
+    def bad(x):
+        f = np.asarray(x, dtype=np.float64).astype(np.float32)
+        u = f.view(np.uint32) & np.uint32(0xFFFFE000)
+        return u.view(np.float32).astype(np.float64)
+    _patch(monkeypatch, "round_tf32", bad)
+    assert _fails(T.test_round_tf32_nearest_ties_away)
