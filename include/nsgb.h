@@ -76,7 +76,7 @@ typedef struct ns_options {
   int pow_mode;        /* 0: F^{2^{j+1}} = F^{2^j} F^{2^j}; 1: F^{2^{j+1}} = I - A X_{j+1} (eq. ua1) */
   int g0_mode;         /* 0: alpha = 1/||A||_F; 1: alpha = 1/(||A||_inf/2 + 1e-8 ||A||_inf);
                           2: Jacobi, G0 = diag(A)^{-1} (Section 2, strictly diagonally dominant A;
-                          single-system path only) */
+                          single-system and batched / served paths) */
   int ns_stop;         /* 0: take exactly `iters` NS steps; 1: stop NS at the precision floor */
   double ns_stop_frob; /* with ns_stop = 1, also stop once ||F_k||_F <= this; default 0.02 */
   int max_sweeps;      /* Richardson-only sweeps allowed after NS stops; default 200 */
@@ -269,7 +269,7 @@ typedef struct ns_batch_stats {
 
 /* Create a batch of `count` systems; n[i] in [1, 16384], nrhs[i] in [1, 1024].
  * order: 3 or a power of two.  opt: precision NS_AUTO, NS_BF16 or NS_BF16X3,
- * form 0, pow_mode 0 (others return NS_ERR_UNSUPPORTED).  Allocates all workspace
+ * form 0, pow_mode 0, g0_mode 0..2, g0_order 0 (others return NS_ERR_UNSUPPORTED).  Allocates all workspace
  * (one device allocation) and the per-instance product descriptors. */
 ns_status ns_batch_create(int count, const int64_t* n, const int* nrhs, int order, const ns_options* opt,
                           ns_batch** out);

@@ -87,7 +87,116 @@ struct SlotLayout {
   size_t bytes;
 };
 
-int tile_width(int n) { return n <= 512 ? 128 : 256; }
+// ---- tile width of a system's list-driven products, by a measured choice
+// Systems of n <= 256 keep 128-column tiles: the fused small-system kernel
+// runs them on 128 x 128 tiles, and the pass-by-pass path must form ||F||^2
+// from the same tiles for the two paths to agree bit for bit.  Above that the
+// width (128 or 256 columns; the K order of every output, hence the product,
+// does not depend on it) is measured once per process and size bucket: a
+// grouped launch of copies of one product of the bucket's largest size on
+// each candidate, the faster kept.  It depends on n alone, so a system gets
+// the same width alone and in any mix.
+std::mutex g_tune_mu;
+int g_tune[6] = {0, 0, 0, 0, 0, 0};  // buckets n <= 512, 1024, 2048, 4096, 8192, 16384
+int g_tune_n[6] = {512, 1024, 2048, 4096, 8192, 16384};
+
+int tune_bucket(int n) {
+  for (int b = 0; b < 6; ++b)
+    if (n <= g_tune_n[b]) return b;
+  return 5;
+}
+
+double time_width(int n, int bn, const CUtensorMap& mL, const CUtensorMap& mR, float* D32, bf16* Dhi, bf16* Dlo,
+                  int* err, int sms, cudaStream_t st) {
+  TcParams p;
+  memset(&p, 0, sizeof(p));
+  const int tiles = tc_tiles(n, n, bn);
+  const int copies = std::max(1, std::min(kTcMaxProblems, (2 * sms + tiles - 1) / tiles));
+  int tile = 0;
+  for (int i = 0; i < copies; ++i) {
+    TcProblem& P = p.prob[i];
+    P.L[0] = P.L[1] = mL;
+    P.R[0] = P.R[1] = mR;
+    P.M = P.N = P.K = n;
+    P.tiles_m = (n + 127) / 128;
+    P.tiles_n = (n + bn - 1) / bn;
+    P.tile_begin = tile;
+    P.tile_count = tiles;
+    tile += tiles;
+    P.s = -1.f;
+    P.gamma = 1.f;
+    P.ldc = P.ldd32 = P.ldd16 = static_cast<int>(rup(n, 64));
+    P.D32 = D32;  // every copy writes the same values
+    P.Dhi = Dhi;
+    P.Dlo = Dlo;
+  }
+  p.nprob = copies;
+  p.total_tiles = tile;
+  p.npass = 1;
+  p.debug_stall_iter = -1;
+  p.timeout_ns = 2000000000ull;
+  p.err = err;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, st);
+    const cudaError_t e = launch_gemm_tc(p, bn, false, sms, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      best = 1e30;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, static_cast<double>(ms) / copies);  // the first launch warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  return best;
+}
+
+int tune_width(int b, int sms) {
+  const int n = g_tune_n[b];
+  const size_t ld = rup(n, 64), cnt = ld * ld;
+  char* w = nullptr;
+  const size_t bytes = cnt * (2 * 2 + 4 + 2 * 2) + 256;
+  if (cudaMalloc(&w, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return n <= 512 ? 128 : 256;  // no room to measure: the width measured on the development box
+  }
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  cudaMemsetAsync(w, 0, bytes, st);
+  bf16* L = reinterpret_cast<bf16*>(w);
+  bf16* R = L + cnt;
+  float* D32 = reinterpret_cast<float*>(R + cnt);
+  bf16* Dhi = reinterpret_cast<bf16*>(D32 + cnt);
+  bf16* Dlo = Dhi + cnt;
+  int* err = reinterpret_cast<int*>(Dlo + cnt);
+  CUtensorMap mL, mR;
+  int pick = n <= 512 ? 128 : 256;
+  if (encode_bf16_map(&mL, L, ld, ld, ld, 0) && encode_bf16_map(&mR, R, ld, ld, ld, 0)) {
+    const double t128 = time_width(n, 128, mL, mR, D32, Dhi, Dlo, err, sms, st);
+    const double t256 = time_width(n, 256, mL, mR, D32, Dhi, Dlo, err, sms, st);
+    if (t128 < 1e30 && t256 < 1e30) pick = t128 <= t256 ? 128 : 256;
+  }
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  cudaFree(w);
+  cudaGetLastError();
+  return pick;
+}
+
+int tile_width(int n, int sms) {
+  if (n <= kFusedMaxN) return 128;
+  const int b = tune_bucket(n);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune[b] == 0) g_tune[b] = tune_width(b, sms);
+  return g_tune[b];
+}
 
 SlotLayout slot_layout(int n, int nrhs, bool copies) {
   SlotLayout L;
@@ -106,8 +215,8 @@ SlotLayout slot_layout(int n, int nrhs, bool copies) {
     L.mat[m][2] = take(sq * 2);
   }
   const size_t nrb = (n + 7) / 8;
-  const int bnv = tile_width(n);
-  const size_t tiles = static_cast<size_t>((n + 127) / 128) * ((n + bnv - 1) / bnv);
+  // partial sums of ||F||^2 for the narrowest tile width a system can get (128)
+  const size_t tiles = static_cast<size_t>((n + 127) / 128) * ((n + 127) / 128);
   L.a1 = take(n * ld * 4);
   L.a2 = take(n * ld * 4);
   L.t1 = take(nrhs * ld * 4);
@@ -307,7 +416,7 @@ int add_slot(ns_batch* b, int n, int nrhs, bool copies) {
   b->n[i] = n;
   b->nrhs[i] = nrhs;
   b->ld[i] = static_cast<int>(rup(n, 64));
-  b->bn[i] = tile_width(n);
+  b->bn[i] = tile_width(n, b->num_sms);
   b->tiles_m[i] = (n + 127) / 128;
   b->tiles_n[i] = (n + b->bn[i] - 1) / b->bn[i];
   const int64_t ldi = b->ld[i];
@@ -901,7 +1010,7 @@ ns_status check_opts(ns_options* o, const ns_options* opt, int order) {
     *o = *opt;
   else
     ns_default_options(o);
-  if (o->form != 0 || o->pow_mode != 0 || o->g0_mode < 0 || o->g0_mode > 1) return NS_ERR_UNSUPPORTED;
+  if (o->form != 0 || o->pow_mode != 0 || o->g0_mode < 0 || o->g0_mode > 2 || o->g0_order != 0) return NS_ERR_UNSUPPORTED;
   if (o->precision != NS_AUTO && o->precision != NS_BF16 && o->precision != NS_BF16X3) return NS_ERR_UNSUPPORTED;
   if (order != 3 && (order < 2 || order > 64 || (order & (order - 1)) != 0)) return NS_ERR_ARG;
   if (o->timeout_s <= 0) o->timeout_s = 2.0;

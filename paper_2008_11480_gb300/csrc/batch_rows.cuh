@@ -141,6 +141,15 @@ __device__ __forceinline__ void bg0_body(const BInst& I, const BItem it, int mod
     if (r >= n) continue;
     const int64_t o = static_cast<int64_t>(r) * I.ld + c;
     const bool d = r == c;
+    if (mode == 2) {
+      // Jacobi splitting S = diag(A) (Section 2): G0 = S^{-1}, as the single-system kernel forms it
+      const float f = d ? static_cast<float>(1.0 / I.A[static_cast<int64_t>(r) * n + r]) : 0.f;
+      const bf16 h = __float2bfloat16_rn(f);
+      I.G32[0][o] = f;
+      I.Ghi[0][o] = d ? h : z;
+      I.Glo[0][o] = d ? __float2bfloat16_rn(f - __bfloat162float(h)) : z;
+      continue;
+    }
     I.G32[0][o] = d ? alpha : 0.f;
     I.Ghi[0][o] = d ? ah : z;
     I.Glo[0][o] = d ? al : z;

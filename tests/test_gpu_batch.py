@@ -155,3 +155,32 @@ def test_fused_matches_pass_by_pass_bitwise(order):
         if r["status"] == nsgb.NS_OK:
             assert float(np.max(O.rel_residual(p.A, th.cpu().numpy(), p.B))) <= 1e-10
     assert fst.converged >= 7
+
+
+def test_batch_jacobi_g0_matches_single_system():
+    """Jacobi G0 = diag(A)^{-1} (Section 2) on the batched path, fused and pass
+    by pass: diagonally dominant systems reach 1e-10, and each system's theta
+    equals the single-system solve's to the residual bar (the same method from
+    the same G0; the single path's controller differs in its cost model)."""
+    rng = np.random.default_rng(80)
+    probs = []
+    for i, n in enumerate([40, 96, 130, 200]):
+        A = rng.uniform(-1, 1, (n, n))
+        A = 0.5 * (A + A.T)
+        np.fill_diagonal(A, np.abs(A).sum(axis=1) + rng.uniform(0.5, 3.0, n))
+        B = rng.standard_normal((n, 2))
+        probs.append((A, B))
+    for fused in (1, 0):
+        with nsgb.Batch([A.shape[0] for A, _ in probs], [2] * len(probs), order=4, g0_mode=2,
+                        batch_fused=fused) as bt:
+            outs, status, st = bt.solve([tens(A) for A, _ in probs], [tens(B) for _, B in probs], iters=60,
+                                        tol=1e-10)
+        assert status == nsgb.NS_OK
+        for (A, B), th in zip(probs, outs):
+            x = th.cpu().numpy()
+            assert float(np.max(O.rel_residual(A, x, B))) <= 1e-10
+            with nsgb.Context(A.shape[0], order=4, g0_mode=2) as ctx:
+                r = ctx.solve(tens(A), tens(B), iters=60, tol=1e-10)
+            y = r.theta.cpu().numpy()
+            cond = float(np.linalg.cond(A))
+            assert np.linalg.norm(x - y) / np.linalg.norm(y) <= 10 * cond * 1e-10
