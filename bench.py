@@ -354,7 +354,7 @@ def run_gram(a):
 
     sampler = ClockSampler(local)
     step_ms, ns_it, sw = [], [], []
-    acc = dict(tc_ms=0.0, tc_flops=0.0, tc_alg=0.0, tc_l=0, gemm_ms=0.0, gemm_l=0, launches=0)
+    acc = dict(tc_ms=0.0, tc_flops=0.0, tc_alg=0.0, tc_l=0, gemm_ms=0.0, gemm_l=0, launches=0, pair_flops=0.0)
     barrier()
     sampler.start()
     for _ in range(a.steps):
@@ -375,6 +375,7 @@ def run_gram(a):
         acc["gemm_ms"] += st.gemm_ms
         acc["gemm_l"] += st.gemm_launches
         acc["launches"] += st.kernel_launches
+        acc["pair_flops"] += st.slice_pair_flops
         ns_it.append(st.ns_iters)
         sw.append(st.sweeps)
     barrier()
@@ -435,14 +436,14 @@ def run_gram(a):
     f3 = 2.0 * float(n) ** 3
     oz_ms = acc["gemm_ms"] - acc["tc_ms"]
     oz_l = acc["gemm_l"] - acc["tc_l"]
-    pairs = GRAM_SLICES * (GRAM_SLICES + 1) // 2
+    pairs = acc["pair_flops"] / (oz_l * f3) if oz_l else 0.0  # mean digit pairs per slice product
     kern = {
         "k_gemm_tc2": {"ms_per_step": acc["tc_ms"] / a.steps, "launches_per_step": acc["tc_l"] / a.steps,
                        "achieved_tflops": acc["tc_alg"] / (acc["tc_ms"] / 1e3) / 1e12 if acc["tc_ms"] else None,
                        "executed_tflops": acc["tc_flops"] / (acc["tc_ms"] / 1e3) / 1e12 if acc["tc_ms"] else None},
-        "k_gemm_oz": {"ms_per_step": oz_ms / a.steps, "products_per_step": oz_l / a.steps, "digit_pairs": pairs,
+        "k_gemm_oz": {"ms_per_step": oz_ms / a.steps, "products_per_step": oz_l / a.steps, "digit_pairs_mean": pairs,
                       "achieved_tflops": oz_l * f3 / (oz_ms / 1e3) / 1e12 if oz_ms > 0 else None,
-                      "executed_tflops": oz_l * pairs * f3 / (oz_ms / 1e3) / 1e12 if oz_ms > 0 else None,
+                      "executed_tflops": acc["pair_flops"] / (oz_ms / 1e3) / 1e12 if oz_ms > 0 else None,
                       "note": "time of the whole slice product: scales, digit slicing, level kernel, combine"}}
     dom = "k_gemm_oz" if oz_ms > acc["tc_ms"] else "k_gemm_tc2"
     kd = kern[dom]
@@ -452,7 +453,8 @@ def run_gram(a):
             "peak_kind": f"bf16 dense sustained ({pk_kind}); kernel timed inside back-to-back solves; achieved and "
                          "frac count algorithmic flops (2 n^3 per product)",
             "executed": exe, "frac_executed": exe / sus if exe else None,
-            "executed_note": "bf16 tensor work run: bf16x3 = 3 passes, a 4-digit slice product = 10 digit pairs",
+            "executed_note": "bf16 tensor work run: bf16x3 = 3 passes, an s-digit slice product = s (s + 1) / 2 digit "
+                             "pairs",
             "traffic": recorded_traffic("traffic_k_gemm_oz_gram16384.md") if dom == "k_gemm_oz" else None,
             "traffic_unit": "bytes per level-kernel launch (ncu dram read + write)",
             "avg_launch_ms": (oz_ms / max(oz_l, 1)) if dom == "k_gemm_oz" else acc["tc_ms"] / max(acc["tc_l"], 1),

@@ -132,6 +132,9 @@ typedef struct ns_options {
   int tf32_rung;        /* NS_AUTO: 1 puts TF32 products between bf16 and bf16x3 (bf16 until its
                           contraction worsens, then TF32 until TF32's does, then bf16x3); 0
                           (default) goes from bf16 straight to bf16x3 */
+  int fp64_slices_pow;  /* slice products (fp64_slices): digits of the powers F^{2^{j+1}} =
+                          F^{2^j} F^{2^j} of a factorized step, 2..7; 0 (default): the step's.
+                          Their error reaches F_{k+1} through A X ~ I, not amplified by kappa */
   int batch_fused;      /* batched solves (ns_batch_solve): 1 (default of ns_default_options) runs
                           a batch whose systems all have n <= 256 as one persistent launch, one
                           CTA per system solving it whole (same arithmetic and controller as the
@@ -164,6 +167,8 @@ typedef struct ns_stats {
                                         -1 when not computed */
   double tc_gemm_alg_flops;          /* algorithmic work of the tcgen05 launches: 2 M N K per
                                         product, whatever its passes (bf16x3 counts once) */
+  double slice_pair_flops;           /* slice products: 2 M N K per digit pair run (s digits:
+                                        s (s + 1) / 2 pairs per product) */
 } ns_stats;
 
 /* Fill *opt with the defaults documented in ns_options. */

@@ -72,6 +72,7 @@ class ns_options(ctypes.Structure):
         ("fp64_slices_early", ctypes.c_int),
         ("pow_bf16", ctypes.c_int),
         ("tf32_rung", ctypes.c_int),
+        ("fp64_slices_pow", ctypes.c_int),
         ("batch_fused", ctypes.c_int),
     ]
 
@@ -98,6 +99,7 @@ class ns_stats(ctypes.Structure):
         ("wall_ms", ctypes.c_double),
         ("final_frob", ctypes.c_double),
         ("tc_gemm_alg_flops", ctypes.c_double),
+        ("slice_pair_flops", ctypes.c_double),
     ]
 
     def frob_history(self) -> list[float]:

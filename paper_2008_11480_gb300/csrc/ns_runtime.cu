@@ -531,6 +531,7 @@ ns_status oz_gemm(ns_ctx* ctx, const double* L, const double* R, double s, const
   if (ctx->st) {
     ctx->st->gemm_launches++;
     ctx->st->gemm_flops += 2.0 * n * static_cast<double>(n) * n;
+    ctx->st->slice_pair_flops += 2.0 * n * static_cast<double>(n) * n * (ns * (ns + 1) / 2);
   }
   return NS_OK;
 }
@@ -800,9 +801,19 @@ ns_status f64_chain(ns_ctx* ctx, const double* Gin, double* Gout, int order) {
     double* po = ctx->P64[j & 1];
     NS_TRY(f64_gemm(ctx, Xc, Pc, 1.0, Xc, 1.0, 0.0, xo, nullptr));
     if (!last) {
-      if (ctx->opt.pow_mode == 0)
-        NS_TRY(f64_gemm(ctx, Pc, Pc, 1.0, nullptr, 0.0, 0.0, po, nullptr));
-      else
+      if (ctx->opt.pow_mode == 0) {
+        // option fp64_slices_pow: the power in fewer digits.  Its error reaches
+        // F_{k+1} through A X_j (~I) unamplified, as ~eps |P_j|^2, where an
+        // error of X_j P_j is amplified by ||A|| ||X_j|| ~ kappa
+        const int saved = ctx->oz_now;
+        if (ctx->opt.fp64_slices > 0 && ctx->opt.fp64_slices_pow > 0) {
+          const int cur = saved > 0 ? saved : ctx->opt.fp64_slices;
+          ctx->oz_now = std::min(cur, ctx->opt.fp64_slices_pow);
+        }
+        const ns_status r = f64_gemm(ctx, Pc, Pc, 1.0, nullptr, 0.0, 0.0, po, nullptr);
+        ctx->oz_now = saved;
+        NS_TRY(r);
+      } else
         NS_TRY(f64_gemm(ctx, ctx->Astage, xo, -1.0, nullptr, 0.0, 1.0, po, nullptr));
     }
     Xc = xo;
@@ -1622,6 +1633,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.gemm_cluster != 0 && o.gemm_cluster != 1 && o.gemm_cluster != -2) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
+  if (o.fp64_slices_pow < 0 || o.fp64_slices_pow == 1 || o.fp64_slices_pow > kOzMaxSlices) return NS_ERR_ARG;
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state
