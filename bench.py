@@ -229,7 +229,7 @@ def run_reference(a):
 # ------------------------------------------------------------------ the Gram system (default workload)
 # Least-squares Gram system of the metric's largest single-GPU configuration:
 # n = 16384, A = X^T X with cond(A) = 1e6, b = X^T y, order 8 factorized.
-GRAM_SIGMA_LO, GRAM_SEED, GRAM_ORDER, GRAM_SLICES = 1e-3, 5, 8, 4
+GRAM_SIGMA_LO, GRAM_SEED, GRAM_ORDER, GRAM_SLICES, GRAM_SLICES_POW = 1e-3, 5, 8, 4, 2
 
 
 def gram_config(a):
@@ -240,9 +240,11 @@ def gram_config(a):
         "n": n, "kappa": 1e6, "nrhs": 1, "order": GRAM_ORDER, "form": "factorized (I+F)(I+F^2)(I+F^4)",
         "precision": "auto: bf16 products while ||F||_F falls, then bf16x3 (f32 accumulate); where the binary32 "
                      "masters stop contracting, the FP64 path with 4-digit slice products (bf16 tensor cores, "
-                     "exact integer accumulation) from the last contracting G; FP64 residual and Richardson",
+                     "exact integer accumulation; the powers F^(2^(j+1)) of a step in 2 digits) from the last "
+                     "contracting G; FP64 residual and Richardson",
         "tol": 1e-10, "l2": "inputs larger than L2 (A: 2 GiB FP64); 512 MiB written between timed steps",
-        "seed": GRAM_SEED, "couple_frob": a.couple, "fp64_slices": GRAM_SLICES}
+        "seed": GRAM_SEED, "couple_frob": a.couple, "fp64_slices": GRAM_SLICES, "fp64_slices_early": 0,
+        "fp64_slices_pow": GRAM_SLICES_POW}
 
 
 def plain_fp64_model(n, seed=GRAM_SEED, order=GRAM_ORDER, stop=0.02, tol=1e-10):
@@ -346,7 +348,8 @@ def run_gram(a):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    opts = dict(order=GRAM_ORDER, stream=stream, couple_frob=a.couple, fp64_slices=GRAM_SLICES, fp64_slices_early=0)
+    opts = dict(order=GRAM_ORDER, stream=stream, couple_frob=a.couple, fp64_slices=GRAM_SLICES, fp64_slices_early=0,
+                fp64_slices_pow=GRAM_SLICES_POW)
     ctx = nsgb.Context(n, profile=1, **opts)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
@@ -853,9 +856,14 @@ def run_batched(a):
     clocks = sampler.stop()
     import oracle as O
     worst = 0.0
+    kap_conv, kap_fail = [], []
     for p, t, i in zip(probs, outs, range(len(probs))):
+        kap = float(np.linalg.cond(p.A))  # reported beside each outcome (outside the timed region)
         if bt.result(i)["status"] == nsgb.NS_OK:
             worst = max(worst, float(np.max(O.rel_residual(p.A, t.cpu().numpy(), p.B))))
+            kap_conv.append(kap)
+        else:
+            kap_fail.append(kap)
     if world > 1:
         dist.barrier()
     pk, pk_kind = peaks()
@@ -899,6 +907,10 @@ def run_batched(a):
         "instances": a.count, "converged_per_step": conv_all / a.steps,
         "not_converged_per_step": a.count - conv_all / a.steps,
         "worst_verified_rel_res_of_converged": worst, "passes": st.passes,
+        "kappa": {"converged_max": max(kap_conv) if kap_conv else None,
+                  "not_converged_min": min(kap_fail) if kap_fail else None,
+                  "not_converged_median": float(np.median(kap_fail)) if kap_fail else None,
+                  "not_converged_count": len(kap_fail), "how": "numpy cond(A) of this rank's systems"},
         "gemm_launches_per_step": st.gemm_launches, "kernel_launches_per_step": st.kernel_launches,
         "gpu_launches": int(st.kernel_launches) * a.steps, "fused": int(st.fused),
         "host_syncs_per_step": 1 if st.fused else int(st.passes), "roofline": roof,

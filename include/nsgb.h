@@ -106,7 +106,14 @@ typedef struct ns_options {
                           (S^{-1}D)^{gamma_k} of eq. riem6; theta starts at L_0 b unless
                           Theta0 is given.  Needs rates = {order} and aux_ahead = 1 (the
                           double NS method); ns_create returns NS_ERR_ARG otherwise.  omega_k r
-                          is applied as u = X_k r, u += L_k (r - A u) without forming omega_k. */
+                          is applied as u = X_k r, u += L_k (r - A u) without forming omega_k.
+                          2: the same iterates by the recursive schedule of Section 6.2 (eqs.
+                          redttk1, redttk2, gkrecu1): omega_k is formed as a matrix (one product),
+                          Q = sum_{j<n} Gamma^j from Gamma = Gamma_k^n (factorized for orders 2^m,
+                          else Horner), then G_{k+1} = Q (omega_k - SG_k) + SG_k and L_{k+1} =
+                          Q L_k in one grouped launch, Gamma_{k+1}^n = I - L_{k+1} A; theta +=
+                          omega_k r is one pass over omega_k (cheaper for many right-hand sides).
+                          Other values: NS_ERR_ARG. */
   int g0_order;         /* 0 or 1: G0 = S^{-1} (g0_mode); h = 2..19: the initial series of Section 3
                           (eq. g01), G0 = {sum_{j<h} (S^{-1}D)^j} S^{-1}, by one tool-kit step of
                           order h from S^{-1} (bf16x3 products on the mixed path) */

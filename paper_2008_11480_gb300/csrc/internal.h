@@ -208,6 +208,11 @@ cudaError_t launch_axpy_theta(double* Th, const double* U, int n, int nrhs, floa
                               cudaStream_t s);
 cudaError_t launch_add_split(float* a32, const float* b32, bf16* hi, bf16* lo, int n, int64_t ld, cudaStream_t s);
 cudaError_t launch_add_f64(double* a, const double* b, int n, int64_t ld, cudaStream_t s);
+// D = a + cb b + cd I (b may be null); the split form also writes D's bf16 hi / lo
+cudaError_t launch_lin_split(float* d32, bf16* hi, bf16* lo, const float* a32, const float* b32, float cb, float cd,
+                             int n, int64_t ld, cudaStream_t s);
+cudaError_t launch_lin_f64(double* d, const double* a, const double* b, double cb, double cd, int n, int64_t ld,
+                           cudaStream_t s);
 // R = B - A theta from the limbs; R (FP64, n x nrhs), R32T (f32, per rhs), partial R^2
 // (resid_x2_blocks(n) blocks x nrhs partials).
 int resid_x2_blocks(int n);

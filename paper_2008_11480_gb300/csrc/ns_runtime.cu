@@ -109,15 +109,18 @@ struct ns_ctx {
   bool comp_ready = false;
   std::vector<MpMat> T[2];  // per rate, ping-pong
   MpMat Gam, Tc[2], Pre[2], Xs[2];
+  MpMat Om;  // omega_k of the recursive accelerated Richardson (accel_richardson = 2)
   // fp64
   bool f64_ready = false;
   // FP64-accurate tensor-core products (option fp64_slices): integer bf16
   // slices of both operands, their scales and column sums of squares
   void* oz_work = nullptr;  // slices, scales and level planes of one product (oz_workspace_bytes)
   int oz_now = 0;  // slices of the current product (fewer while ||F_k||_F >= 1)
+  bool oz_pow_full = false;  // the powers' reduced digits (fp64_slices_pow) withdrawn for this solve
   double *G64[2] = {nullptr, nullptr}, *X64[2] = {nullptr, nullptr}, *F64 = nullptr, *P64[2] = {nullptr, nullptr};
   std::vector<double*> T64[2];
   double *Gam64 = nullptr, *Tc64[2] = {nullptr, nullptr}, *Pre64[2] = {nullptr, nullptr}, *Xs64[2] = {nullptr, nullptr};
+  double* Om64 = nullptr;
 
   // per-call accounting
   std::vector<EventPair> evs;
@@ -254,6 +257,9 @@ ns_status ensure_f64(ns_ctx* ctx) {
 ns_status ensure_composite(ns_ctx* ctx, bool fp64) {
   const size_t w = ctx->rates.size();
   if (w == 0) return NS_OK;
+  // the recursive omega_k schedule keeps f32 masters of Gamma^n and of
+  // omega_k - SG_k (their sums with I and differences are formed elementwise)
+  const bool rec = ctx->opt.accel_richardson == 2;
   const size_t cnt = static_cast<size_t>(ctx->n) * ctx->ld;
   if (fp64) {
     if (!ctx->T64[0].empty()) return NS_OK;
@@ -265,6 +271,7 @@ ns_status ensure_composite(ns_ctx* ctx, bool fp64) {
       NS_TRY(alloc(ctx, &ctx->Xs64[b], cnt));
     }
     NS_TRY(alloc(ctx, &ctx->Gam64, cnt));
+    if (rec) NS_TRY(alloc(ctx, &ctx->Om64, cnt));
     return NS_OK;
   }
   if (ctx->comp_ready) return NS_OK;
@@ -272,10 +279,11 @@ ns_status ensure_composite(ns_ctx* ctx, bool fp64) {
     ctx->T[b].assign(w, MpMat());
     for (size_t i = 0; i < w; ++i) NS_TRY(alloc_mp(ctx, ctx->T[b][i], true));
     NS_TRY(alloc_mp(ctx, ctx->Tc[b], true));
-    NS_TRY(alloc_mp(ctx, ctx->Pre[b], false));
+    NS_TRY(alloc_mp(ctx, ctx->Pre[b], rec));
     NS_TRY(alloc_mp(ctx, ctx->Xs[b], true));
   }
-  NS_TRY(alloc_mp(ctx, ctx->Gam, false));
+  NS_TRY(alloc_mp(ctx, ctx->Gam, rec));
+  if (rec) NS_TRY(alloc_mp(ctx, ctx->Om, true));
   ctx->comp_ready = true;
   return NS_OK;
 }
@@ -806,7 +814,7 @@ ns_status f64_chain(ns_ctx* ctx, const double* Gin, double* Gout, int order) {
         // F_{k+1} through A X_j (~I) unamplified, as ~eps |P_j|^2, where an
         // error of X_j P_j is amplified by ||A|| ||X_j|| ~ kappa
         const int saved = ctx->oz_now;
-        if (ctx->opt.fp64_slices > 0 && ctx->opt.fp64_slices_pow > 0) {
+        if (ctx->opt.fp64_slices > 0 && ctx->opt.fp64_slices_pow > 0 && !ctx->oz_pow_full) {
           const int cur = saved > 0 ? saved : ctx->opt.fp64_slices;
           ctx->oz_now = std::min(cur, ctx->opt.fp64_slices_pow);
         }
@@ -963,6 +971,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   const int oz_full = fp64 ? ctx->opt.fp64_slices : 0;
   const int oz_early = ctx->opt.fp64_slices_early > 0 ? ctx->opt.fp64_slices_early : oz_full;
   ctx->oz_now = oz_full > oz_early ? oz_early : oz_full;
+  ctx->oz_pow_full = false;
+  // reduced digits still in use somewhere in the step: its count, or its powers'
+  auto oz_reduced = [&]() {
+    return ctx->oz_now < oz_full ||
+           (oz_full > 0 && ctx->opt.fp64_slices_pow > 0 && ctx->opt.fp64_slices_pow < oz_full && !ctx->oz_pow_full);
+  };
 
   // Section 3, eq. g01: an initial series of order g0_order from S^{-1},
   // G0 = {sum_{j<h} (S^{-1} D)^j} S^{-1}, is one tool-kit step of order h from
@@ -1055,6 +1069,18 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     aux_steps++;
   }
   const bool accel = richardson && ctx->opt.accel_richardson != 0;
+  // accel_richardson = 2: the recursive omega_k schedule of Section 6.2.
+  // Gamma^n belongs to its L: Pre[c] = I - T[c] A, set here for L_0
+  const bool rec = accel && ctx->opt.accel_richardson == 2;
+  if (rec) {
+    const int cc = S.ccur;
+    if (fp64) {
+      NS_TRY(f64_gemm(ctx, ctx->T64[cc][0], ctx->Astage, -1.0, nullptr, 0.0, 1.0, ctx->Pre64[cc], nullptr));
+    } else {
+      GemmSpec g{&ctx->T[cc][0], &ctx->A, -1.f, nullptr, 0.f, 1.f, &ctx->Pre[cc], true, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, prec));
+    }
+  }
   if (accel) {
     // workspace of omega_k r, and theta_0 = L_0 b (Section 6) unless given
     if (ctx->acc_cap < S.nrhs) {
@@ -1077,6 +1103,105 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
     }
   }
 
+  // One step of the recursive omega_k schedule (Section 6.2), G_k = G[cur],
+  // L_k = T[ccur], Gamma_k^n = Pre[ccur], F_k formed:
+  //   SG_k      = {sum_{j<n} F_k^j} G_k                 (the NS step of G_k)
+  //   omega_k   = L_k + Gamma_k^n SG_k                  (eq. redttk2; applied to
+  //                                                      theta after this step)
+  //   Q         = sum_{j<n} Gamma^j, Gamma = Gamma_k^n  (both parts start here)
+  //   G_{k+1}   = Q (omega_k - SG_k) + SG_k             (eq. gkrecu1, part 1)
+  //   L_{k+1}   = Q L_k,  Gamma_{k+1}^n = I - L_{k+1} A (eqs. lkk1, gamk21, part 2)
+  // Q is formed explicitly: I + Gamma, then the factorized levels
+  // Q <- Q + Q P, P <- P P (order 2^m; 2(m - 1) products), else Horner
+  // Q <- Gamma Q + I (n - 2 products).  The products of the two parts that
+  // share Q run as one grouped launch.
+  auto rec_update = [&](int p) -> ns_status {
+    const int nx = S.cur ^ 1, cc = S.ccur, nc = cc ^ 1;
+    const int order = ctx->order;
+    int levels = 0;
+    while ((1 << levels) < order) ++levels;
+    const bool factorized = (1 << levels) == order && ctx->opt.form != 1;
+    if (fp64) {
+      NS_TRY(f64_chain(ctx, ctx->G64[S.cur], ctx->Xs64[0], order));
+      NS_TRY(f64_gemm(ctx, ctx->Pre64[cc], ctx->Xs64[0], 1.0, ctx->T64[cc][0], 1.0, 0.0, ctx->Om64, nullptr));
+      NS_CK(launch_lin_f64(ctx->Gam64, ctx->Om64, ctx->Xs64[0], -1.0, 0.0, n, ld, s));
+      const double* Gm = ctx->Pre64[cc];
+      NS_CK(launch_lin_f64(ctx->Tc64[0], Gm, nullptr, 0.0, 1.0, n, ld, s));
+      ctx->launches += 2;
+      const double* Q = ctx->Tc64[0];
+      if (factorized && levels > 1) {
+        NS_TRY(f64_gemm(ctx, Gm, Gm, 1.0, nullptr, 0.0, 0.0, ctx->P64[0], nullptr));
+        const double* Pc = ctx->P64[0];
+        for (int j = 1; j < levels; ++j) {
+          double* qn = ctx->Tc64[j & 1];
+          NS_TRY(f64_gemm(ctx, Q, Pc, 1.0, Q, 1.0, 0.0, qn, nullptr));
+          if (j + 1 < levels) {
+            NS_TRY(f64_gemm(ctx, Pc, Pc, 1.0, nullptr, 0.0, 0.0, ctx->P64[j & 1], nullptr));
+            Pc = ctx->P64[j & 1];
+          }
+          Q = qn;
+        }
+      } else if (!factorized) {
+        for (int i = 2; i < order; ++i) {
+          double* qn = ctx->Tc64[(i - 1) & 1];
+          NS_TRY(f64_gemm(ctx, Gm, Q, 1.0, nullptr, 0.0, 1.0, qn, nullptr));
+          Q = qn;
+        }
+      }
+      NS_TRY(f64_gemm(ctx, Q, ctx->Gam64, 1.0, ctx->Xs64[0], 1.0, 0.0, ctx->G64[nx], nullptr));
+      NS_TRY(f64_gemm(ctx, Q, ctx->T64[cc][0], 1.0, nullptr, 0.0, 0.0, ctx->T64[nc][0], nullptr));
+      NS_TRY(f64_gemm(ctx, ctx->T64[nc][0], ctx->Astage, -1.0, nullptr, 0.0, 1.0, ctx->Pre64[nc], nullptr));
+      S.ccur = nc;
+      return NS_OK;
+    }
+    NS_TRY(mp_chain(ctx, ctx->G[S.cur], ctx->Xs[0], order, p));
+    {
+      GemmSpec g{&ctx->Pre[cc], &ctx->Xs[0], 1.f, ctx->T[cc][0].m32, 1.f, 0.f, &ctx->Om, true, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, p));
+    }
+    MpMat& Gm = ctx->Pre[cc];
+    NS_CK(launch_lin_split(ctx->Gam.m32, ctx->Gam.hi, ctx->Gam.lo, ctx->Om.m32, ctx->Xs[0].m32, -1.f, 0.f, n, ld, s));
+    NS_CK(launch_lin_split(ctx->Tc[0].m32, ctx->Tc[0].hi, ctx->Tc[0].lo, Gm.m32, nullptr, 0.f, 1.f, n, ld, s));
+    ctx->launches += 2;
+    ctx->Gam.t_fresh = ctx->Tc[0].t_fresh = false;
+    const MpMat* Q = &ctx->Tc[0];
+    if (factorized && levels > 1) {
+      {
+        GemmSpec g{&Gm, &Gm, 1.f, nullptr, 0.f, 0.f, &ctx->P[0], false, nullptr};
+        NS_TRY(mp_gemm(ctx, &g, 1, p));
+      }
+      const MpMat* Pc = &ctx->P[0];
+      for (int j = 1; j < levels; ++j) {
+        MpMat* qn = &ctx->Tc[j & 1];
+        GemmSpec gq{Q, Pc, 1.f, Q->m32, 1.f, 0.f, qn, true, nullptr};
+        if (j + 1 < levels) {
+          GemmSpec two[2] = {gq, GemmSpec{Pc, Pc, 1.f, nullptr, 0.f, 0.f, &ctx->P[j & 1], false, nullptr}};
+          NS_TRY(mp_gemm(ctx, two, 2, p));
+          Pc = &ctx->P[j & 1];
+        } else {
+          NS_TRY(mp_gemm(ctx, &gq, 1, p));
+        }
+        Q = qn;
+      }
+    } else if (!factorized) {
+      for (int i = 2; i < order; ++i) {
+        MpMat* qn = &ctx->Tc[(i - 1) & 1];
+        GemmSpec g{&Gm, Q, 1.f, nullptr, 0.f, 1.f, qn, true, nullptr};
+        NS_TRY(mp_gemm(ctx, &g, 1, p));
+        Q = qn;
+      }
+    }
+    {
+      GemmSpec two[2] = {GemmSpec{Q, &ctx->Gam, 1.f, ctx->Xs[0].m32, 1.f, 0.f, &ctx->G[nx], true, nullptr},
+                         GemmSpec{Q, &ctx->T[cc][0], 1.f, nullptr, 0.f, 0.f, &ctx->T[nc][0], true, nullptr}};
+      NS_TRY(mp_gemm(ctx, two, 2, p));
+      GemmSpec g{&ctx->T[nc][0], &ctx->A, -1.f, nullptr, 0.f, 1.f, &ctx->Pre[nc], true, nullptr};
+      NS_TRY(mp_gemm(ctx, &g, 1, p));
+    }
+    S.ccur = nc;
+    return NS_OK;
+  };
+
   // G_{k+1} = T_c + Gamma_c X with X the NS step of G_k (eq. gkgen1); the
   // plain NS product chain when there are no rates.
   auto ns_update = [&](int p) -> ns_status {
@@ -1085,6 +1210,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       if (fp64) return f64_chain(ctx, ctx->G64[S.cur], ctx->G64[nx], ctx->order);
       return mp_chain(ctx, ctx->G[S.cur], ctx->G[nx], ctx->order, p);
     }
+    if (rec) return rec_update(p);
     // the main chain consumes the F of G_k, so it runs before the auxiliary
     // loops reuse the F workspace
     if (fp64)
@@ -1253,13 +1379,14 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         goto recompute_F;
       }
       if (frob > 2.0 * sqrt_n + 1.0 && frob > 2.0 * prev_frob) {
-        if (fp64 && ctx->oz_now < oz_full && done > 0) {
+        if (fp64 && oz_reduced() && done > 0) {
           // the reduced slice count threw the step out of the contraction
           // region: back to G_{k-1}, full slices from there
           S.cur ^= 1;
           done--;
           if (st) st->rollbacks++;
           ctx->oz_now = oz_full;
+          ctx->oz_pow_full = true;
           prev_frob = INFINITY;
           prev_ratio = INFINITY;
           goto recompute_F;
@@ -1337,7 +1464,9 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           }
         }
         if (floor_hit && ctx->oz_now < oz_full) {
-          // the floor of the reduced slice count: full slices from G_k on
+          // the floor of the reduced slice count: full slices from G_k on.
+          // (Reduced digits of the powers stay: their error does not set the
+          // floor, and at the floor the sweeps take over.)
           if (frob > prev_frob) {
             S.cur ^= 1;
             done--;
@@ -1378,7 +1507,15 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
         // advance; the first step only sets up the state (theta_0 = L_0 b)
         if (done > 0) {
           NS_TRY(join_streams(ctx, s, rs));
-          NS_TRY(accel_update(S.ccur ^ 1));
+          if (rec) {  // omega_k formed by the step: one update theta += omega_k r
+            if (fp64)
+              NS_CK(launch_update_f64(ctx->Om64, ld, ctx->Rd, S.Th, n, S.nrhs, rs));
+            else
+              NS_CK(launch_update_x2(ctx->Om.m32, ld, ctx->R32T, ld, S.Th, ctx->T1, ctx->T2, n, S.nrhs, rs));
+            ctx->launches += (S.nrhs + 7) / 8;
+          } else {
+            NS_TRY(accel_update(S.ccur ^ 1));
+          }
           if (st) st->sweeps++;
         }
       } else if (rich) {
@@ -1637,6 +1774,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   for (int i = 0; i < n_rates; ++i)
     if (rates[i] < 1 || (rates[i] > 1 && !order_ok(rates[i], o.form))) return NS_ERR_ARG;
   // accelerated Richardson runs on the double Newton-Schulz state
+  if (o.accel_richardson < 0 || o.accel_richardson > 2) return NS_ERR_ARG;
   if (o.accel_richardson && (n_rates != 1 || rates[0] != order || !o.aux_ahead)) return NS_ERR_ARG;
   ns_ctx* c = new ns_ctx();
   c->n = n;

@@ -767,6 +767,41 @@ __global__ void k_add_f64(double* __restrict__ a, const double* __restrict__ b, 
   }
 }
 
+// D = a + cb b + cd I over n x n (leading dimension ld; b may be null): the
+// matrix sums of the recursive omega_k schedule (Section 6.2: omega_k - SG_k,
+// and I + Gamma), f32 master with its bf16 hi / lo split, and in FP64.
+__global__ void k_lin_split(float* __restrict__ d32, bf16* __restrict__ hi, bf16* __restrict__ lo,
+                            const float* __restrict__ a32, const float* __restrict__ b32, float cb, float cd, int n,
+                            int64_t ld) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const int64_t o = i * ld + j;
+    float v = a32[o];
+    if (b32 != nullptr) v = fmaf(cb, b32[o], v);
+    if (i == j) v += cd;
+    d32[o] = v;
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[o] = h;
+    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+__global__ void k_lin_f64(double* __restrict__ d, const double* __restrict__ a, const double* __restrict__ b,
+                          double cb, double cd, int n, int64_t ld) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const int64_t o = i * ld + j;
+    double v = a[o];
+    if (b != nullptr) v = fma(cb, b[o], v);
+    if (i == j) v += cd;
+    d[o] = v;
+  }
+}
+
 // Theta += U (n x nrhs, row-major FP64); with T1 non-null also the f32 limbs
 // of the new theta (T1/T2[c][k], leading dimension ldt).
 __global__ void k_axpy_theta(double* __restrict__ Th, const double* __restrict__ U, int n, int nrhs,
@@ -1039,6 +1074,22 @@ cudaError_t launch_add_split(float* a32, const float* b32, bf16* hi, bf16* lo, i
   const int64_t total = static_cast<int64_t>(n) * n;
   if (total <= 0) return cudaSuccess;
   k_add_split<<<ew_grid(total), 256, 0, s>>>(a32, b32, hi, lo, n, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lin_split(float* d32, bf16* hi, bf16* lo, const float* a32, const float* b32, float cb, float cd,
+                             int n, int64_t ld, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_lin_split<<<ew_grid(total), 256, 0, s>>>(d32, hi, lo, a32, b32, cb, cd, n, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lin_f64(double* d, const double* a, const double* b, double cb, double cd, int n, int64_t ld,
+                           cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  if (total <= 0) return cudaSuccess;
+  k_lin_f64<<<ew_grid(total), 256, 0, s>>>(d, a, b, cb, cd, n, ld);
   return cudaGetLastError();
 }
 

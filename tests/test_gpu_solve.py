@@ -255,11 +255,61 @@ def test_fp64_accelerated_richardson_matches_oracle(n_order, K):
     assert r.stats.sweeps == K
 
 
+@pytest.mark.parametrize("n_order,K", [(2, 2), (2, 3), (3, 2), (4, 2), (8, 2)])
+def test_fp64_recursive_omega_matches_oracle(n_order, K):
+    """accel_richardson = 2, the recursive schedule of Section 6.2: omega_k
+    formed as a matrix (eq. redttk2), G_{k+1} from omega_k by eq. gkrecu1, L
+    and Gamma^n from the same Q = sum_{j<n} Gamma^j (eqs. lkk1, gamk21), and
+    theta_k = theta_{k-1} - omega_k (A theta_{k-1} - b) (eq. redttk1).  The
+    iterate equals the oracle's recursion (``omega_recursive``, Horner applied
+    to each matrix) and follows the error law of eq. riem6."""
+    n = 40
+    p = make_spd(n, 20.0, nrhs=2, seed=16)
+    a = O.alpha_frobenius(p.A)
+    st = O.double_ns_init(p.A, a * np.eye(n), n_order)
+    theta = st.L @ p.B
+    tstar = np.linalg.solve(p.A, p.B)
+    t0 = theta - tstar
+    SG = O.ns_classical_step(st.G, p.A, n_order)
+    omega = st.L + st.GamN @ SG
+    GamN, L = st.GamN, st.L
+    for _ in range(K):
+        omega, SG, GamN, L, _G = O.omega_recursive(p.A, omega, SG, GamN, L, n_order)
+        theta = theta - omega @ (p.A @ theta - p.B)
+    with nsgb.Context(n, order=n_order, rates=(n_order,), precision=nsgb.NS_FP64, ns_stop=0, max_sweeps=0,
+                      aux_ahead=1, accel_richardson=2) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=K + 1, tol=0.0)
+    got = r.theta.cpu().numpy()
+    assert rel(got, theta) <= 1e-12
+    g = int(O.accelerated_richardson_exponent(n_order, 1, K))
+    Fg = (p.Q * (1 - a * p.lam) ** g) @ p.Q.T
+    assert np.linalg.norm((got - tstar) - Fg @ t0) <= 1e-11 * max(1.0, np.linalg.norm(t0))
+    assert r.stats.sweeps == K
+
+
+@pytest.mark.parametrize("n,order,kappa,form", [(300, 4, 1e3, 0), (1000, 8, 1e4, 0), (500, 3, 1e3, 0),
+                                                 (400, 4, 1e3, 1)])
+def test_mixed_recursive_omega_reaches_tolerance(n, order, kappa, form):
+    """The recursive omega_k schedule on the tensor-core path (AUTO precision;
+    factorized Q for orders 2^m, Horner otherwise and for form 1) reaches
+    1e-10, verified in FP64, with theta against the closed form."""
+    p = make_spd(n, kappa, nrhs=3, seed=17)
+    with nsgb.Context(n, order=order, rates=(order,), aux_ahead=1, accel_richardson=2, form=form) as ctx:
+        r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=1e-10)
+    assert r.status == nsgb.NS_OK, r.stats.res_history()
+    th = r.theta.cpu().numpy()
+    assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    assert rel(th, tstar) <= 10 * kappa * 1e-10
+
+
 def test_accelerated_richardson_needs_double_ns():
     with pytest.raises(nsgb.NSError):
         nsgb.Context(32, order=4, precision=nsgb.NS_FP64, accel_richardson=1)
     with pytest.raises(nsgb.NSError):
         nsgb.Context(32, order=4, rates=(4,), precision=nsgb.NS_FP64, accel_richardson=1)  # aux_ahead = 0
+    with pytest.raises(nsgb.NSError):
+        nsgb.Context(32, order=4, rates=(4,), precision=nsgb.NS_FP64, aux_ahead=1, accel_richardson=3)
 
 
 def test_mixed_accelerated_richardson_reaches_tolerance():
@@ -436,6 +486,55 @@ def test_auto_hands_over_to_slice_products():
     assert r.status == nsgb.NS_OK, r.stats.res_history()
     assert nsgb.NS_FP64 in r.stats.prec_history() and nsgb.NS_BF16 in r.stats.prec_history()
     assert float(np.max(O.rel_residual(p.A, r.theta.cpu().numpy(), p.B))) <= 1.1 * tol
+
+
+def test_slice_powers_in_fewer_digits():
+    """Option fp64_slices_pow: the powers F^{2^{j+1}} of a factorized step in 3
+    or 2 digits on the FP64 path with 7-digit slice products (kappa = 1e8,
+    n = 1024, order 8).  The solve reaches the tolerance in as many steps
+    (within one) as with full-digit powers, theta matches the closed form, and
+    the executed digit-pair work falls."""
+    n, kappa, tol = 1024, 1e8, 1e-7
+    p = make_spd(n, kappa, nrhs=1, seed=21)
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    runs = {}
+    for pw in (0, 3, 2):
+        with nsgb.Context(n, order=8, precision=nsgb.NS_FP64, fp64_slices=7, fp64_slices_early=0,
+                          fp64_slices_pow=pw) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=60, tol=tol)
+        assert r.status == nsgb.NS_OK, (pw, r.stats.res_history())
+        th = r.theta.cpu().numpy()
+        assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1.1 * tol, pw
+        assert rel(th, tstar) <= 10 * kappa * tol, pw
+        runs[pw] = r.stats
+    for pw in (3, 2):
+        assert abs(runs[pw].ns_iters - runs[0].ns_iters) <= 1
+        assert runs[pw].slice_pair_flops < runs[0].slice_pair_flops
+
+
+def test_gram_size_solve_bench_configuration():
+    """The n = 16384 least-squares Gram system (A = V diag(sigma^2) V^T, sigma
+    log-uniform in [1e-3, 1], cond 1e6, b = V (sigma z)) in the launch
+    configuration the benchmark times: AUTO, order 8, couple_frob 1,
+    fp64_slices 4 from the hand-over on (fp64_slices_early 0), the powers in 2
+    digits.  Checked at full size by properties: the library's FP64 residual,
+    the residual recomputed in torch, and theta against the closed form
+    theta* = V (z / sigma)."""
+    from workloads import make_gram_device
+    n = 16384
+    A, B, V, sg, z = make_gram_device(n, 1e-3, seed=5, device=dev, return_factors=True)
+    tstar = V @ (z / sg[:, None])
+    del V
+    torch.cuda.empty_cache()
+    with nsgb.Context(n, order=8, couple_frob=1.0, fp64_slices=4, fp64_slices_early=0, fp64_slices_pow=2) as ctx:
+        r = ctx.solve(A, B, iters=80, tol=1e-10)
+        assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history()[-5:])
+        assert nsgb.NS_FP64 in r.stats.prec_history()
+        assert max(ctx.residual(A, r.theta, B)) <= 1e-10
+    res = torch.linalg.vector_norm(B - A @ r.theta) / torch.linalg.vector_norm(B)
+    assert float(res) <= 1e-10 + 8 * 2.0 ** -53 * 1e6
+    err = torch.linalg.vector_norm(r.theta - tstar) / torch.linalg.vector_norm(tstar)
+    assert float(err) <= 10 * 1e6 * 1e-10
 
 
 def test_bf16x6_rejected_where_not_built():
