@@ -383,14 +383,33 @@ __global__ void k_oz_row_scale(const double* __restrict__ X, int64_t ld, int row
   if (lane == 0) mu[row] = scale_from_maxbits(m);
 }
 
-// One thread per column, rows walked in order (coalesced across the warp).
-__global__ void k_oz_col_scale(const double* __restrict__ X, int64_t ld, int rows, int cols, double* __restrict__ nu) {
+// Column maxima of |X| as bit patterns: 256 consecutive columns per block
+// (each warp reads 256 contiguous bytes of a row), kOzColRows rows per block,
+// one atomicMax per column and block into mb (zeroed before).
+constexpr int kOzColRows = 256;
+__global__ void k_oz_col_maxbits(const double* __restrict__ X, int64_t ld, int rows, int cols,
+                                 unsigned long long* __restrict__ mb) {
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= cols) return;
-  unsigned long long m = 0;
-  const unsigned long long* x = reinterpret_cast<const unsigned long long*>(X);
-  for (int r = 0; r < rows; ++r) m = max(m, x[static_cast<int64_t>(r) * ld + col] & 0x7FFFFFFFFFFFFFFFull);
-  nu[col] = scale_from_maxbits(m);
+  const int r0 = blockIdx.y * kOzColRows;
+  const int r1 = r0 + kOzColRows < rows ? r0 + kOzColRows : rows;
+  const unsigned long long* x = reinterpret_cast<const unsigned long long*>(X) + col;
+  unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  int r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    m0 = max(m0, x[static_cast<int64_t>(r) * ld] & 0x7FFFFFFFFFFFFFFFull);
+    m1 = max(m1, x[static_cast<int64_t>(r + 1) * ld] & 0x7FFFFFFFFFFFFFFFull);
+    m2 = max(m2, x[static_cast<int64_t>(r + 2) * ld] & 0x7FFFFFFFFFFFFFFFull);
+    m3 = max(m3, x[static_cast<int64_t>(r + 3) * ld] & 0x7FFFFFFFFFFFFFFFull);
+  }
+  for (; r < r1; ++r) m0 = max(m0, x[static_cast<int64_t>(r) * ld] & 0x7FFFFFFFFFFFFFFFull);
+  const unsigned long long m = max(max(m0, m1), max(m2, m3));
+  if (m != 0) atomicMax(mb + col, m);
+}
+
+__global__ void k_oz_scale_from_bits(const unsigned long long* __restrict__ mb, int cols, double* __restrict__ nu) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col < cols) nu[col] = scale_from_maxbits(mb[col]);
 }
 
 // Signed digits of y = v / (2 scale) in (-1/2, 1/2): a_t = RN(256 x_{t-1}),
@@ -440,22 +459,35 @@ __device__ __forceinline__ void signed_digits(double v, int scale_exp, int s, in
 }
 
 // s digit slices of X / (2 scale), scale per row (by_row) or per column; slice
-// t at out + t * slice_stride, row-major with leading dimension ldo.
+// t at out + t * slice_stride, row-major with leading dimension ldo (even).
+// Blocks walk rows; each thread cuts two neighbouring columns and stores
+// their digits as one bf16 pair per slice.
 __global__ void k_oz_slice(const double* __restrict__ X, int64_t ld, int rows, int cols,
                            const double* __restrict__ scale, int by_row, int s, bf16* __restrict__ out, int64_t ldo,
                            int64_t slice_stride) {
-  const int64_t total = static_cast<int64_t>(rows) * cols;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t r = e / cols, c = e - r * cols;
-    const double sc = scale[by_row ? r : c];
-    const int se = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
-    int a[kOzMaxSlices];
-    signed_digits(X[r * ld + c], se, s, a);
-    bf16* o = out + r * ldo + c;
+  auto exp_of = [](double sc) {
+    return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(sc)) >> 52) & 0x7FF) - 1023;
+  };
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* xr = X + static_cast<int64_t>(r) * ld;
+    bf16* orow = out + static_cast<int64_t>(r) * ldo;
+    const int er = by_row ? exp_of(scale[r]) : 0;
+    for (int c = 2 * threadIdx.x; c < cols; c += 2 * blockDim.x) {
+      int a0[kOzMaxSlices], a1[kOzMaxSlices];
+      signed_digits(xr[c], by_row ? er : exp_of(scale[c]), s, a0);
+      if (c + 1 < cols) {
+        signed_digits(xr[c + 1], by_row ? er : exp_of(scale[c + 1]), s, a1);
 #pragma unroll
-    for (int t = 0; t < kOzMaxSlices; ++t)
-      if (t < s) o[t * slice_stride] = __float2bfloat16_rn(static_cast<float>(a[t]));
+        for (int t = 0; t < kOzMaxSlices; ++t)
+          if (t < s)
+            *reinterpret_cast<__nv_bfloat162*>(orow + t * slice_stride + c) =
+                __floats2bfloat162_rn(static_cast<float>(a0[t]), static_cast<float>(a1[t]));
+      } else {
+#pragma unroll
+        for (int t = 0; t < kOzMaxSlices; ++t)
+          if (t < s) orow[t * slice_stride + c] = __float2bfloat16_rn(static_cast<float>(a0[t]));
+      }
+    }
   }
 }
 
@@ -465,29 +497,45 @@ __global__ void k_oz_slice(const double* __restrict__ X, int64_t ld, int rows, i
 // Levels 2..min(5, s+1) combine exactly into an int64 a, levels 6..s+1 into b:
 //   sum = a 256^{-dA} + b 256^{-(s+1)},  dA = min(5, s + 1).
 // One block per row band; per-block partial sums of D^2 when frob is set.
-__global__ void k_oz_combine(const int32_t* __restrict__ planes, int64_t ldp, int64_t plane_stride, int slices,
-                             int rows, int cols, const double* __restrict__ mu, const double* __restrict__ nu,
-                             double s, const double* C, int64_t ldc, double beta, double gamma, double* D,
-                             int64_t ldd, double* __restrict__ frob) {
-  const int dA = slices + 1 < 5 ? slices + 1 : 5;
+template <int S>
+__global__ void k_oz_combine(const int32_t* __restrict__ planes, int64_t ldp, int64_t plane_stride, int rows,
+                             int cols, const double* __restrict__ mu, const double* __restrict__ nu, double s,
+                             const double* C, int64_t ldc, double beta, double gamma, double* D, int64_t ldd,
+                             double* __restrict__ frob) {
+  constexpr int dA = S + 1 < 5 ? S + 1 : 5;
   const double wa = s * 4.0 * exp2(-8.0 * dA);
-  const double wb = s * 4.0 * exp2(-8.0 * (slices + 1));
+  const double wb = s * 4.0 * exp2(-8.0 * (S + 1));
+  const bool has_c = beta != 0.0 && C != nullptr;
   double f = 0.0;
+  auto one = [&](int r, int c, const long long a, const long long b, double m) {
+    const double mn = m * nu[c];  // product of two powers of two: exact
+    double base = has_c ? beta * C[static_cast<int64_t>(r) * ldc + c] : 0.0;
+    if (r == c) base += gamma;
+    double v = fma(wa * mn, static_cast<double>(a), base);
+    if (S + 1 >= 6) v = fma(wb * mn, static_cast<double>(b), v);
+    D[static_cast<int64_t>(r) * ldd + c] = v;
+    f = fma(v, v, f);
+  };
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
     const double m = mu[r];
     const int32_t* pr = planes + static_cast<int64_t>(r) * ldp;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-      long long a = 0, b = 0;
-      for (int d = 2; d <= dA; ++d) a += static_cast<long long>(pr[(d - 2) * plane_stride + c]) << (8 * (dA - d));
-      for (int d = 6; d <= slices + 1; ++d)
-        b += static_cast<long long>(pr[(d - 2) * plane_stride + c]) << (8 * (slices + 1 - d));
-      const double mn = m * nu[c];  // product of two powers of two: exact
-      double base = (beta != 0.0 && C != nullptr) ? beta * C[static_cast<int64_t>(r) * ldc + c] : 0.0;
-      if (r == c) base += gamma;
-      double v = fma(wa * mn, static_cast<double>(a), base);
-      if (slices + 1 >= 6) v = fma(wb * mn, static_cast<double>(b), v);
-      D[static_cast<int64_t>(r) * ldd + c] = v;
-      f = fma(v, v, f);
+    for (int c = 2 * threadIdx.x; c < cols; c += 2 * blockDim.x) {
+      // rows of the planes start 16-byte aligned (ldp a multiple of 4) and c is even
+      long long a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+#pragma unroll
+      for (int d = 2; d <= dA; ++d) {
+        const int2 q = *reinterpret_cast<const int2*>(pr + (d - 2) * plane_stride + c);
+        a0 += static_cast<long long>(q.x) << (8 * (dA - d));
+        a1 += static_cast<long long>(q.y) << (8 * (dA - d));
+      }
+#pragma unroll
+      for (int d = 6; d <= S + 1; ++d) {
+        const int2 q = *reinterpret_cast<const int2*>(pr + (d - 2) * plane_stride + c);
+        b0 += static_cast<long long>(q.x) << (8 * (S + 1 - d));
+        b1 += static_cast<long long>(q.y) << (8 * (S + 1 - d));
+      }
+      one(r, c, a0, b0, m);
+      if (c + 1 < cols) one(r, c + 1, a1, b1, m);
     }
   }
   if (frob != nullptr) {
@@ -504,11 +552,30 @@ __global__ void k_oz_combine(const int32_t* __restrict__ planes, int64_t ldp, in
   }
 }
 
-int grid_for(int64_t total) {
-  int64_t g = (total + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  return g < 1 ? 1 : static_cast<int>(g);
+cudaError_t launch_combine(int S, int nb, cudaStream_t st, const int32_t* planes, int64_t ldp, int64_t pstride,
+                           int rows, int cols, const double* mu, const double* nu, double s, const double* C,
+                           int64_t ldc, double beta, double gamma, double* D, int64_t ldd, double* frob) {
+#define NSGB_OZ_COMBINE(K)                                                                                         \
+  case K:                                                                                                          \
+    k_oz_combine<K><<<nb, 256, 0, st>>>(planes, ldp, pstride, rows, cols, mu, nu, s, C, ldc, beta, gamma, D, ldd, \
+                                        frob);                                                                     \
+    break;
+  switch (S) {
+    NSGB_OZ_COMBINE(2)
+    NSGB_OZ_COMBINE(3)
+    NSGB_OZ_COMBINE(4)
+    NSGB_OZ_COMBINE(5)
+    NSGB_OZ_COMBINE(6)
+    NSGB_OZ_COMBINE(7)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef NSGB_OZ_COMBINE
+  return cudaGetLastError();
 }
+
+// blocks of the slicing kernel: one row at a time, at most 16 per SM's worth
+int slice_rows_grid(int rows) { return rows < 1 ? 1 : (rows < 152 * 16 ? rows : 152 * 16); }
 
 cudaError_t launch_levels(const OzParams& p, int num_sms, cudaStream_t s) {
   static int max_clusters = -1;
@@ -556,6 +623,7 @@ size_t oz_workspace_bytes(int64_t M, int64_t N, int64_t K, int slices) {
   add(sizeof(double) * static_cast<size_t>(N));
   add(sizeof(int32_t) * static_cast<size_t>(M) * ldp * slices);
   add(sizeof(double) * static_cast<size_t>(oz_combine_blocks(static_cast<int>(M))));
+  add(sizeof(unsigned long long) * static_cast<size_t>(N));
   return b;
 }
 
@@ -582,6 +650,8 @@ cudaError_t launch_oz_product(const OzArgs& g, int num_sms, cudaStream_t st) {
   double* nu = reinterpret_cast<double*>(carve(sizeof(double) * static_cast<size_t>(N)));
   int32_t* planes = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * static_cast<size_t>(M) * ldp * g.slices));
   double* fparts = reinterpret_cast<double*>(carve(sizeof(double) * static_cast<size_t>(oz_combine_blocks(g.M))));
+  unsigned long long* nub =
+      reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * static_cast<size_t>(N)));
   const int64_t lstride = M * ldk, rstride = kb0 * ldn, pstride = M * ldp;
   cudaError_t e = cudaSuccess;
   for (int64_t k0 = 0; k0 < g.K && e == cudaSuccess; k0 += kOzMaxK) {
@@ -589,10 +659,14 @@ cudaError_t launch_oz_product(const OzArgs& g, int num_sms, cudaStream_t st) {
     const bool first = k0 == 0, last = k0 + kb >= g.K;
     // scales and slices of L[:, k0 : k0 + kb] and R[k0 : k0 + kb, :]
     k_oz_row_scale<<<(g.M + 7) / 8, 256, 0, st>>>(g.L + k0, g.ldl, g.M, kb, mu);
-    k_oz_col_scale<<<(g.N + 255) / 256, 256, 0, st>>>(g.R + k0 * g.ldr, g.ldr, kb, g.N, nu);
-    k_oz_slice<<<grid_for(M * kb), 256, 0, st>>>(g.L + k0, g.ldl, g.M, kb, mu, 1, g.slices, Ls, ldk, lstride);
-    k_oz_slice<<<grid_for(static_cast<int64_t>(kb) * N), 256, 0, st>>>(g.R + k0 * g.ldr, g.ldr, kb, g.N, nu, 0,
-                                                                       g.slices, Rs, ldn, rstride);
+    e = cudaMemsetAsync(nub, 0, sizeof(unsigned long long) * static_cast<size_t>(N), st);
+    if (e != cudaSuccess) break;
+    k_oz_col_maxbits<<<dim3((g.N + 255) / 256, (kb + kOzColRows - 1) / kOzColRows), 256, 0, st>>>(
+        g.R + k0 * g.ldr, g.ldr, kb, g.N, nub);
+    k_oz_scale_from_bits<<<(g.N + 255) / 256, 256, 0, st>>>(nub, g.N, nu);
+    k_oz_slice<<<slice_rows_grid(g.M), 256, 0, st>>>(g.L + k0, g.ldl, g.M, kb, mu, 1, g.slices, Ls, ldk, lstride);
+    k_oz_slice<<<slice_rows_grid(kb), 256, 0, st>>>(g.R + k0 * g.ldr, g.ldr, kb, g.N, nu, 0, g.slices, Rs, ldn,
+                                                    rstride);
     e = cudaGetLastError();
     if (e != cudaSuccess) break;
     OzParams p;
@@ -630,10 +704,9 @@ cudaError_t launch_oz_product(const OzArgs& g, int num_sms, cudaStream_t st) {
     e = launch_levels(p, num_sms, st);
     if (e != cudaSuccess) break;
     const int nb = oz_combine_blocks(g.M);
-    k_oz_combine<<<nb, 256, 0, st>>>(planes, ldp, pstride, g.slices, g.M, g.N, mu, nu, g.s, first ? g.C : g.D,
-                                     first ? g.ldc : g.ldd, first ? g.beta : 1.0, first ? g.gamma : 0.0, g.D, g.ldd,
-                                     last && g.frob_out ? fparts : nullptr);
-    e = cudaGetLastError();
+    e = launch_combine(g.slices, nb, st, planes, ldp, pstride, g.M, g.N, mu, nu, g.s, first ? g.C : g.D,
+                       first ? g.ldc : g.ldd, first ? g.beta : 1.0, first ? g.gamma : 0.0, g.D, g.ldd,
+                       last && g.frob_out ? fparts : nullptr);
     if (e == cudaSuccess && last && g.frob_out) e = launch_reduce_sum(fparts, nb, 1, g.frob_out, st);
   }
   return e;
