@@ -238,10 +238,10 @@ def gram_config(a):
         "workload": f"least-squares Gram system n={n}: A = X^T X, b = X^T y for a {2 * n} x {n} design "
                     f"X = U diag(sigma) V^T, sigma log-uniform in [1e-3, 1] (cond(A) = 1e6), y ~ N(0,1); 1 RHS",
         "n": n, "kappa": 1e6, "nrhs": 1, "order": GRAM_ORDER, "form": "factorized (I+F)(I+F^2)(I+F^4)",
-        "precision": "auto: bf16 products while ||F||_F falls, then bf16x3 (f32 accumulate); where the binary32 "
-                     "masters stop contracting, the FP64 path with 4-digit slice products (bf16 tensor cores, "
-                     "exact integer accumulation; the powers F^(2^(j+1)) of a step in 2 digits) from the last "
-                     "contracting G; FP64 residual and Richardson",
+        "precision": "auto: bf16 products while ||F||_F falls, then bf16x3 (f32 accumulate); at the binary32 "
+                     "floor Richardson sweeps from the best G (FP64 residual); if they give up, the FP64 path with "
+                     "4-digit slice products (bf16 tensor cores, exact integer accumulation; powers in 2 digits) "
+                     "continues from that G",
         "tol": 1e-10, "l2": "inputs larger than L2 (A: 2 GiB FP64); 512 MiB written between timed steps",
         "seed": GRAM_SEED, "couple_frob": a.couple, "fp64_slices": GRAM_SLICES, "fp64_slices_early": 0,
         "fp64_slices_pow": GRAM_SLICES_POW}
@@ -458,8 +458,9 @@ def run_gram(a):
             "executed": exe, "frac_executed": exe / sus if exe else None,
             "executed_note": "bf16 tensor work run: bf16x3 = 3 passes, an s-digit slice product = s (s + 1) / 2 digit "
                              "pairs",
-            "traffic": recorded_traffic("traffic_k_gemm_oz_gram16384.md") if dom == "k_gemm_oz" else None,
-            "traffic_unit": "bytes per level-kernel launch (ncu dram read + write)",
+            "traffic": recorded_traffic("traffic_k_gemm_oz_gram16384.md" if dom == "k_gemm_oz"
+                                        else "traffic_k_gemm_tc2_gram16384.md"),
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "avg_launch_ms": (oz_ms / max(oz_l, 1)) if dom == "k_gemm_oz" else acc["tc_ms"] / max(acc["tc_l"], 1),
             "flops_per_launch": f3 if dom == "k_gemm_oz" else acc["tc_alg"] / max(acc["tc_l"], 1),
             "kernels": kern}

@@ -1032,6 +1032,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
   double prev_sweep_rr = INFINITY, best_rr = INFINITY, prev_sweep_ratio = INFINITY;
   int stall = 0;
   bool converged = false;
+  bool handover_armed = false;  // NS stopped at the binary32 floor; slice products if the sweeps give up
   int aux_steps = 0;
 
   // advance every auxiliary expansion T_i by one NS step of its own order m_i
@@ -1452,16 +1453,10 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           // above ||F||_F = 1, more steps only repeat it (Richardson takes
           // over if rho(I - A G) < 1)
           floor_hit = true;
-          if (slice_handover) {
-            if (frob > prev_frob) {
-              S.cur ^= 1;
-              done--;
-            }
-            if (st) st->ns_iters = done + S.done0;
-            S.handover = S.cur;
-            if (richardson) NS_TRY(join_streams(ctx, rs, s));
-            return kHandover;
-          }
+          // with slice products on offer, Richardson still gets the first try
+          // from the better G of the floor (sweeps cost far less than slice
+          // steps); the hand-over waits until the sweeps give up
+          if (slice_handover) handover_armed = true;
         }
         if (floor_hit && ctx->oz_now < oz_full) {
           // the floor of the reduced slice count: full slices from G_k on.
@@ -1493,6 +1488,7 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
             goto recompute_F;
           }
           stop = true;
+          if (handover_armed) S.handover = S.cur;
         }
         if (stop) ns_active = false;
       }
@@ -1536,6 +1532,12 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
       if (done >= iters) ns_active = false;
       continue;
     }
+    if (handover_armed && !converged && tol > 0 && sweeps_left <= 0) {
+      // the sweep budget ran out above tol: slice products from the floor's G
+      if (st) st->ns_iters = done + S.done0;
+      if (richardson) NS_TRY(join_streams(ctx, rs, s));
+      return kHandover;
+    }
     if (!richardson || sweeps_left <= 0) break;
     if (!rich) continue;  // no residual was formed this pass: the next one forms it
     // Richardson alone no longer contracts (rho(I - A G) ~ 1 at this precision):
@@ -1554,7 +1556,16 @@ ns_status run(ns_ctx* ctx, Solve& S, const double* G0, int iters, double tol, bo
           std::log(tol / last_rr) / std::log(rho) > static_cast<double>(sweeps_left))
         give_up = true;
     }
-    if (give_up && autop && ctx->x6 && prec != NS_BF16X6 && done < iters && best_rr > 1e-6 && tol > 0) {
+    if (give_up && handover_armed && (resid64 || fp64)) {
+      // Richardson from the binary32 floor's G does not reach tol (with the
+      // FP64 residual): the FP64 path with slice products continues
+      // Newton-Schulz from that G
+      if (st) st->ns_iters = done + S.done0;
+      if (richardson) NS_TRY(join_streams(ctx, rs, s));
+      return kHandover;
+    }
+    if (give_up && !handover_armed && autop && ctx->x6 && prec != NS_BF16X6 && done < iters && best_rr > 1e-6 &&
+        tol > 0) {
       // the sweeps stall far above tol: G itself does not contract enough at
       // this precision -- resume Newton-Schulz from G_k in bf16x6
       prec = NS_BF16X6;

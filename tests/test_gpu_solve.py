@@ -517,9 +517,10 @@ def test_gram_size_solve_bench_configuration():
     log-uniform in [1e-3, 1], cond 1e6, b = V (sigma z)) in the launch
     configuration the benchmark times: AUTO, order 8, couple_frob 1,
     fp64_slices 4 from the hand-over on (fp64_slices_early 0), the powers in 2
-    digits.  Checked at full size by properties: the library's FP64 residual,
-    the residual recomputed in torch, and theta against the closed form
-    theta* = V (z / sigma)."""
+    digits; at the binary32 floor Richardson gets the first try, the slice
+    products take over only if its sweeps give up.  Checked at full size by
+    properties: the library's FP64 residual, the residual recomputed in torch,
+    and theta against the closed form theta* = V (z / sigma)."""
     from workloads import make_gram_device
     n = 16384
     A, B, V, sg, z = make_gram_device(n, 1e-3, seed=5, device=dev, return_factors=True)
@@ -529,7 +530,6 @@ def test_gram_size_solve_bench_configuration():
     with nsgb.Context(n, order=8, couple_frob=1.0, fp64_slices=4, fp64_slices_early=0, fp64_slices_pow=2) as ctx:
         r = ctx.solve(A, B, iters=80, tol=1e-10)
         assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history()[-5:])
-        assert nsgb.NS_FP64 in r.stats.prec_history()
         assert max(ctx.residual(A, r.theta, B)) <= 1e-10
     res = torch.linalg.vector_norm(B - A @ r.theta) / torch.linalg.vector_norm(B)
     assert float(res) <= 1e-10 + 8 * 2.0 ** -53 * 1e6
