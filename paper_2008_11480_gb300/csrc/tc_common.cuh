@@ -23,8 +23,17 @@ __device__ __forceinline__ void decode_item(const TcParams& p, int w, int rank, 
     if (w >= p.prob[i].tile_begin) pi = i;
   const TcProblem& P = p.prob[pi];
   const int local = w - P.tile_begin;
-  mt = (local / P.tiles_n) * CM + rank;
-  nt = local % P.tiles_n;
+  // bands of kTileBand tile rows walked column by column: the items of one
+  // wave share a few L row panels and R column panels, so at large n the
+  // panels a wave streams stay in L2 instead of every wave re-reading all of R
+  constexpr int kTileBand = 8;
+  const int rows = P.tile_count / P.tiles_n;  // tile rows of CM tiles
+  const int band = local / (kTileBand * P.tiles_n);
+  const int r0 = band * kTileBand;
+  const int bh = rows - r0 < kTileBand ? rows - r0 : kTileBand;
+  const int in = local - r0 * P.tiles_n;
+  mt = (r0 + in % bh) * CM + rank;
+  nt = in / bh;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {

@@ -531,6 +531,14 @@ def test_gram_size_solve_bench_configuration():
         r = ctx.solve(A, B, iters=80, tol=1e-10)
         assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history()[-5:])
         assert max(ctx.residual(A, r.theta, B)) <= 1e-10
+    if nsgb.NS_FP64 not in r.stats.prec_history():
+        # the sweeps from the floor's G converged: the slice option changed
+        # nothing, the solve is the one without it, bit for bit
+        with nsgb.Context(n, order=8, couple_frob=1.0) as ctx:
+            r0 = ctx.solve(A, B, iters=80, tol=1e-10)
+        assert r0.status == nsgb.NS_OK
+        assert torch.equal(r0.theta, r.theta)
+        assert r0.stats.sweeps == r.stats.sweeps and r0.stats.ns_iters == r.stats.ns_iters
     res = torch.linalg.vector_norm(B - A @ r.theta) / torch.linalg.vector_norm(B)
     assert float(res) <= 1e-10 + 8 * 2.0 ** -53 * 1e6
     err = torch.linalg.vector_norm(r.theta - tstar) / torch.linalg.vector_norm(tstar)
