@@ -30,6 +30,28 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// rows x width bytes between pitched buffers: one linear copy when both
+// pitches equal the width (measured faster than the 2-D form for host
+// sources), else the 2-D copy
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+  if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * rows, kind, s);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, kind, s);
+}
+
+// A (n x n, leading dimension n, host memory) into the device staging buffer
+// (leading dimension ld).  Page-locked host memory is read by a copy kernel
+// through its device mapping: for a 2 GiB A from a page-locked buffer that
+// another runtime allocated, the runtime copy took ~160 ms and the kernel
+// ~8 ms.  Other host memory goes through the runtime copy.
+cudaError_t stage_host_matrix(double* dst, int64_t ld, const double* src, int n, cudaStream_t s) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer != nullptr)
+    return launch_copy_f64(static_cast<const double*>(a.devicePointer), n, n, n, dst, ld, s);
+  cudaGetLastError();
+  return copy_rows(dst, ld * sizeof(double), src, n * sizeof(double), n * sizeof(double), n, cudaMemcpyDefault, s);
+}
+
 // A bf16-split matrix with its f32 master and tensor maps (workspace layout:
 // n x n, leading dimension ld, padding never written and kept zero).
 struct MpMat {
@@ -1858,8 +1880,7 @@ ns_status ns_invert(ns_ctx* ctx, const double* A, const double* G0, int iters, d
   if (r == NS_OK && !is_device_ptr(A)) {
     if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
     if (r == NS_OK) {
-      cudaError_t e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double),
-                                        n * sizeof(double), n, cudaMemcpyDefault, ctx->stream);
+      cudaError_t e = stage_host_matrix(ctx->Astage, ctx->ld, A, n, ctx->stream);
       if (e != cudaSuccess) r = fail(ctx, NS_ERR_CUDA, cudaGetErrorString(e));
     }
     A = ctx->Astage;
@@ -1891,7 +1912,7 @@ ns_status ns_invert(ns_ctx* ctx, const double* A, const double* G0, int iters, d
       if (dev)
         e = launch_copy_f64(ctx->G64[S.cur], ctx->ld, n, n, G_out, n, ctx->stream);
       else
-        e = cudaMemcpy2DAsync(G_out, n * sizeof(double), ctx->G64[S.cur], ctx->ld * sizeof(double),
+        e = copy_rows(G_out, n * sizeof(double), ctx->G64[S.cur], ctx->ld * sizeof(double),
                               n * sizeof(double), n, cudaMemcpyDeviceToHost, ctx->stream);
     } else {
       double* tgt = G_out;
@@ -1925,8 +1946,7 @@ ns_status ns_richardson_solve(ns_ctx* ctx, const double* A, const double* B, int
   if (!is_device_ptr(A)) {
     if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
     if (r != NS_OK) return end_call(ctx, r, t0);
-    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
-                          cudaMemcpyDefault, ctx->stream);
+    e = stage_host_matrix(ctx->Astage, ctx->ld, A, n, ctx->stream);
     A = ctx->Astage;
   }
   const double* Bd = B;
@@ -2020,8 +2040,7 @@ ns_status ns_residual(ns_ctx* ctx, const double* A, const double* Theta, const d
   if (!is_device_ptr(A)) {
     if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
     if (r != NS_OK) return end_call(ctx, r, t0);
-    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
-                          cudaMemcpyDefault, ctx->stream);
+    e = stage_host_matrix(ctx->Astage, ctx->ld, A, n, ctx->stream);
     A = ctx->Astage;
     lda = ctx->ld;
   }
@@ -2066,8 +2085,7 @@ ns_status ns_inverse_residual(ns_ctx* ctx, const double* A, const double* G, int
   if (!is_device_ptr(A)) {
     if (!ctx->Astage) r = alloc(ctx, &ctx->Astage, static_cast<size_t>(n) * ctx->ld);
     if (r != NS_OK) return end_call(ctx, r, t0);
-    e = cudaMemcpy2DAsync(ctx->Astage, ctx->ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
-                          cudaMemcpyDefault, ctx->stream);
+    e = stage_host_matrix(ctx->Astage, ctx->ld, A, n, ctx->stream);
     A = ctx->Astage;
     lda = ctx->ld;
   }
