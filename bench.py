@@ -865,6 +865,32 @@ def run_batched(a):
             kap_conv.append(kap)
         else:
             kap_fail.append(kap)
+    # variant: option fp64_slices = 7, the systems the batch leaves unconverged
+    # solved again alone by the single-system slice hand-over (after the timed
+    # region; one batch, wall-timed)
+    variants = {}
+    if not a.no_variants:
+        bs = nsgb.Batch([p.n for p in probs], [1] * len(probs), order=a.order, stream=stream,
+                        couple_frob=a.couple, batch_fused=a.batch_fused, fp64_slices=7)
+        outs_s = [torch.empty_like(b) for b in Bs]
+        bs.solve(As, Bs, iters=a.iters, tol=1e-10, outs=outs_s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, sts = bs.solve(As, Bs, iters=a.iters, tol=1e-10, outs=outs_s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        worst_s = 0.0
+        for p, t, i in zip(probs, outs_s, range(len(probs))):
+            if bs.result(i)["status"] == nsgb.NS_OK:
+                worst_s = max(worst_s, float(np.max(O.rel_residual(p.A, t.cpu().numpy(), p.B))))
+        variants["slice_handover"] = {
+            "converged": sts.converged, "not_converged": sts.not_converged, "ms_per_batch": wall * 1e3,
+            "retried": sts.slice_retried, "retried_converged": sts.slice_retried_converged,
+            "retry_ms": sts.slice_retry_ms, "worst_verified_rel_res_of_converged": worst_s,
+            "how": "option fp64_slices = 7: each system the batch did not converge solved again alone by the "
+                   "single-system AUTO path with 7-digit slice products (8 host worker threads, one stream "
+                   "each); wall time of one batch, this rank"}
+        bs.close()
     if world > 1:
         dist.barrier()
     pk, pk_kind = peaks()
@@ -915,7 +941,8 @@ def run_batched(a):
         "gemm_launches_per_step": st.gemm_launches, "kernel_launches_per_step": st.kernel_launches,
         "gpu_launches": int(st.kernel_launches) * a.steps, "fused": int(st.fused),
         "host_syncs_per_step": 1 if st.fused else int(st.passes), "roofline": roof,
-        "useful_flops_per_product_level": st.useful_flops_per_product, "clocks": clocks}), flush=True)
+        "useful_flops_per_product_level": st.useful_flops_per_product, "clocks": clocks,
+        "variants": variants}), flush=True)
     bt.close()
 
 

@@ -126,8 +126,13 @@ typedef struct ns_options {
                           products on the bf16 tensor cores from s signed digits of 8 bits per
                           operand (see ns_k_gemm_oz; 7 covers binary64) -- for precision NS_FP64,
                           and with NS_AUTO (no composite rates) for a solve the binary32 masters
-                          cannot finish: after NS_NOT_CONVERGED or divergence the solve starts
-                          over on the FP64 path with these products (from G0 and theta0) */
+                          cannot finish: where bf16x3 leaves the contraction region, or stalls
+                          above ||F||_F = 1 and the Richardson sweeps from its best G then give
+                          up, the FP64 path continues Newton-Schulz from the last contracting G
+                          with these products (theta from theta0); after NS_NOT_CONVERGED or
+                          divergence otherwise it starts over on the FP64 path from G0.
+                          ns_batch_solve: every system the batch did not converge is solved
+                          again alone by that AUTO path (ns_batch_stats.slice_retried) */
   int fp64_slices_early; /* slices of the products while ||F_k||_F >= 1 (their error is corrected
                           by the later steps); the full fp64_slices take over below one or at
                           the reduced count's floor.  Default 4; 0: always fp64_slices */
@@ -277,6 +282,9 @@ typedef struct ns_batch_stats {
   int fused_pad;
   double fused_ms;                  /* duration of that launch (opt.profile = 1), else 0 */
   double useful_flops;              /* fused launch: sum over systems of their products x 2 n^3 */
+  int slice_retried;                /* option fp64_slices: systems solved again alone (slice path) */
+  int slice_retried_converged;      /* ... of which converged */
+  double slice_retry_ms;            /* host wall time of those solves */
 } ns_batch_stats;
 
 /* Create a batch of `count` systems; n[i] in [1, 16384], nrhs[i] in [1, 1024].

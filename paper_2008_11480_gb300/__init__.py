@@ -128,6 +128,9 @@ class ns_batch_stats(ctypes.Structure):
         ("fused_pad", ctypes.c_int),
         ("fused_ms", ctypes.c_double),
         ("useful_flops", ctypes.c_double),
+        ("slice_retried", ctypes.c_int),
+        ("slice_retried_converged", ctypes.c_int),
+        ("slice_retry_ms", ctypes.c_double),
     ]
 
 

@@ -235,6 +235,9 @@ SlotLayout slot_layout(int n, int nrhs, bool copies) {
 }  // namespace
 
 struct ns_batch {
+  // slice hand-over workers: per worker a stream and its single-system contexts (by n)
+  std::vector<std::map<int, ns_ctx*>> retry;
+  std::vector<cudaStream_t> retry_streams;
   int cap = 0;  // slots
   int order = 4, levels = 2, ntypes = 0;
   int max_nrhs = 1, scal_stride = 0;
@@ -1097,6 +1100,9 @@ ns_status init_batch(ns_batch* b, int order, const ns_options* opt) {
 void release_batch(ns_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  for (auto& m : b->retry)
+    for (auto& kv : m) ns_destroy(kv.second);
+  for (cudaStream_t st : b->retry_streams) cudaStreamDestroy(st);
   if (b->pstream) {
     cudaStreamSynchronize(b->pstream);
     cudaStreamDestroy(b->pstream);
@@ -1201,6 +1207,115 @@ ns_status ns_batch_set_stream(ns_batch* b, void* stream) {
 
 const char* ns_batch_last_error(const ns_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
+namespace {
+// Option fp64_slices on a batch: every system the batched solve did not
+// converge (the binary32 masters cannot carry it) is solved again alone by the
+// single-system AUTO path with s-digit slice products (its hand-over to the
+// FP64 path from the binary32 floor), from theta = 0.  Each such solve is
+// latency-bound on a few SMs, so kRetryWorkers host threads run them at once,
+// each on its own stream with its own contexts; system k goes to worker
+// k mod kRetryWorkers, and a system's arithmetic does not depend on which
+// systems run beside it.  Its outcome replaces the batched one; ns_iters and
+// sweeps add up both attempts.
+constexpr int kRetryWorkers = 8;
+
+ns_status slice_handover(ns_batch* b, const double* const* A, const double* const* B, double* const* Theta, int iters,
+                         double tol, ns_batch_stats* stats) {
+  const auto t0 = Clock::now();
+  std::vector<int> todo;
+  for (int i = 0; i < b->fixed_count; ++i) {
+    const InstState& s = b->st[i];
+    if (!s.converged && (s.status == NS_NOT_CONVERGED || s.status == NS_ERR_DIVERGED)) todo.push_back(i);
+  }
+  const int nw = std::min<int>(kRetryWorkers, static_cast<int>(todo.size()));
+  if ((int)b->retry.size() < nw) b->retry.resize(nw);
+  while ((int)b->retry_streams.size() < nw) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, NS_ERR_CUDA, "slice hand-over: stream");
+    }
+    b->retry_streams.push_back(st);
+  }
+  std::vector<ns_status> werr(nw, NS_OK);
+  std::vector<std::string> wmsg(nw);
+  std::vector<ns_status> out(todo.size(), NS_NOT_CONVERGED);
+  std::vector<int> out_ns(todo.size(), 0), out_sw(todo.size(), 0);
+  std::vector<double> out_rr(todo.size(), INFINITY);
+  auto work = [&](int w) {
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+      werr[w] = NS_ERR_CUDA;
+      return;
+    }
+    for (size_t k = w; k < todo.size(); k += nw) {
+      const int i = todo[k];
+      const int n = b->n[i];
+      auto it = b->retry[w].find(n);
+      if (it == b->retry[w].end()) {
+        ns_options o = b->opt;
+        o.precision = NS_AUTO;
+        o.batch_fused = 0;
+        o.profile = 0;
+        ns_ctx* c = nullptr;
+        const ns_status r = ns_create(n, b->order, nullptr, 0, &o, &c);
+        if (r != NS_OK) {
+          werr[w] = r;
+          wmsg[w] = "slice hand-over: context";
+          return;
+        }
+        ns_set_stream(c, b->retry_streams[w]);
+        it = b->retry[w].emplace(n, c).first;
+      }
+      ns_stats st;
+      const ns_status r = ns_richardson_solve(it->second, A[i], B[i], b->nrhs[i], nullptr, iters, tol, Theta[i], &st);
+      if (r < 0 && r != NS_ERR_DIVERGED && r != NS_ERR_NONFINITE) {
+        werr[w] = r;
+        wmsg[w] = ns_last_error(it->second);
+        return;
+      }
+      out[k] = r;
+      out_ns[k] = st.ns_iters;
+      out_sw[k] = st.sweeps;
+      if (r == NS_OK) {
+        std::vector<double> rr(b->nrhs[i]);
+        if (ns_residual(it->second, A[i], Theta[i], B[i], b->nrhs[i], rr.data()) == NS_OK)
+          out_rr[k] = *std::max_element(rr.begin(), rr.end());
+      }
+      if (cudaStreamSynchronize(b->retry_streams[w]) != cudaSuccess) {
+        werr[w] = NS_ERR_CUDA;
+        wmsg[w] = "slice hand-over: stream";
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nw; ++w) pool.emplace_back(work, w);
+  if (nw > 0) work(0);
+  for (auto& t : pool) t.join();
+  B_CK(cudaSetDevice(b->device));
+  for (int w = 0; w < nw; ++w)
+    if (werr[w] != NS_OK) return bfail(b, werr[w], wmsg[w]);
+  int conv = 0;
+  for (size_t k = 0; k < todo.size(); ++k) {
+    InstState& s = b->st[todo[k]];
+    s.done += out_ns[k];
+    s.sweeps += out_sw[k];
+    s.status = out[k];
+    s.converged = out[k] == NS_OK;
+    if (s.converged) {
+      conv++;
+      s.rel_res = out_rr[k];
+    }
+  }
+  if (stats) {
+    stats->slice_retried = static_cast<int>(todo.size());
+    stats->slice_retried_converged = conv;
+    stats->slice_retry_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+  }
+  return NS_OK;
+}
+}  // namespace
+
 ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* const* B, double* const* Theta,
                          int iters, double tol, ns_batch_stats* stats) {
   if (!b || !A || !B || !Theta || iters < 0 || b->fixed_count <= 0) return NS_ERR_ARG;
@@ -1241,12 +1356,14 @@ ns_status ns_batch_solve(ns_batch* b, const double* const* A, const double* cons
   B_TRY(join(b, b->pstream, b->stream));
   B_CK(cudaStreamSynchronize(b->stream));
   b->stage_used = 0;
-  int nconv = 0, nfail = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int i = 0; i < count; ++i)
     if (!b->st[i].finished) {
       b->st[i].finished = true;
       b->st[i].status = NS_NOT_CONVERGED;
     }
+  if (b->opt.fp64_slices > 0 && tol > 0) B_TRY(slice_handover(b, A, B, Theta, iters, tol, stats));
+  int nconv = 0, nfail = 0;
+  for (int i = 0; i < count; ++i) {
     if (b->st[i].converged)
       nconv++;
     else

@@ -22,6 +22,7 @@
 // accumulator) persist across products.  Every wait is bounded: a CTA whose
 // wait runs out records NS_ERR_TIMEOUT, marks the system and stops taking
 // systems.
+#include <mutex>
 #include <cmath>
 
 #include "../../include/nsgb.h"
@@ -1131,12 +1132,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bsolve(const __grid_constant__ 
 }  // namespace
 
 cudaError_t launch_fused_solve(const FusedParams& p, int num_sms, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_bsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] { attr = cudaFuncSetAttribute(k_bsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem); });
+  if (attr != cudaSuccess) return attr;
   if (p.count <= 0) return cudaSuccess;
   const int ctas = p.count < num_sms ? p.count : num_sms;
   k_bsolve<<<ctas, kThreads, kSmem, s>>>(p);

@@ -32,6 +32,7 @@
 // int64 (shifts of at most 24 bits of values below 2^31), so the sum has two
 // roundings to binary64 and one more in the final scaled add; the FP64 work
 // (slow on this part) is a few operations per output element, once.
+#include <mutex>
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -578,7 +579,9 @@ cudaError_t launch_combine(int S, int nb, cudaStream_t st, const int32_t* planes
 int slice_rows_grid(int rows) { return rows < 1 ? 1 : (rows < 152 * 16 ? rows : 152 * 16); }
 
 cudaError_t launch_levels(const OzParams& p, int num_sms, cudaStream_t s) {
-  static int max_clusters = -1;
+  static std::once_flag once;  // attribute and occupancy once, safe from several host threads
+  static int max_clusters = 0;
+  static cudaError_t init = cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -590,18 +593,20 @@ cudaError_t launch_levels(const OzParams& p, int num_sms, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (max_clusters < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(2 * (num_sms / 2));
+  std::call_once(once, [&] {
+    init = cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (init != cudaSuccess) return;
+    cudaLaunchConfig_t c = cfg;
+    c.gridDim = dim3(2 * (num_sms / 2));
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_gemm_oz, &cfg);
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_gemm_oz, &c);
     if (e != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = num_sms / 2;
     }
     max_clusters = n;
-  }
+  });
+  if (init != cudaSuccess) return init;
   if (p.total_items <= 0) return cudaSuccess;
   const int clusters = p.total_items < max_clusters ? p.total_items : max_clusters;
   cfg.gridDim = dim3(2 * clusters);

@@ -32,6 +32,7 @@
 // and issues the 6 products L_hi R_hi, L_hi R_lo, L_lo R_hi of its two K=16
 // slices.  Same bytes per stage as one plain pass, 1.5x the tensor work, so
 // the ring covers 1.5x more load latency and L2 is read 1/3 less per product.
+#include <mutex>
 #include <cstdio>
 
 #include "internal.h"
@@ -323,12 +324,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 template <int BN, bool X3>
 cudaError_t launch_bn(const TcParams& p, int num_sms, cudaStream_t s) {
   using Cfg = TcCfg<BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // once per instantiation, safe from several host threads
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_gemm_tc<BN, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  });
+  if (attr != cudaSuccess) return attr;
   const int ctas = p.total_tiles < num_sms ? p.total_tiles : num_sms;
   if (ctas <= 0) return cudaSuccess;
   k_gemm_tc<BN, X3><<<ctas, kThreads, Cfg::kSmem, s>>>(p);
@@ -369,14 +371,14 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeFn get_encode() {
-  static EncodeFn fn = nullptr;
-  if (fn == nullptr) {
+  static const EncodeFn fn = [] {  // initialised once, safe from several host threads
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(ptr);
-  }
+      return reinterpret_cast<EncodeFn>(ptr);
+    return static_cast<EncodeFn>(nullptr);
+  }();
   return fn;
 }
 }  // namespace

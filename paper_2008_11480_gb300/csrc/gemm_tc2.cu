@@ -37,6 +37,7 @@
 // 32-deep K slice, part p of L (128 x 32, 64-byte swizzle) and of R (32 x 128
 // as two 4 KiB chunks) at p x 8 KiB: 32 KiB per stage and 6 stages for NP = 2,
 // 48 KiB and 4 stages for NP = 3.
+#include <mutex>
 #include <cstdio>
 
 #include "internal.h"
@@ -385,7 +386,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
 template <int NP>
 cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
   constexpr int kSmem = PairCfg<NP>::kSmem;
-  static int max_clusters = -1;
+  static std::once_flag once;  // attribute and occupancy once, safe from several host threads
+  static int max_clusters = 0;
+  static cudaError_t init = cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -397,18 +400,20 @@ cudaError_t launch_pair(const TcParams& p, int num_sms, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (max_clusters < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc2<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(2 * (num_sms / 2));
+  std::call_once(once, [&] {
+    init = cudaFuncSetAttribute(k_gemm_tc2<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (init != cudaSuccess) return;
+    cudaLaunchConfig_t c = cfg;
+    c.gridDim = dim3(2 * (num_sms / 2));
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc2<NP>, &cfg);
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc2<NP>, &c);
     if (e != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = num_sms / 2;
     }
     max_clusters = n;
-  }
+  });
+  if (init != cudaSuccess) return init;
   if (p.total_tiles <= 0) return cudaSuccess;
   TcParams q = p;
   // a last wave of `tail` tiles on `max_clusters` clusters runs as 2 tail

@@ -100,6 +100,35 @@ def test_batch_full_harmonic_workload():
     assert nconv >= 1700
 
 
+def test_batch_slice_handover_harmonic_workload():
+    """Option fp64_slices on a batch: the harmonic systems the batched solve
+    leaves unconverged (cond(A) where binary32 masters stop carrying the
+    iteration; numpy's FP64 LU solves every one of them to ~1e-16) are solved
+    again alone by the single-system AUTO path with slice products.  Systems
+    the batch converged keep their theta bit for bit; every system reported
+    converged has an FP64 residual <= 1e-10 recomputed by the oracle; most of
+    the retried ones converge."""
+    probs = make_harmonic_batch(2048, seed=3)
+    As, Bs = [tens(p.A) for p in probs], [tens(p.B) for p in probs]
+    ns, rhs = [p.n for p in probs], [1] * len(probs)
+    with nsgb.Batch(ns, rhs, order=4, couple_frob=1.0) as bt:
+        outs0, _, st0 = bt.solve(As, Bs, iters=60, tol=1e-10)
+        res0 = [bt.result(i) for i in range(len(probs))]
+    with nsgb.Batch(ns, rhs, order=4, couple_frob=1.0, fp64_slices=7) as bt:
+        outs1, _, st1 = bt.solve(As, Bs, iters=60, tol=1e-10)
+        res1 = [bt.result(i) for i in range(len(probs))]
+    assert st1.slice_retried == st0.not_converged > 0
+    nconv = 0
+    for p, t0, t1, r0, r1 in zip(probs, outs0, outs1, res0, res1):
+        if r0["status"] == nsgb.NS_OK:
+            assert r1["status"] == nsgb.NS_OK and torch.equal(t0, t1)
+        if r1["status"] == nsgb.NS_OK:
+            nconv += 1
+            assert float(np.max(O.rel_residual(p.A, t1.cpu().numpy(), p.B))) <= 1e-10, p.n
+    assert nconv == st1.converged == st0.converged + st1.slice_retried_converged
+    assert st1.slice_retried_converged >= 0.8 * st1.slice_retried
+
+
 def test_batch_delayed_coupling():
     """couple_frob = 1: residual and update start once ||F_{k-1}||_F <= 1;
     every instance still converges, with fewer sweeps, and stays bitwise
