@@ -888,7 +888,7 @@ def run_batched(a):
             "retried": sts.slice_retried, "retried_converged": sts.slice_retried_converged,
             "retry_ms": sts.slice_retry_ms, "worst_verified_rel_res_of_converged": worst_s,
             "how": "option fp64_slices = 7: each system the batch did not converge solved again alone by the "
-                   "single-system AUTO path with 7-digit slice products (8 host worker threads, one stream "
+                   "single-system AUTO path with 7-digit slice products (16 host worker threads, one stream "
                    "each); wall time of one batch, this rank"}
         bs.close()
     if world > 1:

@@ -1217,7 +1217,7 @@ namespace {
 // k mod kRetryWorkers, and a system's arithmetic does not depend on which
 // systems run beside it.  Its outcome replaces the batched one; ns_iters and
 // sweeps add up both attempts.
-constexpr int kRetryWorkers = 8;
+constexpr int kRetryWorkers = 16;
 
 ns_status slice_handover(ns_batch* b, const double* const* A, const double* const* B, double* const* Theta, int iters,
                          double tol, ns_batch_stats* stats) {
