@@ -244,7 +244,7 @@ def gram_config(a):
                      "continues from that G",
         "tol": 1e-10, "l2": "inputs larger than L2 (A: 2 GiB FP64); 512 MiB written between timed steps",
         "seed": GRAM_SEED, "couple_frob": a.couple, "fp64_slices": GRAM_SLICES, "fp64_slices_early": 0,
-        "fp64_slices_pow": GRAM_SLICES_POW}
+        "fp64_slices_pow": GRAM_SLICES_POW, "xp_bf16x2": getattr(a, "xp_bf16x2", 0)}
 
 
 def plain_fp64_model(n, seed=GRAM_SEED, order=GRAM_ORDER, stop=0.02, tol=1e-10):
@@ -349,7 +349,7 @@ def run_gram(a):
         torch.cuda.synchronize(dev)
 
     opts = dict(order=GRAM_ORDER, stream=stream, couple_frob=a.couple, fp64_slices=GRAM_SLICES, fp64_slices_early=0,
-                fp64_slices_pow=GRAM_SLICES_POW)
+                fp64_slices_pow=GRAM_SLICES_POW, xp_bf16x2=a.xp_bf16x2)
     ctx = nsgb.Context(n, profile=1, **opts)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=80, tol=1e-10, out=out)
@@ -509,7 +509,7 @@ def dense_variant(a, dev, stream, flush):
     A = torch.from_numpy(p.A).to(dev)
     B = torch.from_numpy(p.B).to(dev)
     out = torch.empty_like(B)
-    ctx = nsgb.Context(n, order=8, stream=stream, profile=1, couple_frob=a.couple)
+    ctx = nsgb.Context(n, order=8, stream=stream, profile=1, couple_frob=a.couple, xp_bf16x2=a.xp_bf16x2)
     for _ in range(3):
         ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
     ms, tc_ms, tc_alg, tc_fl, tc_l, it, sw = [], 0.0, 0.0, 0.0, 0, [], []
@@ -545,7 +545,7 @@ def dense_variant(a, dev, stream, flush):
                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                         "avg_launch_ms": tc_ms / max(tc_l, 1)}}
     if not a.no_fp64:
-        with nsgb.Context(n, order=8, stream=stream, precision=nsgb.NS_FP64, couple_frob=a.couple) as c64:
+        with nsgb.Context(n, order=8, stream=stream, precision=nsgb.NS_FP64, couple_frob=a.couple, xp_bf16x2=a.xp_bf16x2) as c64:
             out64 = torch.empty_like(B)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -589,7 +589,7 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
 
     ctx = nsgb.Context(a.n, order=a.order, stream=stream, profile=1, couple_frob=a.couple,
-                       gemm_cluster=a.gemm_cluster, pow_bf16=a.pow_bf16)
+                       gemm_cluster=a.gemm_cluster, pow_bf16=a.pow_bf16, xp_bf16x2=a.xp_bf16x2)
     for _ in range(max(3, a.warmup)):
         r = ctx.solve(A, B, iters=a.iters, tol=1e-10, out=out)
     assert r.status == nsgb.NS_OK, f"solve did not converge: {r.stats.res_history()}"
@@ -665,7 +665,7 @@ def run_ours(a):
     Bh = torch.from_numpy(p.B).pin_memory()
     Th = torch.empty_like(Bh).pin_memory()
     ctx_h = nsgb.Context(a.n, order=a.order, stream=stream, couple_frob=a.couple, gemm_cluster=a.gemm_cluster,
-                         pow_bf16=a.pow_bf16)
+                         pow_bf16=a.pow_bf16, xp_bf16x2=a.xp_bf16x2)
     ctx_h.solve(Ah, Bh, iters=a.iters, tol=1e-10, out=Th)
     e2e_steps = max(1, min(a.steps, 5))
     barrier()
@@ -1284,6 +1284,8 @@ def main():
     ap.add_argument("--slices", type=int, default=7, help="--kernel gemm --precision fp64slices: digits per operand")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the pow_bf16 variant measured beside the default single-system line")
+    ap.add_argument("--xp-bf16x2", type=int, default=0, choices=(0, 1, 2),
+                    help="option xp_bf16x2: X_j P_j (j >= 1) of bf16x3 steps as two-term products")
     ap.add_argument("--pow-bf16", type=int, default=2, choices=(0, 1, 2),
                     help="powers F^(2^j) of bf16x3 steps in one bf16 pass (library option pow_bf16: "
                          "0 off, 1 on, 2 on from n = 4096)")

@@ -63,8 +63,11 @@ typedef enum ns_precision {
   NS_BF16X6 = 4, /* three-part split hi, lo = bf16(x - hi), lo2 = bf16(x - hi - lo):
                     hi*hi + hi*lo + lo*hi + hi*lo2 + lo*lo + lo2*hi into one f32
                     accumulator (tcgen05 CTA pairs); not with composite rates or form 3 */
-  NS_AUTO = 5    /* bf16 while ||F_k||_F keeps falling, then bf16x3 (one-step rollback);
+  NS_AUTO = 5,   /* bf16 while ||F_k||_F keeps falling, then bf16x3 (one-step rollback);
                     bf16x6 where bf16x3 stalls at a floor Richardson cannot finish from */
+  NS_BF16X2 = 6  /* product form only (ns_k_gemm_bf16; the X_j P_j updates of bf16x3 steps
+                    with option xp_bf16x2), not a solve precision: L split, R's hi part,
+                    Lhi*Rhi + Llo*Rhi into one f32 accumulator (tcgen05 CTA pairs) */
 } ns_precision;
 
 typedef struct ns_options {
@@ -152,6 +155,10 @@ typedef struct ns_options {
                           CTA per system solving it whole (same arithmetic and controller as the
                           pass-by-pass path, so the same results); 0 always runs pass by pass
                           (one launch per product level and one host decision per pass) */
+  int xp_bf16x2;        /* bf16x3 steps of the factorized chain: the updates X_j P_j with j >= 1
+                          as NS_BF16X2 products (P_j's low part dropped: its error reaches
+                          F_{k+1} only through A X_j ~ I, as ~2^-9 |F_k|^(2^j)).  0 (default of
+                          ns_default_options): three terms; 1: on; 2: on where n >= 4096 */
 } ns_options;
 
 #define NS_MAX_HIST 256

@@ -677,6 +677,7 @@ def split3_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
 # whose parts' orders add to at most 2 (hi = 0, lo = 1, lo2 = 2): relative size
 # down to 2^-16, dropping lo*lo2, lo2*lo, lo2*lo2 (2^-24 and below).
 SPLIT_PASSES = {"bf16": (("hi", "hi"),),
+                "bf16x2": (("hi", "hi"), ("lo", "hi")),
                 "bf16x3": (("hi", "hi"), ("hi", "lo"), ("lo", "hi")),
                 "bf16x6": (("hi", "hi"), ("hi", "lo"), ("lo", "hi"), ("hi", "lo2"), ("lo", "lo"), ("lo2", "hi"))}
 
@@ -691,6 +692,7 @@ def split_product(L: np.ndarray, R: np.ndarray, precision: str) -> np.ndarray:
     """Exact (float64) value of the split product the tensor cores form:
     tf32:   RNtf32(L) RNtf32(R)   (one pass; operands rounded by round_tf32)
     bf16:   Lhi Rhi
+    bf16x2: Lhi Rhi + Llo Rhi             (R's low part dropped)
     bf16x3: Lhi Rhi + Lhi Rlo + Llo Rhi   (the lo*lo term is dropped)
     bf16x6: those and Lhi Rlo2 + Llo Rlo + Llo2 Rhi.
     L and R are first rounded to binary32 and split with ``split3_bf16``

@@ -27,7 +27,7 @@ __all__ = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_invert", "ns_richardson_solve", "ns_residual",
     "ns_inverse_residual",
     "ns_last_error", "ns_status_string", "ns_k_split", "ns_k_gemm_bf16", "ns_k_gemm_f64", "ns_k_resid",
-    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6", "ns_k_gemm_oz", "ns_k_gemm_tf32", "NS_TF32",
+    "ns_k_split3", "ns_k_gemm_bf16x6", "NS_BF16X6", "NS_BF16X2", "ns_k_gemm_oz", "ns_k_gemm_tf32", "NS_TF32",
     "ns_k_update", "ns_k_prep_a", "ns_k_resid_x2", "ns_k_resid_noalloc", "Context",
     "ns_batch_stats", "Batch",
 ]
@@ -35,7 +35,7 @@ __all__ = [
 NS_OK, NS_NOT_CONVERGED = 0, 1
 NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_DIVERGED = -1, -2, -3, -4
 NS_ERR_TIMEOUT, NS_ERR_NONFINITE, NS_ERR_UNSUPPORTED = -5, -6, -7
-NS_FP64, NS_TF32, NS_BF16, NS_BF16X3, NS_BF16X6, NS_AUTO = 0, 1, 2, 3, 4, 5
+NS_FP64, NS_TF32, NS_BF16, NS_BF16X3, NS_BF16X6, NS_AUTO, NS_BF16X2 = 0, 1, 2, 3, 4, 5, 6
 NS_MAX_HIST = 256
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +74,7 @@ class ns_options(ctypes.Structure):
         ("tf32_rung", ctypes.c_int),
         ("fp64_slices_pow", ctypes.c_int),
         ("batch_fused", ctypes.c_int),
+        ("xp_bf16x2", ctypes.c_int),
     ]
 
 

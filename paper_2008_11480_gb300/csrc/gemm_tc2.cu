@@ -66,14 +66,19 @@ __host__ __device__ constexpr int term_r(int t) { return (t == 1 || t == 4) ? 1 
 // NP = 4: one TF32 pass; per CTA a stage holds L 128 rows x 32 K and 128 of
 // the tile's R columns x 32 K, both as f32 words K-major (the transposed TF32
 // form of R), 128-byte swizzle: 16 + 16 KiB.
+// NP = 5: the two split terms hi.hi + lo.hi (L split, R's hi part only), for
+// products whose R operand may lose its low part; per 32-deep K slice L hi
+// and lo and R hi: 16 + 8 KiB.
 template <int NP>
 struct PairCfg {
+  static constexpr int kLParts = NP == 5 ? 2 : ((NP == 1 || NP == 4) ? 1 : NP);  // split parts staged
+  static constexpr int kRParts = NP == 5 ? 1 : kLParts;
   static constexpr int kBK = NP == 1 ? 64 : 32;          // K per stage
-  static constexpr int kABytes = (NP == 1 || NP == 4) ? 16384 : NP * kPartBytes;
-  static constexpr int kBBytes = kABytes;                 // 128 of the tile's R columns
+  static constexpr int kABytes = (NP == 1 || NP == 4) ? 16384 : kLParts * kPartBytes;
+  static constexpr int kBBytes = (NP == 1 || NP == 4) ? 16384 : kRParts * kPartBytes;  // 128 of the tile's R columns
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages = (196 * 1024) / kStageBytes > 6 ? 6 : (196 * 1024) / kStageBytes;
-  static constexpr int kTerms = (NP == 1 || NP == 4) ? 1 : (NP == 2 ? 3 : 6);
+  static constexpr int kTerms = (NP == 1 || NP == 4) ? 1 : (NP == 2 ? 3 : (NP == 5 ? 2 : 6));
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + kEpiBytes + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
   static_assert((3 * kStages + 5) * 8 + 8 <= kBarBytes, "barrier area");
@@ -160,11 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producers (both CTAs)
-    for (int i = 0; i < p.nprob; ++i)
-      for (int q = 0; q < NP; ++q) {
-        tma_prefetch_desc(&p.prob[i].L[q]);
-        tma_prefetch_desc(&p.prob[i].R[q]);
-      }
+    for (int i = 0; i < p.nprob; ++i) {
+      for (int q = 0; q < Cfg::kLParts; ++q) tma_prefetch_desc(&p.prob[i].L[q]);
+      for (int q = 0; q < Cfg::kRParts; ++q) tma_prefetch_desc(&p.prob[i].R[q]);
+    }
     int armed[kStages];
     for (int s = 0; s < kStages; ++s) armed[s] = -1;
     int stage = 0;
@@ -202,12 +206,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
           } else if (NP > 1) {
             const int x = kb * kBK;
 #pragma unroll
-            for (int part = 0; part < NP; ++part) {
+            for (int part = 0; part < Cfg::kLParts; ++part) {
               tma_load_2d_pair(a + part * kPartBytes, &P.L[part], bar, x, m0);
               tma_load_2d_pair(a + part * kPartBytes + 4096, &P.L[part], bar, x, m0 + 64);
             }
 #pragma unroll
-            for (int part = 0; part < NP; ++part) {
+            for (int part = 0; part < Cfg::kRParts; ++part) {
               tma_load_2d_pair(b + part * kPartBytes, &P.R[part], bar, nb, x);
               if (half < 0) tma_load_2d_pair(b + part * kPartBytes + 4096, &P.R[part], bar, nb + 64, x);
             }
@@ -285,7 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc2(const __grid_constant_
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
 #pragma unroll
-            for (int t = 0; t < Cfg::kTerms; ++t) {
+            for (int tt = 0; tt < Cfg::kTerms; ++tt) {
+              const int t = NP == 5 ? 2 * tt : tt;  // NP = 5: the terms hi.hi and lo.hi
               const uint64_t ad =
                   make_sdesc(a_base + static_cast<uint32_t>(term_l(t) * kPartBytes) + 32u * k, 16u, 512u, kSwz64);
               const uint64_t bd =
@@ -437,6 +442,7 @@ cudaError_t launch_gemm_tc_pair(const TcParams& p, int parts, int num_sms, cudaS
     case 2: return launch_pair<2>(p, num_sms, s);
     case 3: return launch_pair<3>(p, num_sms, s);
     case 4: return launch_pair<4>(p, num_sms, s);
+    case 5: return launch_pair<5>(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -425,7 +425,8 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   }
   for (int i = 0; i < nspec; ++i) specs[i].D->t_fresh = tf;
   const bool x6 = prec == NS_BF16X6;
-  if (x6) {  // the three-part terms run on CTA pairs only
+  const bool x2 = prec == NS_BF16X2;
+  if (x6 || x2) {  // the three-part and the two-term products run on CTA pairs only
     bn = 256;
     cm = -2;
   }
@@ -433,7 +434,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   TcParams p;
   memset(&p, 0, sizeof(p));
   p.nprob = nspec;
-  p.npass = x6 ? 6 : (prec == NS_BF16X3 ? 3 : 1);
+  p.npass = x6 ? 6 : (prec == NS_BF16X3 ? 3 : (x2 ? 2 : 1));
   p.debug_stall_iter = -1;
   p.timeout_ns = static_cast<unsigned long long>(ctx->opt.timeout_s * 1e9);
   p.err = ctx->derr;
@@ -449,7 +450,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
       P.Dt = g.D->t32;
       P.DtT = g.D->t32T;
       P.ldt = static_cast<int>(ctx->ld);
-    } else if (x3 || x6) {
+    } else if (x3 || x6 || x2) {
       P.L[0] = g.L->l3_hi;
       P.L[1] = g.L->l3_lo;
       P.R[0] = g.R->r3_hi;
@@ -502,7 +503,7 @@ ns_status mp_gemm(ns_ctx* ctx, const GemmSpec* specs, int nspec, int prec) {
   p.total_tiles = tile;
   EventPair* e = ev_begin(ctx, true);
   if (cm == -2)
-    NS_CK(launch_gemm_tc_pair(p, tf ? 4 : (x6 ? 3 : (x3 ? 2 : 1)), ctx->num_sms, ctx->stream));
+    NS_CK(launch_gemm_tc_pair(p, tf ? 4 : (x6 ? 3 : (x3 ? 2 : (x2 ? 5 : 1))), ctx->num_sms, ctx->stream));
   else
     NS_CK(launch_gemm_tc(p, bn, x3, ctx->num_sms, ctx->stream));
   ev_end(ctx, e);
@@ -715,6 +716,7 @@ ns_status mp_chain_nested45(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int prec
 // products of a level into two launches was measured 2-4 % slower (n = 1024,
 // 2048); at n = 4096 it was measured 6-7 % faster per solve.
 bool pow_bf16_on(const ns_ctx* ctx) { return ctx->opt.pow_bf16 == 1 || (ctx->opt.pow_bf16 == 2 && ctx->n >= 4096); }
+bool xp2_on(const ns_ctx* ctx) { return ctx->opt.xp_bf16x2 == 1 || (ctx->opt.xp_bf16x2 == 2 && ctx->n >= 4096); }
 
 ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int prec) {
   if (ctx->opt.form == 2) return mp_chain_toolkit(ctx, Gin, Gout, order, prec);
@@ -744,15 +746,23 @@ ns_status mp_chain(ns_ctx* ctx, const MpMat& Gin, MpMat& Gout, int order, int pr
     MpMat* xo = last ? &Gout : &ctx->X[j & 1];
     MpMat* po = &ctx->P[j & 1];
     GemmSpec gx{Xc, Pc, 1.f, Xc->m32, 1.f, 0.f, xo, true, nullptr};
+    // option xp_bf16x2: in bf16x3 steps X_j P_j for j >= 1 without the
+    // hi(X) lo(P) term.  The dropped part of P_j = F_k^(2^j) reaches F_{k+1}
+    // only through A X_j (~ I), as ~2^-9 |F_k|^(2^j), at least quadratic in F_k
+    const int px = (prec == NS_BF16X3 && j >= 1 && ctx->opt.pow_mode == 0 && xp2_on(ctx)) ? NS_BF16X2 : prec;
     if (last) {
-      NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+      NS_TRY(mp_gemm(ctx, &gx, 1, px));
     } else if (ctx->opt.pow_mode == 0 && pow_bf16_on(ctx) && prec == NS_BF16X3) {
       // option pow_bf16: the power P_{j+1} = P_j P_j in one bf16 pass.  Its
       // error enters G_{k+1} only through X P, as ~2^-9 |P_j|^2, quadratic in
       // F_k, so it stays below the bf16x3 floor once F_k is small
-      NS_TRY(mp_gemm(ctx, &gx, 1, prec));
+      NS_TRY(mp_gemm(ctx, &gx, 1, px));
       GemmSpec gp{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr};
       NS_TRY(mp_gemm(ctx, &gp, 1, NS_BF16));
+    } else if (ctx->opt.pow_mode == 0 && px != prec) {
+      NS_TRY(mp_gemm(ctx, &gx, 1, px));
+      GemmSpec gp{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr};
+      NS_TRY(mp_gemm(ctx, &gp, 1, prec));
     } else if (ctx->opt.pow_mode == 0) {
       GemmSpec two[2] = {gx, GemmSpec{Pc, Pc, 1.f, nullptr, 0.f, 0.f, po, false, nullptr}};
       NS_TRY(mp_gemm(ctx, two, 2, prec));
@@ -1759,6 +1769,7 @@ void ns_default_options(ns_options* o) {
   o->g0_order = 0;
   o->pow_bf16 = 2;
   o->batch_fused = 1;
+  o->xp_bf16x2 = 0;
 }
 
 const char* ns_status_string(ns_status s) {
@@ -1800,6 +1811,7 @@ ns_status ns_create(int64_t n, int order, const int* rates, int n_rates, const n
   if (o.g0_order < 0 || o.g0_order > 19) return NS_ERR_ARG;
   if (o.final_check < -2 || o.final_check > 4096) return NS_ERR_ARG;
   if (o.pow_bf16 < 0 || o.pow_bf16 > 2) return NS_ERR_ARG;
+  if (o.xp_bf16x2 < 0 || o.xp_bf16x2 > 2) return NS_ERR_ARG;
   if (o.gemm_cluster != 0 && o.gemm_cluster != 1 && o.gemm_cluster != -2) return NS_ERR_ARG;
   if (o.fp64_slices != 0 && (o.fp64_slices < 2 || o.fp64_slices > kOzMaxSlices)) return NS_ERR_ARG;
   if (o.fp64_slices_early < 0 || o.fp64_slices_early == 1 || o.fp64_slices_early > kOzMaxSlices) return NS_ERR_ARG;
@@ -2128,8 +2140,10 @@ namespace {
 ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl,
                       const void* const* R, int64_t ldr, float s, const float* C, int64_t ldc, float beta, float gamma,
                       float* D32, int64_t ldd32, void* const* D, int64_t ldd16, double* frob_out, int bn,
-                      int cluster_m, void* stream) {
+                      int cluster_m, void* stream, bool x2 = false) {
   if (M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return NS_ERR_ARG;
+  if (x2 && cluster_m == 0) cluster_m = -2;  // two-term products run on CTA pairs only
+  if (x2 && cluster_m != -2) return NS_ERR_ARG;
   for (int q = 0; q < parts; ++q)
     if (!L[q] || !R[q] || !al16(L[q]) || !al16(R[q])) return NS_ERR_ARG;
   if (ldl < K || ldr < N || ldl % 8 || ldr % 8) return NS_ERR_ARG;
@@ -2149,7 +2163,7 @@ ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* co
   // CTA pairs need 256-column tiles; one-pass and bf16x3 pairs also an even
   // row-tile count (bf16x6 pairs accept an odd one: the last pair's second
   // CTA then covers rows past M, loaded as zeros and not written)
-  if (pair && (bn != 256 || (parts < 3 && tiles_m % 2 != 0))) return NS_ERR_ARG;
+  if (pair && (bn != 256 || (parts < 3 && !x2 && tiles_m % 2 != 0))) return NS_ERR_ARG;
   if (cluster_m == 0 && !pair && bn == 256 && tiles_m % 2 == 0) pair = true;  // automatic: CTA pairs where they apply
   if (!pair && cluster_m != 0 && cluster_m != 1) return NS_ERR_ARG;
   cluster_m = pair ? 2 : 1;  // pairs: same item and partial-sum bookkeeping as two-CTA groups
@@ -2160,7 +2174,7 @@ ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* co
   TcParams p;
   memset(&p, 0, sizeof(p));
   p.nprob = 1;
-  p.npass = parts == 3 ? 6 : (parts == 2 ? 3 : 1);
+  p.npass = parts == 3 ? 6 : (x2 ? 2 : (parts == 2 ? 3 : 1));
   p.debug_stall_iter = -1;
   p.timeout_ns = 2000000000ull;
   // host-side fault injection for the failure-detection tests: the producer
@@ -2214,7 +2228,7 @@ ns_status k_gemm_impl(int parts, int64_t M, int64_t N, int64_t K, const void* co
   cudaMemsetAsync(scratch, 0, sizeof(int) * 4, st);
   p.err = static_cast<int*>(scratch);
   if (frob_out) P.frob_partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
-  cudaError_t e = pair ? launch_gemm_tc_pair(p, parts == 3 ? 3 : (split ? 2 : 1), sms, st)
+  cudaError_t e = pair ? launch_gemm_tc_pair(p, parts == 3 ? 3 : (x2 ? 5 : (split ? 2 : 1)), sms, st)
                        : launch_gemm_tc(p, bn, split, sms, st);
   if (e == cudaSuccess && frob_out) e = launch_reduce_sum(P.frob_partials, ntiles * per_tile, 1, frob_out, st);
   int herr = 0;
@@ -2242,13 +2256,15 @@ ns_status ns_k_gemm_bf16(int precision, int64_t M, int64_t N, int64_t K, const v
                          int64_t ldl, const void* Rhi, const void* Rlo, int64_t ldr, float s, const float* C,
                          int64_t ldc, float beta, float gamma, float* D32, int64_t ldd32, void* Dhi, void* Dlo,
                          int64_t ldd16, double* frob_out, int bn, int cluster_m, void* stream) {
-  if (precision != NS_BF16 && precision != NS_BF16X3) return NS_ERR_ARG;
+  if (precision != NS_BF16 && precision != NS_BF16X3 && precision != NS_BF16X2) return NS_ERR_ARG;
+  const bool x2 = precision == NS_BF16X2;
+  // NS_BF16X2 never reads Rlo (Rhi stands in for its tensor map when Rlo is null)
   const void* L[3] = {Lhi, Llo, nullptr};
-  const void* R[3] = {Rhi, Rlo, nullptr};
+  const void* R[3] = {Rhi, x2 && !Rlo ? Rhi : Rlo, nullptr};
   void* D[3] = {Dhi, Dlo, nullptr};
-  if (!Lhi || !Rhi || (precision == NS_BF16X3 && (!Llo || !Rlo))) return NS_ERR_ARG;
-  return k_gemm_impl(precision == NS_BF16X3 ? 2 : 1, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D,
-                     ldd16, frob_out, bn, cluster_m, stream);
+  if (!Lhi || !Rhi || (precision != NS_BF16 && (!Llo || !R[1]))) return NS_ERR_ARG;
+  return k_gemm_impl(precision == NS_BF16 ? 1 : 2, M, N, K, L, ldl, R, ldr, s, C, ldc, beta, gamma, D32, ldd32, D,
+                     ldd16, frob_out, bn, cluster_m, stream, x2);
 }
 
 ns_status ns_k_gemm_bf16x6(int64_t M, int64_t N, int64_t K, const void* const* L, int64_t ldl, const void* const* R,

@@ -127,7 +127,7 @@ def test_create_validates_precision_options(L):
     for kw in ({"precision": 6}, {"precision": -1}, {"tf32_rung": 2}, {"fp64_slices": 1}, {"fp64_slices": 8}, {"fp64_slices": 9}, {"fp64_slices_early": 1},
                {"fp64_slices_early": 8}, {"fp64_slices_early": 9}, {"final_check": -3}, {"final_check": 4097}, {"pow_bf16": 3}, {"pow_bf16": -1},
                {"gemm_cluster": 2}, {"gemm_cluster": 4}, {"fp64_slices_pow": 1}, {"fp64_slices_pow": 8},
-               {"fp64_slices_pow": -1}):
+               {"fp64_slices_pow": -1}, {"xp_bf16x2": 3}, {"xp_bf16x2": -1}):
         opt = nsgb.default_options(**kw)
         assert L.ns_create(64, 4, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_ARG, kw
     # bf16x6 needs the third split part, which composite loops and form 3 do not carry
@@ -143,7 +143,7 @@ def test_create_validates_precision_options(L):
         assert L.ns_create(64, 45, None, 0, ctypes.byref(opt), ctypes.byref(h)) == nsgb.NS_ERR_UNSUPPORTED, kw
     d = nsgb.default_options()
     assert d.fp64_slices == 0 and d.fp64_slices_early == 4 and d.final_check == 0 and d.pow_bf16 == 2
-    assert d.tf32_rung == 0 and d.batch_fused == 1 and d.fp64_slices_pow == 0
+    assert d.tf32_rung == 0 and d.batch_fused == 1 and d.fp64_slices_pow == 0 and d.xp_bf16x2 == 0
 
 
 def test_new_kernel_entry_points_validate_before_launch(L):

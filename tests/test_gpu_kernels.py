@@ -75,7 +75,7 @@ def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0
     nsgb.ns_k_gemm_bf16(prec, M, N, K, Lh, Ll, ldl, Rh, Rl, ldr, s, Cd, ldd if with_c else 0, beta, gamma,
                         D32, ldd, Dh, Dl, ldd, fro, bn, cm)
     torch.cuda.synchronize()
-    pname = "bf16" if prec == nsgb.NS_BF16 else "bf16x3"
+    pname = {nsgb.NS_BF16: "bf16", nsgb.NS_BF16X3: "bf16x3", nsgb.NS_BF16X2: "bf16x2"}[prec]
     prod = O.split_product(L, R, pname)
     absprod = O.split_abs_product(L, R, pname)
     ref = O.gemm_epilogue(prod, s, O.round_f32(C) if with_c else None, beta, gamma)
@@ -100,6 +100,13 @@ def run_gemm(prec, M, N, K, seed, s=1.0, beta=0.0, gamma=0.0, with_c=False, bn=0
                                    (17, 33, 9), (300, 130, 257)])
 def test_gemm_tc_plain(prec, M, N, K):
     run_gemm(prec, M, N, K, seed=M + N + K)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 512, 1024), (130, 200, 70), (300, 130, 257), (640, 768, 333), (1, 1, 1)])
+def test_gemm_two_term_pairs(M, N, K):
+    """NS_BF16X2 (Lhi Rhi + Llo Rhi, CTA pairs, any row-tile count) against the
+    oracle's bf16x2 terms, with the C and identity terms of the NS epilogue."""
+    run_gemm(nsgb.NS_BF16X2, M, N, K, seed=3 * M + K, s=-1.0, beta=1.0, with_c=True, gamma=1.0)
 
 
 @pytest.mark.parametrize("bn", [64, 128, 256])

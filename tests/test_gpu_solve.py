@@ -653,6 +653,26 @@ def test_config5_size_solve_with_slice_products():
     assert float(err) <= 10 * kappa * 1e-10
 
 
+@pytest.mark.parametrize("n,kappa,nrhs", [(4096, 1e4, 4), (4096, 1e5, 4), (1000, 1e5, 2)])
+def test_two_term_updates_in_split_steps(n, kappa, nrhs):
+    """Option xp_bf16x2: in bf16x3 steps the updates X_j P_j (j >= 1) drop the
+    hi(X) lo(P) term.  The solve reaches the tolerance (FP64 residual), theta
+    matches the closed form, and it takes the three-term solve's Newton-Schulz
+    steps within one."""
+    p = make_spd(n, kappa, nrhs=nrhs, seed=1)
+    tstar = (p.Q / p.lam) @ (p.Q.T @ p.B)
+    runs = {}
+    for xp in (0, 1):
+        with nsgb.Context(n, order=8, couple_frob=1.0, xp_bf16x2=xp) as ctx:
+            r = ctx.solve(tens(p.A), tens(p.B), iters=80, tol=1e-10)
+        assert r.status == nsgb.NS_OK, (xp, r.stats.res_history()[-5:])
+        th = r.theta.cpu().numpy()
+        assert float(np.max(O.rel_residual(p.A, th, p.B))) <= 1e-10 + 0.5 * 2.0 ** -53 * kappa
+        assert rel(th, tstar) <= 10 * kappa * 1e-10
+        runs[xp] = r.stats
+    assert abs(runs[1].ns_iters - runs[0].ns_iters) <= 1
+
+
 @pytest.mark.parametrize("kappa,nrhs", [(1e4, 4), (1e5, 4)])
 def test_bf16_powers_in_split_steps(kappa, nrhs):
     """Option pow_bf16: in bf16x3 steps the powers F^{2^{j+1}} run as one bf16

@@ -582,6 +582,29 @@ def test_split_product_terms():
     assert np.all(np.abs(O.split_product(L, R, "bf16x3") - full) <= bound)
 
 
+def test_split_product_two_terms():
+    """bf16x2 keeps hi*hi and lo*hi: it is L's binary32 value (hi + lo to 16
+    bits) times R's bfloat16 part.  For R exact in bfloat16 (Rlo = 0) it equals
+    bf16x3 exactly; for L exact in bfloat16 it equals the one-pass bf16
+    product; in general its error against the binary32 product is bounded by
+    R's rounding (2^-8) plus L's split remainder (2^-16)."""
+    rng = np.random.default_rng(21)
+    L = rng.standard_normal((7, 24))
+    R = rng.standard_normal((24, 6))
+    Lh, Ll = O.split_bf16(L)
+    Rh, _ = O.split_bf16(R)
+    assert np.max(np.abs(O.split_product(L, R, "bf16x2") - (Lh + Ll) @ Rh)) <= 1e-13
+    Rb = O.round_bf16(O.round_f32(R))
+    assert np.max(np.abs(O.split_product(L, Rb, "bf16x2") - O.split_product(L, Rb, "bf16x3"))) <= 1e-13
+    Lb = O.round_bf16(O.round_f32(L))
+    assert np.array_equal(O.split_product(Lb, R, "bf16x2"), O.split_product(Lb, R, "bf16"))
+    full = O.round_f32(L) @ O.round_f32(R)
+    bound = (2.0 ** -8 + 2.0 ** -16) * (np.abs(L) @ np.abs(R)) + 1e-12
+    assert np.all(np.abs(O.split_product(L, R, "bf16x2") - full) <= bound)
+    ab = O.split_abs_product(L, R, "bf16x2")
+    assert np.all(np.abs(O.split_product(L, R, "bf16x2")) <= ab)
+
+
 def test_split3_exact_and_matches_torch():
     """hi + lo + lo2 reproduces binary32 exactly, each part is a bfloat16, and
     the parts equal torch's own bfloat16 rounding of the successive binary32
