@@ -136,6 +136,15 @@ def test_split_dropping_cross_term(monkeypatch):
     assert _fails(T.test_split_product_terms)
 
 
+def test_two_term_split_wrong_terms(monkeypatch):
+    # the term kept by mistake is the one the reading drops (hi of L times lo
+    # of R) instead of lo of L times hi of R
+    monkeypatch.setitem(N.SPLIT_PASSES, "bf16x2", (("hi", "hi"), ("hi", "lo")))
+    assert _fails(T.test_split_product_two_terms)
+    monkeypatch.setitem(N.SPLIT_PASSES, "bf16x2", (("hi", "hi"),))
+    assert _fails(T.test_split_product_two_terms)
+
+
 def test_splitmix64_wrong_shift(monkeypatch):
     def bad(seed, k):
         z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & N._U64
