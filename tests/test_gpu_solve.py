@@ -516,8 +516,9 @@ def test_gram_size_solve_bench_configuration():
     """The n = 16384 least-squares Gram system (A = V diag(sigma^2) V^T, sigma
     log-uniform in [1e-3, 1], cond 1e6, b = V (sigma z)) in the launch
     configuration the benchmark times: AUTO, order 8, couple_frob 1,
-    fp64_slices 4 from the hand-over on (fp64_slices_early 0), the powers in 2
-    digits; at the binary32 floor Richardson gets the first try, the slice
+    two-term updates in bf16x3 steps (xp_bf16x2 2), fp64_slices 4 from the
+    hand-over on (fp64_slices_early 0), the powers in 2 digits; at the binary32
+    floor Richardson gets the first try, the slice
     products take over only if its sweeps give up.  Checked at full size by
     properties: the library's FP64 residual, the residual recomputed in torch,
     and theta against the closed form theta* = V (z / sigma)."""
@@ -527,14 +528,15 @@ def test_gram_size_solve_bench_configuration():
     tstar = V @ (z / sg[:, None])
     del V
     torch.cuda.empty_cache()
-    with nsgb.Context(n, order=8, couple_frob=1.0, fp64_slices=4, fp64_slices_early=0, fp64_slices_pow=2) as ctx:
+    with nsgb.Context(n, order=8, couple_frob=1.0, fp64_slices=4, fp64_slices_early=0, fp64_slices_pow=2,
+                      xp_bf16x2=2) as ctx:
         r = ctx.solve(A, B, iters=80, tol=1e-10)
         assert r.status == nsgb.NS_OK, (r.stats.prec_history(), r.stats.res_history()[-5:])
         assert max(ctx.residual(A, r.theta, B)) <= 1e-10
     if nsgb.NS_FP64 not in r.stats.prec_history():
         # the sweeps from the floor's G converged: the slice option changed
         # nothing, the solve is the one without it, bit for bit
-        with nsgb.Context(n, order=8, couple_frob=1.0) as ctx:
+        with nsgb.Context(n, order=8, couple_frob=1.0, xp_bf16x2=2) as ctx:
             r0 = ctx.solve(A, B, iters=80, tol=1e-10)
         assert r0.status == nsgb.NS_OK
         assert torch.equal(r0.theta, r.theta)
