@@ -605,6 +605,53 @@ def test_split_product_two_terms():
     assert np.all(np.abs(O.split_product(L, R, "bf16x2")) <= ab)
 
 
+def _step_with_rounded_factor(A, G, which):
+    """One order-8 factorized step (three levels) with, for j >= 1, the factor
+    `which` of X_j P_j rounded to bfloat16 (its low part dropped); returns
+    F_{k+1} = I - A G_{k+1}."""
+    n = A.shape[0]
+    X, P = G, np.eye(n) - A @ G
+    for j in range(3):
+        if j >= 1 and which == "P":
+            XP = X @ O.round_bf16(O.round_f32(P))
+        elif j >= 1 and which == "X":
+            XP = O.round_bf16(O.round_f32(X)) @ P
+        else:
+            XP = X @ P
+        if j + 1 < 3:
+            P = P @ P
+        X = X + XP
+    return np.eye(n) - A @ X
+
+
+def test_dropped_power_bits_enter_unamplified():
+    """The reading behind the reduced-precision powers and updates (bf16
+    powers, two-term updates, fewer-digit slice powers): in a factorized step,
+    an error in P_j = F_k^(2^j) reaches F_{k+1} = I - A G_{k+1} through
+    A X_j ~ I, so rounding P_j to bfloat16 moves F_{k+1} by about
+    2^-8 |F_k^(2^j)| whatever kappa, while rounding X_j by the same relative
+    amount is amplified by ||A|| ||X_j|| ~ kappa."""
+    dps = {}
+    for kappa in (1e3, 1e5):
+        p = spd(60, kappa, nrhs=1, seed=30)
+        A = p.A
+        G = O.alpha_frobenius(A) * np.eye(60)
+        for _ in range(20):
+            if np.linalg.norm(np.eye(60) - A @ G, 2) < 0.5:
+                break
+            G, _ = O.ns_step_binary(A, G, 3)
+        F0 = np.eye(60) - A @ G
+        Fe = _step_with_rounded_factor(A, G, "none")
+        dp = np.linalg.norm(_step_with_rounded_factor(A, G, "P") - Fe)
+        dx = np.linalg.norm(_step_with_rounded_factor(A, G, "X") - Fe)
+        bound = 2.0 ** -8 * np.linalg.norm(A @ G, 2) * sum(np.linalg.norm(np.linalg.matrix_power(F0, 2 ** j))
+                                                            for j in (1, 2))
+        assert dp <= bound
+        assert dx >= kappa / 100.0 * dp
+        dps[kappa] = dp
+    assert dps[1e5] <= 10.0 * dps[1e3]
+
+
 def test_split3_exact_and_matches_torch():
     """hi + lo + lo2 reproduces binary32 exactly, each part is a bfloat16, and
     the parts equal torch's own bfloat16 rounding of the successive binary32
